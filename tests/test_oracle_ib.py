@@ -1,0 +1,256 @@
+"""Pins of the oracle's immersed-boundary and structure parts (Sec. 2.2, 2.3)
+against closed forms, invariants and brute force.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import icosphere, edges_of
+
+
+# ---------------------------------------------------------------- delta kernel
+
+@pytest.mark.parametrize("kernel,h", [(oracle.PESKIN4, 2), (oracle.LINEAR2, 1)])
+def test_delta_partition_of_unity_and_first_moment(kernel, h):
+    rng = np.random.default_rng(0)
+    for p in rng.uniform(-3, 3, 50):
+        js = np.arange(math.floor(p) - h + 1, math.floor(p) + h + 1)
+        ph = np.array([oracle.phi(j - p, kernel) for j in js])
+        assert ph.sum() == pytest.approx(1.0, abs=1e-15)
+        assert ((js - p) * ph).sum() == pytest.approx(0.0, abs=1e-15)
+        # nothing outside the support
+        assert oracle.phi(js[0] - 1 - p, kernel) == 0.0 and oracle.phi(js[-1] + 1 - p, kernel) == 0.0
+
+
+def test_peskin4_sum_of_squares_and_values():
+    """Peskin's 4-point kernel: sum_j phi(r - j)^2 = 3/8 for every r; phi(0) = 1/2,
+    phi(1) = 1/4, phi(2) = 0 (values of the piecewise definition)."""
+    rng = np.random.default_rng(1)
+    for p in rng.uniform(0, 1, 30):
+        s = sum(oracle.phi(j - p) ** 2 for j in range(-1, 3))
+        assert s == pytest.approx(3.0 / 8.0, abs=1e-15)
+    assert oracle.phi(0.0) == 0.5
+    assert oracle.phi(1.0) == 0.25
+    assert oracle.phi(2.0) == 0.0
+    assert oracle.phi(0.5) == pytest.approx((2 + math.sqrt(2)) / 8, abs=1e-16)
+
+
+def test_peskin4_is_c1():
+    for r0 in (1.0, 2.0, 0.0):
+        h = 1e-6
+        left = (oracle.phi(r0) - oracle.phi(r0 - h)) / h
+        right = (oracle.phi(r0 + h) - oracle.phi(r0)) / h
+        assert left == pytest.approx(right, abs=5e-5)
+
+
+# ----------------------------------------------------------- spread / interpolate
+
+def _brute_delta(cellpos, r, dims, kernel):
+    """Delta(x - r) over every cell with the minimum-image displacement."""
+    d = cellpos - r[None, :]
+    L = np.array(dims, dtype=np.float64)
+    d = d - L * np.round(d / L)
+    phis = np.vectorize(lambda q: oracle.phi(q, kernel))
+    return phis(d[:, 0]) * phis(d[:, 1]) * phis(d[:, 2])
+
+
+@pytest.mark.parametrize("kernel", [oracle.PESKIN4, oracle.LINEAR2])
+def test_spread_matches_brute_force(kernel):
+    dims = (7, 6, 9)
+    nx, ny, nz = dims
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cellpos = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(np.float64)
+    rng = np.random.default_rng(2)
+    # include nodes across the periodic seams and far outside the box (unwrapped)
+    r = np.concatenate([rng.uniform(-1, 1, (4, 3)) * np.array(dims),
+                        rng.uniform(0, 1, (4, 3)) * np.array(dims) + np.array(dims) * 3])
+    fn = rng.normal(size=r.shape)
+    F = oracle.spread(r, fn, dims, kernel)
+    Fb = np.zeros_like(F)
+    for j in range(r.shape[0]):
+        Fb += _brute_delta(cellpos, r[j], dims, kernel)[:, None] * fn[j][None, :]
+    np.testing.assert_allclose(F, Fb, atol=1e-14)
+    np.testing.assert_allclose(F.sum(0), fn.sum(0), atol=1e-13)
+
+
+@pytest.mark.parametrize("kernel", [oracle.PESKIN4, oracle.LINEAR2])
+def test_interpolate_adjoint_constant_linear(kernel):
+    dims = (12, 10, 11)
+    N = 12 * 10 * 11
+    rng = np.random.default_rng(3)
+    r = rng.uniform(3, 7, (20, 3))
+    u = rng.normal(size=(N, 3))
+    fn = rng.normal(size=(20, 3))
+    # <spread(f), u> = <f, interp(u)>
+    lhs = (oracle.spread(r, fn, dims, kernel) * u).sum()
+    rhs = (fn * oracle.interpolate(r, u, dims, kernel)).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    # constants interpolate exactly
+    c = np.tile([0.3, -0.2, 0.7], (N, 1))
+    np.testing.assert_allclose(oracle.interpolate(r, c, dims, kernel), np.tile([0.3, -0.2, 0.7], (20, 1)),
+                               atol=1e-15)
+    # linear fields interpolate exactly away from the seams (first-moment condition)
+    nx, ny, nz = dims
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lin = np.stack([2 * xx.ravel() - yy.ravel(), 0.5 * zz.ravel(), xx.ravel() + yy.ravel() + zz.ravel()], 1)
+    v = oracle.interpolate(r, lin.astype(np.float64), dims, kernel)
+    expect = np.stack([2 * r[:, 0] - r[:, 1], 0.5 * r[:, 2], r.sum(1)], 1)
+    np.testing.assert_allclose(v, expect, atol=1e-12)
+
+
+def test_interpolate_periodic_translation():
+    dims = (8, 8, 8)
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=(512, 3))
+    r = rng.uniform(-1, 9, (10, 3))
+    v0 = oracle.interpolate(r, u, dims)
+    v1 = oracle.interpolate(r + np.array([8.0, -16.0, 24.0]), u, dims)
+    np.testing.assert_allclose(v0, v1, atol=1e-13)
+
+
+# ------------------------------------------------------------------- membrane
+
+def _tri():
+    X = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.3, 0.9, 0.0]])
+    return X, np.array([[0, 1, 2]], dtype=np.int32)
+
+
+def _rot(seed):
+    q = np.random.default_rng(seed).normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+@pytest.mark.parametrize("law,p1,p2", [(oracle.NEOHOOKE, 0.01, 0.0), (oracle.SKALAK, 0.05, 9.5)])
+def test_membrane_forces_are_minus_energy_gradient(law, p1, p2):
+    nodes, tris = icosphere(1)
+    X = nodes * 4.0
+    x = X + 0.05 * np.random.default_rng(5).normal(size=X.shape)
+    f = oracle.membrane_forces(X, x, tris, p1, p2, law)
+    h = 1e-6
+    g = np.zeros_like(x)
+    for j in range(x.shape[0]):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[j, a] += h
+            xm[j, a] -= h
+            g[j, a] = (oracle.membrane_energy(X, xp, tris, p1, p2, law) -
+                       oracle.membrane_energy(X, xm, tris, p1, p2, law)) / (2 * h)
+    np.testing.assert_allclose(f, -g, atol=1e-7 * np.abs(f).max())
+    # internal forces: zero net force and zero net torque
+    np.testing.assert_allclose(f.sum(0), 0.0, atol=1e-15)
+    np.testing.assert_allclose(np.cross(x, f).sum(0), 0.0, atol=1e-14)
+
+
+def test_membrane_rest_and_rigid_motion():
+    nodes, tris = icosphere(2)
+    X = nodes * 6.0 + np.array([10.0, 20.0, 30.0])
+    assert oracle.membrane_energy(X, X, tris, 0.01) == pytest.approx(0.0, abs=1e-15)
+    np.testing.assert_allclose(oracle.membrane_forces(X, X, tris, 0.01), 0.0, atol=1e-15)
+    Rm = _rot(6)
+    x = (X - X.mean(0)) @ Rm.T + np.array([1.5, -2.0, 0.25]) + X.mean(0)
+    assert oracle.membrane_energy(X, x, tris, 0.01) == pytest.approx(0.0, abs=1e-12)
+    np.testing.assert_allclose(oracle.membrane_forces(X, x, tris, 0.01), 0.0, atol=1e-13)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-2])
+def test_neohookean_small_shear_modulus(eps):
+    """Pure shear stretch (1+e, 1/(1+e)) of one triangle: energy 2 Gs e^2 A0 to
+    leading order, so Gs is the small-strain shear modulus."""
+    X, t = _tri()
+    A0 = 0.5 * 0.9
+    Gs = 0.01
+    F = np.diag([1 + eps, 1 / (1 + eps), 1.0])
+    x = X @ F.T
+    W = oracle.membrane_energy(X, x, t, Gs)
+    assert W == pytest.approx(2 * Gs * eps ** 2 * A0, rel=3 * eps)
+    # rotated in space, identical
+    x2 = x @ _rot(7).T
+    assert oracle.membrane_energy(X, x2, t, Gs) == pytest.approx(W, rel=1e-10)
+
+
+@pytest.mark.parametrize("lam", [0.9, 1.05, 1.3])
+def test_equibiaxial_closed_forms(lam):
+    """Isotropic stretch lambda: I1 = 2 lam^2 - 2, I2 = lam^4 - 1 in both laws."""
+    X, t = _tri()
+    A0 = 0.45
+    x = X * lam
+    Gs = 0.01
+    I1, I2 = 2 * lam ** 2 - 2, lam ** 4 - 1
+    assert oracle.membrane_energy(X, x, t, Gs) == pytest.approx(A0 * Gs / 2 * (I1 - 1 + 1 / (I2 + 1)), rel=1e-12)
+    ks, C = 0.05, 9.5
+    assert oracle.membrane_energy(X, x, t, ks, C, oracle.SKALAK) == pytest.approx(
+        A0 * ks / 4 * (I1 ** 2 + 2 * I1 - 2 * I2 + C * I2 ** 2), rel=1e-12)
+
+
+def test_uniaxial_closed_form():
+    """Stretch lam along one rest edge direction only: I1 = lam^2 - 1, I2 = lam^2 - 1."""
+    X, t = _tri()
+    lam = 1.2
+    x = X * np.array([lam, 1.0, 1.0])
+    I1 = I2 = lam ** 2 - 1
+    assert oracle.membrane_energy(X, x, t, 0.01) == pytest.approx(0.45 * 0.005 * (I1 - 1 + 1 / (I2 + 1)), rel=1e-12)
+
+
+# ----------------------------------------------------------- springs and drive
+
+def test_springs_closed_form():
+    R = np.array([[0.0, 0.0, 0.0], [13.0, 0.0, 0.0], [13.0, 11.0, 0.0]])
+    k, L = 0.005, 12.0
+    fs = oracle.springs(k, L, R)
+    np.testing.assert_allclose(fs[0], [-k * (13 - L) * (-13) / 13, 0, 0], atol=1e-17)
+    np.testing.assert_allclose(fs[2], [0, -k * (11 - L) * 11 / 11, 0], atol=1e-17)
+    np.testing.assert_allclose(fs.sum(0), 0.0, atol=1e-18)
+
+
+def test_drive_closed_form():
+    A, B, alpha, T = 1e-3, 2e-3, math.pi / 2, 500.0
+    for t in (0, 17, 125, 333):
+        fd = oracle.drive((A, 0.0, B), (0.0, 0.0, alpha), True, T, t)
+        w = 2 * math.pi / T
+        assert fd[0, 0] == pytest.approx(A * math.sin(w * t), abs=1e-18)
+        assert fd[2, 0] == pytest.approx(B * math.sin(w * t + alpha), abs=1e-18)
+        assert fd[1, 0] == -fd[0, 0] - fd[2, 0]
+        assert np.all(fd[:, 1:] == 0)
+    fd = oracle.drive((1.0, 2.0, 3.0), (0.1, 0.2, 0.3), False, 100.0, 10.0)
+    np.testing.assert_allclose(fd[:, 0], [1.0 * math.sin(0.2 * math.pi + 0.1),
+                                          2.0 * math.sin(0.2 * math.pi + 0.2),
+                                          3.0 * math.sin(0.2 * math.pi + 0.3)], rtol=1e-15)
+
+
+# ------------------------------------------------------------------- icosphere
+
+@pytest.mark.parametrize("s", [0, 1, 2, 3])
+def test_icosphere_counts_and_shape(s):
+    nodes, tris = icosphere(s)
+    V, F = nodes.shape[0], tris.shape[0]
+    E = edges_of(tris).shape[0]
+    assert (V, E, F) == (10 * 4 ** s + 2, 30 * 4 ** s, 20 * 4 ** s)
+    assert V - E + F == 2
+    np.testing.assert_allclose(np.linalg.norm(nodes, axis=1), 1.0, atol=1e-15)
+    # outward orientation: every triangle's signed volume w.r.t. the centre is positive
+    a, b, c = nodes[tris[:, 0]], nodes[tris[:, 1]], nodes[tris[:, 2]]
+    vol = np.einsum("ij,ij->i", a, np.cross(b, c)) / 6.0
+    assert (vol > 0).all()
+    # mirror symmetry of the node set in x, y, z
+    key = {tuple(np.round(p, 12)) for p in nodes}
+    for ax in range(3):
+        m = nodes.copy()
+        m[:, ax] *= -1
+        assert {tuple(np.round(p, 12)) for p in m} == key
+
+
+def test_icosphere_volume_converges():
+    vols = []
+    for s in range(5):
+        nodes, tris = icosphere(s)
+        a, b, c = nodes[tris[:, 0]], nodes[tris[:, 1]], nodes[tris[:, 2]]
+        vols.append(np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6.0)
+    errs = [4 * math.pi / 3 - v for v in vols]
+    assert all(e > 0 for e in errs)
+    assert errs[4] < 0.01 * 4 * math.pi / 3
+    assert all(errs[i + 1] < errs[i] / 3 for i in range(4))

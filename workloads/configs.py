@@ -1,0 +1,185 @@
+"""Seeded synthetic workloads: periodic boxes with three-bead swimmers.
+
+Input generators only.  Nothing here evaluates the time step; the oracle and
+the CUDA path both consume the plain arrays that `assemble` returns.
+
+Conventions (readings of a paper that leaves them open):
+  * lattice nodes sit at integer coordinates 0..N-1 of a periodic box; x is
+    the swimming axis (Sec. 2.2 drives the beads along x);
+  * a swimmer is three equal icosphere beads on the x axis whose centres are
+    `spacing` apart; the middle bead sits at `center` (Sec. 2.2, Fig. 1);
+  * the drive on bead b is amp[b] * sin(2 pi t / T + phase[b]) along x; with
+    `balance` the middle bead instead carries minus the sum of the outer two,
+    which is the paper's protocol f1 = A sin(wt), f3 = B sin(wt + alpha),
+    f2 = -f1 - f3 (Sec. 2.2, driving-force equation);
+  * "separation of n bead radii" between two swimmers is the surface gap
+    between their nearest beads, n * a (in-line: centre-bead distance
+    2*spacing + 2a + gap; side by side along y: 2a + gap), placed
+    symmetrically about the box centre.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+from .mesh import icosphere
+
+
+@dataclass(frozen=True)
+class SwimmerSpec:
+    center: tuple
+    radius: float = 4.0
+    subdiv: int = 2
+    spacing: float = 12.0
+    k_spring: float = 0.005
+    Gs: float = 0.01
+    amp: tuple = (1e-3, 0.0, 1e-3)
+    phase: tuple = (0.0, 0.0, math.pi / 2)
+    balance: bool = True
+    period: float = 500.0
+
+    def with_drive(self, A, B, alpha):
+        """The paper's protocol: f1 = A sin(wt), f3 = B sin(wt+alpha), f2 = -f1-f3."""
+        return replace(self, amp=(A, 0.0, B), phase=(0.0, 0.0, alpha), balance=True)
+
+
+@dataclass(frozen=True)
+class BoxSpec:
+    dims: tuple  # (nx, ny, nz), x fastest in memory
+    tau: float = 1.0
+    rho0: float = 1.0
+    swimmers: tuple = field(default_factory=tuple)
+    forcing: str = "guo"        # "guo" | "shan_chen"
+    kernel: str = "peskin4"     # "peskin4" | "linear2"
+    g: tuple = (0.0, 0.0, 0.0)  # uniform body-force density (test flows)
+    name: str = ""
+
+    @property
+    def n_cells(self):
+        nx, ny, nz = self.dims
+        return nx * ny * nz
+
+
+def assemble(box: BoxSpec):
+    """Flatten a box into plain arrays.
+
+    Returns a dict:
+      nodes   (M,3) float64  initial node positions (= membrane rest shape)
+      tris    (T,3) int32    global node ids, outward orientation
+      beads   (B,4) int32    node_start, node_count, tri_start, tri_count
+      bead_Gs (B,)  float64  neo-Hookean shear modulus per bead
+      swimmers list of dicts: beads (3 ids), k, L, amp, phase, balance, period
+    """
+    nodes, tris, beads, gs, sw = [], [], [], [], []
+    m0 = 0
+    t0 = 0
+    cache = {}
+    for s in box.swimmers:
+        if s.subdiv not in cache:
+            cache[s.subdiv] = icosphere(s.subdiv)
+        unit, utris = cache[s.subdiv]
+        ids = []
+        for b in range(3):
+            c = np.array(s.center, dtype=np.float64) + np.array([(b - 1) * s.spacing, 0.0, 0.0])
+            nodes.append(unit * s.radius + c)
+            tris.append(utris + m0)
+            beads.append((m0, len(unit), t0, len(utris)))
+            gs.append(s.Gs)
+            ids.append(len(beads) - 1)
+            m0 += len(unit)
+            t0 += len(utris)
+        sw.append(dict(beads=ids, k=s.k_spring, L=s.spacing, amp=tuple(s.amp),
+                       phase=tuple(s.phase), balance=bool(s.balance), period=float(s.period),
+                       radius=float(s.radius)))
+    if nodes:
+        nodes = np.concatenate(nodes)
+        tris = np.concatenate(tris).astype(np.int32)
+    else:
+        nodes = np.zeros((0, 3))
+        tris = np.zeros((0, 3), dtype=np.int32)
+    return dict(nodes=nodes, tris=tris, beads=np.array(beads, dtype=np.int32).reshape(-1, 4),
+                bead_Gs=np.array(gs, dtype=np.float64), swimmers=sw)
+
+
+# ----------------------------------------------------------------------------
+# The workloads.  Sizes follow the three-bead swimmer problem of Sec. 3 scaled
+# to boxes that one GPU steps thousands of times per second.
+# ----------------------------------------------------------------------------
+
+def single_swimmer_48(period=500.0, alpha=math.pi / 2, A=1e-3, B=1e-3, dims=(48, 48, 48)):
+    """One swimmer, D3Q19 tau=1 rho0=1, periodic 48^3; beads of radius 4 at
+    subdivision 2 (162 nodes, 320 triangles), spacing 12, k=0.005, Gs=0.01,
+    drive amplitude 1e-3, period 500 steps, phase shift pi/2."""
+    c = tuple(float(d // 2) for d in dims)
+    s = SwimmerSpec(center=c, radius=4.0, subdiv=2, spacing=12.0, k_spring=0.005, Gs=0.01,
+                    period=period).with_drive(A, B, alpha)
+    return BoxSpec(dims=dims, swimmers=(s,), name="single_swimmer_48")
+
+
+def _pair_swimmer(center, period):
+    return SwimmerSpec(center=center, radius=6.0, subdiv=3, spacing=18.0, k_spring=0.005,
+                       Gs=0.01, period=period).with_drive(1e-3, 1e-3, math.pi / 2)
+
+
+def swimmer_pair(arrangement: str, gap_radii: int, dims=(256, 128, 128), period=2000.0):
+    """Two swimmers (radius 6, subdivision 3 = 642 nodes, spacing 18, k=0.005,
+    drive 1e-3, period 2000) in-line along x or side by side along y, with a
+    surface gap of `gap_radii` bead radii, placed symmetrically about the box
+    centre."""
+    a, L = 6.0, 18.0
+    gap = gap_radii * a
+    cx, cy, cz = (float(d // 2) for d in dims)
+    if arrangement == "inline":
+        h = (2 * L + 2 * a + gap) / 2.0
+        centers = ((cx - h, cy, cz), (cx + h, cy, cz))
+    elif arrangement == "side":
+        h = (2 * a + gap) / 2.0
+        centers = ((cx, cy - h, cz), (cx, cy + h, cz))
+    else:
+        raise ValueError(arrangement)
+    sw = tuple(_pair_swimmer(c, period) for c in centers)
+    return BoxSpec(dims=dims, swimmers=sw, name=f"pair_{arrangement}_{gap_radii}a_{dims[0]}x{dims[1]}x{dims[2]}")
+
+
+PAIR_CASES = [(arr, n) for arr in ("inline", "side") for n in (3, 5, 8)]
+
+
+def pair_boxes_256x128x128():
+    """The six two-swimmer boxes: in-line and side-by-side at gaps 3, 5, 8 radii."""
+    return [swimmer_pair(arr, n) for arr, n in PAIR_CASES]
+
+
+def pair_side_256cube():
+    """Precision workload: 256^3 with two side-by-side swimmers, gap 3 radii."""
+    return swimmer_pair("side", 3, dims=(256, 256, 256))
+
+
+def adjoint_single_96(period=1000.0):
+    """Single swimmer (radius 6, subdivision 3, spacing 18) in 96^3, period 1000."""
+    s = _pair_swimmer((48.0, 48.0, 48.0), period)
+    return BoxSpec(dims=(96, 96, 96), swimmers=(s,), name="adjoint_single_96")
+
+
+def fluid_box(dims, tau=1.0, g=(0.0, 0.0, 0.0), forcing="guo"):
+    return BoxSpec(dims=dims, tau=tau, g=tuple(g), forcing=forcing, name=f"fluid_{dims}")
+
+
+# ----------------------------------------------------------------------------
+# Seeded random state for parity tests
+# ----------------------------------------------------------------------------
+
+def random_populations(n_cells, weights, seed=0, rho_amp=1e-3, u_amp=1e-3):
+    """Raw populations f_i = w_i (rho0 + noise) with small seeded noise, as an
+    (n_cells, 19) float64 array in the order of `weights`.  Each side maps
+    the columns to its own lattice order by velocity vector."""
+    rng = np.random.default_rng(seed)
+    w = np.asarray(weights, dtype=np.float64)
+    noise = rng.uniform(-1.0, 1.0, size=(n_cells, len(w)))
+    return w[None, :] * (1.0 + rho_amp * noise) + u_amp * w[None, :] * rng.uniform(-1, 1, size=(n_cells, 1))
+
+
+def perturbed_nodes(nodes, seed=0, amp=0.05):
+    rng = np.random.default_rng(seed)
+    return nodes + amp * rng.uniform(-1.0, 1.0, size=nodes.shape)
