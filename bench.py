@@ -1,0 +1,326 @@
+"""Throughput of the coupled LB/IB swimmer step (MLUPS including the IB cost)
+and the HBM-roofline fraction of its dominant kernel.
+
+Workload: the two-swimmer boxes, 256 x 128 x 128 (x = swimming axis) with two
+three-bead swimmers (bead radius 6 at icosphere subdivision 3 = 642 nodes,
+spacing 18, k = 0.005, Gs = 0.01, drive 1e-3, period 2000, phase pi/2),
+in-line and side by side at surface gaps of 3, 5 and 8 bead radii: six boxes.
+One step advances all six boxes by one coupled time step.  Synthetic inputs
+(the problem has no dataset): the fluid starts at rest, the beads at their
+rest shape.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs the same six boxes on its own GPU (replicas;
+the boxes are independent), timing is max over ranks and value is the
+whole-job aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS incl. IBM and % of HBM roofline (FP32 vs FP16-storage vs batched) at stated error"
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = "two_swimmer_boxes_256x128x128_x6"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=192)
+    ap.add_argument("--warmup", type=int, default=16)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _boxes():
+    from workloads import pair_boxes_256x128x128
+    return pair_boxes_256x128x128()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not getattr(self, "out", ""):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _masked_cells(sim_dims, nodes, tile=256):
+    """Cells in LB tiles touched by the 4^3 stencils of the nodes."""
+    nx, ny, nz = sim_dims
+    b = np.floor(nodes).astype(np.int64) - 1
+    cells = set()
+    for dz in range(4):
+        for dy in range(4):
+            for dx in range(4):
+                x = (b[:, 0] + dx) % nx
+                y = (b[:, 1] + dy) % ny
+                z = (b[:, 2] + dz) % nz
+                cells.update(((x + nx * (y + ny * z)) // tile).tolist())
+    return min(len(cells) * tile, nx * ny * nz)
+
+
+def _oracle_sample(seconds):
+    """The FP64 oracle, as it stands, on one 256x128x128 two-swimmer box:
+    coupled steps until `seconds` have elapsed (at least two)."""
+    import oracle
+    box = _boxes()[3]  # side by side, gap 3 radii
+    sim = oracle.OracleSim(box)
+    sim.step(1)  # first-touch of the arrays outside the timing
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step(1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if n >= 2 and dt >= seconds:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    mlups = box.n_cells * n / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle",
+            "sample": f"{n} coupled steps of one 256x128x128 two-swimmer box (side by side, gap 3 radii), "
+                      f"FP64, {dt:.1f} s"}
+
+
+def run_reference(a):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import oracle
+    box = _boxes()[3]
+    sim = oracle.OracleSim(box)
+    t0 = time.perf_counter()
+    sim.step(1)
+    t_step = time.perf_counter() - t0
+    # bounded sample: the whole arm stays within about two minutes
+    n_warm = max(0, min(a.warmup - 1, int(20.0 / t_step)))
+    n_timed = max(2, min(a.steps, int(90.0 / t_step)))
+    sim.step(n_warm)
+    t0 = time.perf_counter()
+    sim.step(n_timed)
+    dt = time.perf_counter() - t0
+    mlups = box.n_cells * n_timed / dt / 1e6
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / n_timed * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "one of the six boxes per step (side by side, gap 3 radii)"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{n_timed} timed coupled steps (after {n_warm + 1} warm-up) of one "
+                                       f"256x128x128 two-swimmer box, FP64; each step is one sixth of a "
+                                       f"workload step"},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+    from paper_2202_12147_gb300 import Simulation
+    from workloads import assemble
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    boxes = _boxes()
+    asms = [assemble(b) for b in boxes]
+    sims = [Simulation(b.dims, asm, tau=b.tau, rho0=b.rho0, storage=a.storage) for b, asm in zip(boxes, asms)]
+    N = boxes[0].n_cells
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+
+    for s in sims:
+        s.lb_step(a.warmup)
+    for s in sims:
+        s.sync()
+    barrier()
+    for s in sims:
+        s.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        for s in sims:
+            s.lb_step(a.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    lb_ms, lb_n = 0.0, 0
+    for s in sims:
+        t, n = s.profile_read()
+        lb_ms += t
+        lb_n += n
+        s.profile(False)
+    for s in sims:
+        s.sync()  # latched device errors surface here
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells_per_step = N * len(sims)
+    value = ws * cells_per_step * a.steps / (ms / 1e3) / 1e6
+    esize = {"f32": 4, "f16": 2, "bf16": 2}[a.storage]
+    masked = statistics.mean(_masked_cells(b.dims, asm["nodes"]) for b, asm in zip(boxes, asms))
+    bytes_per_launch = N * 19 * 2 * esize + masked * 48
+    lb_avg_s = lb_ms / lb_n / 1e3
+    peak, peak_kind = _peak()
+    achieved = bytes_per_launch / lb_avg_s / 1e9
+    launches = a.steps * len(sims) * 4
+
+    e2e = None
+    if not a.no_e2e:
+        # End to end through the public API: structure upload from host arrays
+        # (lb_init), then per step one coupled step of every box and a
+        # device-to-host read of every swimmer's observables.
+        for s in sims:
+            s.close()
+        del sims
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        sims2 = [Simulation(b.dims, asm, tau=b.tau, rho0=b.rho0, storage=a.storage) for b, asm in zip(boxes, asms)]
+        h2d = sum(asm["nodes"].nbytes * 2 + asm["tris"].nbytes * 6 for asm in asms)
+        import ctypes
+        from paper_2202_12147_gb300 import _lib
+        rec = ctypes.sizeof(_lib.SwimmerState) + 16
+        d2h = 0
+        for _ in range(a.steps):
+            for s in sims2:
+                s.lb_step(1)
+            for s in sims2:
+                for k in range(s.n_swimmers):
+                    s.swimmer_state(k)
+                    d2h += rec  # control block + state record
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * cells_per_step * a.steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(h2d / a.steps), "d2h_bytes_per_step": int(d2h / a.steps)}
+        for s in sims2:
+            s.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        cpu = _oracle_sample(a.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": a.storage, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "boxes": len(boxes), "dims": list(boxes[0].dims), "cells_per_box": N,
+                       "swimmers_per_box": 2, "nodes_per_box": int(asms[0]["nodes"].shape[0]),
+                       "cases": [b.name for b in boxes], "storage": f"{a.storage} shifted deviations",
+                       "tau": 1.0, "delta_kernel": "peskin4", "forcing": "guo",
+                       "l2": "inputs larger than L2 (populations 318 MB per box in FP32)",
+                       "timing": "kernels launched one by one with CUDA events around every fluid-kernel launch"},
+            "roofline": {"bound": "hbm", "kernel": "k_lb_step", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
+                         "launches": lb_n},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

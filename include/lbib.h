@@ -1,0 +1,224 @@
+/*
+ * lbib — C ABI of the coupled lattice-Boltzmann / immersed-boundary time step
+ * for three-bead microswimmers (Geyer et al., "Lattice Boltzmann Simulations
+ * of Two Linear Microswimmers Using the Immersed Boundary Method",
+ * arXiv 2202.12147), implemented as CUDA kernels for sm_103a.
+ *
+ * One coupled step (Sec. 2, in this order):
+ *   1. bead centres R_b = mean of the bead's mesh nodes        (Fig. 1 caption)
+ *   2. drive f^d(t) and spring forces f^s(R) per swimmer       (Sec. 2.2)
+ *   3. membrane forces f^part = -dW/dr on each node (linear FEM) (Sec. 2.2)
+ *      and f^tot = f^part + (f^d + f^s)/N_v                    (Sec. 2.2)
+ *   4. force spreading F(x) = sum_j f^tot_j Delta(x - r_j)     (Sec. 2.3, Eq. spreading)
+ *   5. D3Q19 BGK collide with body force, then stream           (Sec. 2.1, Eqs. lbe, lbm:equilibrium)
+ *   6. velocity interpolation rdot_j = sum_x u(x) Delta(x-r_j) (Sec. 2.3, Eq. interpolation)
+ *   7. front tracking r_j += rdot_j (dt = 1)                   (Sec. 2.3)
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: LBIB_OK (0) or a negative code.
+ *     Nothing aborts or throws across this boundary.  lbib_last_error() gives
+ *     a message for the most recent failure on the calling thread.
+ *   - Lattice nodes sit at integer coordinates 0..n-1 of a periodic box,
+ *     cell index = x + nx*(y + ny*z).  Lagrangian node coordinates are
+ *     unwrapped doubles (they may leave [0, n)).
+ *   - Large device buffers are owned by the caller (allocate them with the
+ *     sizes from lbib_required_sizes), borrowed by the context and must
+ *     outlive it.  The context owns only host metadata, a private capture
+ *     stream, CUDA graphs and a small pinned host block.
+ *   - Work is queued on the stream given to lb_init.  Calls are asynchronous
+ *     unless stated otherwise; device-side errors (non-finite values, unstable
+ *     node speeds) are latched in device memory and reported by the next
+ *     synchronising call (swimmer_state, lb_sync, the lb_get_* calls).
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LBIB_OK 0
+#define LBIB_EINVAL -1     /* invalid argument, detected before any launch */
+#define LBIB_ECUDA -2      /* a CUDA runtime call failed */
+#define LBIB_ENONFINITE -3 /* a density, velocity or node position became NaN/Inf */
+#define LBIB_EUNSTABLE -4  /* a node moved faster than 0.1 lattice units per step */
+#define LBIB_ETIMEOUT -5   /* a bounded device-side wait gave up */
+#define LBIB_ESIZE -6      /* a buffer is too small or a size exceeds a limit */
+
+/* ---- options ----------------------------------------------------------- */
+/* Population storage.  Every format stores the shifted deviation
+ * d_i = f_i - w_i rho0 (F32 as is; F16/BF16 as d_i / w_i * store_scale);
+ * collisions always run in FP32. */
+#define LBIB_F32 0
+#define LBIB_F16 1
+#define LBIB_BF16 2
+/* Body-force inclusion: Guo's source term, or the paper's Shan-Chen velocity
+ * shift rho u^eq = sum f c + tau F (Sec. 2.1, Eq. sc). */
+#define LBIB_GUO 0
+#define LBIB_SHAN_CHEN 1
+/* Discrete delta kernel (Sec. 2.3): Peskin's 4-point kernel (4^3 stencil) or
+ * the paper's 2-point linear kernel (2^3 stencil). */
+#define LBIB_PESKIN4 0
+#define LBIB_LINEAR2 1
+
+/* Fluid box.  tau > 1/2 is the BGK relaxation time (viscosity
+ * nu = (tau - 1/2)/3, Sec. 2.1); rho0 the rest density; g a uniform
+ * force density added in every cell (zero for swimmer runs).
+ * deterministic = 1 makes spreading bitwise reproducible run to run
+ * (fixed-point integer accumulation instead of float atomics).
+ * store_scale: scale S of the F16/BF16 formats, 0 selects 4096. */
+typedef struct {
+    int nx, ny, nz;
+    double tau;
+    double rho0;
+    int storage;
+    int forcing;
+    int kernel;
+    int deterministic;
+    double g[3];
+    double store_scale;
+} lb_params;
+
+/* One bead: its mesh nodes [node_start, node_start + node_count) and
+ * triangles [tri_start, tri_start + tri_count) of the structure arrays;
+ * Gs the neo-Hookean shear modulus of its membrane. */
+typedef struct {
+    int node_start, node_count;
+    int tri_start, tri_count;
+    double Gs;
+} lbib_bead;
+
+/* One three-bead swimmer (Sec. 2.2).  bead[0..2] index the bead table in
+ * swimming-axis order.  Springs: stiffness k_spring, rest length L_spring.
+ * Drive along x on bead b: amp[b] sin(2 pi t / period + phase[b]); with
+ * balance = 1 the middle bead instead carries -(f_0 + f_2), the paper's
+ * protocol (f1 = A sin(wt), f3 = B sin(wt + alpha), f2 = -f1 - f3). */
+typedef struct {
+    int bead[3];
+    double k_spring, L_spring;
+    double amp[3], phase[3];
+    int balance;
+    double period;
+} lbib_swimmer;
+
+/* The Lagrangian structure.  All pointers are HOST memory, read during
+ * lb_init only.  rest_nodes (n_nodes x 3, row-major) is both the
+ * stress-free membrane shape and the initial node positions; tris
+ * (n_tris x 3) are global node ids, counter-clockwise seen from outside. */
+typedef struct {
+    int n_beads, n_swimmers, n_nodes, n_tris;
+    const lbib_bead *beads;
+    const lbib_swimmer *swimmers;
+    const double *rest_nodes;
+    const int *tris;
+} lbib_structure;
+
+/* Caller-owned device buffers (each 256-byte aligned) of at least the sizes
+ * lbib_required_sizes returns, in this order. */
+#define LBIB_NBUF 3
+typedef struct {
+    void *pops;   /* populations: 19 planes of the padded cell count */
+    void *fields; /* force density F and velocity u per cell, tile flags */
+    void *aux;    /* node positions, node forces/velocities, mesh tables, control block */
+} lbib_buffers;
+
+/* Observables of one swimmer (Sec. 3, Eq. vel_swim, Sec. 2.2 Reynolds
+ * numbers need the bead velocities).  All FP64. */
+typedef struct {
+    long long step;        /* time steps taken since lb_init */
+    double R[3][3];        /* bead centres, unwrapped */
+    double V[3][3];        /* bead velocities: mean interpolated node velocity of the last step */
+    double F[3][3];        /* sum of the total nodal forces of each bead at the last force evaluation */
+    double T[3][3];        /* torque of those forces about each bead centre */
+    double x_cm[3];        /* mean of the three bead centres */
+    double disp[3];        /* x_cm minus x_cm at lb_init */
+} lbib_swimmer_state;
+
+typedef struct lbib_ctx lbib_ctx;
+
+/* Version string of the library. */
+const char *lbib_version(void);
+/* Message for a status code. */
+const char *lbib_strerror(int status);
+/* Message of the most recent failure on the calling thread. */
+const char *lbib_last_error(void);
+
+/* The library's D3Q19 velocity set (Sec. 2.1): c[19][3] and w[19], in the
+ * order the population planes are stored.  Opposite directions are adjacent
+ * (i, i+1 for odd i). */
+int lbib_lattice(int *c, double *w);
+
+/* Byte sizes of the three caller buffers for this box and structure.
+ * out_bytes[LBIB_NBUF].  structure may be NULL (no swimmers). */
+int lbib_required_sizes(const lb_params *p, const lbib_structure *s, size_t *out_bytes);
+
+/* Create a context over caller buffers.  Uploads the mesh tables (reference
+ * metrics per triangle, node-to-triangle lists), sets every population to
+ * rest (f_i = w_i rho0, Sec. 2.1 with u = 0), places the nodes at rest_nodes
+ * and captures the CUDA graphs of the step.  stream: a cudaStream_t (NULL =
+ * legacy default stream).  Synchronous.  *out receives the context. */
+int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, void *stream, lbib_ctx **out);
+
+/* Advance n_steps full coupled steps (1-7 above) asynchronously on the
+ * context stream, replaying captured CUDA graphs. */
+int lb_step(lbib_ctx *ctx, long long n_steps);
+
+/* Steps 1-4 alone at the current positions and time: evaluate f^tot on every
+ * node and add its spread into the force field F; the next lb_step applies
+ * and clears F.  For tests and custom coupling. */
+int ib_spread(lbib_ctx *ctx);
+
+/* Step 6 alone: interpolate the velocity field u held in the fields buffer
+ * at the current node positions, without moving the nodes.  node_vel_out is
+ * a DEVICE pointer to n_nodes x 3 floats.  (lb_step writes u only in the
+ * tiles around the nodes; lb_set_velocity fills it everywhere.) */
+int ib_interpolate(lbib_ctx *ctx, float *node_vel_out);
+
+/* Copy one swimmer's observables to host memory.  Synchronises the context
+ * stream and reports latched device errors. */
+int swimmer_state(lbib_ctx *ctx, int swimmer, lbib_swimmer_state *out);
+
+/* Wait for queued work and report latched device errors. */
+int lb_sync(lbib_ctx *ctx);
+
+/* Density and momentum velocity u = sum f c / rho (no force term) of the
+ * current populations into DEVICE arrays rho[n_cells], u[n_cells x 3]. */
+int lb_get_macros(lbib_ctx *ctx, float *rho, float *u);
+
+/* Current populations as raw f_i (not deviations), HOST array [19][n_cells]
+ * in lbib_lattice order, FP64.  Synchronous. */
+int lb_get_populations(lbib_ctx *ctx, double *host_f);
+/* Replace the populations with raw f_i from HOST [19][n_cells] FP64. */
+int lb_set_populations(lbib_ctx *ctx, const double *host_f);
+
+/* Node positions as HOST n_nodes x 3 FP64 (get is synchronous). */
+int lb_get_nodes(lbib_ctx *ctx, double *host_xyz);
+int lb_set_nodes(lbib_ctx *ctx, const double *host_xyz);
+
+/* Total nodal forces f^tot of the last force evaluation, HOST n_nodes x 3. */
+int ib_get_node_forces(lbib_ctx *ctx, float *host_f);
+/* The force field F currently accumulated, HOST n_cells x 3. */
+int lb_get_force_field(lbib_ctx *ctx, float *host_F);
+/* Overwrite the velocity field u with HOST n_cells x 3 values. */
+int lb_set_velocity(lbib_ctx *ctx, const float *host_u);
+
+/* Timing hook.  With on = 1, lb_step launches its kernels one by one and
+ * brackets every fluid (LB) kernel launch with a pair of CUDA events on the
+ * context stream; with on = 0 (the default) it replays captured graphs.
+ * Switching on discards earlier measurements. */
+int lb_profile(lbib_ctx *ctx, int on);
+/* Sum of the bracketed fluid-kernel durations in milliseconds and the
+ * number of launches measured since profiling was switched on.
+ * Synchronises the context stream. */
+int lb_profile_read(lbib_ctx *ctx, double *total_ms, long long *launches);
+
+/* Release the context (not the caller's buffers).  Synchronises. */
+int lb_destroy(lbib_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBIB_H */

@@ -1,0 +1,16 @@
+"""GB300-native coupled lattice-Boltzmann / immersed-boundary step for
+three-bead microswimmers (Geyer et al., arXiv 2202.12147).
+
+The compute path is liblbib.so (hand-written CUDA for sm_103a behind the C ABI
+in include/lbib.h); this package only marshals arguments to it.
+"""
+from . import _lib  # noqa: F401
+from .build import build  # noqa: F401
+
+
+def __getattr__(name):
+    # the simulation wrapper needs torch; import it lazily
+    if name in ("Simulation", "lattice", "required_sizes"):
+        from . import sim
+        return getattr(sim, name)
+    raise AttributeError(name)

@@ -1,0 +1,116 @@
+"""ctypes mirror of include/lbib.h.  Argument marshalling only: every step of
+the coupled update runs inside liblbib.so.  There is no fallback; if the
+library cannot be loaded the import of a caller fails loudly."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+LBIB_OK, LBIB_EINVAL, LBIB_ECUDA, LBIB_ENONFINITE, LBIB_EUNSTABLE, LBIB_ETIMEOUT, LBIB_ESIZE = 0, -1, -2, -3, -4, -5, -6
+F32, F16, BF16 = 0, 1, 2
+GUO, SHAN_CHEN = 0, 1
+PESKIN4, LINEAR2 = 0, 1
+NBUF = 3
+
+EXPORTS = [
+    "lbib_version", "lbib_strerror", "lbib_last_error", "lbib_lattice", "lbib_required_sizes", "lb_init", "lb_step",
+    "ib_spread", "ib_interpolate", "swimmer_state", "lb_sync", "lb_get_macros", "lb_get_populations",
+    "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces", "lb_get_force_field",
+    "lb_set_velocity", "lb_profile", "lb_profile_read", "lb_destroy",
+]
+
+
+class LbParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("tau", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("storage", ctypes.c_int), ("forcing", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("deterministic", ctypes.c_int), ("g", ctypes.c_double * 3),
+                ("store_scale", ctypes.c_double)]
+
+
+class Bead(ctypes.Structure):
+    _fields_ = [("node_start", ctypes.c_int), ("node_count", ctypes.c_int), ("tri_start", ctypes.c_int),
+                ("tri_count", ctypes.c_int), ("Gs", ctypes.c_double)]
+
+
+class Swimmer(ctypes.Structure):
+    _fields_ = [("bead", ctypes.c_int * 3), ("k_spring", ctypes.c_double), ("L_spring", ctypes.c_double),
+                ("amp", ctypes.c_double * 3), ("phase", ctypes.c_double * 3), ("balance", ctypes.c_int),
+                ("period", ctypes.c_double)]
+
+
+class Structure(ctypes.Structure):
+    _fields_ = [("n_beads", ctypes.c_int), ("n_swimmers", ctypes.c_int), ("n_nodes", ctypes.c_int),
+                ("n_tris", ctypes.c_int), ("beads", ctypes.POINTER(Bead)), ("swimmers", ctypes.POINTER(Swimmer)),
+                ("rest_nodes", ctypes.c_void_p), ("tris", ctypes.c_void_p)]
+
+
+class Buffers(ctypes.Structure):
+    _fields_ = [("pops", ctypes.c_void_p), ("fields", ctypes.c_void_p), ("aux", ctypes.c_void_p)]
+
+
+class SwimmerState(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("R", (ctypes.c_double * 3) * 3), ("V", (ctypes.c_double * 3) * 3),
+                ("F", (ctypes.c_double * 3) * 3), ("T", (ctypes.c_double * 3) * 3), ("x_cm", ctypes.c_double * 3),
+                ("disp", ctypes.c_double * 3)]
+
+
+class LbibError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbib error {code}: {msg}")
+        self.code = code
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbib.so (building it in-tree with nvcc when it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise OSError(f"{_build.LIB} missing: run paper_2202_12147_gb300.build.build()")
+            _build.build()
+        L = ctypes.CDLL(_build.LIB)
+        P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+        L.lbib_version.restype = ctypes.c_char_p
+        L.lbib_strerror.restype = ctypes.c_char_p
+        L.lbib_strerror.argtypes = [I]
+        L.lbib_last_error.restype = ctypes.c_char_p
+        L.lbib_lattice.argtypes = [P, P]
+        L.lbib_required_sizes.argtypes = [ctypes.POINTER(LbParams), ctypes.POINTER(Structure), P]
+        L.lb_init.argtypes = [ctypes.POINTER(LbParams), ctypes.POINTER(Structure), ctypes.POINTER(Buffers), P,
+                              ctypes.POINTER(P)]
+        L.lb_step.argtypes = [P, LL]
+        L.ib_spread.argtypes = [P]
+        L.ib_interpolate.argtypes = [P, P]
+        L.swimmer_state.argtypes = [P, I, ctypes.POINTER(SwimmerState)]
+        L.lb_sync.argtypes = [P]
+        L.lb_get_macros.argtypes = [P, P, P]
+        for n in ("lb_get_populations", "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces",
+                  "lb_get_force_field", "lb_set_velocity"):
+            getattr(L, n).argtypes = [P, P]
+        L.lb_profile.argtypes = [P, I]
+        L.lb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)]
+        L.lb_destroy.argtypes = [P]
+        for n in EXPORTS:
+            if n not in ("lbib_version", "lbib_strerror", "lbib_last_error"):
+                getattr(L, n).restype = I
+        _lib = L
+        return L
+
+
+def check(code):
+    if code != LBIB_OK:
+        L = load()
+        raise LbibError(code, L.lbib_last_error().decode())
+    return code

@@ -1,0 +1,643 @@
+// C ABI of liblbib (declared in include/lbib.h): argument checks, the layout
+// of the caller buffers, mesh preprocessing, CUDA-graph capture of the step
+// and the host-side accessors.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbib_internal.cuh"
+
+using namespace lbib;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(LBIB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+constexpr size_t ALIGN = 256;
+size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+constexpr int GRAPH_STEPS = 16;  // steps per captured graph (even: both AA parities)
+
+struct Layout {
+    long long N = 0, Npad = 0;
+    int n_tiles = 0;
+    size_t esize = 4;
+    size_t bytes[LBIB_NBUF] = {0, 0, 0};
+    // fields
+    size_t oF = 0, oFdet = 0, oU = 0, oFlags = 0;
+    // aux
+    size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
+           obead = 0, oswim = 0, obd = 0, octl = 0, osws = 0, oxcm = 0;
+};
+
+bool valid_params(const lb_params *p, std::string &why) {
+    if (!p) { why = "params is NULL"; return false; }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "box dimensions must be >= 1"; return false; }
+    long long N = (long long)p->nx * p->ny * p->nz;
+    if (N >= (1ll << 31)) { why = "box has 2^31 cells or more"; return false; }
+    if (!(p->tau > 0.5)) { why = "tau must exceed 1/2 (positive viscosity)"; return false; }
+    if (!(p->rho0 > 0.0)) { why = "rho0 must be positive"; return false; }
+    if (p->storage < LBIB_F32 || p->storage > LBIB_BF16) { why = "unknown storage format"; return false; }
+    if (p->forcing != LBIB_GUO && p->forcing != LBIB_SHAN_CHEN) { why = "unknown forcing scheme"; return false; }
+    if (p->kernel != LBIB_PESKIN4 && p->kernel != LBIB_LINEAR2) { why = "unknown delta kernel"; return false; }
+    if (p->store_scale < 0.0) { why = "store_scale must be >= 0"; return false; }
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->g[a])) { why = "g must be finite"; return false; }
+    return true;
+}
+
+bool valid_structure(const lb_params *p, const lbib_structure *s, std::string &why) {
+    if (!s) return true;
+    if (s->n_beads < 0 || s->n_swimmers < 0 || s->n_nodes < 0 || s->n_tris < 0) { why = "negative count"; return false; }
+    if (s->n_swimmers > 0 && (!s->swimmers || !s->beads)) { why = "swimmer/bead table missing"; return false; }
+    if (s->n_nodes > 0 && !s->rest_nodes) { why = "rest_nodes missing"; return false; }
+    if (s->n_tris > 0 && !s->tris) { why = "tris missing"; return false; }
+    if (s->n_beads != 3 * s->n_swimmers) { why = "every bead must belong to exactly one three-bead swimmer"; return false; }
+    std::vector<int> owner(s->n_beads, -1);
+    for (int k = 0; k < s->n_swimmers; ++k) {
+        const lbib_swimmer &w = s->swimmers[k];
+        for (int q = 0; q < 3; ++q) {
+            int b = w.bead[q];
+            if (b < 0 || b >= s->n_beads) { why = "swimmer bead index out of range"; return false; }
+            if (owner[b] >= 0) { why = "bead used by two swimmers"; return false; }
+            owner[b] = k;
+        }
+        if (!(w.period > 0.0) || !std::isfinite(w.k_spring) || !(w.L_spring >= 0.0)) {
+            why = "swimmer needs period > 0, finite k_spring, L_spring >= 0";
+            return false;
+        }
+    }
+    for (int b = 0; b < s->n_beads; ++b) {
+        const lbib_bead &d = s->beads[b];
+        if (d.node_count < 4 || d.node_start < 0 || d.node_start + d.node_count > s->n_nodes) {
+            why = "bead node range invalid";
+            return false;
+        }
+        if (d.tri_count < 1 || d.tri_start < 0 || d.tri_start + d.tri_count > s->n_tris) {
+            why = "bead triangle range invalid";
+            return false;
+        }
+        for (int t = d.tri_start; t < d.tri_start + d.tri_count; ++t)
+            for (int q = 0; q < 3; ++q) {
+                int v = s->tris[3 * t + q];
+                if (v < d.node_start || v >= d.node_start + d.node_count) {
+                    why = "triangle uses a node outside its bead";
+                    return false;
+                }
+            }
+    }
+    for (long long j = 0; j < 3ll * s->n_nodes; ++j)
+        if (!std::isfinite(s->rest_nodes[j])) { why = "non-finite node coordinate"; return false; }
+    (void)p;
+    return true;
+}
+
+Layout make_layout(const lb_params *p, const lbib_structure *s) {
+    Layout L;
+    L.N = (long long)p->nx * p->ny * p->nz;
+    L.Npad = (L.N + 63) / 64 * 64;
+    L.n_tiles = (int)((L.N + LB_TPB - 1) / LB_TPB);
+    L.esize = p->storage == LBIB_F32 ? 4 : 2;
+    L.bytes[0] = up((size_t)Q * L.Npad * L.esize);
+    size_t o = 0;
+    if (p->deterministic) {
+        L.oFdet = o;
+        o += up(3 * (size_t)L.Npad * 8);
+    } else {
+        L.oF = o;
+        o += up((size_t)L.Npad * 16);
+    }
+    L.oU = o;
+    o += up((size_t)L.Npad * 16);
+    L.oFlags = o;
+    o += up((size_t)L.n_tiles);
+    L.bytes[1] = o;
+    const int M = s ? s->n_nodes : 0, T = s ? s->n_tris : 0, B = s ? s->n_beads : 0, S = s ? s->n_swimmers : 0;
+    o = 0;
+    L.orx = o; o += up((size_t)M * 8 + 8);
+    L.ory = o; o += up((size_t)M * 8 + 8);
+    L.orz = o; o += up((size_t)M * 8 + 8);
+    L.onf = o; o += up((size_t)M * 16 + 16);
+    L.onv = o; o += up((size_t)M * 16 + 16);
+    L.otf = o; o += up((size_t)T * 48 + 16);
+    L.otri = o; o += up((size_t)T * sizeof(TriDev) + 16);
+    L.ocp = o; o += up((size_t)(M + 1) * 4);
+    L.oce = o; o += up((size_t)3 * T * 4 + 4);
+    L.onb = o; o += up((size_t)M * 4 + 4);
+    L.obead = o; o += up((size_t)B * sizeof(BeadDev) + 16);
+    L.oswim = o; o += up((size_t)S * sizeof(SwimDev) + 16);
+    L.obd = o; o += up((size_t)B * 64 + 64);
+    L.octl = o; o += up(sizeof(Control));
+    L.osws = o; o += up((size_t)S * sizeof(lbib_swimmer_state) + 16);
+    L.oxcm = o; o += up((size_t)S * 24 + 24);
+    L.bytes[2] = o;
+    return L;
+}
+
+}  // namespace
+
+struct lbib_ctx {
+    lb_params p;
+    Layout L;
+    DevCtx d;
+    cudaStream_t user = nullptr;   // caller stream: all work goes here
+    cudaStream_t cap = nullptr;    // private stream used only to capture graphs
+    cudaGraphExec_t graph = nullptr;
+    long long step = 0;            // host mirror of the device step counter
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;   // event pairs around fluid-kernel launches
+    size_t ev_used = 0;
+    Control *h_ctl = nullptr;      // pinned
+    lbib_swimmer_state *h_sws = nullptr;  // pinned
+    int n_nodes = 0, n_swimmers = 0;
+};
+
+namespace {
+
+cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t s, bool timed = false) {
+    cudaError_t e;
+    if (c->n_nodes > 0) {
+        if ((e = launch_ib_prepare(c->d, s)) != cudaSuccess) return e;
+        if ((e = launch_ib_gather_spread(c->d, c->p.kernel, s)) != cudaSuccess) return e;
+    }
+    if (timed) {
+        while (c->ev.size() < c->ev_used + 2) {
+            cudaEvent_t ev;
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+            c->ev.push_back(ev);
+        }
+        if ((e = cudaEventRecord(c->ev[c->ev_used], s)) != cudaSuccess) return e;
+    }
+    if ((e = launch_lb_step(c->d, c->p.storage, c->p.forcing, odd, s)) != cudaSuccess) return e;
+    if (timed) {
+        if ((e = cudaEventRecord(c->ev[c->ev_used + 1], s)) != cudaSuccess) return e;
+        c->ev_used += 2;
+    }
+    if (c->n_nodes > 0) {
+        if ((e = launch_ib_interp(c->d, c->p.kernel, true, nullptr, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int check_device_errors(lbib_ctx *c) {
+    CU(cudaMemcpyAsync(c->h_ctl, c->d.ctl, sizeof(Control), cudaMemcpyDeviceToHost, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    const int e = c->h_ctl->err;
+    if (e & ERR_NONFINITE) return fail(LBIB_ENONFINITE, "non-finite density, velocity or node position");
+    if (e & ERR_UNSTABLE) return fail(LBIB_EUNSTABLE, "a node moved faster than 0.1 lattice units per step");
+    if (e & ERR_TIMEOUT) return fail(LBIB_ETIMEOUT, "a bounded device wait gave up");
+    return LBIB_OK;
+}
+
+// index of direction i's value for cell (x,y,z) in the storage, given the parity of the next step
+inline size_t slot_of(const lbib_ctx *c, int i, long long x, long long y, long long z, bool odd) {
+    const long long nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    if (!odd) return (size_t)i * c->L.Npad + (size_t)(x + nx * (y + ny * z));
+    const long long xs = (x - cx(i) + nx) % nx, ys = (y - cy(i) + ny) % ny, zs = (z - cz(i) + nz) % nz;
+    return (size_t)opp(i) * c->L.Npad + (size_t)(xs + nx * (ys + ny * zs));
+}
+
+float store_scale(const lb_params *p) { return p->store_scale > 0.0 ? (float)p->store_scale : 4096.0f; }
+
+}  // namespace
+
+extern "C" {
+
+const char *lbib_version(void) { return "lbib 0.1 (sm_103a)"; }
+
+const char *lbib_strerror(int s) {
+    switch (s) {
+        case LBIB_OK: return "ok";
+        case LBIB_EINVAL: return "invalid argument";
+        case LBIB_ECUDA: return "CUDA runtime error";
+        case LBIB_ENONFINITE: return "non-finite value in the simulation state";
+        case LBIB_EUNSTABLE: return "node speed above 0.1 lattice units per step";
+        case LBIB_ETIMEOUT: return "device-side wait timed out";
+        case LBIB_ESIZE: return "buffer too small or size above a limit";
+        default: return "unknown status";
+    }
+}
+
+const char *lbib_last_error(void) { return g_last_error.c_str(); }
+
+int lbib_lattice(int *c, double *w) {
+    if (!c || !w) return fail(LBIB_EINVAL, "lbib_lattice: NULL output");
+    for (int i = 0; i < Q; ++i) {
+        c[3 * i + 0] = cx(i);
+        c[3 * i + 1] = cy(i);
+        c[3 * i + 2] = cz(i);
+        w[i] = wgt_d(i);
+    }
+    return LBIB_OK;
+}
+
+int lbib_required_sizes(const lb_params *p, const lbib_structure *s, size_t *out) {
+    std::string why;
+    if (!out) return fail(LBIB_EINVAL, "out_bytes is NULL");
+    if (!valid_params(p, why) || !valid_structure(p, s, why)) return fail(LBIB_EINVAL, why);
+    Layout L = make_layout(p, s);
+    for (int k = 0; k < LBIB_NBUF; ++k) out[k] = L.bytes[k];
+    return LBIB_OK;
+}
+
+int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, void *stream, lbib_ctx **out) {
+    std::string why;
+    if (!out) return fail(LBIB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!valid_params(p, why) || !valid_structure(p, s, why)) return fail(LBIB_EINVAL, why);
+    if (!b || !b->pops || !b->fields || !b->aux) return fail(LBIB_EINVAL, "a buffer pointer is NULL");
+    if (((uintptr_t)b->pops | (uintptr_t)b->fields | (uintptr_t)b->aux) % ALIGN)
+        return fail(LBIB_EINVAL, "buffers must be 256-byte aligned");
+    const int M = s ? s->n_nodes : 0, T = s ? s->n_tris : 0, B = s ? s->n_beads : 0, S = s ? s->n_swimmers : 0;
+    Layout L = make_layout(p, s);
+
+    // mesh preprocessing on the host (reference shapes, node -> triangle lists)
+    std::vector<TriDev> tri(T);
+    std::vector<int> cptr(M + 1, 0), cent(3 * (size_t)T), nbead(M, 0);
+    std::vector<BeadDev> beads(B);
+    std::vector<SwimDev> swims(S);
+    for (int bi = 0; bi < B; ++bi) {
+        const lbib_bead &bd = s->beads[bi];
+        beads[bi].node_start = bd.node_start;
+        beads[bi].node_count = bd.node_count;
+        for (int j = bd.node_start; j < bd.node_start + bd.node_count; ++j) nbead[j] = bi;
+        for (int t = bd.tri_start; t < bd.tri_start + bd.tri_count; ++t) {
+            const int *v = s->tris + 3 * t;
+            const double *X = s->rest_nodes;
+            double e1[3], e2[3];
+            for (int a = 0; a < 3; ++a) {
+                e1[a] = X[3 * v[1] + a] - X[3 * v[0] + a];
+                e2[a] = X[3 * v[2] + a] - X[3 * v[0] + a];
+            }
+            TriDev &td = tri[t];
+            td.G[0] = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+            td.G[1] = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+            td.G[2] = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+            const double det = td.G[0] * td.G[2] - td.G[1] * td.G[1];
+            if (!(det > 0.0)) return fail(LBIB_EINVAL, "degenerate rest triangle");
+            td.Gi[0] = (float)(td.G[2] / det);
+            td.Gi[1] = (float)(-td.G[1] / det);
+            td.Gi[2] = (float)(td.G[0] / det);
+            td.K = (float)(0.5 * std::sqrt(det) * bd.Gs / det);
+            td.inv_detG = (float)(1.0 / det);
+            td.v[0] = v[0];
+            td.v[1] = v[1];
+            td.v[2] = v[2];
+            td.pad[0] = td.pad[1] = 0;
+        }
+    }
+    for (int t = 0; t < T; ++t)
+        for (int q = 0; q < 3; ++q) cptr[s->tris[3 * t + q] + 1]++;
+    for (int j = 0; j < M; ++j) cptr[j + 1] += cptr[j];
+    {
+        std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+        for (int t = 0; t < T; ++t)
+            for (int q = 0; q < 3; ++q) cent[fill[s->tris[3 * t + q]]++] = 3 * t + q;
+    }
+    for (int k = 0; k < S; ++k) {
+        const lbib_swimmer &w = s->swimmers[k];
+        SwimDev &d = swims[k];
+        for (int q = 0; q < 3; ++q) {
+            d.bead[q] = w.bead[q];
+            d.amp[q] = w.amp[q];
+            d.phase[q] = w.phase[q];
+            beads[w.bead[q]].swimmer = k;
+            beads[w.bead[q]].slot = q;
+        }
+        d.balance = w.balance;
+        d.k = w.k_spring;
+        d.L = w.L_spring;
+        d.period = w.period;
+    }
+
+    lbib_ctx *c = new lbib_ctx();
+    c->p = *p;
+    c->L = L;
+    c->user = (cudaStream_t)stream;
+    c->n_nodes = M;
+    c->n_swimmers = S;
+    DevCtx &d = c->d;
+    memset(&d, 0, sizeof(d));
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.nz = p->nz;
+    d.N = L.N;
+    d.Npad = L.Npad;
+    d.n_tiles = L.n_tiles;
+    d.tau = (float)p->tau;
+    d.omega = (float)(1.0 / p->tau);
+    d.rho0 = (float)p->rho0;
+    for (int a = 0; a < 3; ++a) d.g[a] = (float)p->g[a];
+    d.has_g = (p->g[0] != 0.0 || p->g[1] != 0.0 || p->g[2] != 0.0);
+    d.st_scale = store_scale(p);
+    d.st_inv_scale = 1.0f / d.st_scale;
+    d.n_nodes = M;
+    d.n_tris = T;
+    d.n_beads = B;
+    d.n_swimmers = S;
+    d.deterministic = p->deterministic ? 1 : 0;
+    char *F = (char *)b->fields, *A = (char *)b->aux;
+    d.pops = b->pops;
+    d.F = p->deterministic ? nullptr : (float4 *)(F + L.oF);
+    d.Fdet = p->deterministic ? (unsigned long long *)(F + L.oFdet) : nullptr;
+    d.U = (float4 *)(F + L.oU);
+    d.flags = (unsigned char *)(F + L.oFlags);
+    d.rx = (double *)(A + L.orx);
+    d.ry = (double *)(A + L.ory);
+    d.rz = (double *)(A + L.orz);
+    d.node_force = (float4 *)(A + L.onf);
+    d.node_vel = (float4 *)(A + L.onv);
+    d.tri_force = (float4 *)(A + L.otf);
+    d.tris = (const TriDev *)(A + L.otri);
+    d.csr_ptr = (const int *)(A + L.ocp);
+    d.csr_ent = (const int *)(A + L.oce);
+    d.node_bead = (const int *)(A + L.onb);
+    d.beads = (const BeadDev *)(A + L.obead);
+    d.swims = (const SwimDev *)(A + L.oswim);
+    d.bead_data = (double *)(A + L.obd);
+    d.ctl = (Control *)(A + L.octl);
+    d.sw_state = (lbib_swimmer_state *)(A + L.osws);
+    d.xcm0 = (double *)(A + L.oxcm);
+
+    auto bail = [&](int code) {
+        lb_destroy(c);
+        return code;
+    };
+    if (cudaMallocHost(&c->h_ctl, sizeof(Control)) != cudaSuccess ||
+        cudaMallocHost(&c->h_sws, sizeof(lbib_swimmer_state) * (S > 0 ? S : 1)) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "cudaMallocHost failed"));
+    cudaStream_t u = c->user;
+    // rest state: all deviations zero, fields and flags zero
+    if (cudaMemsetAsync(b->pops, 0, L.bytes[0], u) != cudaSuccess || cudaMemsetAsync(b->fields, 0, L.bytes[1], u) != cudaSuccess ||
+        cudaMemsetAsync(b->aux, 0, L.bytes[2], u) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "cudaMemsetAsync failed"));
+    std::vector<double> sx(M), sy(M), sz(M);
+    for (int j = 0; j < M; ++j) {
+        sx[j] = s->rest_nodes[3 * j];
+        sy[j] = s->rest_nodes[3 * j + 1];
+        sz[j] = s->rest_nodes[3 * j + 2];
+    }
+    auto h2d = [&](void *dst, const void *src, size_t n) {
+        return n == 0 || cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, u) == cudaSuccess;
+    };
+    bool ok = h2d(d.rx, sx.data(), M * 8) && h2d(d.ry, sy.data(), M * 8) && h2d(d.rz, sz.data(), M * 8) &&
+              h2d((void *)d.tris, tri.data(), T * sizeof(TriDev)) && h2d((void *)d.csr_ptr, cptr.data(), (M + 1) * 4) &&
+              h2d((void *)d.csr_ent, cent.data(), 3 * (size_t)T * 4) && h2d((void *)d.node_bead, nbead.data(), M * 4) &&
+              h2d((void *)d.beads, beads.data(), B * sizeof(BeadDev)) && h2d((void *)d.swims, swims.data(), S * sizeof(SwimDev));
+    if (!ok) return bail(fail(LBIB_ECUDA, "uploading mesh tables failed"));
+    if (launch_swimmer_state(d, true, u) != cudaSuccess) return bail(fail(LBIB_ECUDA, "swimmer_state init launch failed"));
+    if (cudaStreamSynchronize(u) != cudaSuccess) return bail(fail(LBIB_ECUDA, "init synchronisation failed"));
+
+    // capture GRAPH_STEPS coupled steps (alternating AA parity) into one graph
+    cudaGraph_t g = nullptr;
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "cudaStreamCreate failed"));
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "cudaStreamBeginCapture failed"));
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k) ce = enqueue_step(c, (k & 1) != 0, c->cap);
+    cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee)));
+    ce = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return bail(fail(LBIB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce)));
+    *out = c;
+    return LBIB_OK;
+}
+
+int lb_step(lbib_ctx *c, long long n) {
+    if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(LBIB_EINVAL, "n_steps < 0");
+    while (n > 0) {
+        if (c->profiling) {
+            CU(enqueue_step(c, (c->step & 1) != 0, c->user, true));
+            c->step += 1;
+            n -= 1;
+        } else if ((c->step & 1) == 0 && n >= GRAPH_STEPS) {
+            CU(cudaGraphLaunch(c->graph, c->user));
+            c->step += GRAPH_STEPS;
+            n -= GRAPH_STEPS;
+        } else {
+            CU(enqueue_step(c, (c->step & 1) != 0, c->user));
+            c->step += 1;
+            n -= 1;
+        }
+    }
+    return LBIB_OK;
+}
+
+int ib_spread(lbib_ctx *c) {
+    if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
+    if (c->n_nodes == 0) return LBIB_OK;
+    CU(launch_ib_prepare(c->d, c->user));
+    CU(launch_ib_gather_spread(c->d, c->p.kernel, c->user));
+    return LBIB_OK;
+}
+
+int ib_interpolate(lbib_ctx *c, float *vel) {
+    if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
+    if (c->n_nodes == 0) return LBIB_OK;
+    if (!vel) return fail(LBIB_EINVAL, "node_vel_out is NULL");
+    CU(launch_ib_interp(c->d, c->p.kernel, false, vel, c->user));
+    return LBIB_OK;
+}
+
+int swimmer_state(lbib_ctx *c, int s, lbib_swimmer_state *out) {
+    if (!c || !out) return fail(LBIB_EINVAL, "NULL argument");
+    if (s < 0 || s >= c->n_swimmers) return fail(LBIB_EINVAL, "swimmer index out of range");
+    CU(launch_swimmer_state(c->d, false, c->user));
+    CU(cudaMemcpyAsync(c->h_sws + s, c->d.sw_state + s, sizeof(lbib_swimmer_state), cudaMemcpyDeviceToHost, c->user));
+    int st = check_device_errors(c);
+    *out = c->h_sws[s];
+    return st;
+}
+
+int lb_sync(lbib_ctx *c) {
+    if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
+    return check_device_errors(c);
+}
+
+int lb_get_macros(lbib_ctx *c, float *rho, float *u) {
+    if (!c || !rho || !u) return fail(LBIB_EINVAL, "NULL argument");
+    CU(launch_lb_macros(c->d, c->p.storage, (c->step & 1) != 0, rho, u, c->user));
+    return LBIB_OK;
+}
+
+int lb_get_populations(lbib_ctx *c, double *hf) {
+    if (!c || !hf) return fail(LBIB_EINVAL, "NULL argument");
+    const size_t n = c->L.bytes[0];
+    std::vector<unsigned char> raw(n);
+    CU(cudaMemcpyAsync(raw.data(), c->d.pops, n, cudaMemcpyDeviceToHost, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    const bool odd = (c->step & 1) != 0;
+    const long long nx = c->p.nx, ny = c->p.ny, nz = c->p.nz, N = c->L.N;
+    const float sc = store_scale(&c->p);
+    for (int i = 0; i < Q; ++i)
+        for (long long z = 0; z < nz; ++z)
+            for (long long y = 0; y < ny; ++y)
+                for (long long x = 0; x < nx; ++x) {
+                    const size_t k = slot_of(c, i, x, y, z, odd);
+                    double dv;
+                    if (c->p.storage == LBIB_F32) dv = ((const float *)raw.data())[k];
+                    else if (c->p.storage == LBIB_F16) dv = (double)__half2float(((const __half *)raw.data())[k]) * wgt_d(i) / sc;
+                    else dv = (double)__bfloat162float(((const __nv_bfloat16 *)raw.data())[k]) * wgt_d(i) / sc;
+                    hf[(size_t)i * N + x + nx * (y + ny * z)] = wgt_d(i) * c->p.rho0 + dv;
+                }
+    return LBIB_OK;
+}
+
+int lb_set_populations(lbib_ctx *c, const double *hf) {
+    if (!c || !hf) return fail(LBIB_EINVAL, "NULL argument");
+    const size_t n = c->L.bytes[0];
+    std::vector<unsigned char> raw(n, 0);
+    const bool odd = (c->step & 1) != 0;
+    const long long nx = c->p.nx, ny = c->p.ny, nz = c->p.nz, N = c->L.N;
+    const float sc = store_scale(&c->p);
+    for (int i = 0; i < Q; ++i)
+        for (long long z = 0; z < nz; ++z)
+            for (long long y = 0; y < ny; ++y)
+                for (long long x = 0; x < nx; ++x) {
+                    const size_t k = slot_of(c, i, x, y, z, odd);
+                    const double dv = hf[(size_t)i * N + x + nx * (y + ny * z)] - wgt_d(i) * c->p.rho0;
+                    if (c->p.storage == LBIB_F32) ((float *)raw.data())[k] = (float)dv;
+                    else if (c->p.storage == LBIB_F16) ((__half *)raw.data())[k] = __float2half_rn((float)(dv / wgt_d(i) * sc));
+                    else ((__nv_bfloat16 *)raw.data())[k] = __float2bfloat16_rn((float)(dv / wgt_d(i) * sc));
+                }
+    CU(cudaMemcpyAsync(c->d.pops, raw.data(), n, cudaMemcpyHostToDevice, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    return LBIB_OK;
+}
+
+int lb_get_nodes(lbib_ctx *c, double *h) {
+    if (!c || (!h && c->n_nodes)) return fail(LBIB_EINVAL, "NULL argument");
+    const int M = c->n_nodes;
+    if (M == 0) return LBIB_OK;
+    std::vector<double> x(M), y(M), z(M);
+    CU(cudaMemcpyAsync(x.data(), c->d.rx, M * 8, cudaMemcpyDeviceToHost, c->user));
+    CU(cudaMemcpyAsync(y.data(), c->d.ry, M * 8, cudaMemcpyDeviceToHost, c->user));
+    CU(cudaMemcpyAsync(z.data(), c->d.rz, M * 8, cudaMemcpyDeviceToHost, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    for (int j = 0; j < M; ++j) {
+        h[3 * j] = x[j];
+        h[3 * j + 1] = y[j];
+        h[3 * j + 2] = z[j];
+    }
+    return LBIB_OK;
+}
+
+int lb_set_nodes(lbib_ctx *c, const double *h) {
+    if (!c || (!h && c->n_nodes)) return fail(LBIB_EINVAL, "NULL argument");
+    const int M = c->n_nodes;
+    if (M == 0) return LBIB_OK;
+    std::vector<double> x(M), y(M), z(M);
+    for (int j = 0; j < M; ++j) {
+        if (!std::isfinite(h[3 * j]) || !std::isfinite(h[3 * j + 1]) || !std::isfinite(h[3 * j + 2]))
+            return fail(LBIB_EINVAL, "non-finite node coordinate");
+        x[j] = h[3 * j];
+        y[j] = h[3 * j + 1];
+        z[j] = h[3 * j + 2];
+    }
+    CU(cudaMemcpyAsync(c->d.rx, x.data(), M * 8, cudaMemcpyHostToDevice, c->user));
+    CU(cudaMemcpyAsync(c->d.ry, y.data(), M * 8, cudaMemcpyHostToDevice, c->user));
+    CU(cudaMemcpyAsync(c->d.rz, z.data(), M * 8, cudaMemcpyHostToDevice, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    return LBIB_OK;
+}
+
+int ib_get_node_forces(lbib_ctx *c, float *h) {
+    if (!c || (!h && c->n_nodes)) return fail(LBIB_EINVAL, "NULL argument");
+    const int M = c->n_nodes;
+    if (M == 0) return LBIB_OK;
+    std::vector<float4> v(M);
+    CU(cudaMemcpyAsync(v.data(), c->d.node_force, M * 16, cudaMemcpyDeviceToHost, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    for (int j = 0; j < M; ++j) {
+        h[3 * j] = v[j].x;
+        h[3 * j + 1] = v[j].y;
+        h[3 * j + 2] = v[j].z;
+    }
+    return LBIB_OK;
+}
+
+int lb_get_force_field(lbib_ctx *c, float *h) {
+    if (!c || !h) return fail(LBIB_EINVAL, "NULL argument");
+    const long long N = c->L.N, Np = c->L.Npad;
+    if (c->p.deterministic) {
+        std::vector<long long> v(3 * (size_t)Np);
+        CU(cudaMemcpyAsync(v.data(), c->d.Fdet, 3 * (size_t)Np * 8, cudaMemcpyDeviceToHost, c->user));
+        CU(cudaStreamSynchronize(c->user));
+        for (long long k = 0; k < N; ++k)
+            for (int a = 0; a < 3; ++a) h[3 * k + a] = (float)((double)v[a * Np + k] * FIX_INV);
+    } else {
+        std::vector<float4> v(N);
+        CU(cudaMemcpyAsync(v.data(), c->d.F, (size_t)N * 16, cudaMemcpyDeviceToHost, c->user));
+        CU(cudaStreamSynchronize(c->user));
+        for (long long k = 0; k < N; ++k) {
+            h[3 * k] = v[k].x;
+            h[3 * k + 1] = v[k].y;
+            h[3 * k + 2] = v[k].z;
+        }
+    }
+    return LBIB_OK;
+}
+
+int lb_set_velocity(lbib_ctx *c, const float *h) {
+    if (!c || !h) return fail(LBIB_EINVAL, "NULL argument");
+    const long long N = c->L.N;
+    std::vector<float4> v(N);
+    for (long long k = 0; k < N; ++k) v[k] = make_float4(h[3 * k], h[3 * k + 1], h[3 * k + 2], 0.f);
+    CU(cudaMemcpyAsync(c->d.U, v.data(), (size_t)N * 16, cudaMemcpyHostToDevice, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    return LBIB_OK;
+}
+
+int lb_profile(lbib_ctx *c, int on) {
+    if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
+    CU(cudaStreamSynchronize(c->user));
+    c->profiling = on != 0;
+    c->ev_used = 0;
+    return LBIB_OK;
+}
+
+int lb_profile_read(lbib_ctx *c, double *total_ms, long long *launches) {
+    if (!c || !total_ms || !launches) return fail(LBIB_EINVAL, "NULL argument");
+    CU(cudaStreamSynchronize(c->user));
+    double t = 0.0;
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = (long long)(c->ev_used / 2);
+    return LBIB_OK;
+}
+
+int lb_destroy(lbib_ctx *c) {
+    if (!c) return LBIB_OK;
+    cudaStreamSynchronize(c->user);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->h_sws) cudaFreeHost(c->h_sws);
+    delete c;
+    return LBIB_OK;
+}
+
+}  // extern "C"

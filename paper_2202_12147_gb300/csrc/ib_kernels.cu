@@ -1,0 +1,418 @@
+// Immersed-boundary side of the coupled step: bead reductions, drive and
+// springs, the linear-FEM membrane, spreading and interpolation.
+//
+//   k_ib_prepare       blocks [0, n_swimmers): bead centres R_b (FP64 block
+//                      reduction in a fixed order, Fig. 1 caption), drive
+//                      f^d(t) and springs f^s(R) (Sec. 2.2), stored as the
+//                      per-node share (f^d + f^s)/N_v;
+//                      remaining blocks: one thread per triangle computes the
+//                      three corner forces -dW/dr of the neo-Hookean linear
+//                      FEM element (Sec. 2.2, virtual work).
+//   k_ib_gather_spread one thread per node sums its incident corner forces in
+//                      a fixed order plus the bead share (total nodal force,
+//                      Sec. 2.2), then KW^2 threads per node spread it over the
+//                      KW^3 stencil (Sec. 2.3, Eq. spreading) with vector float
+//                      atomics, or 64-bit fixed-point atomics (bitwise
+//                      reproducible), and mark the LB tiles they touch.
+//   k_ib_interp        KW^2 threads per node gather u over the stencil
+//                      (Sec. 2.3, Eq. interpolation), reduce with shuffles in
+//                      a fixed order and move the node r += rdot in FP64
+//                      (front tracking, Sec. 2.3).
+//
+// Membrane element.  With rest edge metric G = D^T D, current metric
+// g = d^T d = G + 2E and J^2 = det g / det G, the neo-Hookean energy
+// A0 Gs/2 (I1 - 1 + 1/J^2) has gradient
+//   dW/dd = A0 Gs / (det G J^4) * d * [ I2 (I2 + 2) adj(G) - 2 adj(E) ],
+// with I1 = 2 tr(G^{-1}E) and I2 = J^2 - 1 = 2 tr(G^{-1}E) + 4 det(E)/det(G).
+// Only E = (g - G)/2 is formed in FP64 (it is a small difference of O(1)
+// numbers); everything after it runs in FP32 without cancellation.
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+constexpr int PREP_TPB = 128;
+constexpr int GS_TPB = 128;
+constexpr int GS_NODES = 32;   // nodes per gather/spread block
+constexpr int INT_TPB = 128;
+
+// deterministic block reduction of 3 doubles (fixed shuffle tree, then warps in order)
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double *sm /* 3*32 */) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) {
+        sm[w] = a;
+        sm[32 + w] = b;
+        sm[64 + w] = c;
+    }
+    __syncthreads();
+    a = b = c = 0.0;
+    for (int k = 0; k < nw; ++k) {
+        a += sm[k];
+        b += sm[32 + k];
+        c += sm[64 + k];
+    }
+    __syncthreads();
+}
+
+__device__ void swimmer_forces(const DevCtx &c, int s, double *sm) {
+    const SwimDev sw = c.swims[s];
+    __shared__ double sR[3][3];
+    for (int q = 0; q < 3; ++q) {
+        const BeadDev bd = c.beads[sw.bead[q]];
+        double a = 0.0, b = 0.0, cc = 0.0;
+        for (int j = bd.node_start + threadIdx.x; j < bd.node_start + bd.node_count; j += blockDim.x) {
+            a += c.rx[j];
+            b += c.ry[j];
+            cc += c.rz[j];
+        }
+        block_sum3(a, b, cc, sm);
+        if (threadIdx.x == 0) {
+            const double inv = 1.0 / bd.node_count;
+            sR[q][0] = a * inv;
+            sR[q][1] = b * inv;
+            sR[q][2] = cc * inv;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // drive along x (Sec. 2.2, driving-force equation); t mod T taken exactly
+        const double om = 2.0 * 3.14159265358979323846 / sw.period;
+        const double tm = fmod((double)c.ctl->step, sw.period);
+        double fd[3];
+        fd[0] = sw.amp[0] * sin(om * tm + sw.phase[0]);
+        fd[2] = sw.amp[2] * sin(om * tm + sw.phase[2]);
+        fd[1] = sw.balance ? -fd[0] - fd[2] : sw.amp[1] * sin(om * tm + sw.phase[1]);
+        // springs between beads 0-1 and 2-1 (Sec. 2.2)
+        double fs[3][3];
+        for (int side = 0; side < 2; ++side) {
+            const int q = side ? 2 : 0;
+            double d[3], n2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = sR[q][a] - sR[1][a];
+                n2 += d[a] * d[a];
+            }
+            const double n = sqrt(n2);
+            const double m = -sw.k * (n - sw.L) / n;
+            for (int a = 0; a < 3; ++a) fs[q][a] = m * d[a];
+        }
+        for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
+        for (int q = 0; q < 3; ++q) {
+            const int b = sw.bead[q];
+            const double inv = 1.0 / c.beads[b].node_count;
+            double *bdat = c.bead_data + 8 * b;
+            bdat[0] = sR[q][0];
+            bdat[1] = sR[q][1];
+            bdat[2] = sR[q][2];
+            bdat[4] = (fd[q] + fs[q][0]) * inv;
+            bdat[5] = fs[q][1] * inv;
+            bdat[6] = fs[q][2] * inv;
+        }
+    }
+}
+
+__device__ void triangle_forces(const DevCtx &c, int t) {
+    const TriDev T = c.tris[t];
+    const int n0 = T.v[0], n1 = T.v[1], n2 = T.v[2];
+    const double x0 = c.rx[n0], y0 = c.ry[n0], z0 = c.rz[n0];
+    const double ax = c.rx[n1] - x0, ay = c.ry[n1] - y0, az = c.rz[n1] - z0;
+    const double bx = c.rx[n2] - x0, by = c.ry[n2] - y0, bz = c.rz[n2] - z0;
+    const float E00 = (float)(0.5 * (fma(ax, ax, fma(ay, ay, az * az)) - T.G[0]));
+    const float E01 = (float)(0.5 * (fma(ax, bx, fma(ay, by, az * bz)) - T.G[1]));
+    const float E11 = (float)(0.5 * (fma(bx, bx, fma(by, by, bz * bz)) - T.G[2]));
+    const float trM = T.Gi[0] * E00 + 2.0f * T.Gi[1] * E01 + T.Gi[2] * E11;
+    const float detM = (E00 * E11 - E01 * E01) * T.inv_detG;
+    const float I2 = 2.0f * trM + 4.0f * detM;
+    const float J2 = 1.0f + I2;
+    const float coef = T.K / (J2 * J2);
+    const float a = I2 * (I2 + 2.0f);
+    const float S00 = coef * (a * (float)T.G[2] - 2.0f * E11);
+    const float S01 = coef * (-a * (float)T.G[1] + 2.0f * E01);
+    const float S11 = coef * (a * (float)T.G[0] - 2.0f * E00);
+    const float d1x = (float)ax, d1y = (float)ay, d1z = (float)az;
+    const float d2x = (float)bx, d2y = (float)by, d2z = (float)bz;
+    // dW/dd1 = d1 S00 + d2 S01, dW/dd2 = d1 S01 + d2 S11
+    const float w1x = d1x * S00 + d2x * S01, w1y = d1y * S00 + d2y * S01, w1z = d1z * S00 + d2z * S01;
+    const float w2x = d1x * S01 + d2x * S11, w2y = d1y * S01 + d2y * S11, w2z = d1z * S01 + d2z * S11;
+    float4 *o = c.tri_force + 3 * (size_t)t;
+    o[0] = make_float4(w1x + w2x, w1y + w2y, w1z + w2z, 0.f);
+    o[1] = make_float4(-w1x, -w1y, -w1z, 0.f);
+    o[2] = make_float4(-w2x, -w2y, -w2z, 0.f);
+}
+
+__global__ void __launch_bounds__(PREP_TPB) k_ib_prepare(const DevCtx c) {
+    __shared__ double sm[96];
+    if ((int)blockIdx.x < c.n_swimmers) {
+        swimmer_forces(c, blockIdx.x, sm);
+        return;
+    }
+    const int t = (blockIdx.x - c.n_swimmers) * PREP_TPB + threadIdx.x;
+    if (t < c.n_tris) triangle_forces(c, t);
+}
+
+// 1-D kernel weights on the KW stencil cells floor(p) - KW/2 + 1 ... floor(p) + KW/2.
+// Peskin's 4-point kernel evaluated at the four distances 1+f, f, 1-f, 2-f
+// (f = p - floor p) needs one square root: with q = sqrt(1 + 4f - 4f^2)
+// the weights are (3 - 2f - q)/8, (3 - 2f + q)/8, (1 + 2f + q)/8, (1 + 2f - q)/8.
+template <int KW>
+__device__ __forceinline__ void weights1d(float f, float *w) {
+    if (KW == 4) {
+        const float q = sqrtf(1.0f + 4.0f * f - 4.0f * f * f);
+        w[0] = (3.0f - 2.0f * f - q) * 0.125f;
+        w[1] = (3.0f - 2.0f * f + q) * 0.125f;
+        w[2] = (1.0f + 2.0f * f + q) * 0.125f;
+        w[3] = (1.0f + 2.0f * f - q) * 0.125f;
+    } else {
+        w[0] = 1.0f - f;
+        w[1] = f;
+    }
+}
+
+// stencil origin (wrapped) and fractional offset along one axis
+__device__ __forceinline__ int stencil_axis(double p, int n, int kw, float &frac) {
+    const double fl = floor(p);
+    frac = (float)(p - fl);
+    long long o = (long long)fl - (kw / 2 - 1);
+    o %= n;
+    if (o < 0) o += n;
+    return (int)o;
+}
+
+template <int KW, bool DET>
+__global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
+    __shared__ float4 sf[GS_NODES];
+    const int j0 = blockIdx.x * GS_NODES;
+    const int nloc = min(GS_NODES, c.n_nodes - j0);
+    if ((int)threadIdx.x < nloc) {
+        const int j = j0 + threadIdx.x;
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int e = c.csr_ptr[j]; e < c.csr_ptr[j + 1]; ++e) {
+            const float4 v = c.tri_force[c.csr_ent[e]];
+            fx += v.x;
+            fy += v.y;
+            fz += v.z;
+        }
+        const double *bd = c.bead_data + 8 * c.node_bead[j];
+        fx += (float)bd[4];
+        fy += (float)bd[5];
+        fz += (float)bd[6];
+        const float4 f = make_float4(fx, fy, fz, 0.f);
+        sf[threadIdx.x] = f;
+        c.node_force[j] = f;
+    }
+    __syncthreads();
+    constexpr int ROWS = KW * KW;
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    for (int task = threadIdx.x; task < nloc * ROWS; task += GS_TPB) {
+        const int ln = task / ROWS, row = task % ROWS;
+        const int j = j0 + ln;
+        float fxr, fyr, fzr;
+        const int ox = stencil_axis(c.rx[j], nx, KW, fxr);
+        const int oy = stencil_axis(c.ry[j], ny, KW, fyr);
+        const int oz = stencil_axis(c.rz[j], nz, KW, fzr);
+        float wx[KW], wy[KW], wz[KW];
+        weights1d<KW>(fxr, wx);
+        weights1d<KW>(fyr, wy);
+        weights1d<KW>(fzr, wz);
+        const int dy = row % KW, dz = row / KW;
+        const int yy = (oy + dy) % ny, zz = (oz + dz) % nz;  // boxes may be narrower than the stencil
+        const float wyz = wy[dy] * wz[dz];
+        const float4 f = sf[ln];
+        const unsigned rowbase = (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz);
+        int last_tile = -1;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            const int xx = (ox + k) % nx;
+            const unsigned cell = rowbase + (unsigned)xx;
+            const float w = wx[k] * wyz;
+            if (DET) {
+                atomicAdd(&c.Fdet[cell], (unsigned long long)llrint((double)(w * f.x) * FIX_SCALE));
+                atomicAdd(&c.Fdet[c.Npad + cell], (unsigned long long)llrint((double)(w * f.y) * FIX_SCALE));
+                atomicAdd(&c.Fdet[2 * c.Npad + cell], (unsigned long long)llrint((double)(w * f.z) * FIX_SCALE));
+            } else {
+                atomicAdd(&c.F[cell], make_float4(w * f.x, w * f.y, w * f.z, 0.f));
+            }
+            const int tile = (int)(cell / LB_TPB);
+            if (tile != last_tile) {
+                c.flags[tile] = 1;
+                last_tile = tile;
+            }
+        }
+    }
+}
+
+template <int KW, bool ADVECT>
+__global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *vel_out) {
+    constexpr int ROWS = KW * KW;
+    const int gt = blockIdx.x * INT_TPB + threadIdx.x;
+    const int j = gt / ROWS, row = gt % ROWS;
+    const bool active = j < c.n_nodes;
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+    double px = 0.0, py = 0.0, pz = 0.0;
+    if (active) {
+        px = c.rx[j];
+        py = c.ry[j];
+        pz = c.rz[j];
+        float fxr, fyr, fzr;
+        const int ox = stencil_axis(px, c.nx, KW, fxr);
+        const int oy = stencil_axis(py, c.ny, KW, fyr);
+        const int oz = stencil_axis(pz, c.nz, KW, fzr);
+        float wx[KW], wy[KW], wz[KW];
+        weights1d<KW>(fxr, wx);
+        weights1d<KW>(fyr, wy);
+        weights1d<KW>(fzr, wz);
+        const int dy = row % KW, dz = row / KW;
+        const int yy = (oy + dy) % c.ny, zz = (oz + dz) % c.nz;
+        const float wyz = wy[dy] * wz[dz];
+        const unsigned rowbase = (unsigned)c.nx * ((unsigned)yy + (unsigned)c.ny * (unsigned)zz);
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            const int xx = (ox + k) % c.nx;
+            const float4 u = c.U[rowbase + (unsigned)xx];
+            const float w = wx[k] * wyz;
+            vx += w * u.x;
+            vy += w * u.y;
+            vz += w * u.z;
+        }
+    }
+    // fixed-order reduction over the ROWS lanes of this node (aligned groups within a warp)
+#pragma unroll
+    for (int o = ROWS / 2; o > 0; o >>= 1) {
+        vx += __shfl_xor_sync(0xffffffffu, vx, o);
+        vy += __shfl_xor_sync(0xffffffffu, vy, o);
+        vz += __shfl_xor_sync(0xffffffffu, vz, o);
+    }
+    if (active && row == 0) {
+        c.node_vel[j] = make_float4(vx, vy, vz, 0.f);
+        if (vel_out) {
+            vel_out[3 * j + 0] = vx;
+            vel_out[3 * j + 1] = vy;
+            vel_out[3 * j + 2] = vz;
+        }
+        if (ADVECT) {
+            const double nxp = px + (double)vx, nyp = py + (double)vy, nzp = pz + (double)vz;
+            c.rx[j] = nxp;
+            c.ry[j] = nyp;
+            c.rz[j] = nzp;
+            const float sp2 = vx * vx + vy * vy + vz * vz;
+            if (!isfinite(sp2) || !isfinite(nxp + nyp + nzp)) atomicOr(&c.ctl->err, ERR_NONFINITE);
+            else if (sp2 > 0.01f) atomicOr(&c.ctl->err, ERR_UNSTABLE);
+        }
+    }
+}
+
+// Observables: one block per swimmer, FP64 reductions in a fixed order.
+__global__ void __launch_bounds__(PREP_TPB) k_swimmer_state(const DevCtx c, int init) {
+    __shared__ double sm[96];
+    const int s = blockIdx.x;
+    const SwimDev sw = c.swims[s];
+    lbib_swimmer_state *st = c.sw_state + s;
+    double xcm[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < 3; ++q) {
+        const BeadDev bd = c.beads[sw.bead[q]];
+        const int j0 = bd.node_start, j1 = bd.node_start + bd.node_count;
+        const double inv = 1.0 / bd.node_count;
+        double a = 0.0, b = 0.0, cc = 0.0;
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            a += c.rx[j];
+            b += c.ry[j];
+            cc += c.rz[j];
+        }
+        block_sum3(a, b, cc, sm);
+        const double R0 = a * inv, R1 = b * inv, R2 = cc * inv;
+        double va = 0.0, vb = 0.0, vc = 0.0;
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            const float4 v = c.node_vel[j];
+            va += v.x;
+            vb += v.y;
+            vc += v.z;
+        }
+        block_sum3(va, vb, vc, sm);
+        double fa = 0.0, fb = 0.0, fc = 0.0, ta = 0.0, tb = 0.0, tc = 0.0;
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            const float4 f = c.node_force[j];
+            const double dx = c.rx[j] - R0, dy = c.ry[j] - R1, dz = c.rz[j] - R2;
+            fa += f.x;
+            fb += f.y;
+            fc += f.z;
+            ta += dy * f.z - dz * f.y;
+            tb += dz * f.x - dx * f.z;
+            tc += dx * f.y - dy * f.x;
+        }
+        block_sum3(fa, fb, fc, sm);
+        block_sum3(ta, tb, tc, sm);
+        if (threadIdx.x == 0) {
+            st->R[q][0] = R0;
+            st->R[q][1] = R1;
+            st->R[q][2] = R2;
+            st->V[q][0] = va * inv;
+            st->V[q][1] = vb * inv;
+            st->V[q][2] = vc * inv;
+            st->F[q][0] = fa;
+            st->F[q][1] = fb;
+            st->F[q][2] = fc;
+            st->T[q][0] = ta;
+            st->T[q][1] = tb;
+            st->T[q][2] = tc;
+        }
+        xcm[0] += R0;
+        xcm[1] += R1;
+        xcm[2] += R2;
+    }
+    if (threadIdx.x == 0) {
+        st->step = c.ctl->step;
+        for (int a = 0; a < 3; ++a) {
+            const double x = xcm[a] / 3.0;
+            st->x_cm[a] = x;
+            if (init) c.xcm0[3 * s + a] = x;
+            st->disp[a] = x - c.xcm0[3 * s + a];
+        }
+    }
+}
+
+cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s) {
+    const int blocks = c.n_swimmers + (c.n_tris + PREP_TPB - 1) / PREP_TPB;
+    if (blocks == 0) return cudaSuccess;
+    k_ib_prepare<<<blocks, PREP_TPB, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s) {
+    if (c.n_nodes == 0) return cudaSuccess;
+    const int blocks = (c.n_nodes + GS_NODES - 1) / GS_NODES;
+    if (kernel == LBIB_LINEAR2) {
+        if (c.deterministic) k_ib_gather_spread<2, true><<<blocks, GS_TPB, 0, s>>>(c);
+        else k_ib_gather_spread<2, false><<<blocks, GS_TPB, 0, s>>>(c);
+    } else {
+        if (c.deterministic) k_ib_gather_spread<4, true><<<blocks, GS_TPB, 0, s>>>(c);
+        else k_ib_gather_spread<4, false><<<blocks, GS_TPB, 0, s>>>(c);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, cudaStream_t s) {
+    if (c.n_nodes == 0) return cudaSuccess;
+    const int rows = kernel == LBIB_LINEAR2 ? 4 : 16;
+    const long long threads = (long long)c.n_nodes * rows;
+    const int blocks = (int)((threads + INT_TPB - 1) / INT_TPB);
+    if (kernel == LBIB_LINEAR2) {
+        if (advect) k_ib_interp<2, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
+        else k_ib_interp<2, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
+    } else {
+        if (advect) k_ib_interp<4, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
+        else k_ib_interp<4, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s) {
+    if (c.n_swimmers == 0) return cudaSuccess;
+    k_swimmer_state<<<c.n_swimmers, PREP_TPB, 0, s>>>(c, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

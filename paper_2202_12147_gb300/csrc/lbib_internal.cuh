@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA translation units of liblbib.
+// Device data layouts, the D3Q19 lattice of the CUDA path, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "lbib.h"
+
+namespace lbib {
+
+// ---------------------------------------------------------------- lattice
+// D3Q19 (Sec. 2.1).  Opposite directions are adjacent: (1,2), (3,4), ...
+// 0 rest; 1,2 +-x; 3,4 +-y; 5,6 +-z; 7,8 (1,1,0)/(-1,-1,0); 9,10 (1,-1,0)/(-1,1,0);
+// 11,12 (1,0,1)/(-1,0,-1); 13,14 (1,0,-1)/(-1,0,1); 15,16 (0,1,1)/(0,-1,-1);
+// 17,18 (0,1,-1)/(0,-1,1).
+constexpr int Q = 19;
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// weights 1/3, 1/18, 1/36 (Sec. 2.1)
+__host__ __device__ constexpr float wgt(int i) { return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
+__host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// cells per LB thread block; one tile flag per block of cells
+constexpr int LB_TPB = 256;
+// threads per node in spreading / interpolation (one per (y, z) stencil row)
+constexpr int ROWS4 = 16;
+
+// device error bits, latched in Control::err
+constexpr int ERR_NONFINITE = 1;
+constexpr int ERR_UNSTABLE = 2;
+constexpr int ERR_TIMEOUT = 4;
+
+struct Control {
+    long long step;  // time steps completed; t of the next step
+    int err;
+    int pad;
+};
+
+// Per-triangle reference data of the linear FEM membrane.
+struct TriDev {
+    double G[3];     // rest metric G = D^T D: G00, G01, G11
+    float Gi[3];     // G^{-1}: Gi00, Gi01, Gi11
+    float K;         // A0 * Gs / det G
+    float inv_detG;  // 1 / det G
+    int v[3];        // node ids
+    int pad[2];
+};
+static_assert(sizeof(TriDev) == 64, "TriDev layout");
+
+struct BeadDev {
+    int node_start, node_count;
+    int swimmer, slot;  // owning swimmer and position 0..2 along its axis
+};
+
+struct SwimDev {
+    int bead[3];
+    int balance;
+    double k, L, period;
+    double amp[3], phase[3];
+};
+
+// Everything a kernel needs, by value.
+struct DevCtx {
+    int nx, ny, nz;
+    long long N;      // cells
+    long long Npad;   // population plane stride
+    int n_tiles;
+    float tau, omega, rho0;
+    float g[3];
+    int has_g;
+    float st_scale, st_inv_scale;  // F16/BF16 scaling
+    int n_nodes, n_tris, n_beads, n_swimmers;
+    int deterministic;
+    // buffers
+    void *pops;
+    float4 *F;                 // force density per cell (float atomics)
+    unsigned long long *Fdet;  // 3 x Npad fixed-point force (deterministic mode)
+    float4 *U;                 // velocity (x, y, z, rho) per cell
+    unsigned char *flags;      // one byte per LB tile
+    double *rx, *ry, *rz;      // node positions (SoA)
+    float4 *node_force;        // f^tot per node
+    float4 *node_vel;          // interpolated velocity per node
+    float4 *tri_force;         // 3 corner forces per triangle
+    const TriDev *tris;
+    const int *csr_ptr;        // node -> incident (triangle*3 + corner)
+    const int *csr_ent;
+    const int *node_bead;
+    const BeadDev *beads;
+    const SwimDev *swims;
+    double *bead_data;         // per bead, 8 doubles: centre R[0..2], external force / N_v [4..6]
+    Control *ctl;
+    lbib_swimmer_state *sw_state;
+    double *xcm0;              // x_cm at init, 3 per swimmer
+};
+
+// fixed-point scale of deterministic spreading: 2^48 units per force unit
+// (resolution 3.6e-15, range +-32768 per cell)
+constexpr double FIX_SCALE = 281474976710656.0;
+constexpr double FIX_INV = 1.0 / 281474976710656.0;
+
+// ---------------------------------------------------------------- launchers
+// LB (lb_kernels.cu)
+cudaError_t launch_lb_step(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
+cudaError_t launch_lb_macros(const DevCtx &c, int storage, bool odd, float *rho, float *u, cudaStream_t s);
+// IB (ib_kernels.cu)
+cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s);
+cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s);
+cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, cudaStream_t s);
+cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s);
+
+}  // namespace lbib

@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every function the header
+declares; argument errors are reported before any launch.  CPU only (no
+call here touches a device)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbib.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith("LBIB")))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("lb_init", "lb_step", "ib_interpolate", "ib_spread", "swimmer_state", "lb_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2202_12147_gb300 import _lib
+    L = _lib.load()
+    for n in _declared():
+        assert hasattr(L, n), n
+    assert set(_lib.EXPORTS) == set(_declared())
+
+
+def test_lattice_and_sizes_without_gpu():
+    from paper_2202_12147_gb300 import lattice, required_sizes
+    from workloads import assemble, single_swimmer_48
+    c, w = lattice()
+    assert w.sum() == pytest.approx(1.0)
+    for i in range(1, 19, 2):  # opposite directions adjacent
+        assert (c[i] == -c[i + 1]).all()
+    s0 = required_sizes((48, 48, 48))
+    s1 = required_sizes((48, 48, 48), assemble(single_swimmer_48()))
+    assert s0[0] == 19 * 48 ** 3 * 4
+    assert s1[2] > s0[2]
+    s16 = required_sizes((48, 48, 48), storage="f16")
+    assert s16[0] == 19 * 48 ** 3 * 2
+    assert all(v % 256 == 0 for v in s1)
+
+
+@pytest.mark.parametrize("bad", [dict(tau=0.5), dict(rho0=0.0), dict(storage="f8"), dict(dims=(0, 4, 4))])
+def test_invalid_arguments_rejected(bad):
+    from paper_2202_12147_gb300 import _lib, required_sizes
+    kw = dict(tau=1.0, rho0=1.0, storage="f32")
+    dims = bad.pop("dims", (8, 8, 8))
+    kw.update(bad)
+    with pytest.raises((_lib.LbibError, KeyError)):
+        required_sizes(dims, **kw)
+
+
+def test_structure_validation():
+    import numpy as np
+    from paper_2202_12147_gb300 import _lib, required_sizes
+    from workloads import assemble, single_swimmer_48
+    a = assemble(single_swimmer_48())
+    a["tris"] = a["tris"].copy()
+    a["tris"][0, 0] = 200  # node of another bead
+    with pytest.raises(_lib.LbibError, match="outside its bead"):
+        required_sizes((48, 48, 48), a)
+    a = assemble(single_swimmer_48())
+    a["nodes"] = a["nodes"].copy()
+    a["nodes"][3, 1] = np.nan
+    with pytest.raises(_lib.LbibError, match="non-finite"):
+        required_sizes((48, 48, 48), a)

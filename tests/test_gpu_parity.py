@@ -1,0 +1,187 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element
+by element on seeded inputs.
+
+Tolerances.  The CUDA path stores FP32 deviations f_i - w_i rho0 and
+collides in FP32; each step rounds every deviation at ~6e-8 relative, so
+deviation fields agree to ~1e-6 relative after tens of steps; the velocity
+field criterion is a relative L2 error <= 1e-5 after the stated step count.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import gpu_f_to_oracle, gpu_sim, lattice_perm, oracle_f_to_gpu, rel_l2
+from workloads import BoxSpec, SwimmerSpec, assemble, fluid_box, random_populations, single_swimmer_48, perturbed_nodes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def perm(gpu_lib):
+    return lattice_perm()
+
+
+def _dev(f, w, rho0=1.0):
+    return f - w[None, :] * rho0
+
+
+@pytest.mark.parametrize("steps", [1, 2, 5])
+@pytest.mark.parametrize("forcing", ["guo", "shan_chen"])
+def test_fluid_random_state_ragged_box(perm, steps, forcing):
+    """Random populations, uniform force, a box whose cell count (2717) leaves
+    a ragged last tile; both AA parities."""
+    box = fluid_box((19, 13, 11), tau=0.8, g=(2e-6, -1e-6, 5e-7), forcing=forcing)
+    c, w = oracle.lattice()
+    f0 = random_populations(box.n_cells, w, seed=steps, rho_amp=1e-3, u_amp=1e-3)
+    sim = gpu_sim(box)
+    sim.set_populations(oracle_f_to_gpu(f0, perm))
+    sim.lb_step(steps)
+    fg = gpu_f_to_oracle(sim.get_populations(), perm)
+    fo = f0
+    for _ in range(steps):
+        fo, _, _ = oracle.lb_step(fo, box.dims, box.tau, g=box.g, forcing=oracle.SHAN_CHEN if forcing == "shan_chen" else oracle.GUO)
+    assert rel_l2(_dev(fg, w), _dev(fo, w)) < 1e-6
+    assert np.abs(fg - fo).max() < 1e-9
+    rho, u = sim.lb_get_macros()
+    ro, uo = oracle.macros(fo)
+    assert rel_l2(u.cpu().numpy(), uo) < 1e-5
+    np.testing.assert_allclose(rho.cpu().numpy(), ro, rtol=1e-6)
+    sim.close()
+
+
+def test_fluid_many_steps_graph_path(perm):
+    """37 steps: graph replays (16 steps each) plus single-step tails."""
+    box = fluid_box((32, 24, 20), tau=0.7)
+    c, w = oracle.lattice()
+    f0 = random_populations(box.n_cells, w, seed=9, rho_amp=1e-3, u_amp=1e-3)
+    sim = gpu_sim(box)
+    sim.set_populations(oracle_f_to_gpu(f0, perm))
+    sim.lb_step(3)
+    sim.lb_step(34)
+    fg = gpu_f_to_oracle(sim.get_populations(), perm)
+    fo = f0
+    for _ in range(37):
+        fo, _, _ = oracle.lb_step(fo, box.dims, box.tau)
+    assert rel_l2(_dev(fg, w), _dev(fo, w)) < 2e-6
+    # mass and momentum conserved on the GPU itself
+    assert fg.sum() == pytest.approx(f0.sum(), rel=1e-7)
+    np.testing.assert_allclose((fg @ c).sum(0), (f0 @ c).sum(0), atol=1e-6)
+    sim.close()
+
+
+def test_uniform_force_closed_form_gpu(perm):
+    """Resting fluid under uniform g: after n steps every cell has momentum n g."""
+    g = np.array([1e-5, -2e-6, 3e-6])
+    box = fluid_box((16, 8, 8), tau=0.9, g=g)
+    sim = gpu_sim(box)
+    sim.lb_step(20)
+    rho, u = sim.lb_get_macros()
+    np.testing.assert_allclose(u.cpu().numpy(), np.tile(20 * g, (box.n_cells, 1)), rtol=2e-5, atol=1e-12)
+    sim.close()
+
+
+def _perturbed_swimmer_box(kernel="peskin4", dims=(40, 36, 34), center=(20.3, 18.6, 17.2)):
+    s = SwimmerSpec(center=center, radius=4.0, subdiv=2, spacing=12.0).with_drive(1e-3, 1e-3, math.pi / 2)
+    return BoxSpec(dims=dims, swimmers=(s,), kernel=kernel)
+
+
+@pytest.mark.parametrize("kernel", ["peskin4", "linear2"])
+def test_node_forces_and_spread(perm, kernel):
+    box = _perturbed_swimmer_box(kernel)
+    asm = assemble(box)
+    sim = gpu_sim(box, asm)
+    r = perturbed_nodes(asm["nodes"], seed=1, amp=0.05)
+    sim.set_nodes(r)
+    sim.ib_spread()
+    fg = sim.get_node_forces().astype(np.float64)
+    osim = oracle.OracleSim(box, asm)
+    osim.r = r.copy()
+    fo = osim.node_forces()
+    assert np.abs(fg - fo).max() < 1e-5 * np.abs(fo).max()
+    Fg = sim.get_force_field().astype(np.float64)
+    Fo = oracle.spread(r, fg, box.dims, oracle.LINEAR2 if kernel == "linear2" else oracle.PESKIN4)
+    assert np.abs(Fg - Fo).max() < 1e-6 * np.abs(Fo).max()
+    # FP32 atomics round each of ~25 contributions per cell; the sums agree to rounding
+    np.testing.assert_allclose(Fg.sum(0), fg.sum(0), atol=1e-6 * np.abs(fg).sum())
+    sim.close()
+
+
+@pytest.mark.parametrize("kernel", ["peskin4", "linear2"])
+def test_interpolate(perm, kernel):
+    import torch
+    box = _perturbed_swimmer_box(kernel, center=(1.4, 18.6, 33.5))  # straddles the periodic seams
+    asm = assemble(box)
+    sim = gpu_sim(box, asm)
+    rng = np.random.default_rng(3)
+    u = rng.normal(size=(box.n_cells, 3)).astype(np.float32)
+    sim.set_velocity(u)
+    v = sim.ib_interpolate().cpu().numpy()
+    vo = oracle.interpolate(asm["nodes"], u.astype(np.float64), box.dims,
+                            oracle.LINEAR2 if kernel == "linear2" else oracle.PESKIN4)
+    assert np.abs(v - vo).max() < 2e-6 * np.abs(vo).max()
+    sim.close()
+
+
+def test_deterministic_spread_is_bitwise_reproducible(perm):
+    box = _perturbed_swimmer_box()
+    asm = assemble(box)
+    r = perturbed_nodes(asm["nodes"], seed=2, amp=0.05)
+    outs = []
+    for _ in range(2):
+        sim = gpu_sim(box, asm, deterministic=True)
+        sim.set_nodes(r)
+        sim.ib_spread()
+        outs.append(sim.get_force_field())
+        sim.close()
+    assert np.array_equal(outs[0], outs[1])
+    sim = gpu_sim(box, asm)
+    sim.set_nodes(r)
+    sim.ib_spread()
+    Fa = sim.get_force_field()
+    assert np.abs(outs[0] - Fa).max() < 1e-6 * np.abs(Fa).max()
+    sim.close()
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_coupled_single_swimmer_48(perm, deterministic):
+    """The 48^3 single-swimmer workload (beads of radius 4 at subdivision 2,
+    k = 0.005, Gs = 0.01, drive 1e-3, period 500, phase pi/2), a full period
+    of 500 steps: velocity field within 1e-5 relative L2, swimmer
+    displacement within 1%."""
+    box = single_swimmer_48()
+    asm = assemble(box)
+    sim = gpu_sim(box, asm, deterministic=deterministic)
+    sim.lb_step(500)
+    st = sim.swimmer_state(0)
+    osim = oracle.OracleSim(box, asm).step(500)
+    fg = gpu_f_to_oracle(sim.get_populations(), perm)
+    _, ug = oracle.macros(fg)
+    _, uo = oracle.macros(osim.f)
+    err = rel_l2(ug, uo)
+    assert err < 1e-5, err
+    rg = sim.get_nodes()
+    assert np.abs(rg - osim.r).max() < 1e-6
+    xo = osim.swimmer_centres()[0]
+    dx_o = xo - asm["nodes"].reshape(3, -1, 3).mean(axis=(0, 1))
+    assert st["step"] == 500
+    assert abs(st["disp"][0] - dx_o[0]) < 0.01 * abs(dx_o[0]) + 1e-9
+    np.testing.assert_allclose(st["x_cm"], xo, atol=1e-6)
+    sim.close()
+
+
+def test_empty_structure_and_tiny_box(perm):
+    """No swimmers, a box smaller than one tile (5^3 = 125 cells)."""
+    box = fluid_box((5, 5, 5), tau=1.3)
+    c, w = oracle.lattice()
+    f0 = random_populations(box.n_cells, w, seed=4, rho_amp=1e-3, u_amp=1e-3)
+    sim = gpu_sim(box)
+    sim.set_populations(oracle_f_to_gpu(f0, perm))
+    sim.lb_step(7)
+    fo = f0
+    for _ in range(7):
+        fo, _, _ = oracle.lb_step(fo, box.dims, box.tau)
+    fg = gpu_f_to_oracle(sim.get_populations(), perm)
+    assert rel_l2(_dev(fg, w), _dev(fo, w)) < 1e-6
+    sim.close()
