@@ -34,14 +34,14 @@ constexpr int GRAPH_STEPS = 16;  // steps per captured graph (even: both AA pari
 
 struct Layout {
     long long N = 0, Npad = 0;
-    int n_tiles = 0;
+    int n_tiles = 0, tile_x = 0, tiles_x = 0;
     size_t esize = 4;
     size_t bytes[LBIB_NBUF] = {0, 0, 0};
     // fields
     size_t oF = 0, oFdet = 0, oU = 0, oFlags = 0;
     // aux
     size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
-           obead = 0, oswim = 0, obd = 0, octl = 0, osws = 0, oxcm = 0;
+           obead = 0, oswim = 0, obd = 0, obe = 0, obp = 0, octl = 0, osws = 0, oxcm = 0;
 };
 
 bool valid_params(const lb_params *p, std::string &why) {
@@ -110,7 +110,9 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     Layout L;
     L.N = (long long)p->nx * p->ny * p->nz;
     L.Npad = (L.N + 63) / 64 * 64;
-    L.n_tiles = (int)((L.N + LB_TPB - 1) / LB_TPB);
+    L.tile_x = p->nx <= LB_TPB ? p->nx : LB_TPB;
+    L.tiles_x = (p->nx + L.tile_x - 1) / L.tile_x;
+    L.n_tiles = L.tiles_x * p->ny * p->nz;
     L.esize = p->storage == LBIB_F32 ? 4 : 2;
     L.bytes[0] = up((size_t)Q * L.Npad * L.esize);
     size_t o = 0;
@@ -140,7 +142,9 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     L.onb = o; o += up((size_t)M * 4 + 4);
     L.obead = o; o += up((size_t)B * sizeof(BeadDev) + 16);
     L.oswim = o; o += up((size_t)S * sizeof(SwimDev) + 16);
-    L.obd = o; o += up((size_t)B * 64 + 64);
+    L.obd = o; o += up((size_t)B * 32 + 32);
+    L.obe = o; o += up((size_t)B * 16 + 16);
+    L.obp = o; o += up((size_t)B * 4 + 4);
     L.octl = o; o += up(sizeof(Control));
     L.osws = o; o += up((size_t)S * sizeof(lbib_swimmer_state) + 16);
     L.oxcm = o; o += up((size_t)S * 24 + 24);
@@ -274,6 +278,8 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         const lbib_bead &bd = s->beads[bi];
         beads[bi].node_start = bd.node_start;
         beads[bi].node_count = bd.node_count;
+        beads[bi].inv_count = (float)(1.0 / bd.node_count);
+        beads[bi].pad[0] = beads[bi].pad[1] = beads[bi].pad[2] = 0;
         for (int j = bd.node_start; j < bd.node_start + bd.node_count; ++j) nbead[j] = bi;
         for (int t = bd.tri_start; t < bd.tri_start + bd.tri_count; ++t) {
             const int *v = s->tris + 3 * t;
@@ -313,15 +319,17 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         SwimDev &d = swims[k];
         for (int q = 0; q < 3; ++q) {
             d.bead[q] = w.bead[q];
-            d.amp[q] = w.amp[q];
-            d.phase[q] = w.phase[q];
+            d.amp[q] = (float)w.amp[q];
+            d.phase_turns[q] = w.phase[q] / (2.0 * 3.14159265358979323846);
             beads[w.bead[q]].swimmer = k;
             beads[w.bead[q]].slot = q;
         }
         d.balance = w.balance;
         d.k = w.k_spring;
         d.L = w.L_spring;
-        d.period = w.period;
+        d.L2 = w.L_spring * w.L_spring;
+        d.inv_period = 1.0 / w.period;
+        d.pad = 0;
     }
 
     lbib_ctx *c = new lbib_ctx();
@@ -338,6 +346,8 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.N = L.N;
     d.Npad = L.Npad;
     d.n_tiles = L.n_tiles;
+    d.tile_x = L.tile_x;
+    d.tiles_x = L.tiles_x;
     d.tau = (float)p->tau;
     d.omega = (float)(1.0 / p->tau);
     d.rho0 = (float)p->rho0;
@@ -368,7 +378,9 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.node_bead = (const int *)(A + L.onb);
     d.beads = (const BeadDev *)(A + L.obead);
     d.swims = (const SwimDev *)(A + L.oswim);
-    d.bead_data = (double *)(A + L.obd);
+    d.bead_R = (double *)(A + L.obd);
+    d.bead_ext = (float4 *)(A + L.obe);
+    d.bead_pending = (int *)(A + L.obp);
     d.ctl = (Control *)(A + L.octl);
     d.sw_state = (lbib_swimmer_state *)(A + L.osws);
     d.xcm0 = (double *)(A + L.oxcm);
@@ -399,7 +411,8 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
               h2d((void *)d.csr_ent, cent.data(), 3 * (size_t)T * 4) && h2d((void *)d.node_bead, nbead.data(), M * 4) &&
               h2d((void *)d.beads, beads.data(), B * sizeof(BeadDev)) && h2d((void *)d.swims, swims.data(), S * sizeof(SwimDev));
     if (!ok) return bail(fail(LBIB_ECUDA, "uploading mesh tables failed"));
-    if (launch_swimmer_state(d, true, u) != cudaSuccess) return bail(fail(LBIB_ECUDA, "swimmer_state init launch failed"));
+    if (launch_bead_init(d, u) != cudaSuccess || launch_swimmer_state(d, true, u) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "bead initialisation launch failed"));
     if (cudaStreamSynchronize(u) != cudaSuccess) return bail(fail(LBIB_ECUDA, "init synchronisation failed"));
 
     // capture GRAPH_STEPS coupled steps (alternating AA parity) into one graph
@@ -555,6 +568,7 @@ int lb_set_nodes(lbib_ctx *c, const double *h) {
     CU(cudaMemcpyAsync(c->d.rx, x.data(), M * 8, cudaMemcpyHostToDevice, c->user));
     CU(cudaMemcpyAsync(c->d.ry, y.data(), M * 8, cudaMemcpyHostToDevice, c->user));
     CU(cudaMemcpyAsync(c->d.rz, z.data(), M * 8, cudaMemcpyHostToDevice, c->user));
+    CU(launch_bead_init(c->d, c->user));
     CU(cudaStreamSynchronize(c->user));
     return LBIB_OK;
 }

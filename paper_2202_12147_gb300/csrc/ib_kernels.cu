@@ -1,23 +1,32 @@
 // Immersed-boundary side of the coupled step: bead reductions, drive and
 // springs, the linear-FEM membrane, spreading and interpolation.
 //
-//   k_ib_prepare       blocks [0, n_swimmers): bead centres R_b (FP64 block
-//                      reduction in a fixed order, Fig. 1 caption), drive
-//                      f^d(t) and springs f^s(R) (Sec. 2.2), stored as the
-//                      per-node share (f^d + f^s)/N_v;
+//   k_ib_prepare       blocks [0, n_swimmers): bead centres, drive f^d(t)
+//                      and springs f^s(R) (Sec. 2.2), stored as the per-node
+//                      share (f^d + f^s)/N_v;
 //                      remaining blocks: one thread per triangle computes the
 //                      three corner forces -dW/dr of the neo-Hookean linear
 //                      FEM element (Sec. 2.2, virtual work).
 //   k_ib_gather_spread one thread per node sums its incident corner forces in
 //                      a fixed order plus the bead share (total nodal force,
-//                      Sec. 2.2), then KW^2 threads per node spread it over the
-//                      KW^3 stencil (Sec. 2.3, Eq. spreading) with vector float
-//                      atomics, or 64-bit fixed-point atomics (bitwise
-//                      reproducible), and mark the LB tiles they touch.
+//                      Sec. 2.2) and sets up its stencil; then KW^2 threads
+//                      per node spread it over the KW^3 stencil (Sec. 2.3,
+//                      Eq. spreading) with vector float atomics, or 64-bit
+//                      fixed-point atomics (bitwise reproducible), marking
+//                      the LB tiles they touch.
 //   k_ib_interp        KW^2 threads per node gather u over the stencil
 //                      (Sec. 2.3, Eq. interpolation), reduce with shuffles in
 //                      a fixed order and move the node r += rdot in FP64
 //                      (front tracking, Sec. 2.3).
+//
+// FP64 on this GPU issues at a small fraction of the FP32 rate, so it is kept
+// to what needs it: node positions and their update, the bead centres, the
+// metric difference of the membrane element, and the argument of the drive.
+// The bead centre R_b = mean of the bead's nodes (Fig. 1 caption) is kept up
+// to date incrementally: after an advection by node velocities v_j,
+// R_b += mean_j v_j (the mean is linear), folded in by the next step's
+// swimmer block; k_bead_init recomputes it from the positions whenever they
+// are set from outside.
 //
 // Membrane element.  With rest edge metric G = D^T D, current metric
 // g = d^T d = G + 2E and J^2 = det g / det G, the neo-Hookean energy
@@ -32,11 +41,13 @@ namespace lbib {
 
 constexpr int PREP_TPB = 128;
 constexpr int GS_TPB = 128;
-constexpr int GS_NODES = 32;   // nodes per gather/spread block
+constexpr int GS_NODES = 32;  // nodes per gather/spread block
 constexpr int INT_TPB = 128;
 
-// deterministic block reduction of 3 doubles (fixed shuffle tree, then warps in order)
-__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double *sm /* 3*32 */) {
+// deterministic block reductions (fixed shuffle tree, then warps in order)
+template <typename T>
+__device__ __forceinline__ void block_sum3(T &a, T &b, T &c, T *sm /* 3*32 */) {
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -50,7 +61,7 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
         sm[64 + w] = c;
     }
     __syncthreads();
-    a = b = c = 0.0;
+    a = b = c = T(0);
     for (int k = 0; k < nw; ++k) {
         a += sm[k];
         b += sm[32 + k];
@@ -59,58 +70,71 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
     __syncthreads();
 }
 
-__device__ void swimmer_forces(const DevCtx &c, int s, double *sm) {
-    const SwimDev sw = c.swims[s];
+// Swimmer block: fold the last advection into the bead centres, then the
+// drive (Sec. 2.2, driving-force equation) and springs (Sec. 2.2).
+__device__ void swimmer_forces(const DevCtx &c, int s) {
+    __shared__ float smf[96];
     __shared__ double sR[3][3];
+    const SwimDev sw = c.swims[s];
     for (int q = 0; q < 3; ++q) {
-        const BeadDev bd = c.beads[sw.bead[q]];
-        double a = 0.0, b = 0.0, cc = 0.0;
-        for (int j = bd.node_start + threadIdx.x; j < bd.node_start + bd.node_count; j += blockDim.x) {
-            a += c.rx[j];
-            b += c.ry[j];
-            cc += c.rz[j];
-        }
-        block_sum3(a, b, cc, sm);
-        if (threadIdx.x == 0) {
-            const double inv = 1.0 / bd.node_count;
-            sR[q][0] = a * inv;
-            sR[q][1] = b * inv;
-            sR[q][2] = cc * inv;
+        const int b = sw.bead[q];
+        const BeadDev bd = c.beads[b];
+        if (c.bead_pending[b]) {  // uniform across the block
+            float a = 0.f, bb = 0.f, cc = 0.f;
+            for (int j = bd.node_start + threadIdx.x; j < bd.node_start + bd.node_count; j += blockDim.x) {
+                const float4 v = c.node_vel[j];
+                a += v.x;
+                bb += v.y;
+                cc += v.z;
+            }
+            block_sum3(a, bb, cc, smf);
+            if (threadIdx.x == 0) {
+                double *R = c.bead_R + 4 * b;
+                R[0] += (double)(a * bd.inv_count);
+                R[1] += (double)(bb * bd.inv_count);
+                R[2] += (double)(cc * bd.inv_count);
+            }
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // drive along x (Sec. 2.2, driving-force equation); t mod T taken exactly
-        const double om = 2.0 * 3.14159265358979323846 / sw.period;
-        const double tm = fmod((double)c.ctl->step, sw.period);
-        double fd[3];
-        fd[0] = sw.amp[0] * sin(om * tm + sw.phase[0]);
-        fd[2] = sw.amp[2] * sin(om * tm + sw.phase[2]);
-        fd[1] = sw.balance ? -fd[0] - fd[2] : sw.amp[1] * sin(om * tm + sw.phase[1]);
-        // springs between beads 0-1 and 2-1 (Sec. 2.2)
-        double fs[3][3];
-        for (int side = 0; side < 2; ++side) {
-            const int q = side ? 2 : 0;
-            double d[3], n2 = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                d[a] = sR[q][a] - sR[1][a];
-                n2 += d[a] * d[a];
-            }
-            const double n = sqrt(n2);
-            const double m = -sw.k * (n - sw.L) / n;
-            for (int a = 0; a < 3; ++a) fs[q][a] = m * d[a];
+        for (int q = 0; q < 3; ++q) {
+            const double *R = c.bead_R + 4 * sw.bead[q];
+            sR[q][0] = R[0];
+            sR[q][1] = R[1];
+            sR[q][2] = R[2];
+            c.bead_pending[sw.bead[q]] = 0;
+        }
+        // drive: sin(2 pi (t / T + phase / 2 pi)), argument reduced in FP64
+        const double tt = (double)c.ctl->step * sw.inv_period;
+        float fd[3];
+        for (int q = 0; q < 3; q += 2) {
+            const double x = tt + sw.phase_turns[q];
+            fd[q] = sw.amp[q] * sinpif(2.0f * (float)(x - floor(x)));
+        }
+        if (sw.balance) {
+            fd[1] = -fd[0] - fd[2];
+        } else {
+            const double x = tt + sw.phase_turns[1];
+            fd[1] = sw.amp[1] * sinpif(2.0f * (float)(x - floor(x)));
+        }
+        // springs: |d| - L = (|d|^2 - L^2) / (|d| + L), the difference in FP64
+        float fs[3][3];
+        for (int q = 0; q < 3; q += 2) {
+            const double dx = sR[q][0] - sR[1][0], dy = sR[q][1] - sR[1][1], dz = sR[q][2] - sR[1][2];
+            const double n2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            const float nf = sqrtf((float)n2);
+            const float stretch = (float)(n2 - sw.L2) / (nf + (float)sw.L);
+            const float m = -(float)sw.k * stretch / nf;
+            fs[q][0] = m * (float)dx;
+            fs[q][1] = m * (float)dy;
+            fs[q][2] = m * (float)dz;
         }
         for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
         for (int q = 0; q < 3; ++q) {
             const int b = sw.bead[q];
-            const double inv = 1.0 / c.beads[b].node_count;
-            double *bdat = c.bead_data + 8 * b;
-            bdat[0] = sR[q][0];
-            bdat[1] = sR[q][1];
-            bdat[2] = sR[q][2];
-            bdat[4] = (fd[q] + fs[q][0]) * inv;
-            bdat[5] = fs[q][1] * inv;
-            bdat[6] = fs[q][2] * inv;
+            const float inv = c.beads[b].inv_count;
+            c.bead_ext[b] = make_float4((fd[q] + fs[q][0]) * inv, fs[q][1] * inv, fs[q][2] * inv, 0.f);
         }
     }
 }
@@ -145,13 +169,34 @@ __device__ void triangle_forces(const DevCtx &c, int t) {
 }
 
 __global__ void __launch_bounds__(PREP_TPB) k_ib_prepare(const DevCtx c) {
-    __shared__ double sm[96];
     if ((int)blockIdx.x < c.n_swimmers) {
-        swimmer_forces(c, blockIdx.x, sm);
+        swimmer_forces(c, blockIdx.x);
         return;
     }
     const int t = (blockIdx.x - c.n_swimmers) * PREP_TPB + threadIdx.x;
     if (t < c.n_tris) triangle_forces(c, t);
+}
+
+// Bead centres from the positions (FP64 mean, fixed order); clears the
+// pending advection marks.
+__global__ void __launch_bounds__(PREP_TPB) k_bead_init(const DevCtx c) {
+    __shared__ double sm[96];
+    const int b = blockIdx.x;
+    const BeadDev bd = c.beads[b];
+    double a = 0.0, bb = 0.0, cc = 0.0;
+    for (int j = bd.node_start + threadIdx.x; j < bd.node_start + bd.node_count; j += blockDim.x) {
+        a += c.rx[j];
+        bb += c.ry[j];
+        cc += c.rz[j];
+    }
+    block_sum3(a, bb, cc, sm);
+    if (threadIdx.x == 0) {
+        double *R = c.bead_R + 4 * b;
+        R[0] = a / bd.node_count;
+        R[1] = bb / bd.node_count;
+        R[2] = cc / bd.node_count;
+        c.bead_pending[b] = 0;
+    }
 }
 
 // 1-D kernel weights on the KW stencil cells floor(p) - KW/2 + 1 ... floor(p) + KW/2.
@@ -172,7 +217,7 @@ __device__ __forceinline__ void weights1d(float f, float *w) {
     }
 }
 
-// stencil origin (wrapped) and fractional offset along one axis
+// stencil origin (wrapped into [0, n)) and fractional offset along one axis
 __device__ __forceinline__ int stencil_axis(double p, int n, int kw, float &frac) {
     const double fl = floor(p);
     frac = (float)(p - fl);
@@ -185,6 +230,8 @@ __device__ __forceinline__ int stencil_axis(double p, int n, int kw, float &frac
 template <int KW, bool DET>
 __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
     __shared__ float4 sf[GS_NODES];
+    __shared__ int so[GS_NODES][3];
+    __shared__ float sw[GS_NODES][3][KW];
     const int j0 = blockIdx.x * GS_NODES;
     const int nloc = min(GS_NODES, c.n_nodes - j0);
     if ((int)threadIdx.x < nloc) {
@@ -196,39 +243,36 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
             fy += v.y;
             fz += v.z;
         }
-        const double *bd = c.bead_data + 8 * c.node_bead[j];
-        fx += (float)bd[4];
-        fy += (float)bd[5];
-        fz += (float)bd[6];
-        const float4 f = make_float4(fx, fy, fz, 0.f);
+        const float4 ext = c.bead_ext[c.node_bead[j]];
+        const float4 f = make_float4(fx + ext.x, fy + ext.y, fz + ext.z, 0.f);
         sf[threadIdx.x] = f;
         c.node_force[j] = f;
+        float fr;
+        so[threadIdx.x][0] = stencil_axis(c.rx[j], c.nx, KW, fr);
+        weights1d<KW>(fr, sw[threadIdx.x][0]);
+        so[threadIdx.x][1] = stencil_axis(c.ry[j], c.ny, KW, fr);
+        weights1d<KW>(fr, sw[threadIdx.x][1]);
+        so[threadIdx.x][2] = stencil_axis(c.rz[j], c.nz, KW, fr);
+        weights1d<KW>(fr, sw[threadIdx.x][2]);
     }
     __syncthreads();
     constexpr int ROWS = KW * KW;
     const int nx = c.nx, ny = c.ny, nz = c.nz;
     for (int task = threadIdx.x; task < nloc * ROWS; task += GS_TPB) {
         const int ln = task / ROWS, row = task % ROWS;
-        const int j = j0 + ln;
-        float fxr, fyr, fzr;
-        const int ox = stencil_axis(c.rx[j], nx, KW, fxr);
-        const int oy = stencil_axis(c.ry[j], ny, KW, fyr);
-        const int oz = stencil_axis(c.rz[j], nz, KW, fzr);
-        float wx[KW], wy[KW], wz[KW];
-        weights1d<KW>(fxr, wx);
-        weights1d<KW>(fyr, wy);
-        weights1d<KW>(fzr, wz);
         const int dy = row % KW, dz = row / KW;
-        const int yy = (oy + dy) % ny, zz = (oz + dz) % nz;  // boxes may be narrower than the stencil
-        const float wyz = wy[dy] * wz[dz];
+        const int ox = so[ln][0];
+        const int yy = (so[ln][1] + dy) % ny, zz = (so[ln][2] + dz) % nz;  // boxes may be narrower than the stencil
+        const float wyz = sw[ln][1][dy] * sw[ln][2][dz];
         const float4 f = sf[ln];
         const unsigned rowbase = (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz);
+        const int tile_row = c.tiles_x * (yy + ny * zz);
         int last_tile = -1;
 #pragma unroll
         for (int k = 0; k < KW; ++k) {
             const int xx = (ox + k) % nx;
             const unsigned cell = rowbase + (unsigned)xx;
-            const float w = wx[k] * wyz;
+            const float w = sw[ln][0][k] * wyz;
             if (DET) {
                 atomicAdd(&c.Fdet[cell], (unsigned long long)llrint((double)(w * f.x) * FIX_SCALE));
                 atomicAdd(&c.Fdet[c.Npad + cell], (unsigned long long)llrint((double)(w * f.y) * FIX_SCALE));
@@ -236,7 +280,7 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
             } else {
                 atomicAdd(&c.F[cell], make_float4(w * f.x, w * f.y, w * f.z, 0.f));
             }
-            const int tile = (int)(cell / LB_TPB);
+            const int tile = xx / c.tile_x + tile_row;
             if (tile != last_tile) {
                 c.flags[tile] = 1;
                 last_tile = tile;
@@ -251,16 +295,20 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
     const int gt = blockIdx.x * INT_TPB + threadIdx.x;
     const int j = gt / ROWS, row = gt % ROWS;
     const bool active = j < c.n_nodes;
+    const int lane = threadIdx.x & 31, gbase = lane & ~(ROWS - 1);
+    // lanes 0..2 of each node's group set up one axis each; the rest read them by shuffle
+    int o = 0;
+    float fr = 0.f;
+    if (active && row < 3) {
+        const double p = row == 0 ? c.rx[j] : (row == 1 ? c.ry[j] : c.rz[j]);
+        o = stencil_axis(p, row == 0 ? c.nx : (row == 1 ? c.ny : c.nz), KW, fr);
+    }
+    const int ox = __shfl_sync(0xffffffffu, o, gbase), oy = __shfl_sync(0xffffffffu, o, gbase + 1),
+              oz = __shfl_sync(0xffffffffu, o, gbase + 2);
+    const float fxr = __shfl_sync(0xffffffffu, fr, gbase), fyr = __shfl_sync(0xffffffffu, fr, gbase + 1),
+                fzr = __shfl_sync(0xffffffffu, fr, gbase + 2);
     float vx = 0.f, vy = 0.f, vz = 0.f;
-    double px = 0.0, py = 0.0, pz = 0.0;
     if (active) {
-        px = c.rx[j];
-        py = c.ry[j];
-        pz = c.rz[j];
-        float fxr, fyr, fzr;
-        const int ox = stencil_axis(px, c.nx, KW, fxr);
-        const int oy = stencil_axis(py, c.ny, KW, fyr);
-        const int oz = stencil_axis(pz, c.nz, KW, fzr);
         float wx[KW], wy[KW], wz[KW];
         weights1d<KW>(fxr, wx);
         weights1d<KW>(fyr, wy);
@@ -281,23 +329,24 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
     }
     // fixed-order reduction over the ROWS lanes of this node (aligned groups within a warp)
 #pragma unroll
-    for (int o = ROWS / 2; o > 0; o >>= 1) {
-        vx += __shfl_xor_sync(0xffffffffu, vx, o);
-        vy += __shfl_xor_sync(0xffffffffu, vy, o);
-        vz += __shfl_xor_sync(0xffffffffu, vz, o);
+    for (int s = ROWS / 2; s > 0; s >>= 1) {
+        vx += __shfl_xor_sync(0xffffffffu, vx, s);
+        vy += __shfl_xor_sync(0xffffffffu, vy, s);
+        vz += __shfl_xor_sync(0xffffffffu, vz, s);
     }
     if (active && row == 0) {
-        c.node_vel[j] = make_float4(vx, vy, vz, 0.f);
         if (vel_out) {
             vel_out[3 * j + 0] = vx;
             vel_out[3 * j + 1] = vy;
             vel_out[3 * j + 2] = vz;
         }
         if (ADVECT) {
-            const double nxp = px + (double)vx, nyp = py + (double)vy, nzp = pz + (double)vz;
+            c.node_vel[j] = make_float4(vx, vy, vz, 0.f);
+            const double nxp = c.rx[j] + (double)vx, nyp = c.ry[j] + (double)vy, nzp = c.rz[j] + (double)vz;
             c.rx[j] = nxp;
             c.ry[j] = nyp;
             c.rz[j] = nzp;
+            c.bead_pending[c.node_bead[j]] = 1;
             const float sp2 = vx * vx + vy * vy + vz * vz;
             if (!isfinite(sp2) || !isfinite(nxp + nyp + nzp)) atomicOr(&c.ctl->err, ERR_NONFINITE);
             else if (sp2 > 0.01f) atomicOr(&c.ctl->err, ERR_UNSTABLE);
@@ -378,6 +427,12 @@ cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s) {
     const int blocks = c.n_swimmers + (c.n_tris + PREP_TPB - 1) / PREP_TPB;
     if (blocks == 0) return cudaSuccess;
     k_ib_prepare<<<blocks, PREP_TPB, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bead_init(const DevCtx &c, cudaStream_t s) {
+    if (c.n_beads == 0) return cudaSuccess;
+    k_bead_init<<<c.n_beads, PREP_TPB, 0, s>>>(c);
     return cudaGetLastError();
 }
 

@@ -20,8 +20,8 @@
 // and a location is only ever read and written by the thread of one cell, so
 // one array suffices.
 //
-// Immersed-boundary coupling: spreading marks the LB_TPB-cell tiles its
-// stencils touch.  A block whose tile is marked reads F there, writes the
+// Immersed-boundary coupling: spreading marks the tiles (runs of up to
+// tile_x cells along x) its stencils touch.  A block whose tile is marked reads F there, writes the
 // physical velocity u (for the interpolation that follows), clears F and the
 // mark; every other block skips both fields.
 #include "lbib_internal.cuh"
@@ -61,29 +61,33 @@ __device__ __forceinline__ float3 take_fdet(unsigned long long *Fd, long long Np
     return make_float3((float)((double)a * FIX_INV), (float)((double)b * FIX_INV), (float)((double)c * FIX_INV));
 }
 
+// One block per run of up to tile_x consecutive cells of one (y, z) row: the
+// y/z neighbour rows are uniform across the block, so every population
+// address is a block-uniform plane/row base plus a per-thread x offset.
 template <int ST, bool ODD, int FORCING, bool DET>
-__global__ void __launch_bounds__(LB_TPB) k_lb_step(const DevCtx c) {
+__global__ void __launch_bounds__(LB_TPB, 3) k_lb_step(const DevCtx c) {
     using S = Store<ST>;
     using T = typename S::T;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
+    const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     __shared__ int s_flag;
     if (threadIdx.x == 0) {
-        int f = c.flags[blockIdx.x];
+        int f = c.flags[tile];
         s_flag = f;
-        if (f) c.flags[blockIdx.x] = 0;
+        if (f) c.flags[tile] = 0;
     }
     __syncthreads();
     const bool flagged = s_flag != 0;
     const bool forced = flagged || c.has_g;
-    const unsigned cell = blockIdx.x * LB_TPB + threadIdx.x;
+    const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
+    const unsigned x = blockIdx.x * c.tile_x + threadIdx.x;
+    const unsigned y = blockIdx.y, z = blockIdx.z;
     bool bad = false;
-    if (cell < (unsigned)c.N) {
-        const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
-        const unsigned yz = cell / nx, x = cell - yz * nx;
-        const unsigned z = yz / ny, y = yz - z * ny;
+    if (threadIdx.x < (unsigned)c.tile_x && x < nx) {
         const unsigned xm = x ? x - 1 : nx - 1, xp = (x + 1 == nx) ? 0 : x + 1;
         const unsigned rm = (y ? y - 1 : ny - 1) * nx, r0 = y * nx, rp = ((y + 1 == ny) ? 0 : y + 1) * nx;
         const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
+        const unsigned cell = x + r0 + s0;
         const size_t Np = (size_t)c.Npad;
         float d[Q];
 #pragma unroll
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(LB_TPB) k_lb_step(const DevCtx c) {
         }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&c.ctl->err, ERR_NONFINITE);
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.ctl->step += 1;
+    if (tile == 0 && threadIdx.x == 0) c.ctl->step += 1;
 }
 
 template <int ST, bool ODD>
@@ -201,13 +205,14 @@ __global__ void __launch_bounds__(LB_TPB) k_lb_macros(const DevCtx c, float *rho
 
 template <int ST, int FORCING>
 static cudaError_t lb_step_dispatch(const DevCtx &c, bool odd, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((c.N + LB_TPB - 1) / LB_TPB);
+    const dim3 blocks((unsigned)c.tiles_x, (unsigned)c.ny, (unsigned)c.nz);
+    const unsigned threads = (unsigned)((c.tile_x + 31) / 32 * 32);
     if (c.deterministic) {
-        if (odd) k_lb_step<ST, true, FORCING, true><<<blocks, LB_TPB, 0, s>>>(c);
-        else k_lb_step<ST, false, FORCING, true><<<blocks, LB_TPB, 0, s>>>(c);
+        if (odd) k_lb_step<ST, true, FORCING, true><<<blocks, threads, 0, s>>>(c);
+        else k_lb_step<ST, false, FORCING, true><<<blocks, threads, 0, s>>>(c);
     } else {
-        if (odd) k_lb_step<ST, true, FORCING, false><<<blocks, LB_TPB, 0, s>>>(c);
-        else k_lb_step<ST, false, FORCING, false><<<blocks, LB_TPB, 0, s>>>(c);
+        if (odd) k_lb_step<ST, true, FORCING, false><<<blocks, threads, 0, s>>>(c);
+        else k_lb_step<ST, false, FORCING, false><<<blocks, threads, 0, s>>>(c);
     }
     return cudaGetLastError();
 }

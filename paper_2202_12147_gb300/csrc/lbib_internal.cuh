@@ -34,7 +34,8 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 __host__ __device__ constexpr float wgt(int i) { return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
 __host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 
-// cells per LB thread block; one tile flag per block of cells
+// maximum cells per LB thread block (a run along x of one row); one tile
+// flag per block
 constexpr int LB_TPB = 256;
 // threads per node in spreading / interpolation (one per (y, z) stencil row)
 constexpr int ROWS4 = 16;
@@ -64,13 +65,18 @@ static_assert(sizeof(TriDev) == 64, "TriDev layout");
 struct BeadDev {
     int node_start, node_count;
     int swimmer, slot;  // owning swimmer and position 0..2 along its axis
+    float inv_count;    // 1 / node_count
+    int pad[3];
 };
 
 struct SwimDev {
     int bead[3];
     int balance;
-    double k, L, period;
-    double amp[3], phase[3];
+    double k, L, L2;        // spring stiffness, rest length, its square
+    double inv_period;      // 1 / drive period
+    double phase_turns[3];  // phase / (2 pi)
+    float amp[3];
+    int pad;
 };
 
 // Everything a kernel needs, by value.
@@ -79,6 +85,7 @@ struct DevCtx {
     long long N;      // cells
     long long Npad;   // population plane stride
     int n_tiles;
+    int tile_x, tiles_x;  // cells per tile along x, tiles per row
     float tau, omega, rho0;
     float g[3];
     int has_g;
@@ -90,7 +97,7 @@ struct DevCtx {
     float4 *F;                 // force density per cell (float atomics)
     unsigned long long *Fdet;  // 3 x Npad fixed-point force (deterministic mode)
     float4 *U;                 // velocity (x, y, z, rho) per cell
-    unsigned char *flags;      // one byte per LB tile
+    unsigned char *flags;      // one byte per LB tile (tile = x / tile_x + tiles_x * (y + ny * z))
     double *rx, *ry, *rz;      // node positions (SoA)
     float4 *node_force;        // f^tot per node
     float4 *node_vel;          // interpolated velocity per node
@@ -101,7 +108,9 @@ struct DevCtx {
     const int *node_bead;
     const BeadDev *beads;
     const SwimDev *swims;
-    double *bead_data;         // per bead, 8 doubles: centre R[0..2], external force / N_v [4..6]
+    double *bead_R;            // bead centres, 4 doubles per bead
+    float4 *bead_ext;          // (f^d + f^s) / N_v per bead
+    int *bead_pending;         // 1: node velocities of the last advection not yet folded into bead_R
     Control *ctl;
     lbib_swimmer_state *sw_state;
     double *xcm0;              // x_cm at init, 3 per swimmer
@@ -121,5 +130,6 @@ cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s);
 cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s);
 cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, cudaStream_t s);
 cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s);
+cudaError_t launch_bead_init(const DevCtx &c, cudaStream_t s);
 
 }  // namespace lbib
