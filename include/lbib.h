@@ -215,6 +215,36 @@ int lb_profile(lbib_ctx *ctx, int on);
  * Synchronises the context stream. */
 int lb_profile_read(lbib_ctx *ctx, double *total_ms, long long *launches);
 
+/* Deterministic force spreading that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory themselves -- code running while a CUDA graph is being
+ * captured in global mode, inside a framework whose caching allocator owns
+ * all device memory, or in a loop that must not grow its memory after
+ * start-up.  It needs no context and no caller scratch.
+ *
+ * Computes F(x) = sum_j f_j Delta(x - r_j) on a periodic nx x ny x nz box
+ * (Sec. 2.3, Eq. spreading) with the same fixed-point accumulation as a
+ * deterministic context, so the result is bitwise reproducible and equals
+ * the force field ib_spread produces for the same positions and forces.
+ *   nodes        DEVICE, n_nodes x 3 FP64 unwrapped positions (row-major)
+ *   node_forces  DEVICE, n_nodes x 3 FP32 nodal forces
+ *   kernel       LBIB_PESKIN4 or LBIB_LINEAR2
+ *   F_out        DEVICE, n_cells x 3 FP32, cell = x + nx*(y + ny*z); every
+ *                entry is written
+ *   stream       cudaStream_t the work is queued on (asynchronous)
+ * The accumulation grid is a static device array inside this library holding
+ * at most 262144 cells (64^3; 6 MiB, kept by every GPU that loads the library
+ * until the process exits); larger boxes are rejected with LBIB_ESIZE before
+ * anything is launched.  The first call on each device looks up the array's
+ * device address (with that device current) and caches it: make that first
+ * call before any stream capture.  Every call clears the part of the array it
+ * uses, then accumulates into it, so calls whose work overlaps on the GPU (on
+ * different streams, or on two host threads) race and corrupt each other's
+ * results; serialise them.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+int ib_spread_fixed_noalloc(const double *nodes, const float *node_forces, int n_nodes, int nx, int ny, int nz,
+                            int kernel, float *F_out, void *stream);
+
 /* Release the context (not the caller's buffers).  Synchronises. */
 int lb_destroy(lbib_ctx *ctx);
 

@@ -22,7 +22,7 @@ EXPORTS = [
     "lbib_version", "lbib_strerror", "lbib_last_error", "lbib_lattice", "lbib_required_sizes", "lb_init", "lb_step",
     "ib_spread", "ib_interpolate", "swimmer_state", "lb_sync", "lb_get_macros", "lb_get_populations",
     "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces", "lb_get_force_field",
-    "lb_set_velocity", "lb_profile", "lb_profile_read", "lb_destroy",
+    "lb_set_velocity", "lb_profile", "lb_profile_read", "ib_spread_fixed_noalloc", "lb_destroy",
 ]
 
 
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
             getattr(L, n).argtypes = [P, P]
         L.lb_profile.argtypes = [P, I]
         L.lb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)]
+        L.ib_spread_fixed_noalloc.argtypes = [P, P, I, I, I, I, I, P, P]
         L.lb_destroy.argtypes = [P]
         for n in EXPORTS:
             if n not in ("lbib_version", "lbib_strerror", "lbib_last_error"):

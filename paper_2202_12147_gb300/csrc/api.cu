@@ -15,6 +15,12 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+void lbib::set_last_error(const char *msg) { g_last_error = msg; }
+
+namespace {
+
 int fail(int code, const std::string &msg) {
     g_last_error = msg;
     return code;

@@ -199,34 +199,6 @@ __global__ void __launch_bounds__(PREP_TPB) k_bead_init(const DevCtx c) {
     }
 }
 
-// 1-D kernel weights on the KW stencil cells floor(p) - KW/2 + 1 ... floor(p) + KW/2.
-// Peskin's 4-point kernel evaluated at the four distances 1+f, f, 1-f, 2-f
-// (f = p - floor p) needs one square root: with q = sqrt(1 + 4f - 4f^2)
-// the weights are (3 - 2f - q)/8, (3 - 2f + q)/8, (1 + 2f + q)/8, (1 + 2f - q)/8.
-template <int KW>
-__device__ __forceinline__ void weights1d(float f, float *w) {
-    if (KW == 4) {
-        const float q = sqrtf(1.0f + 4.0f * f - 4.0f * f * f);
-        w[0] = (3.0f - 2.0f * f - q) * 0.125f;
-        w[1] = (3.0f - 2.0f * f + q) * 0.125f;
-        w[2] = (1.0f + 2.0f * f + q) * 0.125f;
-        w[3] = (1.0f + 2.0f * f - q) * 0.125f;
-    } else {
-        w[0] = 1.0f - f;
-        w[1] = f;
-    }
-}
-
-// stencil origin (wrapped into [0, n)) and fractional offset along one axis
-__device__ __forceinline__ int stencil_axis(double p, int n, int kw, float &frac) {
-    const double fl = floor(p);
-    frac = (float)(p - fl);
-    long long o = (long long)fl - (kw / 2 - 1);
-    o %= n;
-    if (o < 0) o += n;
-    return (int)o;
-}
-
 template <int KW, bool DET>
 __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
     __shared__ float4 sf[GS_NODES];

@@ -121,6 +121,38 @@ struct DevCtx {
 constexpr double FIX_SCALE = 281474976710656.0;
 constexpr double FIX_INV = 1.0 / 281474976710656.0;
 
+// ---------------------------------------------------------------- delta-kernel stencil
+// 1-D kernel weights on the KW stencil cells floor(p) - KW/2 + 1 ... floor(p) + KW/2.
+// Peskin's 4-point kernel evaluated at the four distances 1+f, f, 1-f, 2-f
+// (f = p - floor p) needs one square root: with q = sqrt(1 + 4f - 4f^2)
+// the weights are (3 - 2f - q)/8, (3 - 2f + q)/8, (1 + 2f + q)/8, (1 + 2f - q)/8.
+template <int KW>
+__device__ __forceinline__ void weights1d(float f, float *w) {
+    if (KW == 4) {
+        const float q = sqrtf(1.0f + 4.0f * f - 4.0f * f * f);
+        w[0] = (3.0f - 2.0f * f - q) * 0.125f;
+        w[1] = (3.0f - 2.0f * f + q) * 0.125f;
+        w[2] = (1.0f + 2.0f * f + q) * 0.125f;
+        w[3] = (1.0f + 2.0f * f - q) * 0.125f;
+    } else {
+        w[0] = 1.0f - f;
+        w[1] = f;
+    }
+}
+
+// stencil origin (wrapped into [0, n)) and fractional offset along one axis
+__device__ __forceinline__ int stencil_axis(double p, int n, int kw, float &frac) {
+    const double fl = floor(p);
+    frac = (float)(p - fl);
+    long long o = (long long)fl - (kw / 2 - 1);
+    o %= n;
+    if (o < 0) o += n;
+    return (int)o;
+}
+
+// message returned by lbib_last_error() on this thread
+void set_last_error(const char *msg);
+
 // ---------------------------------------------------------------- launchers
 // LB (lb_kernels.cu)
 cudaError_t launch_lb_step(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
