@@ -206,9 +206,10 @@ int lb_get_force_field(lbib_ctx *ctx, float *host_F);
 int lb_set_velocity(lbib_ctx *ctx, const float *host_u);
 
 /* Timing hook.  With on = 1, lb_step launches its kernels one by one and
- * brackets every fluid (LB) kernel launch with a pair of CUDA events on the
- * context stream; with on = 0 (the default) it replays captured graphs.
- * Switching on discards earlier measurements. */
+ * brackets every launch of the main fluid kernel (the update of every tile no
+ * node stencil touches) with a pair of CUDA events on the context stream;
+ * with on = 0 (the default) it replays captured graphs.  Switching on
+ * discards earlier measurements. */
 int lb_profile(lbib_ctx *ctx, int on);
 /* Sum of the bracketed fluid-kernel durations in milliseconds and the
  * number of launches measured since profiling was switched on.
@@ -244,6 +245,12 @@ int lb_profile_read(lbib_ctx *ctx, double *total_ms, long long *launches);
  * routine is called. */
 int ib_spread_fixed_noalloc(const double *nodes, const float *node_forces, int n_nodes, int nx, int ny, int nz,
                             int kernel, float *F_out, void *stream);
+
+/* Number of cells in the fluid tiles marked for the next step (the tiles the
+ * delta-kernel stencils of the current node positions touch; they are updated
+ * with the force field by the immersed-boundary stream, every other cell by
+ * the main fluid kernel).  Synchronous. */
+int lb_marked_cells(lbib_ctx *ctx, long long *cells);
 
 /* Release the context (not the caller's buffers).  Synchronises. */
 int lb_destroy(lbib_ctx *ctx);

@@ -22,7 +22,8 @@ EXPORTS = [
     "lbib_version", "lbib_strerror", "lbib_last_error", "lbib_lattice", "lbib_required_sizes", "lb_init", "lb_step",
     "ib_spread", "ib_interpolate", "swimmer_state", "lb_sync", "lb_get_macros", "lb_get_populations",
     "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces", "lb_get_force_field",
-    "lb_set_velocity", "lb_profile", "lb_profile_read", "ib_spread_fixed_noalloc", "lb_destroy",
+    "lb_set_velocity", "lb_profile", "lb_profile_read", "lb_marked_cells", "ib_spread_fixed_noalloc",
+    "lb_destroy",
 ]
 
 
@@ -67,7 +68,9 @@ class LbibError(RuntimeError):
 
 
 def library_path():
-    return _build.LIB
+    """liblbib.so in the package directory, or the build named by the
+    LBIB_LIBRARY environment variable (used to compare build variants)."""
+    return os.environ.get("LBIB_LIBRARY") or _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -76,11 +79,12 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB):
-            if not build_if_missing:
-                raise OSError(f"{_build.LIB} missing: run paper_2202_12147_gb300.build.build()")
+        path = library_path()
+        if not os.path.exists(path):
+            if not build_if_missing or path != _build.LIB:
+                raise OSError(f"{path} missing: run paper_2202_12147_gb300.build.build()")
             _build.build()
-        L = ctypes.CDLL(_build.LIB)
+        L = ctypes.CDLL(path)
         P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
         L.lbib_version.restype = ctypes.c_char_p
         L.lbib_strerror.restype = ctypes.c_char_p
@@ -101,6 +105,7 @@ def load(build_if_missing: bool = True):
             getattr(L, n).argtypes = [P, P]
         L.lb_profile.argtypes = [P, I]
         L.lb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)]
+        L.lb_marked_cells.argtypes = [P, ctypes.POINTER(LL)]
         L.ib_spread_fixed_noalloc.argtypes = [P, P, I, I, I, I, I, P, P]
         L.lb_destroy.argtypes = [P]
         for n in EXPORTS:

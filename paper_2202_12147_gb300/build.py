@@ -33,14 +33,17 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()):
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra=(), out=None):
+    """Compile liblbib.so (to `out` when given, e.g. a variant with extra -D flags)."""
+    target = out or LIB
+    if out is None and not force and not _stale():
         return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    obj_dir = OBJ if out is None else out + ".objs"
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
 
     def comp(src):
-        obj = os.path.join(OBJ, src.replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -51,12 +54,12 @@ def build(force: bool = False, verbose: bool = False, extra=()):
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(comp, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = target + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -2,6 +2,7 @@
 // of the caller buffers, mesh preprocessing, CUDA-graph capture of the step
 // and the host-side accessors.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -38,13 +39,33 @@ size_t up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 constexpr int GRAPH_STEPS = 16;  // steps per captured graph (even: both AA parities)
 
+int env_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    return (v && v[0]) ? atoi(v) : dflt;
+}
+
+// Priority of the immersed-boundary stream: the highest by default;
+// LBIB_IB_PRIORITY=0 gives it the default priority (for comparisons).
+int ib_priority(int lo, int hi) { return env_int("LBIB_IB_PRIORITY", 1) ? hi : lo; }
+
+// Extra cells between population planes (a multiple of 64), so that the 19
+// planes do not start a power of two apart; LBIB_PLANE_PAD overrides it.
+long long plane_pad() {
+    const char *v = getenv("LBIB_PLANE_PAD");
+    if (v && v[0]) {
+        long long k = atoll(v);
+        return k < 0 ? 0 : (k + 63) / 64 * 64;
+    }
+    return 0;
+}
+
 struct Layout {
     long long N = 0, Npad = 0;
     int n_tiles = 0, tile_x = 0, tiles_x = 0;
     size_t esize = 4;
     size_t bytes[LBIB_NBUF] = {0, 0, 0};
     // fields
-    size_t oF = 0, oFdet = 0, oU = 0, oFlags = 0;
+    size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0;
     // aux
     size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
            obead = 0, oswim = 0, obd = 0, obe = 0, obp = 0, octl = 0, osws = 0, oxcm = 0;
@@ -115,11 +136,11 @@ bool valid_structure(const lb_params *p, const lbib_structure *s, std::string &w
 Layout make_layout(const lb_params *p, const lbib_structure *s) {
     Layout L;
     L.N = (long long)p->nx * p->ny * p->nz;
-    L.Npad = (L.N + 63) / 64 * 64;
+    L.Npad = (L.N + 63) / 64 * 64 + plane_pad();
+    L.esize = p->storage == LBIB_F32 ? 4 : 2;
     L.tile_x = p->nx <= LB_TPB ? p->nx : LB_TPB;
     L.tiles_x = (p->nx + L.tile_x - 1) / L.tile_x;
     L.n_tiles = L.tiles_x * p->ny * p->nz;
-    L.esize = p->storage == LBIB_F32 ? 4 : 2;
     L.bytes[0] = up((size_t)Q * L.Npad * L.esize);
     size_t o = 0;
     if (p->deterministic) {
@@ -131,8 +152,12 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     }
     L.oU = o;
     o += up((size_t)L.Npad * 16);
-    L.oFlags = o;
-    o += up((size_t)L.n_tiles);
+    L.oMarks = o;
+    o += up(2 * (size_t)L.n_tiles * 4);
+    L.oList = o;
+    o += up(2 * (size_t)L.n_tiles * 4);
+    L.oCount = o;
+    o += up(4 * 4);
     L.bytes[1] = o;
     const int M = s ? s->n_nodes : 0, T = s ? s->n_tris : 0, B = s ? s->n_beads : 0, S = s ? s->n_swimmers : 0;
     o = 0;
@@ -164,8 +189,11 @@ struct lbib_ctx {
     lb_params p;
     Layout L;
     DevCtx d;
-    cudaStream_t user = nullptr;   // caller stream: all work goes here
-    cudaStream_t cap = nullptr;    // private stream used only to capture graphs
+    cudaStream_t user = nullptr;   // caller stream: the fluid update of unmarked tiles and every other call
+    cudaStream_t ib = nullptr;     // immersed-boundary chain of a step, concurrent with the fluid update
+    cudaStream_t cap = nullptr;    // private streams used only to capture graphs
+    cudaStream_t cap_ib = nullptr;
+    cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr;  // step-to-step dependencies
     cudaGraphExec_t graph = nullptr;
     long long step = 0;            // host mirror of the device step counter
     bool profiling = false;
@@ -178,29 +206,68 @@ struct lbib_ctx {
 
 namespace {
 
-cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t s, bool timed = false) {
+cudaError_t timed_event(lbib_ctx *c, cudaStream_t s) {
     cudaError_t e;
-    if (c->n_nodes > 0) {
-        if ((e = launch_ib_prepare(c->d, s)) != cudaSuccess) return e;
-        if ((e = launch_ib_gather_spread(c->d, c->p.kernel, s)) != cudaSuccess) return e;
+    while (c->ev.size() < c->ev_used + 1) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+        c->ev.push_back(ev);
     }
-    if (timed) {
-        while (c->ev.size() < c->ev_used + 2) {
-            cudaEvent_t ev;
-            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
-            c->ev.push_back(ev);
-        }
-        if ((e = cudaEventRecord(c->ev[c->ev_used], s)) != cudaSuccess) return e;
-    }
-    if ((e = launch_lb_step(c->d, c->p.storage, c->p.forcing, odd, s)) != cudaSuccess) return e;
-    if (timed) {
-        if ((e = cudaEventRecord(c->ev[c->ev_used + 1], s)) != cudaSuccess) return e;
-        c->ev_used += 2;
-    }
-    if (c->n_nodes > 0) {
-        if ((e = launch_ib_interp(c->d, c->p.kernel, true, nullptr, s)) != cudaSuccess) return e;
-    }
+    if ((e = cudaEventRecord(c->ev[c->ev_used], s)) != cudaSuccess) return e;
+    c->ev_used += 1;
     return cudaSuccess;
+}
+
+// Order the immersed-boundary stream after everything queued on the main stream.
+cudaError_t fork(lbib_ctx *c, cudaStream_t sm, cudaStream_t sib) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(c->e_fork, sm)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(sib, c->e_fork, 0)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->e_main, sm)) != cudaSuccess) return e;
+    return cudaEventRecord(c->e_ib, sm);
+}
+
+// Order the main stream after the immersed-boundary stream.
+cudaError_t join(lbib_ctx *c, cudaStream_t sm) { return cudaStreamWaitEvent(sm, c->e_ib, 0); }
+
+// One coupled step on two streams (between fork and join).  Main stream: the
+// fluid update of every unmarked tile (the bulk of the bytes).  IB stream,
+// concurrently: forces and spreading, the fluid update of the marked tiles,
+// interpolation and advection, then the marks for the next step (other
+// parity).  The main stream's next step waits for this step's IB chain
+// (populations of marked tiles and the next marks); the IB stream's fluid
+// update waits for the previous step's main-stream update.
+cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t sm, cudaStream_t sib, bool timed = false) {
+    cudaError_t e;
+    const int p = odd ? 1 : 0;
+    if (c->n_nodes == 0) {
+        if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
+        if ((e = launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, sm)) != cudaSuccess) return e;
+        if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    if ((e = cudaStreamWaitEvent(sm, c->e_ib, 0)) != cudaSuccess) return e;
+    if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
+    if ((e = launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, sm)) != cudaSuccess) return e;
+    if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
+    if ((e = launch_ib_prepare(c->d, sib)) != cudaSuccess) return e;
+    if ((e = launch_ib_gather_spread(c->d, c->p.kernel, sib)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(sib, c->e_main, 0)) != cudaSuccess) return e;  // previous step's main update
+    if ((e = cudaEventRecord(c->e_main, sm)) != cudaSuccess) return e;
+    // the previous step's marks (other parity) are no longer read by anyone
+    if ((e = launch_ib_clear_marks(c->d, 1 - p, true, sib)) != cudaSuccess) return e;
+    if ((e = launch_lb_marked(c->d, c->p.storage, c->p.forcing, odd, sib)) != cudaSuccess) return e;
+    if ((e = launch_ib_interp(c->d, c->p.kernel, true, nullptr, 1 - p, sib)) != cudaSuccess) return e;
+    return cudaEventRecord(c->e_ib, sib);
+}
+
+// Re-mark the tiles for the current positions (after they are set from outside).
+cudaError_t remark(lbib_ctx *c) {
+    cudaError_t e;
+    if (c->n_nodes == 0) return cudaSuccess;
+    if ((e = launch_ib_clear_marks(c->d, 0, false, c->user)) != cudaSuccess) return e;
+    if ((e = launch_ib_clear_marks(c->d, 1, false, c->user)) != cudaSuccess) return e;
+    return launch_ib_mark(c->d, c->p.kernel, (int)(c->step & 1), c->user);
 }
 
 int check_device_errors(lbib_ctx *c) {
@@ -354,6 +421,7 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.n_tiles = L.n_tiles;
     d.tile_x = L.tile_x;
     d.tiles_x = L.tiles_x;
+
     d.tau = (float)p->tau;
     d.omega = (float)(1.0 / p->tau);
     d.rho0 = (float)p->rho0;
@@ -371,7 +439,9 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.F = p->deterministic ? nullptr : (float4 *)(F + L.oF);
     d.Fdet = p->deterministic ? (unsigned long long *)(F + L.oFdet) : nullptr;
     d.U = (float4 *)(F + L.oU);
-    d.flags = (unsigned char *)(F + L.oFlags);
+    d.marks = (int *)(F + L.oMarks);
+    d.tile_list = (int *)(F + L.oList);
+    d.tile_count = (int *)(F + L.oCount);
     d.rx = (double *)(A + L.orx);
     d.ry = (double *)(A + L.ory);
     d.rz = (double *)(A + L.orz);
@@ -399,7 +469,14 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         cudaMallocHost(&c->h_sws, sizeof(lbib_swimmer_state) * (S > 0 ? S : 1)) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "cudaMallocHost failed"));
     cudaStream_t u = c->user;
-    // rest state: all deviations zero, fields and flags zero
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return bail(fail(LBIB_ECUDA, "querying the device failed"));
+        // persistent grid of the marked-tile fluid kernel: one block per SM
+        d.marked_grid = env_int("LBIB_MARKED_GRID", sms);
+    }
+    // rest state: all deviations zero, fields, marks and lists zero
     if (cudaMemsetAsync(b->pops, 0, L.bytes[0], u) != cudaSuccess || cudaMemsetAsync(b->fields, 0, L.bytes[1], u) != cudaSuccess ||
         cudaMemsetAsync(b->aux, 0, L.bytes[2], u) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "cudaMemsetAsync failed"));
@@ -417,18 +494,30 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
               h2d((void *)d.csr_ent, cent.data(), 3 * (size_t)T * 4) && h2d((void *)d.node_bead, nbead.data(), M * 4) &&
               h2d((void *)d.beads, beads.data(), B * sizeof(BeadDev)) && h2d((void *)d.swims, swims.data(), S * sizeof(SwimDev));
     if (!ok) return bail(fail(LBIB_ECUDA, "uploading mesh tables failed"));
-    if (launch_bead_init(d, u) != cudaSuccess || launch_swimmer_state(d, true, u) != cudaSuccess)
+    if (launch_bead_init(d, u) != cudaSuccess || launch_swimmer_state(d, true, u) != cudaSuccess ||
+        launch_ib_mark(d, p->kernel, 0, u) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "bead initialisation launch failed"));
     if (cudaStreamSynchronize(u) != cudaSuccess) return bail(fail(LBIB_ECUDA, "init synchronisation failed"));
 
+    // streams and events of the two-stream step; the IB stream gets the
+    // highest priority so its small kernels are scheduled between fluid blocks
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->cap_ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->e_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->e_main, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->e_ib, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "creating streams or events failed"));
+
     // capture GRAPH_STEPS coupled steps (alternating AA parity) into one graph
     cudaGraph_t g = nullptr;
-    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(fail(LBIB_ECUDA, "cudaStreamCreate failed"));
     if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "cudaStreamBeginCapture failed"));
-    cudaError_t ce = cudaSuccess;
-    for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k) ce = enqueue_step(c, (k & 1) != 0, c->cap);
+    cudaError_t ce = fork(c, c->cap, c->cap_ib);
+    for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k) ce = enqueue_step(c, (k & 1) != 0, c->cap, c->cap_ib);
+    if (ce == cudaSuccess) ce = join(c, c->cap);
     cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
     if (ce != cudaSuccess || ee != cudaSuccess)
         return bail(fail(LBIB_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee)));
@@ -442,21 +531,27 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
 int lb_step(lbib_ctx *c, long long n) {
     if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
     if (n < 0) return fail(LBIB_EINVAL, "n_steps < 0");
+    bool forked = false;
     while (n > 0) {
-        if (c->profiling) {
-            CU(enqueue_step(c, (c->step & 1) != 0, c->user, true));
-            c->step += 1;
-            n -= 1;
-        } else if ((c->step & 1) == 0 && n >= GRAPH_STEPS) {
+        if (!c->profiling && (c->step & 1) == 0 && n >= GRAPH_STEPS) {
+            if (forked) {
+                CU(join(c, c->user));
+                forked = false;
+            }
             CU(cudaGraphLaunch(c->graph, c->user));
             c->step += GRAPH_STEPS;
             n -= GRAPH_STEPS;
         } else {
-            CU(enqueue_step(c, (c->step & 1) != 0, c->user));
+            if (!forked) {
+                CU(fork(c, c->user, c->ib));
+                forked = true;
+            }
+            CU(enqueue_step(c, (c->step & 1) != 0, c->user, c->ib, c->profiling));
             c->step += 1;
             n -= 1;
         }
     }
+    if (forked) CU(join(c, c->user));
     return LBIB_OK;
 }
 
@@ -472,7 +567,7 @@ int ib_interpolate(lbib_ctx *c, float *vel) {
     if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
     if (c->n_nodes == 0) return LBIB_OK;
     if (!vel) return fail(LBIB_EINVAL, "node_vel_out is NULL");
-    CU(launch_ib_interp(c->d, c->p.kernel, false, vel, c->user));
+    CU(launch_ib_interp(c->d, c->p.kernel, false, vel, -1, c->user));
     return LBIB_OK;
 }
 
@@ -575,6 +670,7 @@ int lb_set_nodes(lbib_ctx *c, const double *h) {
     CU(cudaMemcpyAsync(c->d.ry, y.data(), M * 8, cudaMemcpyHostToDevice, c->user));
     CU(cudaMemcpyAsync(c->d.rz, z.data(), M * 8, cudaMemcpyHostToDevice, c->user));
     CU(launch_bead_init(c->d, c->user));
+    CU(remark(c));
     CU(cudaStreamSynchronize(c->user));
     return LBIB_OK;
 }
@@ -648,12 +744,28 @@ int lb_profile_read(lbib_ctx *c, double *total_ms, long long *launches) {
     return LBIB_OK;
 }
 
+int lb_marked_cells(lbib_ctx *c, long long *cells) {
+    if (!c || !cells) return fail(LBIB_EINVAL, "NULL argument");
+    int cnt[2] = {0, 0};
+    CU(cudaMemcpyAsync(cnt, c->d.tile_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->user));
+    CU(cudaStreamSynchronize(c->user));
+    const long long n = (long long)cnt[c->step & 1] * c->L.tile_x;
+    *cells = n < c->L.N ? n : c->L.N;
+    return LBIB_OK;
+}
+
 int lb_destroy(lbib_ctx *c) {
     if (!c) return LBIB_OK;
     cudaStreamSynchronize(c->user);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->ib) cudaStreamSynchronize(c->ib);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->cap_ib) cudaStreamDestroy(c->cap_ib);
+    if (c->ib) cudaStreamDestroy(c->ib);
+    if (c->e_fork) cudaEventDestroy(c->e_fork);
+    if (c->e_main) cudaEventDestroy(c->e_main);
+    if (c->e_ib) cudaEventDestroy(c->e_ib);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->h_sws) cudaFreeHost(c->h_sws);
     delete c;

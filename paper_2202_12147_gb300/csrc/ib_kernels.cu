@@ -12,12 +12,14 @@
 //                      Sec. 2.2) and sets up its stencil; then KW^2 threads
 //                      per node spread it over the KW^3 stencil (Sec. 2.3,
 //                      Eq. spreading) with vector float atomics, or 64-bit
-//                      fixed-point atomics (bitwise reproducible), marking
-//                      the LB tiles they touch.
-//   k_ib_interp        KW^2 threads per node gather u over the stencil
+//                      fixed-point atomics (bitwise reproducible).
+//   k_ib_mark          marks (and lists) the fluid tiles the stencils of the
+//                      current node positions touch, for one step parity;
+//   k_ib_clear_marks   unmarks a parity's listed tiles and empties its list.
+//   k_ib_interp        KW threads per node gather u over the stencil
 //                      (Sec. 2.3, Eq. interpolation), reduce with shuffles in
-//                      a fixed order and move the node r += rdot in FP64
-//                      (front tracking, Sec. 2.3).
+//                      a fixed order, move the node r += rdot in FP64 (front
+//                      tracking, Sec. 2.3) and mark the next step's tiles.
 //
 // FP64 on this GPU issues at a small fraction of the FP32 rate, so it is kept
 // to what needs it: node positions and their update, the bead centres, the
@@ -71,39 +73,73 @@ __device__ __forceinline__ void block_sum3(T &a, T &b, T &c, T *sm /* 3*32 */) {
 }
 
 // Swimmer block: fold the last advection into the bead centres, then the
-// drive (Sec. 2.2, driving-force equation) and springs (Sec. 2.2).
+// drive (Sec. 2.2, driving-force equation) and springs (Sec. 2.2).  The
+// three beads are reduced together: each thread strides over all of the
+// swimmer's nodes with its loads unrolled, keeping one partial sum per bead.
 __device__ void swimmer_forces(const DevCtx &c, int s) {
-    __shared__ float smf[96];
+    __shared__ float smf[9][32];
     __shared__ double sR[3][3];
     const SwimDev sw = c.swims[s];
+    BeadDev bd[3];
+    int pend[3];
+#pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const int b = sw.bead[q];
-        const BeadDev bd = c.beads[b];
-        if (c.bead_pending[b]) {  // uniform across the block
-            float a = 0.f, bb = 0.f, cc = 0.f;
-            for (int j = bd.node_start + threadIdx.x; j < bd.node_start + bd.node_count; j += blockDim.x) {
-                const float4 v = c.node_vel[j];
-                a += v.x;
-                bb += v.y;
-                cc += v.z;
+        bd[q] = c.beads[sw.bead[q]];
+        pend[q] = c.bead_pending[sw.bead[q]];
+    }
+    float acc[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    if (pend[0] | pend[1] | pend[2]) {  // uniform across the block
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (!pend[q]) continue;
+            const int j0 = bd[q].node_start, n = bd[q].node_count;
+            int k = threadIdx.x;
+            for (; k + 3 * (int)blockDim.x < n; k += 4 * blockDim.x) {
+                const float4 v0 = c.node_vel[j0 + k], v1 = c.node_vel[j0 + k + blockDim.x];
+                const float4 v2 = c.node_vel[j0 + k + 2 * blockDim.x], v3 = c.node_vel[j0 + k + 3 * blockDim.x];
+                acc[q][0] += (v0.x + v1.x) + (v2.x + v3.x);
+                acc[q][1] += (v0.y + v1.y) + (v2.y + v3.y);
+                acc[q][2] += (v0.z + v1.z) + (v2.z + v3.z);
             }
-            block_sum3(a, bb, cc, smf);
-            if (threadIdx.x == 0) {
-                double *R = c.bead_R + 4 * b;
-                R[0] += (double)(a * bd.inv_count);
-                R[1] += (double)(bb * bd.inv_count);
-                R[2] += (double)(cc * bd.inv_count);
+            for (; k < n; k += blockDim.x) {
+                const float4 v = c.node_vel[j0 + k];
+                acc[q][0] += v.x;
+                acc[q][1] += v.y;
+                acc[q][2] += v.z;
             }
         }
+        // fixed-order block reduction of the 9 partial sums
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[q][a] += __shfl_xor_sync(0xffffffffu, acc[q][a], o);
+        const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        if ((threadIdx.x & 31) == 0)
+            for (int q = 0; q < 3; ++q)
+                for (int a = 0; a < 3; ++a) smf[3 * q + a][w] = acc[q][a];
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 3; ++q)
+                for (int a = 0; a < 3; ++a) {
+                    float t = 0.f;
+                    for (int k = 0; k < nw; ++k) t += smf[3 * q + a][k];
+                    acc[q][a] = t;
+                }
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
         for (int q = 0; q < 3; ++q) {
-            const double *R = c.bead_R + 4 * sw.bead[q];
+            double *R = c.bead_R + 4 * sw.bead[q];
+            if (pend[q]) {
+                R[0] += (double)(acc[q][0] * bd[q].inv_count);
+                R[1] += (double)(acc[q][1] * bd[q].inv_count);
+                R[2] += (double)(acc[q][2] * bd[q].inv_count);
+                c.bead_pending[sw.bead[q]] = 0;
+            }
             sR[q][0] = R[0];
             sR[q][1] = R[1];
             sR[q][2] = R[2];
-            c.bead_pending[sw.bead[q]] = 0;
         }
         // drive: sin(2 pi (t / T + phase / 2 pi)), argument reduced in FP64
         const double tt = (double)c.ctl->step * sw.inv_period;
@@ -132,9 +168,8 @@ __device__ void swimmer_forces(const DevCtx &c, int s) {
         }
         for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
         for (int q = 0; q < 3; ++q) {
-            const int b = sw.bead[q];
-            const float inv = c.beads[b].inv_count;
-            c.bead_ext[b] = make_float4((fd[q] + fs[q][0]) * inv, fs[q][1] * inv, fs[q][2] * inv, 0.f);
+            const float inv = bd[q].inv_count;
+            c.bead_ext[sw.bead[q]] = make_float4((fd[q] + fs[q][0]) * inv, fs[q][1] * inv, fs[q][2] * inv, 0.f);
         }
     }
 }
@@ -209,11 +244,25 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
     if ((int)threadIdx.x < nloc) {
         const int j = j0 + threadIdx.x;
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for (int e = c.csr_ptr[j]; e < c.csr_ptr[j + 1]; ++e) {
-            const float4 v = c.tri_force[c.csr_ent[e]];
-            fx += v.x;
-            fy += v.y;
-            fz += v.z;
+        const int e0 = c.csr_ptr[j], e1 = c.csr_ptr[j + 1];
+        // up to 8 incident corners with independent loads, in list order
+        int ent[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ent[k] = e0 + k < e1 ? c.csr_ent[e0 + k] : -1;
+        float4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = ent[k] >= 0 ? c.tri_force[ent[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            fx += v[k].x;
+            fy += v[k].y;
+            fz += v[k].z;
+        }
+        for (int e = e0 + 8; e < e1; ++e) {
+            const float4 w = c.tri_force[c.csr_ent[e]];
+            fx += w.x;
+            fy += w.y;
+            fz += w.z;
         }
         const float4 ext = c.bead_ext[c.node_bead[j]];
         const float4 f = make_float4(fx + ext.x, fy + ext.y, fz + ext.z, 0.f);
@@ -238,8 +287,6 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
         const float wyz = sw[ln][1][dy] * sw[ln][2][dz];
         const float4 f = sf[ln];
         const unsigned rowbase = (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz);
-        const int tile_row = c.tiles_x * (yy + ny * zz);
-        int last_tile = -1;
 #pragma unroll
         for (int k = 0; k < KW; ++k) {
             const int xx = (ox + k) % nx;
@@ -252,77 +299,142 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
             } else {
                 atomicAdd(&c.F[cell], make_float4(w * f.x, w * f.y, w * f.z, 0.f));
             }
-            const int tile = xx / c.tile_x + tile_row;
-            if (tile != last_tile) {
-                c.flags[tile] = 1;
-                last_tile = tile;
-            }
         }
     }
 }
 
+// KW lanes per node, lane l gathering the KW x KW cells of stencil plane
+// z = oz + l; the lanes' partial sums are reduced with shuffles in a fixed
+// order.  With ADVECT, lane 0 moves the node (FP64) and, if mark_parity >= 0,
+// the lanes mark the tiles of the moved node's stencil for the next step.
 template <int KW, bool ADVECT>
-__global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *vel_out) {
-    constexpr int ROWS = KW * KW;
+__global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *vel_out, int mark_parity) {
     const int gt = blockIdx.x * INT_TPB + threadIdx.x;
-    const int j = gt / ROWS, row = gt % ROWS;
+    const int j = gt / KW, l = gt % KW;
     const bool active = j < c.n_nodes;
-    const int lane = threadIdx.x & 31, gbase = lane & ~(ROWS - 1);
-    // lanes 0..2 of each node's group set up one axis each; the rest read them by shuffle
-    int o = 0;
-    float fr = 0.f;
-    if (active && row < 3) {
-        const double p = row == 0 ? c.rx[j] : (row == 1 ? c.ry[j] : c.rz[j]);
-        o = stencil_axis(p, row == 0 ? c.nx : (row == 1 ? c.ny : c.nz), KW, fr);
-    }
-    const int ox = __shfl_sync(0xffffffffu, o, gbase), oy = __shfl_sync(0xffffffffu, o, gbase + 1),
-              oz = __shfl_sync(0xffffffffu, o, gbase + 2);
-    const float fxr = __shfl_sync(0xffffffffu, fr, gbase), fyr = __shfl_sync(0xffffffffu, fr, gbase + 1),
-                fzr = __shfl_sync(0xffffffffu, fr, gbase + 2);
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    double px = 0.0, py = 0.0, pz = 0.0;
     float vx = 0.f, vy = 0.f, vz = 0.f;
     if (active) {
+        px = c.rx[j];
+        py = c.ry[j];
+        pz = c.rz[j];
+        float fx, fy, fz;
+        const int ox = stencil_axis(px, nx, KW, fx), oy = stencil_axis(py, ny, KW, fy), oz = stencil_axis(pz, nz, KW, fz);
         float wx[KW], wy[KW], wz[KW];
-        weights1d<KW>(fxr, wx);
-        weights1d<KW>(fyr, wy);
-        weights1d<KW>(fzr, wz);
-        const int dy = row % KW, dz = row / KW;
-        const int yy = (oy + dy) % c.ny, zz = (oz + dz) % c.nz;
-        const float wyz = wy[dy] * wz[dz];
-        const unsigned rowbase = (unsigned)c.nx * ((unsigned)yy + (unsigned)c.ny * (unsigned)zz);
+        weights1d<KW>(fx, wx);
+        weights1d<KW>(fy, wy);
+        weights1d<KW>(fz, wz);
+        float wzl = wz[0];
 #pragma unroll
-        for (int k = 0; k < KW; ++k) {
-            const int xx = (ox + k) % c.nx;
-            const float4 u = c.U[rowbase + (unsigned)xx];
-            const float w = wx[k] * wyz;
-            vx += w * u.x;
-            vy += w * u.y;
-            vz += w * u.z;
+        for (int k = 1; k < KW; ++k)
+            if (l == k) wzl = wz[k];
+        const unsigned zoff = (unsigned)nx * (unsigned)ny * (unsigned)((oz + l) % nz);
+#pragma unroll
+        for (int dy = 0; dy < KW; ++dy) {
+            const unsigned rowbase = zoff + (unsigned)nx * (unsigned)((oy + dy) % ny);
+            const float wyz = wy[dy] * wzl;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                const float4 u = c.U[rowbase + (unsigned)((ox + k) % nx)];
+                const float w = wx[k] * wyz;
+                vx += w * u.x;
+                vy += w * u.y;
+                vz += w * u.z;
+            }
         }
     }
-    // fixed-order reduction over the ROWS lanes of this node (aligned groups within a warp)
+    // fixed-order reduction over the KW lanes of this node (aligned groups within a warp)
 #pragma unroll
-    for (int s = ROWS / 2; s > 0; s >>= 1) {
+    for (int s = KW / 2; s > 0; s >>= 1) {
         vx += __shfl_xor_sync(0xffffffffu, vx, s);
         vy += __shfl_xor_sync(0xffffffffu, vy, s);
         vz += __shfl_xor_sync(0xffffffffu, vz, s);
     }
-    if (active && row == 0) {
+    if (active && l == 0) {
         if (vel_out) {
             vel_out[3 * j + 0] = vx;
             vel_out[3 * j + 1] = vy;
             vel_out[3 * j + 2] = vz;
         }
         if (ADVECT) {
+            // front tracking (Sec. 2.3): r <- r + rdot (dt = 1) in FP64
+            px += (double)vx;
+            py += (double)vy;
+            pz += (double)vz;
+            c.rx[j] = px;
+            c.ry[j] = py;
+            c.rz[j] = pz;
             c.node_vel[j] = make_float4(vx, vy, vz, 0.f);
-            const double nxp = c.rx[j] + (double)vx, nyp = c.ry[j] + (double)vy, nzp = c.rz[j] + (double)vz;
-            c.rx[j] = nxp;
-            c.ry[j] = nyp;
-            c.rz[j] = nzp;
             c.bead_pending[c.node_bead[j]] = 1;
             const float sp2 = vx * vx + vy * vy + vz * vz;
-            if (!isfinite(sp2) || !isfinite(nxp + nyp + nzp)) atomicOr(&c.ctl->err, ERR_NONFINITE);
+            if (!isfinite(sp2) || !isfinite(px + py + pz)) atomicOr(&c.ctl->err, ERR_NONFINITE);
             else if (sp2 > 0.01f) atomicOr(&c.ctl->err, ERR_UNSTABLE);
         }
+    }
+    if (ADVECT && mark_parity >= 0) {
+        // tiles of the moved node's stencil, for the next step: lane l marks plane z = oz' + l
+        const int gbase = (threadIdx.x & 31) & ~(KW - 1);
+        px = __shfl_sync(0xffffffffu, px, gbase);
+        py = __shfl_sync(0xffffffffu, py, gbase);
+        pz = __shfl_sync(0xffffffffu, pz, gbase);
+        if (active) {
+            float fr;
+            const int ox = stencil_axis(px, nx, KW, fr), oy = stencil_axis(py, ny, KW, fr), oz = stencil_axis(pz, nz, KW, fr);
+            int *marks = c.marks + (size_t)mark_parity * c.n_tiles;
+            const int zz = (oz + l) % nz;
+#pragma unroll
+            for (int dy = 0; dy < KW; ++dy) {
+                const int trow = c.tiles_x * ((oy + dy) % ny + ny * zz);
+                int last = -1;
+#pragma unroll
+                for (int k = 0; k < KW; ++k) {
+                    const int tile = ((ox + k) % nx) / c.tile_x + trow;
+                    if (tile != last && marks[tile] == 0 && atomicExch(&marks[tile], 1) == 0)
+                        c.tile_list[(size_t)mark_parity * c.n_tiles + atomicAdd(&c.tile_count[mark_parity], 1)] = tile;
+                    last = tile;
+                }
+            }
+        }
+    }
+}
+
+// Mark the tiles touched by the node stencils (parity p): KW^2 threads per
+// node, one per (y, z) stencil row; a tile is appended to the list by the
+// thread that flips its mark from 0 to 1.
+template <int KW>
+__global__ void __launch_bounds__(INT_TPB) k_ib_mark(const DevCtx c, int p) {
+    constexpr int ROWS = KW * KW;
+    const int gt = blockIdx.x * INT_TPB + threadIdx.x;
+    const int j = gt / ROWS, row = gt % ROWS;
+    if (j >= c.n_nodes) return;
+    float fr;
+    const int ox = stencil_axis(c.rx[j], c.nx, KW, fr);
+    const int oy = stencil_axis(c.ry[j], c.ny, KW, fr);
+    const int oz = stencil_axis(c.rz[j], c.nz, KW, fr);
+    const int yy = (oy + row % KW) % c.ny, zz = (oz + row / KW) % c.nz;
+    int *marks = c.marks + (size_t)p * c.n_tiles;
+    int last = -1;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        const int tile = ((ox + k) % c.nx) / c.tile_x + c.tiles_x * (yy + c.ny * zz);
+        if (tile != last && marks[tile] == 0 && atomicExch(&marks[tile], 1) == 0)
+            c.tile_list[(size_t)p * c.n_tiles + atomicAdd(&c.tile_count[p], 1)] = tile;
+        last = tile;
+    }
+}
+
+// Unmark parity p's listed tiles and empty its list; with `advance` also
+// count the step as finished (the step counter feeds the drive).
+__global__ void __launch_bounds__(256) k_ib_clear_marks(const DevCtx c, int p, int advance) {
+    const int n = c.tile_count[p];
+    const int *list = c.tile_list + (size_t)p * c.n_tiles;
+    int *marks = c.marks + (size_t)p * c.n_tiles;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) marks[list[k]] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c.tile_count[p] = 0;
+        if (advance) c.ctl->step += 1;
     }
 }
 
@@ -421,18 +533,32 @@ cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, cudaStream_t s) {
+cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, int mark_parity, cudaStream_t s) {
     if (c.n_nodes == 0) return cudaSuccess;
-    const int rows = kernel == LBIB_LINEAR2 ? 4 : 16;
-    const long long threads = (long long)c.n_nodes * rows;
+    const int lanes = kernel == LBIB_LINEAR2 ? 2 : 4;
+    const long long threads = (long long)c.n_nodes * lanes;
     const int blocks = (int)((threads + INT_TPB - 1) / INT_TPB);
     if (kernel == LBIB_LINEAR2) {
-        if (advect) k_ib_interp<2, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
-        else k_ib_interp<2, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
+        if (advect) k_ib_interp<2, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out, mark_parity);
+        else k_ib_interp<2, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out, -1);
     } else {
-        if (advect) k_ib_interp<4, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
-        else k_ib_interp<4, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out);
+        if (advect) k_ib_interp<4, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out, mark_parity);
+        else k_ib_interp<4, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out, -1);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_mark(const DevCtx &c, int kernel, int parity, cudaStream_t s) {
+    if (c.n_nodes == 0) return cudaSuccess;
+    const int rows = kernel == LBIB_LINEAR2 ? 4 : 16;
+    const int blocks = (int)(((long long)c.n_nodes * rows + INT_TPB - 1) / INT_TPB);
+    if (kernel == LBIB_LINEAR2) k_ib_mark<2><<<blocks, INT_TPB, 0, s>>>(c, parity);
+    else k_ib_mark<4><<<blocks, INT_TPB, 0, s>>>(c, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_clear_marks(const DevCtx &c, int parity, bool advance, cudaStream_t s) {
+    k_ib_clear_marks<<<1, 256, 0, s>>>(c, parity, advance ? 1 : 0);
     return cudaGetLastError();
 }
 

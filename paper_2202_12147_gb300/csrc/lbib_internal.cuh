@@ -86,6 +86,7 @@ struct DevCtx {
     long long Npad;   // population plane stride
     int n_tiles;
     int tile_x, tiles_x;  // cells per tile along x, tiles per row
+    int marked_grid;      // persistent grid of the marked-tile fluid kernel
     float tau, omega, rho0;
     float g[3];
     int has_g;
@@ -97,7 +98,10 @@ struct DevCtx {
     float4 *F;                 // force density per cell (float atomics)
     unsigned long long *Fdet;  // 3 x Npad fixed-point force (deterministic mode)
     float4 *U;                 // velocity (x, y, z, rho) per cell
-    unsigned char *flags;      // one byte per LB tile (tile = x / tile_x + tiles_x * (y + ny * z))
+    int *marks;                // [2][n_tiles]: tile touched by a node stencil, per step parity
+                               // (tile = x / tile_x + tiles_x * (y + ny * z))
+    int *tile_list;            // [2][n_tiles]: the marked tiles of each parity, in marking order
+    int *tile_count;           // [2]: entries in each list
     double *rx, *ry, *rz;      // node positions (SoA)
     float4 *node_force;        // f^tot per node
     float4 *node_vel;          // interpolated velocity per node
@@ -155,13 +159,16 @@ void set_last_error(const char *msg);
 
 // ---------------------------------------------------------------- launchers
 // LB (lb_kernels.cu)
-cudaError_t launch_lb_step(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
+cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
+cudaError_t launch_lb_marked(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
 cudaError_t launch_lb_macros(const DevCtx &c, int storage, bool odd, float *rho, float *u, cudaStream_t s);
 // IB (ib_kernels.cu)
 cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s);
 cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s);
-cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, cudaStream_t s);
+cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, int mark_parity, cudaStream_t s);
 cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s);
 cudaError_t launch_bead_init(const DevCtx &c, cudaStream_t s);
+cudaError_t launch_ib_mark(const DevCtx &c, int kernel, int parity, cudaStream_t s);
+cudaError_t launch_ib_clear_marks(const DevCtx &c, int parity, bool advance, cudaStream_t s);
 
 }  // namespace lbib

@@ -197,6 +197,12 @@ class Simulation:
         check(self.L.lb_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def marked_cells(self):
+        """Cells in the tiles marked for the next step (updated with the force field)."""
+        n = ctypes.c_longlong()
+        check(self.L.lb_marked_cells(self.ctx, ctypes.byref(n)))
+        return n.value
+
     def close(self):
         if self.ctx:
             self.L.lb_destroy(self.ctx)
