@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the FP16/BF16-storage lines")
     return ap.parse_args()
 
 
@@ -238,6 +240,43 @@ def run_ours(a):
     achieved = bytes_per_launch / lb_avg_s / 1e9
     launches = a.steps * len(sims) * 7  # per box-step: main fluid + prepare, spread, marked fluid, interp, clear, mark
 
+    variants = None
+    if a.variants and a.storage == "f32":
+        # the same workload with 16-bit population storage (FP32 collision)
+        for s in sims:
+            s.close()
+        variants = {}
+        for st in ("f16", "bf16"):
+            vs = [Simulation(b.dims, asm, tau=b.tau, rho0=b.rho0, storage=st) for b, asm in zip(boxes, asms)]
+            for s in vs:
+                s.lb_step(a.warmup)
+            for s in vs:
+                s.profile(True)
+            barrier()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for s in vs:
+                s.lb_step(a.steps)
+            f1.record(stream)
+            barrier()
+            vms = f0.elapsed_time(f1)
+            t_lb, n_lb = 0.0, 0
+            for s in vs:
+                t, n = s.profile_read()
+                t_lb += t
+                n_lb += n
+                s.sync()
+            vmarked = statistics.mean(s.marked_cells() for s in vs)
+            vbytes = (N - vmarked) * 19 * 2 * 2
+            vach = vbytes / (t_lb / n_lb / 1e3) / 1e9
+            variants[st] = {"value": ws * cells_per_step * a.steps / (vms / 1e3) / 1e6, "unit": "MLUPS",
+                            "ms_per_step": vms / a.steps, "speedup_vs_f32": ms / vms,
+                            "roofline": {"achieved": vach, "peak": peak, "frac": vach / peak,
+                                         "avg_launch_us": t_lb / n_lb * 1e3, "bytes_per_launch": vbytes}}
+            for s in vs:
+                s.close()
+        sims = []
+
     e2e = None
     if not a.no_e2e:
         # End to end through the public API: structure upload from host arrays
@@ -293,6 +332,7 @@ def run_ours(a):
                          "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
                          "launches": lb_n, "cells_per_launch": N - marked},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -1,7 +1,9 @@
 // C ABI of liblbib (declared in include/lbib.h): argument checks, the layout
 // of the caller buffers, mesh preprocessing, CUDA-graph capture of the step
 // and the host-side accessors.
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -68,7 +70,7 @@ struct Layout {
     size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0;
     // aux
     size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
-           obead = 0, oswim = 0, obd = 0, obe = 0, obp = 0, octl = 0, osws = 0, oxcm = 0;
+           obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0;
 };
 
 bool valid_params(const lb_params *p, std::string &why) {
@@ -175,7 +177,6 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     L.oswim = o; o += up((size_t)S * sizeof(SwimDev) + 16);
     L.obd = o; o += up((size_t)B * 32 + 32);
     L.obe = o; o += up((size_t)B * 16 + 16);
-    L.obp = o; o += up((size_t)B * 4 + 4);
     L.octl = o; o += up(sizeof(Control));
     L.osws = o; o += up((size_t)S * sizeof(lbib_swimmer_state) + 16);
     L.oxcm = o; o += up((size_t)S * 24 + 24);
@@ -254,20 +255,16 @@ cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t sm, cudaStream_t si
     if ((e = launch_ib_gather_spread(c->d, c->p.kernel, sib)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(sib, c->e_main, 0)) != cudaSuccess) return e;  // previous step's main update
     if ((e = cudaEventRecord(c->e_main, sm)) != cudaSuccess) return e;
-    // the previous step's marks (other parity) are no longer read by anyone
-    if ((e = launch_ib_clear_marks(c->d, 1 - p, true, sib)) != cudaSuccess) return e;
     if ((e = launch_lb_marked(c->d, c->p.storage, c->p.forcing, odd, sib)) != cudaSuccess) return e;
     if ((e = launch_ib_interp(c->d, c->p.kernel, true, nullptr, 1 - p, sib)) != cudaSuccess) return e;
     return cudaEventRecord(c->e_ib, sib);
 }
 
-// Re-mark the tiles for the current positions (after they are set from outside).
+// Stamp the tiles of the current positions for the current step (after the
+// positions are set from outside); tiles stamped before stay listed, harmlessly.
 cudaError_t remark(lbib_ctx *c) {
-    cudaError_t e;
     if (c->n_nodes == 0) return cudaSuccess;
-    if ((e = launch_ib_clear_marks(c->d, 0, false, c->user)) != cudaSuccess) return e;
-    if ((e = launch_ib_clear_marks(c->d, 1, false, c->user)) != cudaSuccess) return e;
-    return launch_ib_mark(c->d, c->p.kernel, (int)(c->step & 1), c->user);
+    return launch_ib_mark(c->d, c->p.kernel, c->user);
 }
 
 int check_device_errors(lbib_ctx *c) {
@@ -277,6 +274,8 @@ int check_device_errors(lbib_ctx *c) {
     if (e & ERR_NONFINITE) return fail(LBIB_ENONFINITE, "non-finite density, velocity or node position");
     if (e & ERR_UNSTABLE) return fail(LBIB_EUNSTABLE, "a node moved faster than 0.1 lattice units per step");
     if (e & ERR_TIMEOUT) return fail(LBIB_ETIMEOUT, "a bounded device wait gave up");
+    if (e & ERR_MARK)
+        return fail(LBIB_EUNSTABLE, "a node left the region marked around its bead (membrane deformed by more than 1 lattice unit)");
     return LBIB_OK;
 }
 
@@ -352,7 +351,22 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         beads[bi].node_start = bd.node_start;
         beads[bi].node_count = bd.node_count;
         beads[bi].inv_count = (float)(1.0 / bd.node_count);
-        beads[bi].pad[0] = beads[bi].pad[1] = beads[bi].pad[2] = 0;
+        beads[bi].pad[0] = beads[bi].pad[1] = 0;
+        {
+            // reach: largest rest distance of a node from the bead centre, plus a
+            // margin of 1 lattice unit for membrane deformation
+            double m[3] = {0.0, 0.0, 0.0};
+            for (int j = bd.node_start; j < bd.node_start + bd.node_count; ++j)
+                for (int a = 0; a < 3; ++a) m[a] += s->rest_nodes[3 * j + a];
+            for (int a = 0; a < 3; ++a) m[a] /= bd.node_count;
+            double r2 = 0.0;
+            for (int j = bd.node_start; j < bd.node_start + bd.node_count; ++j) {
+                double q = 0.0;
+                for (int a = 0; a < 3; ++a) q += (s->rest_nodes[3 * j + a] - m[a]) * (s->rest_nodes[3 * j + a] - m[a]);
+                r2 = std::max(r2, q);
+            }
+            beads[bi].reach = (float)(std::sqrt(r2) + 1.0);
+        }
         for (int j = bd.node_start; j < bd.node_start + bd.node_count; ++j) nbead[j] = bi;
         for (int t = bd.tri_start; t < bd.tri_start + bd.tri_count; ++t) {
             const int *v = s->tris + 3 * t;
@@ -421,6 +435,14 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.n_tiles = L.n_tiles;
     d.tile_x = L.tile_x;
     d.tiles_x = L.tiles_x;
+    // adjacent cells per fluid thread: four for 16-bit storage, two for FP32,
+    // when the rows split into tiles of that many cells (LBIB_CELLS_PER_THREAD caps it)
+    {
+        int cpt = p->storage == LBIB_F32 ? 2 : 4;
+        cpt = std::min(cpt, env_int("LBIB_CELLS_PER_THREAD", 4));
+        while (cpt > 1 && (L.tile_x % cpt || p->nx % cpt)) cpt /= 2;
+        d.cells_per_thread = cpt < 1 ? 1 : (cpt == 3 ? 2 : cpt);
+    }
 
     d.tau = (float)p->tau;
     d.omega = (float)(1.0 / p->tau);
@@ -456,7 +478,6 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.swims = (const SwimDev *)(A + L.oswim);
     d.bead_R = (double *)(A + L.obd);
     d.bead_ext = (float4 *)(A + L.obe);
-    d.bead_pending = (int *)(A + L.obp);
     d.ctl = (Control *)(A + L.octl);
     d.sw_state = (lbib_swimmer_state *)(A + L.osws);
     d.xcm0 = (double *)(A + L.oxcm);
@@ -474,11 +495,15 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return bail(fail(LBIB_ECUDA, "querying the device failed"));
         // persistent grid of the marked-tile fluid kernel: one block per SM
-        d.marked_grid = env_int("LBIB_MARKED_GRID", sms);
+        d.marked_grid = sms;
     }
     // rest state: all deviations zero, fields, marks and lists zero
     if (cudaMemsetAsync(b->pops, 0, L.bytes[0], u) != cudaSuccess || cudaMemsetAsync(b->fields, 0, L.bytes[1], u) != cudaSuccess ||
-        cudaMemsetAsync(b->aux, 0, L.bytes[2], u) != cudaSuccess)
+        cudaMemsetAsync(b->aux, 0, L.bytes[2], u) != cudaSuccess ||
+        // stamps -1 (never marked); generations a different negative value, so no
+        // tile counts as marked until a step stamps it
+        cudaMemsetAsync(d.marks, 0xff, 2 * (size_t)L.n_tiles * 4, u) != cudaSuccess ||
+        cudaMemsetAsync((char *)d.ctl + offsetof(Control, gen), 0xfe, sizeof(int) * 2, u) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "cudaMemsetAsync failed"));
     std::vector<double> sx(M), sy(M), sz(M);
     for (int j = 0; j < M; ++j) {
@@ -495,9 +520,17 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
               h2d((void *)d.beads, beads.data(), B * sizeof(BeadDev)) && h2d((void *)d.swims, swims.data(), S * sizeof(SwimDev));
     if (!ok) return bail(fail(LBIB_ECUDA, "uploading mesh tables failed"));
     if (launch_bead_init(d, u) != cudaSuccess || launch_swimmer_state(d, true, u) != cudaSuccess ||
-        launch_ib_mark(d, p->kernel, 0, u) != cudaSuccess)
+        launch_ib_mark(d, p->kernel, u) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "bead initialisation launch failed"));
     if (cudaStreamSynchronize(u) != cudaSuccess) return bail(fail(LBIB_ECUDA, "init synchronisation failed"));
+    if (M > 0) {
+        // size the marked-tile kernel's grid to the tiles the stencils mark now,
+        // with room for the swimmers to move into new tiles (more are handled in a loop)
+        int cnt = 0;
+        if (cudaMemcpy(&cnt, d.tile_count, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(LBIB_ECUDA, "reading the marked-tile count failed"));
+        d.marked_grid = env_int("LBIB_MARKED_GRID", std::min(L.n_tiles, std::max(32, cnt + cnt / 4 + 16)));
+    }
 
     // streams and events of the two-stream step; the IB stream gets the
     // highest priority so its small kernels are scheduled between fluid blocks

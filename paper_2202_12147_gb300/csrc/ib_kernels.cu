@@ -13,21 +13,21 @@
 //                      per node spread it over the KW^3 stencil (Sec. 2.3,
 //                      Eq. spreading) with vector float atomics, or 64-bit
 //                      fixed-point atomics (bitwise reproducible).
-//   k_ib_mark          marks (and lists) the fluid tiles the stencils of the
-//                      current node positions touch, for one step parity;
-//   k_ib_clear_marks   unmarks a parity's listed tiles and empties its list.
+//   k_ib_mark          stamps (and lists) the fluid tiles the node stencils
+//                      touch with the step number (the advecting interpolation
+//                      does the same for the next step).
 //   k_ib_interp        KW threads per node gather u over the stencil
 //                      (Sec. 2.3, Eq. interpolation), reduce with shuffles in
 //                      a fixed order, move the node r += rdot in FP64 (front
-//                      tracking, Sec. 2.3) and mark the next step's tiles.
+//                      tracking, Sec. 2.3) and stamp the next step's tiles.
 //
 // FP64 on this GPU issues at a small fraction of the FP32 rate, so it is kept
 // to what needs it: node positions and their update, the bead centres, the
 // metric difference of the membrane element, and the argument of the drive.
 // The bead centre R_b = mean of the bead's nodes (Fig. 1 caption) is kept up
 // to date incrementally: after an advection by node velocities v_j,
-// R_b += mean_j v_j (the mean is linear), folded in by the next step's
-// swimmer block; k_bead_init recomputes it from the positions whenever they
+// R_b += mean_j v_j (the mean is linear), folded in by the last block of the
+// interpolation; k_bead_init recomputes it from the positions whenever they
 // are set from outside.
 //
 // Membrane element.  With rest edge metric G = D^T D, current metric
@@ -72,105 +72,48 @@ __device__ __forceinline__ void block_sum3(T &a, T &b, T &c, T *sm /* 3*32 */) {
     __syncthreads();
 }
 
-// Swimmer block: fold the last advection into the bead centres, then the
-// drive (Sec. 2.2, driving-force equation) and springs (Sec. 2.2).  The
-// three beads are reduced together: each thread strides over all of the
-// swimmer's nodes with its loads unrolled, keeping one partial sum per bead.
+// Swimmer block: drive (Sec. 2.2, driving-force equation) and springs
+// (Sec. 2.2) from the bead centres, stored as the per-node share.
 __device__ void swimmer_forces(const DevCtx &c, int s) {
-    __shared__ float smf[9][32];
-    __shared__ double sR[3][3];
+    if (threadIdx.x != 0) return;
     const SwimDev sw = c.swims[s];
-    BeadDev bd[3];
-    int pend[3];
+    double R[3][3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        bd[q] = c.beads[sw.bead[q]];
-        pend[q] = c.bead_pending[sw.bead[q]];
+        const double *r = c.bead_R + 4 * sw.bead[q];
+        R[q][0] = r[0];
+        R[q][1] = r[1];
+        R[q][2] = r[2];
     }
-    float acc[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    if (pend[0] | pend[1] | pend[2]) {  // uniform across the block
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            if (!pend[q]) continue;
-            const int j0 = bd[q].node_start, n = bd[q].node_count;
-            int k = threadIdx.x;
-            for (; k + 3 * (int)blockDim.x < n; k += 4 * blockDim.x) {
-                const float4 v0 = c.node_vel[j0 + k], v1 = c.node_vel[j0 + k + blockDim.x];
-                const float4 v2 = c.node_vel[j0 + k + 2 * blockDim.x], v3 = c.node_vel[j0 + k + 3 * blockDim.x];
-                acc[q][0] += (v0.x + v1.x) + (v2.x + v3.x);
-                acc[q][1] += (v0.y + v1.y) + (v2.y + v3.y);
-                acc[q][2] += (v0.z + v1.z) + (v2.z + v3.z);
-            }
-            for (; k < n; k += blockDim.x) {
-                const float4 v = c.node_vel[j0 + k];
-                acc[q][0] += v.x;
-                acc[q][1] += v.y;
-                acc[q][2] += v.z;
-            }
-        }
-        // fixed-order block reduction of the 9 partial sums
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc[q][a] += __shfl_xor_sync(0xffffffffu, acc[q][a], o);
-        const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        if ((threadIdx.x & 31) == 0)
-            for (int q = 0; q < 3; ++q)
-                for (int a = 0; a < 3; ++a) smf[3 * q + a][w] = acc[q][a];
-        __syncthreads();
-        if (threadIdx.x == 0)
-            for (int q = 0; q < 3; ++q)
-                for (int a = 0; a < 3; ++a) {
-                    float t = 0.f;
-                    for (int k = 0; k < nw; ++k) t += smf[3 * q + a][k];
-                    acc[q][a] = t;
-                }
+    // drive: sin(2 pi (t / T + phase / 2 pi)), argument reduced in FP64
+    const double tt = (double)c.ctl->step * sw.inv_period;
+    float fd[3];
+    for (int q = 0; q < 3; q += 2) {
+        const double x = tt + sw.phase_turns[q];
+        fd[q] = sw.amp[q] * sinpif(2.0f * (float)(x - floor(x)));
     }
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 3; ++q) {
-            double *R = c.bead_R + 4 * sw.bead[q];
-            if (pend[q]) {
-                R[0] += (double)(acc[q][0] * bd[q].inv_count);
-                R[1] += (double)(acc[q][1] * bd[q].inv_count);
-                R[2] += (double)(acc[q][2] * bd[q].inv_count);
-                c.bead_pending[sw.bead[q]] = 0;
-            }
-            sR[q][0] = R[0];
-            sR[q][1] = R[1];
-            sR[q][2] = R[2];
-        }
-        // drive: sin(2 pi (t / T + phase / 2 pi)), argument reduced in FP64
-        const double tt = (double)c.ctl->step * sw.inv_period;
-        float fd[3];
-        for (int q = 0; q < 3; q += 2) {
-            const double x = tt + sw.phase_turns[q];
-            fd[q] = sw.amp[q] * sinpif(2.0f * (float)(x - floor(x)));
-        }
-        if (sw.balance) {
-            fd[1] = -fd[0] - fd[2];
-        } else {
-            const double x = tt + sw.phase_turns[1];
-            fd[1] = sw.amp[1] * sinpif(2.0f * (float)(x - floor(x)));
-        }
-        // springs: |d| - L = (|d|^2 - L^2) / (|d| + L), the difference in FP64
-        float fs[3][3];
-        for (int q = 0; q < 3; q += 2) {
-            const double dx = sR[q][0] - sR[1][0], dy = sR[q][1] - sR[1][1], dz = sR[q][2] - sR[1][2];
-            const double n2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            const float nf = sqrtf((float)n2);
-            const float stretch = (float)(n2 - sw.L2) / (nf + (float)sw.L);
-            const float m = -(float)sw.k * stretch / nf;
-            fs[q][0] = m * (float)dx;
-            fs[q][1] = m * (float)dy;
-            fs[q][2] = m * (float)dz;
-        }
-        for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
-        for (int q = 0; q < 3; ++q) {
-            const float inv = bd[q].inv_count;
-            c.bead_ext[sw.bead[q]] = make_float4((fd[q] + fs[q][0]) * inv, fs[q][1] * inv, fs[q][2] * inv, 0.f);
-        }
+    if (sw.balance) {
+        fd[1] = -fd[0] - fd[2];
+    } else {
+        const double x = tt + sw.phase_turns[1];
+        fd[1] = sw.amp[1] * sinpif(2.0f * (float)(x - floor(x)));
+    }
+    // springs: |d| - L = (|d|^2 - L^2) / (|d| + L), the difference in FP64
+    float fs[3][3];
+    for (int q = 0; q < 3; q += 2) {
+        const double dx = R[q][0] - R[1][0], dy = R[q][1] - R[1][1], dz = R[q][2] - R[1][2];
+        const double n2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const float nf = sqrtf((float)n2);
+        const float stretch = (float)(n2 - sw.L2) / (nf + (float)sw.L);
+        const float m = -(float)sw.k * stretch / nf;
+        fs[q][0] = m * (float)dx;
+        fs[q][1] = m * (float)dy;
+        fs[q][2] = m * (float)dz;
+    }
+    for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
+    for (int q = 0; q < 3; ++q) {
+        const float inv = c.beads[sw.bead[q]].inv_count;
+        c.bead_ext[sw.bead[q]] = make_float4((fd[q] + fs[q][0]) * inv, fs[q][1] * inv, fs[q][2] * inv, 0.f);
     }
 }
 
@@ -204,6 +147,9 @@ __device__ void triangle_forces(const DevCtx &c, int t) {
 }
 
 __global__ void __launch_bounds__(PREP_TPB) k_ib_prepare(const DevCtx c) {
+    // the other parity's tile list (the previous step's) is consumed: empty it
+    // for the marks of the next step
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.tile_count[(c.ctl->step + 1) & 1] = 0;
     if ((int)blockIdx.x < c.n_swimmers) {
         swimmer_forces(c, blockIdx.x);
         return;
@@ -230,7 +176,6 @@ __global__ void __launch_bounds__(PREP_TPB) k_bead_init(const DevCtx c) {
         R[0] = a / bd.node_count;
         R[1] = bb / bd.node_count;
         R[2] = cc / bd.node_count;
-        c.bead_pending[b] = 0;
     }
 }
 
@@ -279,6 +224,9 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
     __syncthreads();
     constexpr int ROWS = KW * KW;
     const int nx = c.nx, ny = c.ny, nz = c.nz;
+    const int stamp = (int)c.ctl->step;
+    const int *marks = c.marks + (size_t)(stamp & 1) * c.n_tiles;
+    bool unmarked = false;
     for (int task = threadIdx.x; task < nloc * ROWS; task += GS_TPB) {
         const int ln = task / ROWS, row = task % ROWS;
         const int dy = row % KW, dz = row / KW;
@@ -287,6 +235,9 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
         const float wyz = sw[ln][1][dy] * sw[ln][2][dz];
         const float4 f = sf[ln];
         const unsigned rowbase = (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz);
+        // the marked region of this step must cover every cell the stencil touches
+        const int trow = c.tiles_x * (yy + ny * zz);
+        unmarked |= (marks[ox / c.tile_x + trow] != stamp) | (marks[((ox + KW - 1) % nx) / c.tile_x + trow] != stamp);
 #pragma unroll
         for (int k = 0; k < KW; ++k) {
             const int xx = (ox + k) % nx;
@@ -301,6 +252,76 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
             }
         }
     }
+    if (__any_sync(0xffffffffu, unmarked) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_MARK);
+}
+
+// Fold an advection into the bead centres: R_b += mean_j v_j (the mean is
+// linear, so this keeps R_b the centre of mass of its nodes, Fig. 1 caption).
+// One warp per bead, fixed-order sums.  Run by one block.
+__device__ void fold_bead_velocities(const DevCtx &c) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int b = w; b < c.n_beads; b += nw) {
+        const BeadDev bd = c.beads[b];
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int j = bd.node_start + l; j < bd.node_start + bd.node_count; j += 32) {
+            const float4 v = c.node_vel[j];
+            sx += v.x;
+            sy += v.y;
+            sz += v.z;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        if (l == 0) {
+            double *R = c.bead_R + 4 * b;
+            R[0] += (double)(sx * bd.inv_count);
+            R[1] += (double)(sy * bd.inv_count);
+            R[2] += (double)(sz * bd.inv_count);
+        }
+    }
+}
+
+// Stamp, with step number `stamp`, the tiles of the KW x KW stencil rows of
+// plane z = oz + l of a node whose stencil origin is (ox, oy, oz); a tile is
+// appended to its parity's list by the thread that changes its stamp.
+template <int KW>
+__device__ __forceinline__ void mark_stencil_plane(const DevCtx &c, int ox, int oy, int oz, int l, int stamp) {
+    const int p = stamp & 1;
+    int *marks = c.marks + (size_t)p * c.n_tiles;
+    const int zz = (oz + l) % c.nz;
+    const int t0 = ox / c.tile_x, t1 = ((ox + KW - 1) % c.nx) / c.tile_x;
+    int tile[2 * KW];
+    int old[2 * KW];
+#pragma unroll
+    for (int dy = 0; dy < KW; ++dy) {
+        const int trow = c.tiles_x * ((oy + dy) % c.ny + c.ny * zz);
+        tile[2 * dy] = t0 + trow;
+        tile[2 * dy + 1] = t1 + trow;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * KW; ++k) old[k] = marks[tile[k]];
+#pragma unroll
+    for (int k = 0; k < 2 * KW; ++k) {
+        if ((k & 1) && tile[k] == tile[k - 1]) continue;  // both ends of the row in one tile
+        if (old[k] != stamp && atomicExch(&marks[tile[k]], stamp) != stamp)
+            c.tile_list[(size_t)p * c.n_tiles + atomicAdd(&c.tile_count[p], 1)] = tile[k];
+    }
+}
+
+// Stamp the tiles of every node's stencil for the current step (KW lanes per node).
+template <int KW>
+__global__ void __launch_bounds__(INT_TPB) k_ib_mark(const DevCtx c) {
+    const int gt = blockIdx.x * INT_TPB + threadIdx.x;
+    const int j = gt / KW, l = gt % KW;
+    if (j >= c.n_nodes) return;
+    float fr;
+    const int ox = stencil_axis(c.rx[j], c.nx, KW, fr), oy = stencil_axis(c.ry[j], c.ny, KW, fr),
+              oz = stencil_axis(c.rz[j], c.nz, KW, fr);
+    mark_stencil_plane<KW>(c, ox, oy, oz, l, (int)c.ctl->step);
+    if (gt == 0) c.ctl->gen[c.ctl->step & 1] = (int)c.ctl->step;
 }
 
 // KW lanes per node, lane l gathering the KW x KW cells of stencil plane
@@ -366,14 +387,14 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
             c.ry[j] = py;
             c.rz[j] = pz;
             c.node_vel[j] = make_float4(vx, vy, vz, 0.f);
-            c.bead_pending[c.node_bead[j]] = 1;
             const float sp2 = vx * vx + vy * vy + vz * vz;
             if (!isfinite(sp2) || !isfinite(px + py + pz)) atomicOr(&c.ctl->err, ERR_NONFINITE);
             else if (sp2 > 0.01f) atomicOr(&c.ctl->err, ERR_UNSTABLE);
         }
     }
     if (ADVECT && mark_parity >= 0) {
-        // tiles of the moved node's stencil, for the next step: lane l marks plane z = oz' + l
+        // stamp the tiles of the moved node's stencil for the next step
+        const int next = (int)c.ctl->step + 1;
         const int gbase = (threadIdx.x & 31) & ~(KW - 1);
         px = __shfl_sync(0xffffffffu, px, gbase);
         py = __shfl_sync(0xffffffffu, py, gbase);
@@ -381,60 +402,24 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
         if (active) {
             float fr;
             const int ox = stencil_axis(px, nx, KW, fr), oy = stencil_axis(py, ny, KW, fr), oz = stencil_axis(pz, nz, KW, fr);
-            int *marks = c.marks + (size_t)mark_parity * c.n_tiles;
-            const int zz = (oz + l) % nz;
-#pragma unroll
-            for (int dy = 0; dy < KW; ++dy) {
-                const int trow = c.tiles_x * ((oy + dy) % ny + ny * zz);
-                int last = -1;
-#pragma unroll
-                for (int k = 0; k < KW; ++k) {
-                    const int tile = ((ox + k) % nx) / c.tile_x + trow;
-                    if (tile != last && marks[tile] == 0 && atomicExch(&marks[tile], 1) == 0)
-                        c.tile_list[(size_t)mark_parity * c.n_tiles + atomicAdd(&c.tile_count[mark_parity], 1)] = tile;
-                    last = tile;
-                }
+            mark_stencil_plane<KW>(c, ox, oy, oz, l, next);
+        }
+        // the last block to finish folds the step's velocities into the bead
+        // centres and closes the step (a completion count, no waiting)
+        __shared__ int s_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&c.ctl->done, 1) == (int)gridDim.x - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            fold_bead_velocities(c);
+            if (threadIdx.x == 0) {
+                c.ctl->done = 0;
+                c.ctl->gen[next & 1] = next;
+                c.ctl->step = next;
             }
         }
-    }
-}
-
-// Mark the tiles touched by the node stencils (parity p): KW^2 threads per
-// node, one per (y, z) stencil row; a tile is appended to the list by the
-// thread that flips its mark from 0 to 1.
-template <int KW>
-__global__ void __launch_bounds__(INT_TPB) k_ib_mark(const DevCtx c, int p) {
-    constexpr int ROWS = KW * KW;
-    const int gt = blockIdx.x * INT_TPB + threadIdx.x;
-    const int j = gt / ROWS, row = gt % ROWS;
-    if (j >= c.n_nodes) return;
-    float fr;
-    const int ox = stencil_axis(c.rx[j], c.nx, KW, fr);
-    const int oy = stencil_axis(c.ry[j], c.ny, KW, fr);
-    const int oz = stencil_axis(c.rz[j], c.nz, KW, fr);
-    const int yy = (oy + row % KW) % c.ny, zz = (oz + row / KW) % c.nz;
-    int *marks = c.marks + (size_t)p * c.n_tiles;
-    int last = -1;
-#pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        const int tile = ((ox + k) % c.nx) / c.tile_x + c.tiles_x * (yy + c.ny * zz);
-        if (tile != last && marks[tile] == 0 && atomicExch(&marks[tile], 1) == 0)
-            c.tile_list[(size_t)p * c.n_tiles + atomicAdd(&c.tile_count[p], 1)] = tile;
-        last = tile;
-    }
-}
-
-// Unmark parity p's listed tiles and empty its list; with `advance` also
-// count the step as finished (the step counter feeds the drive).
-__global__ void __launch_bounds__(256) k_ib_clear_marks(const DevCtx c, int p, int advance) {
-    const int n = c.tile_count[p];
-    const int *list = c.tile_list + (size_t)p * c.n_tiles;
-    int *marks = c.marks + (size_t)p * c.n_tiles;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) marks[list[k]] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        c.tile_count[p] = 0;
-        if (advance) c.ctl->step += 1;
     }
 }
 
@@ -548,19 +533,15 @@ cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *ve
     return cudaGetLastError();
 }
 
-cudaError_t launch_ib_mark(const DevCtx &c, int kernel, int parity, cudaStream_t s) {
+cudaError_t launch_ib_mark(const DevCtx &c, int kernel, cudaStream_t s) {
     if (c.n_nodes == 0) return cudaSuccess;
-    const int rows = kernel == LBIB_LINEAR2 ? 4 : 16;
-    const int blocks = (int)(((long long)c.n_nodes * rows + INT_TPB - 1) / INT_TPB);
-    if (kernel == LBIB_LINEAR2) k_ib_mark<2><<<blocks, INT_TPB, 0, s>>>(c, parity);
-    else k_ib_mark<4><<<blocks, INT_TPB, 0, s>>>(c, parity);
+    const int lanes = kernel == LBIB_LINEAR2 ? 2 : 4;
+    const int blocks = (int)(((long long)c.n_nodes * lanes + INT_TPB - 1) / INT_TPB);
+    if (kernel == LBIB_LINEAR2) k_ib_mark<2><<<blocks, INT_TPB, 0, s>>>(c);
+    else k_ib_mark<4><<<blocks, INT_TPB, 0, s>>>(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ib_clear_marks(const DevCtx &c, int parity, bool advance, cudaStream_t s) {
-    k_ib_clear_marks<<<1, 256, 0, s>>>(c, parity, advance ? 1 : 0);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s) {
     if (c.n_swimmers == 0) return cudaSuccess;

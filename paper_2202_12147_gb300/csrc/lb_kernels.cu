@@ -23,8 +23,8 @@
 //
 // Immersed-boundary coupling: the cells are grouped in tiles (runs of up to
 // tile_x cells along x of one (y, z) row).  Before a step, the tiles that the
-// nodes' delta-kernel stencils touch are marked and listed (one mark array and
-// one list per step parity).  k_lb_main updates every unmarked tile and never
+// nodes' delta-kernel stencils touch are stamped with the step number and
+// listed (one stamp array and one list per step parity).  k_lb_main updates every unmarked tile and never
 // touches the force and velocity fields; k_lb_marked walks the list, reads F
 // there, writes the physical velocity u for the interpolation and clears F.
 // The two kernels cover disjoint cells, so k_lb_main can run while the
@@ -35,11 +35,15 @@ namespace lbib {
 
 template <int S>
 struct Store;
+// ld/st: one value; ld2/st2: two adjacent values from a pair-aligned address
+// (the second index even); m scales deviations to and from the stored format.
 template <>
 struct Store<LBIB_F32> {
     using T = float;
     static __device__ __forceinline__ float ld(const T *p, float) { return *p; }
     static __device__ __forceinline__ void st(T *p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float2 ld2(const T *p, float) { return *reinterpret_cast<const float2 *>(p); }
+    static __device__ __forceinline__ void st2(T *p, float2 v, float) { *reinterpret_cast<float2 *>(p) = v; }
     static constexpr bool scaled = false;
 };
 template <>
@@ -47,6 +51,12 @@ struct Store<LBIB_F16> {
     using T = __half;
     static __device__ __forceinline__ float ld(const T *p, float m) { return __half2float(*p) * m; }
     static __device__ __forceinline__ void st(T *p, float v, float m) { *p = __float2half_rn(v * m); }
+    static __device__ __forceinline__ float2 ld2(const T *p, float m) {
+        return __fmul2_rn(__half22float2(*reinterpret_cast<const __half2 *>(p)), make_float2(m, m));
+    }
+    static __device__ __forceinline__ void st2(T *p, float2 v, float m) {
+        *reinterpret_cast<__half2 *>(p) = __float22half2_rn(__fmul2_rn(v, make_float2(m, m)));
+    }
     static constexpr bool scaled = true;
 };
 template <>
@@ -54,8 +64,21 @@ struct Store<LBIB_BF16> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float ld(const T *p, float m) { return __bfloat162float(*p) * m; }
     static __device__ __forceinline__ void st(T *p, float v, float m) { *p = __float2bfloat16_rn(v * m); }
+    static __device__ __forceinline__ float2 ld2(const T *p, float m) {
+        return __fmul2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p)), make_float2(m, m));
+    }
+    static __device__ __forceinline__ void st2(T *p, float2 v, float m) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(__fmul2_rn(v, make_float2(m, m)));
+    }
     static constexpr bool scaled = true;
 };
+
+// Packed FP32 arithmetic on pairs of cells (two lanes per instruction).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sp2(float s) { return make_float2(s, s); }
 
 // BGK collision with body force on one cell, in deviation form (Sec. 2.1,
 // Eqs. lbe and lbm:equilibrium; physical velocity with F/2).  Opposite
@@ -189,6 +212,276 @@ __device__ __forceinline__ bool lb_cell(const DevCtx &c, unsigned x, unsigned y,
     return isfinite(rho) && isfinite(ux + uy + uz);
 }
 
+// collide_cell on two cells at once, in packed FP32 (same arithmetic).
+template <int FORCING>
+__device__ __forceinline__ void collide_pair(float2 (&d)[Q], const DevCtx &c, bool forced, float2 Fx, float2 Fy, float2 Fz,
+                                             float2 &ux, float2 &uy, float2 &uz, float2 &rho) {
+    float2 drho = d[0], jx = sp2(0.f), jy = sp2(0.f), jz = sp2(0.f);
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) {
+        const float2 sm = add2(d[k], d[k + 1]), df = sub2(d[k], d[k + 1]);
+        drho = add2(drho, sm);
+        if (cx(k)) jx = cx(k) > 0 ? add2(jx, df) : sub2(jx, df);
+        if (cy(k)) jy = cy(k) > 0 ? add2(jy, df) : sub2(jy, df);
+        if (cz(k)) jz = cz(k) > 0 ? add2(jz, df) : sub2(jz, df);
+    }
+    rho = add2(sp2(c.rho0), drho);
+    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    ux = mul2(fma2(sp2(0.5f), Fx, jx), irho);
+    uy = mul2(fma2(sp2(0.5f), Fy, jy), irho);
+    uz = mul2(fma2(sp2(0.5f), Fz, jz), irho);
+    float2 ex = ux, ey = uy, ez = uz;
+    if (FORCING == LBIB_SHAN_CHEN) {
+        ex = mul2(fma2(sp2(c.tau), Fx, jx), irho);
+        ey = mul2(fma2(sp2(c.tau), Fy, jy), irho);
+        ez = mul2(fma2(sp2(c.tau), Fz, jz), irho);
+    }
+    const float2 om = sp2(c.omega);
+    const float2 usq = fma2(ex, ex, fma2(ey, ey, mul2(ez, ez)));
+    const float2 base = sub2(drho, mul2(mul2(sp2(1.5f), rho), usq));
+    const bool guo = FORCING == LBIB_GUO && forced;
+    const float gus = guo ? 1.0f - 0.5f * c.omega : 0.f;
+    const float2 uF3 = guo ? mul2(sp2(3.0f), fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)))) : sp2(0.f);
+    const float2 rho45 = mul2(sp2(4.5f), rho);
+    {
+        float2 post = fma2(om, sub2(mul2(sp2(wgt(0)), base), d[0]), d[0]);
+        if (guo) post = fma2(sp2(-gus * wgt(0)), uF3, post);
+        d[0] = post;
+    }
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) {
+        const float w = wgt(k);
+        float2 cu = sp2(0.f);
+        bool first = true;
+        if (cx(k)) { cu = first ? (cx(k) > 0 ? ex : sub2(cu, ex)) : (cx(k) > 0 ? add2(cu, ex) : sub2(cu, ex)); first = false; }
+        if (cy(k)) { cu = first ? (cy(k) > 0 ? ey : sub2(cu, ey)) : (cy(k) > 0 ? add2(cu, ey) : sub2(cu, ey)); first = false; }
+        if (cz(k)) { cu = first ? (cz(k) > 0 ? ez : sub2(cu, ez)) : (cz(k) > 0 ? add2(cu, ez) : sub2(cu, ez)); first = false; }
+        const float2 ev = mul2(sp2(w), fma2(mul2(rho45, cu), cu, base));
+        const float2 od = mul2(mul2(sp2(3.0f * w), rho), cu);
+        float2 p0 = fma2(om, sub2(add2(ev, od), d[k]), d[k]);
+        float2 p1 = fma2(om, sub2(sub2(ev, od), d[k + 1]), d[k + 1]);
+        if (guo) {
+            float2 cF = sp2(0.f);
+            bool f1 = true;
+            if (cx(k)) { cF = f1 ? (cx(k) > 0 ? Fx : sub2(cF, Fx)) : (cx(k) > 0 ? add2(cF, Fx) : sub2(cF, Fx)); f1 = false; }
+            if (cy(k)) { cF = f1 ? (cy(k) > 0 ? Fy : sub2(cF, Fy)) : (cy(k) > 0 ? add2(cF, Fy) : sub2(cF, Fy)); f1 = false; }
+            if (cz(k)) { cF = f1 ? (cz(k) > 0 ? Fz : sub2(cF, Fz)) : (cz(k) > 0 ? add2(cF, Fz) : sub2(cF, Fz)); f1 = false; }
+            const float2 sev = mul2(sp2(gus * w), fma2(mul2(sp2(9.0f), cu), cF, make_float2(-uF3.x, -uF3.y)));
+            const float2 sod = mul2(sp2(3.0f * gus * w), cF);
+            p0 = add2(p0, add2(sev, sod));
+            p1 = add2(p1, sub2(sev, sod));
+        }
+        d[k] = p0;
+        d[k + 1] = p1;
+    }
+}
+
+// Update of the two cells (x0, y, z), (x0 + 1, y, z), x0 even.  Populations
+// whose source or destination keeps the pair adjacent (even steps, and
+// directions with c_x = 0 on odd steps) move as one pair-aligned vector; the
+// x-shifted ones of odd steps move one value at a time (with periodic wrap).
+template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
+__device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
+    using S = Store<ST>;
+    using T = typename S::T;
+    T *__restrict__ P = reinterpret_cast<T *>(c.pops);
+    const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
+    const unsigned x1 = x0 + 1;
+    const unsigned xm = x0 ? x0 - 1 : nx - 1;           // x0 - 1
+    const unsigned xp = (x1 + 1 == nx) ? 0 : x1 + 1;    // x1 + 1
+    const unsigned rm = (y ? y - 1 : ny - 1) * nx, r0 = y * nx, rp = ((y + 1 == ny) ? 0 : y + 1) * nx;
+    const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
+    const unsigned cell = x0 + r0 + s0;
+    const size_t Np = (size_t)c.Npad;
+    float2 d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float m = S::scaled ? wgt(i) * c.st_inv_scale : 1.0f;
+        if (ODD) {
+            // direction i of cell x sits in slot opp(i) of cell x - c_i
+            const int dy = -cy(i), dz = -cz(i);
+            const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
+            const T *pl = P + opp(i) * Np + row;
+            if (cx(i) == 0) d[i] = S::ld2(pl + x0, m);
+            else if (cx(i) > 0) d[i] = make_float2(S::ld(pl + xm, m), S::ld(pl + x0, m));
+            else d[i] = make_float2(S::ld(pl + x1, m), S::ld(pl + xp, m));
+        } else {
+            d[i] = S::ld2(P + i * Np + cell, m);
+        }
+    }
+    const bool forced = MARKED || c.has_g;
+    float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
+    if (MARKED) {
+        if (DET) {
+            const float3 f0 = take_fdet(c.Fdet, c.Npad, cell), f1 = take_fdet(c.Fdet, c.Npad, cell + 1);
+            Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
+        } else {
+            const float4 f0 = c.F[cell], f1 = c.F[cell + 1];
+            c.F[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+            c.F[cell + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
+        }
+    }
+    if (forced) {
+        Fx = add2(Fx, sp2(c.g[0]));
+        Fy = add2(Fy, sp2(c.g[1]));
+        Fz = add2(Fz, sp2(c.g[2]));
+    }
+    float2 ux, uy, uz, rho;
+    collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
+    if (MARKED) {
+        c.U[cell] = make_float4(ux.x, uy.x, uz.x, rho.x);
+        c.U[cell + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float m = S::scaled ? c.st_scale / wgt(i) : 1.0f;
+        if (ODD) {
+            // direction i of cell x goes to slot i of cell x + c_i
+            const int dy = cy(i), dz = cz(i);
+            const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
+            T *pl = P + i * Np + row;
+            if (cx(i) == 0) {
+                S::st2(pl + x0, d[i], m);
+            } else if (cx(i) > 0) {
+                S::st(pl + x1, d[i].x, m);
+                S::st(pl + xp, d[i].y, m);
+            } else {
+                S::st(pl + xm, d[i].x, m);
+                S::st(pl + x0, d[i].y, m);
+            }
+        } else {
+            S::st2(P + opp(i) * Np + cell, d[i], m);
+        }
+    }
+    return isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
+}
+
+// 16-bit formats: convert a packed pair of stored values to scaled FP32 and back.
+template <int ST>
+__device__ __forceinline__ float2 unpack2(unsigned v, float m) {
+    float2 f;
+    if (ST == LBIB_F16) f = __half22float2(*reinterpret_cast<const __half2 *>(&v));
+    else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
+    return __fmul2_rn(f, make_float2(m, m));
+}
+template <int ST>
+__device__ __forceinline__ unsigned pack2(float2 v, float m) {
+    v = __fmul2_rn(v, make_float2(m, m));
+    unsigned r;
+    if (ST == LBIB_F16) {
+        const __half2 h = __float22half2_rn(v);
+        r = *reinterpret_cast<const unsigned *>(&h);
+    } else {
+        const __nv_bfloat162 h = __float22bfloat162_rn(v);
+        r = *reinterpret_cast<const unsigned *>(&h);
+    }
+    return r;
+}
+
+// Update of four cells x0 .. x0 + 3 (x0 a multiple of 4) with 16-bit storage.
+// Each direction moves as one 8-byte word when its cells stay aligned; the
+// x-shifted directions of odd steps read the aligned word plus the one value
+// across its edge and reassemble with byte permutes, and write one value, an
+// aligned pair and one value.  The collision runs as two packed pairs.
+template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
+__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
+    using T = unsigned short;
+    T *__restrict__ P = reinterpret_cast<T *>(c.pops);
+    const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
+    const unsigned xm = x0 ? x0 - 1 : nx - 1;          // x0 - 1
+    const unsigned x4 = (x0 + 4 == nx) ? 0 : x0 + 4;   // x0 + 4
+    const unsigned rm = (y ? y - 1 : ny - 1) * nx, r0 = y * nx, rp = ((y + 1 == ny) ? 0 : y + 1) * nx;
+    const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
+    const unsigned cell = x0 + r0 + s0;
+    const size_t Np = (size_t)c.Npad;
+    uint2 raw[Q];  // cells x0..x0+3 of each direction, 2 values per word
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (ODD) {
+            // direction i of cell x sits in slot opp(i) of cell x - c_i
+            const int dy = -cy(i), dz = -cz(i);
+            const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
+            const T *pl = P + opp(i) * Np + row;
+            const uint2 w = *reinterpret_cast<const uint2 *>(pl + x0);
+            if (cx(i) == 0) {
+                raw[i] = w;
+            } else if (cx(i) > 0) {  // cells x0-1 .. x0+2
+                const unsigned e = pl[xm];
+                raw[i] = make_uint2(__byte_perm(e, w.x, 0x5410), __byte_perm(w.x, w.y, 0x5432));
+            } else {                 // cells x0+1 .. x0+4
+                const unsigned e = pl[x4];
+                raw[i] = make_uint2(__byte_perm(w.x, w.y, 0x5432), __byte_perm(w.y, e, 0x5432));
+            }
+        } else {
+            raw[i] = *reinterpret_cast<const uint2 *>(P + i * Np + cell);
+        }
+    }
+    const bool forced = MARKED || c.has_g;
+    bool ok = true;
+    unsigned keep[Q];  // first pair's x-shifted outputs, written together with the second pair's
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float2 d[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = unpack2<ST>(h ? raw[i].y : raw[i].x, wgt(i) * c.st_inv_scale);
+        const unsigned cl = cell + 2 * h;
+        float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
+        if (MARKED) {
+            if (DET) {
+                const float3 f0 = take_fdet(c.Fdet, c.Npad, cl), f1 = take_fdet(c.Fdet, c.Npad, cl + 1);
+                Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
+            } else {
+                const float4 f0 = c.F[cl], f1 = c.F[cl + 1];
+                c.F[cl] = make_float4(0.f, 0.f, 0.f, 0.f);
+                c.F[cl + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
+            }
+        }
+        if (forced) {
+            Fx = add2(Fx, sp2(c.g[0]));
+            Fy = add2(Fy, sp2(c.g[1]));
+            Fz = add2(Fz, sp2(c.g[2]));
+        }
+        float2 ux, uy, uz, rho;
+        collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
+        if (MARKED) {
+            c.U[cl] = make_float4(ux.x, uy.x, uz.x, rho.x);
+            c.U[cl + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
+        }
+        ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned e = pack2<ST>(d[i], c.st_scale / wgt(i));  // this pair's cells (x0 + 2h, x0 + 2h + 1)
+            if (ODD) {
+                // direction i of cell x goes to slot i of cell x + c_i
+                const int dy = cy(i), dz = cz(i);
+                const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
+                T *pl = P + i * Np + row;
+                if (cx(i) == 0) {
+                    *reinterpret_cast<unsigned *>(pl + x0 + 2 * h) = e;
+                } else if (h == 0) {
+                    keep[i] = e;
+                } else {
+                    const unsigned a = keep[i], b = e;
+                    if (cx(i) > 0) {  // to cells x0+1 .. x0+4
+                        pl[x0 + 1] = (T)(a & 0xffffu);
+                        *reinterpret_cast<unsigned *>(pl + x0 + 2) = __byte_perm(a, b, 0x5432);
+                        pl[x4] = (T)(b >> 16);
+                    } else {          // to cells x0-1 .. x0+2
+                        pl[xm] = (T)(a & 0xffffu);
+                        *reinterpret_cast<unsigned *>(pl + x0) = __byte_perm(a, b, 0x5432);
+                        pl[x0 + 2] = (T)(b >> 16);
+                    }
+                }
+            } else {
+                *reinterpret_cast<unsigned *>(P + opp(i) * Np + cl) = e;
+            }
+        }
+    }
+    return ok;
+}
+
 __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_NONFINITE);
 }
@@ -197,21 +490,35 @@ __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
 #ifndef LBIB_LB_GENERIC_MINB
 #define LBIB_LB_GENERIC_MINB 3
 #endif
-template <int ST, bool ODD, int FORCING>
-__global__ void __launch_bounds__(LB_TPB, LBIB_LB_GENERIC_MINB) k_lb_main(const DevCtx c) {
+// CPT = cells per thread: 1, or 2 (adjacent pairs, packed arithmetic; even tile_x).
+// Register budget: one cell per thread, 3 blocks of 256 threads per SM; two
+// cells per thread, 4 blocks of 128 threads (1024 cells in flight per SM);
+// four cells per thread (16-bit storage), 8 blocks of 64 threads.
+#ifndef LBIB_LB_QUAD_MINB
+#define LBIB_LB_QUAD_MINB 8
+#endif
+#define LBIB_LB_BOUNDS(CPT) \
+    __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? 4 : LBIB_LB_QUAD_MINB))
+template <int ST, bool ODD, int FORCING, int CPT>
+__global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
     const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    if (c.marks[(ODD ? c.n_tiles : 0) + tile]) return;  // updated by k_lb_marked
-    const unsigned x = blockIdx.x * c.tile_x + threadIdx.x;
+    // tiles stamped with this step's number are updated by k_lb_marked; gen[p]
+    // is written before this launch and not again until it has finished
+    if (c.marks[(ODD ? c.n_tiles : 0) + tile] == c.ctl->gen[ODD ? 1 : 0]) return;
+    const unsigned x = blockIdx.x * c.tile_x + CPT * threadIdx.x;
     bool ok = true;
-    if (threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx)
-        ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, blockIdx.y, blockIdx.z);
+    if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+        if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, blockIdx.y, blockIdx.z);
+        else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, blockIdx.y, blockIdx.z);
+        else ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, blockIdx.y, blockIdx.z);
+    }
     report_bad(c, !ok);
     if (c.n_nodes == 0 && tile == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
 }
 
 // The marked tiles of this parity's list: a persistent grid walks the list.
-template <int ST, bool ODD, int FORCING, bool DET>
-__global__ void __launch_bounds__(LB_TPB, LBIB_LB_GENERIC_MINB) k_lb_marked(const DevCtx c) {
+template <int ST, bool ODD, int FORCING, bool DET, int CPT>
+__global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked(const DevCtx c) {
     const int p = ODD ? 1 : 0;
     const int n = c.tile_count[p];
     const int *list = c.tile_list + (size_t)p * c.n_tiles;
@@ -220,9 +527,12 @@ __global__ void __launch_bounds__(LB_TPB, LBIB_LB_GENERIC_MINB) k_lb_marked(cons
         const int tile = list[k];
         const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
         const unsigned y = yz % c.ny, z = yz / c.ny;
-        const unsigned x = tx * c.tile_x + threadIdx.x;
-        if (threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx)
-            ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
+        const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
+        if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+            if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
+        }
     }
     report_bad(c, !ok);
 }
@@ -263,25 +573,42 @@ __global__ void __launch_bounds__(LB_TPB) k_lb_macros(const DevCtx c, float *rho
 
 // ---------------------------------------------------------------- launchers
 
-static unsigned tile_threads(const DevCtx &c) { return (unsigned)((c.tile_x + 31) / 32 * 32); }
+static unsigned tile_threads(const DevCtx &c) {
+    const int t = c.tile_x / c.cells_per_thread;
+    return (unsigned)((t + 31) / 32 * 32);
+}
+
+template <int ST, int FORCING, int CPT>
+static void main_dispatch_cpt(const DevCtx &c, bool odd, cudaStream_t s) {
+    const dim3 blocks((unsigned)c.tiles_x, (unsigned)c.ny, (unsigned)c.nz);
+    if (odd) k_lb_main<ST, true, FORCING, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+    else k_lb_main<ST, false, FORCING, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+}
 
 template <int ST, int FORCING>
 static void main_dispatch(const DevCtx &c, bool odd, cudaStream_t s) {
-    const dim3 blocks((unsigned)c.tiles_x, (unsigned)c.ny, (unsigned)c.nz);
-    if (odd) k_lb_main<ST, true, FORCING><<<blocks, tile_threads(c), 0, s>>>(c);
-    else k_lb_main<ST, false, FORCING><<<blocks, tile_threads(c), 0, s>>>(c);
+    if (ST != LBIB_F32 && c.cells_per_thread == 4) main_dispatch_cpt<ST, FORCING, ST == LBIB_F32 ? 2 : 4>(c, odd, s);
+    else if (c.cells_per_thread >= 2) main_dispatch_cpt<ST, FORCING, 2>(c, odd, s);
+    else main_dispatch_cpt<ST, FORCING, 1>(c, odd, s);
+}
+
+template <int ST, int FORCING, int CPT>
+static void marked_dispatch_cpt(const DevCtx &c, bool odd, cudaStream_t s) {
+    const unsigned blocks = (unsigned)(c.n_tiles < c.marked_grid ? c.n_tiles : c.marked_grid);
+    if (c.deterministic) {
+        if (odd) k_lb_marked<ST, true, FORCING, true, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+        else k_lb_marked<ST, false, FORCING, true, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+    } else {
+        if (odd) k_lb_marked<ST, true, FORCING, false, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+        else k_lb_marked<ST, false, FORCING, false, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+    }
 }
 
 template <int ST, int FORCING>
 static void marked_dispatch(const DevCtx &c, bool odd, cudaStream_t s) {
-    const unsigned blocks = (unsigned)(c.n_tiles < c.marked_grid ? c.n_tiles : c.marked_grid);
-    if (c.deterministic) {
-        if (odd) k_lb_marked<ST, true, FORCING, true><<<blocks, tile_threads(c), 0, s>>>(c);
-        else k_lb_marked<ST, false, FORCING, true><<<blocks, tile_threads(c), 0, s>>>(c);
-    } else {
-        if (odd) k_lb_marked<ST, true, FORCING, false><<<blocks, tile_threads(c), 0, s>>>(c);
-        else k_lb_marked<ST, false, FORCING, false><<<blocks, tile_threads(c), 0, s>>>(c);
-    }
+    if (ST != LBIB_F32 && c.cells_per_thread == 4) marked_dispatch_cpt<ST, FORCING, ST == LBIB_F32 ? 2 : 4>(c, odd, s);
+    else if (c.cells_per_thread >= 2) marked_dispatch_cpt<ST, FORCING, 2>(c, odd, s);
+    else marked_dispatch_cpt<ST, FORCING, 1>(c, odd, s);
 }
 
 #define LBIB_DISPATCH(fn, storage, forcing, ...)                                        \

@@ -44,11 +44,13 @@ constexpr int ROWS4 = 16;
 constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_UNSTABLE = 2;
 constexpr int ERR_TIMEOUT = 4;
+constexpr int ERR_MARK = 8;  // a node stencil reached a tile its bead's marked region does not cover
 
 struct Control {
-    long long step;  // time steps completed; t of the next step
+    long long step;  // time steps completed by the immersed-boundary chain; t of its next step
     int err;
-    int pad;
+    int done;        // blocks of the current interpolation launch that have finished
+    int gen[2];      // per step parity: the step whose stamps mark the tiles (see k_lb_main)
 };
 
 // Per-triangle reference data of the linear FEM membrane.
@@ -66,7 +68,8 @@ struct BeadDev {
     int node_start, node_count;
     int swimmer, slot;  // owning swimmer and position 0..2 along its axis
     float inv_count;    // 1 / node_count
-    int pad[3];
+    float reach;        // bound on |r_j - R| over the bead's nodes (rest radius + margin)
+    int pad[2];
 };
 
 struct SwimDev {
@@ -87,6 +90,7 @@ struct DevCtx {
     int n_tiles;
     int tile_x, tiles_x;  // cells per tile along x, tiles per row
     int marked_grid;      // persistent grid of the marked-tile fluid kernel
+    int cells_per_thread; // adjacent cells per fluid thread: 1, 2 (even rows) or 4 (16-bit storage, rows of 4k)
     float tau, omega, rho0;
     float g[3];
     int has_g;
@@ -98,7 +102,7 @@ struct DevCtx {
     float4 *F;                 // force density per cell (float atomics)
     unsigned long long *Fdet;  // 3 x Npad fixed-point force (deterministic mode)
     float4 *U;                 // velocity (x, y, z, rho) per cell
-    int *marks;                // [2][n_tiles]: tile touched by a node stencil, per step parity
+    int *marks;                // [2][n_tiles]: step number whose node stencils touch the tile, per step parity
                                // (tile = x / tile_x + tiles_x * (y + ny * z))
     int *tile_list;            // [2][n_tiles]: the marked tiles of each parity, in marking order
     int *tile_count;           // [2]: entries in each list
@@ -114,7 +118,7 @@ struct DevCtx {
     const SwimDev *swims;
     double *bead_R;            // bead centres, 4 doubles per bead
     float4 *bead_ext;          // (f^d + f^s) / N_v per bead
-    int *bead_pending;         // 1: node velocities of the last advection not yet folded into bead_R
+
     Control *ctl;
     lbib_swimmer_state *sw_state;
     double *xcm0;              // x_cm at init, 3 per swimmer
@@ -168,7 +172,6 @@ cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s)
 cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, int mark_parity, cudaStream_t s);
 cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s);
 cudaError_t launch_bead_init(const DevCtx &c, cudaStream_t s);
-cudaError_t launch_ib_mark(const DevCtx &c, int kernel, int parity, cudaStream_t s);
-cudaError_t launch_ib_clear_marks(const DevCtx &c, int parity, bool advance, cudaStream_t s);
+cudaError_t launch_ib_mark(const DevCtx &c, int kernel, cudaStream_t s);
 
 }  // namespace lbib
