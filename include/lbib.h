@@ -252,7 +252,32 @@ int ib_spread_fixed_noalloc(const double *nodes, const float *node_forces, int n
  * the main fluid kernel).  Synchronous. */
 int lb_marked_cells(lbib_ctx *ctx, long long *cells);
 
-/* Release the context (not the caller's buffers).  Synchronises. */
+/* ---- batches of independent boxes -------------------------------------
+ * A batch advances many contexts (each its own periodic box with its own
+ * swimmers, as in the single-box problem of Sec. 2) with one set of kernel
+ * launches per step for all of them: every launch covers the tiles, nodes or
+ * triangles of every box, on the same two-stream schedule as lb_step, and
+ * the step sequence is captured in CUDA graphs.  The contexts keep their own
+ * buffers and accessors (swimmer_state, lb_get_*). */
+typedef struct lbib_batch lbib_batch;
+
+/* Group n contexts.  They must share storage, forcing, delta kernel and the
+ * deterministic flag, have taken the same number of steps, and use the same
+ * stream (the batch works on the stream of ctxs[0]); n <= 1024.  The contexts
+ * must outlive the batch, and lb_step on a batched context fails with
+ * LBIB_EINVAL until the batch is destroyed.  Synchronous. */
+int lb_batch_create(lbib_ctx *const *ctxs, int n, lbib_batch **out);
+/* Advance every box of the batch by n_steps coupled steps (asynchronous). */
+int lb_batch_step(lbib_batch *b, long long n_steps);
+/* Timing hook of the batch, as lb_profile / lb_profile_read: brackets every
+ * batched main fluid launch with CUDA events. */
+int lb_batch_profile(lbib_batch *b, int on);
+int lb_batch_profile_read(lbib_batch *b, double *total_ms, long long *launches);
+/* Release the batch (not the contexts).  Synchronises. */
+int lb_batch_destroy(lbib_batch *b);
+
+/* Release the context (not the caller's buffers).  Synchronises.  Fails with
+ * LBIB_EINVAL while the context belongs to a batch. */
 int lb_destroy(lbib_ctx *ctx);
 
 #ifdef __cplusplus

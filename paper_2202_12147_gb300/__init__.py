@@ -10,7 +10,7 @@ from .build import build  # noqa: F401
 
 def __getattr__(name):
     # the simulation wrapper needs torch; import it lazily
-    if name in ("Simulation", "lattice", "required_sizes"):
+    if name in ("Simulation", "Batch", "lattice", "required_sizes"):
         from . import sim
         return getattr(sim, name)
     raise AttributeError(name)

@@ -23,6 +23,7 @@ EXPORTS = [
     "ib_spread", "ib_interpolate", "swimmer_state", "lb_sync", "lb_get_macros", "lb_get_populations",
     "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces", "lb_get_force_field",
     "lb_set_velocity", "lb_profile", "lb_profile_read", "lb_marked_cells", "ib_spread_fixed_noalloc",
+    "lb_batch_create", "lb_batch_step", "lb_batch_profile", "lb_batch_profile_read", "lb_batch_destroy",
     "lb_destroy",
 ]
 
@@ -107,6 +108,11 @@ def load(build_if_missing: bool = True):
         L.lb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)]
         L.lb_marked_cells.argtypes = [P, ctypes.POINTER(LL)]
         L.ib_spread_fixed_noalloc.argtypes = [P, P, I, I, I, I, I, P, P]
+        L.lb_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
+        L.lb_batch_step.argtypes = [P, LL]
+        L.lb_batch_profile.argtypes = [P, I]
+        L.lb_batch_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)]
+        L.lb_batch_destroy.argtypes = [P]
         L.lb_destroy.argtypes = [P]
         for n in EXPORTS:
             if n not in ("lbib_version", "lbib_strerror", "lbib_last_error"):

@@ -203,6 +203,22 @@ struct lbib_ctx {
     Control *h_ctl = nullptr;      // pinned
     lbib_swimmer_state *h_sws = nullptr;  // pinned
     int n_nodes = 0, n_swimmers = 0;
+    lbib_batch *batch = nullptr;   // set while the context belongs to a batch
+};
+
+struct lbib_batch {
+    std::vector<lbib_ctx *> ctx;
+    BatchDev bt;
+    void *dev = nullptr;           // device copy of the descriptors and prefix tables
+    int storage = 0, forcing = 0, kernel = 0, det = 0;
+    bool any_nodes = false;
+    cudaStream_t user = nullptr, ib = nullptr, cap = nullptr, cap_ib = nullptr;
+    cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    long long step = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
 };
 
 namespace {
@@ -563,6 +579,7 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
 
 int lb_step(lbib_ctx *c, long long n) {
     if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
+    if (c->batch) return fail(LBIB_EINVAL, "the context belongs to a batch: advance it with lb_batch_step");
     if (n < 0) return fail(LBIB_EINVAL, "n_steps < 0");
     bool forked = false;
     while (n > 0) {
@@ -789,6 +806,7 @@ int lb_marked_cells(lbib_ctx *c, long long *cells) {
 
 int lb_destroy(lbib_ctx *c) {
     if (!c) return LBIB_OK;
+    if (c->batch) return fail(LBIB_EINVAL, "the context belongs to a batch: destroy the batch first");
     cudaStreamSynchronize(c->user);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->ib) cudaStreamSynchronize(c->ib);
@@ -802,6 +820,229 @@ int lb_destroy(lbib_ctx *c) {
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->h_sws) cudaFreeHost(c->h_sws);
     delete c;
+    return LBIB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+namespace {
+
+cudaError_t batch_timed_event(lbib_batch *b, cudaStream_t s) {
+    cudaError_t e;
+    while (b->ev.size() < b->ev_used + 1) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+        b->ev.push_back(ev);
+    }
+    if ((e = cudaEventRecord(b->ev[b->ev_used], s)) != cudaSuccess) return e;
+    b->ev_used += 1;
+    return cudaSuccess;
+}
+
+cudaError_t batch_fork(lbib_batch *b, cudaStream_t sm, cudaStream_t sib) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(b->e_fork, sm)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(sib, b->e_fork, 0)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->e_main, sm)) != cudaSuccess) return e;
+    return cudaEventRecord(b->e_ib, sm);
+}
+
+// The two-stream coupled step of enqueue_step, with every launch covering all boxes.
+cudaError_t batch_enqueue_step(lbib_batch *b, bool odd, cudaStream_t sm, cudaStream_t sib, bool timed) {
+    cudaError_t e;
+    const BatchDev &bt = b->bt;
+    if (!b->any_nodes) {
+        if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
+        if ((e = launch_lb_batch(bt, b->storage, b->forcing, b->det, false, odd, sm)) != cudaSuccess) return e;
+        if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    if ((e = cudaStreamWaitEvent(sm, b->e_ib, 0)) != cudaSuccess) return e;
+    if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
+    if ((e = launch_lb_batch(bt, b->storage, b->forcing, b->det, false, odd, sm)) != cudaSuccess) return e;
+    if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
+    if ((e = launch_ib_batch(bt, b->kernel, b->det, 0, sib)) != cudaSuccess) return e;
+    if ((e = launch_ib_batch(bt, b->kernel, b->det, 1, sib)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(sib, b->e_main, 0)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->e_main, sm)) != cudaSuccess) return e;
+    if ((e = launch_lb_batch(bt, b->storage, b->forcing, b->det, true, odd, sib)) != cudaSuccess) return e;
+    if ((e = launch_ib_batch(bt, b->kernel, b->det, 2, sib)) != cudaSuccess) return e;
+    return cudaEventRecord(b->e_ib, sib);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_batch_create(lbib_ctx *const *ctxs, int n, lbib_batch **out) {
+    if (!out) return fail(LBIB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1 || n > LBIB_MAX_BATCH) return fail(LBIB_EINVAL, "need 1..1024 contexts");
+    const lbib_ctx *c0 = ctxs[0];
+    if (!c0) return fail(LBIB_EINVAL, "a context is NULL");
+    int cpt = 4;
+    for (int i = 0; i < n; ++i) {
+        const lbib_ctx *c = ctxs[i];
+        if (!c) return fail(LBIB_EINVAL, "a context is NULL");
+        if (c->batch) return fail(LBIB_EINVAL, "a context already belongs to a batch");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(LBIB_EINVAL, "a context appears twice");
+        if (c->p.storage != c0->p.storage || c->p.forcing != c0->p.forcing || c->p.kernel != c0->p.kernel ||
+            c->p.deterministic != c0->p.deterministic)
+            return fail(LBIB_EINVAL, "batched contexts must share storage, forcing, kernel and determinism");
+        if (c->step != c0->step) return fail(LBIB_EINVAL, "batched contexts must have taken the same number of steps");
+        if (c->user != c0->user) return fail(LBIB_EINVAL, "batched contexts must use the same stream");
+        cpt = std::min(cpt, c->d.cells_per_thread);
+    }
+    lbib_batch *b = new lbib_batch();
+    auto bail = [&](int code) {
+        lb_batch_destroy(b);
+        return code;
+    };
+    b->ctx.assign(ctxs, ctxs + n);
+    b->storage = c0->p.storage;
+    b->forcing = c0->p.forcing;
+    b->kernel = c0->p.kernel;
+    b->det = c0->p.deterministic;
+    b->user = c0->user;
+    b->step = c0->step;
+    std::vector<DevCtx> boxes(n);
+    std::vector<int> om(n + 1, 0), op(n + 1, 0), og(n + 1, 0), oi(n + 1, 0);
+    int max_threads = 1, marked = 0;
+    for (int i = 0; i < n; ++i) {
+        boxes[i] = ctxs[i]->d;
+        boxes[i].cells_per_thread = cpt;
+        om[i + 1] = om[i] + boxes[i].n_tiles;
+        op[i + 1] = op[i] + (boxes[i].n_nodes ? ib_blocks_prepare(boxes[i]) : 0);
+        og[i + 1] = og[i] + (boxes[i].n_nodes ? ib_blocks_spread(boxes[i]) : 0);
+        oi[i + 1] = oi[i] + (boxes[i].n_nodes ? ib_blocks_interp(boxes[i], b->kernel) : 0);
+        max_threads = std::max(max_threads, boxes[i].tile_x / cpt);
+        if (boxes[i].n_nodes) {
+            b->any_nodes = true;
+            marked += boxes[i].marked_grid;
+        }
+    }
+    const size_t bytes = sizeof(DevCtx) * n + 4 * sizeof(int) * (n + 1);
+    if (cudaMalloc(&b->dev, bytes) != cudaSuccess) return bail(fail(LBIB_ECUDA, "cudaMalloc of the batch tables failed"));
+    char *dp = (char *)b->dev;
+    if (cudaMemcpy(dp, boxes.data(), sizeof(DevCtx) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "uploading the batch tables failed"));
+    int *offs[4];
+    const std::vector<int> *src[4] = {&om, &op, &og, &oi};
+    for (int k = 0; k < 4; ++k) {
+        offs[k] = (int *)(dp + sizeof(DevCtx) * n + k * sizeof(int) * (n + 1));
+        if (cudaMemcpy(offs[k], src[k]->data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(LBIB_ECUDA, "uploading the batch tables failed"));
+    }
+    BatchDev &bt = b->bt;
+    bt.n_boxes = n;
+    bt.boxes = (const DevCtx *)dp;
+    bt.off_main = offs[0];
+    bt.off_prep = offs[1];
+    bt.off_gs = offs[2];
+    bt.off_int = offs[3];
+    bt.blocks_main = om[n];
+    bt.blocks_prep = op[n];
+    bt.blocks_gs = og[n];
+    bt.blocks_int = oi[n];
+    bt.blocks_marked = std::max(1, std::min(marked, 65535));
+    bt.max_tile_threads = max_threads;
+    bt.cells_per_thread = cpt;
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&b->ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&b->cap_ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->e_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->e_main, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->e_ib, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "creating batch streams or events failed"));
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, "cudaStreamBeginCapture failed"));
+    cudaError_t ce = batch_fork(b, b->cap, b->cap_ib);
+    for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k)
+        ce = batch_enqueue_step(b, ((b->step + k) & 1) != 0, b->cap, b->cap_ib, false);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->e_ib, 0);
+    cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, std::string("batch graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee)));
+    ce = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return bail(fail(LBIB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce)));
+    for (lbib_ctx *c : b->ctx) c->batch = b;
+    *out = b;
+    return LBIB_OK;
+}
+
+int lb_batch_step(lbib_batch *b, long long n) {
+    if (!b) return fail(LBIB_EINVAL, "batch is NULL");
+    if (n < 0) return fail(LBIB_EINVAL, "n_steps < 0");
+    // the graph was captured starting at the creation step's parity
+    bool forked = false;
+    while (n > 0) {
+        const long long s = b->ctx[0]->step;
+        if (!b->profiling && ((s - b->step) & 1) == 0 && n >= GRAPH_STEPS) {
+            if (forked) {
+                CU(cudaStreamWaitEvent(b->user, b->e_ib, 0));
+                forked = false;
+            }
+            CU(cudaGraphLaunch(b->graph, b->user));
+            for (lbib_ctx *c : b->ctx) c->step += GRAPH_STEPS;
+            n -= GRAPH_STEPS;
+        } else {
+            if (!forked) {
+                CU(batch_fork(b, b->user, b->ib));
+                forked = true;
+            }
+            CU(batch_enqueue_step(b, (s & 1) != 0, b->user, b->ib, b->profiling));
+            for (lbib_ctx *c : b->ctx) c->step += 1;
+            n -= 1;
+        }
+    }
+    if (forked) CU(cudaStreamWaitEvent(b->user, b->e_ib, 0));
+    return LBIB_OK;
+}
+
+int lb_batch_profile(lbib_batch *b, int on) {
+    if (!b) return fail(LBIB_EINVAL, "batch is NULL");
+    CU(cudaStreamSynchronize(b->user));
+    b->profiling = on != 0;
+    b->ev_used = 0;
+    return LBIB_OK;
+}
+
+int lb_batch_profile_read(lbib_batch *b, double *total_ms, long long *launches) {
+    if (!b || !total_ms || !launches) return fail(LBIB_EINVAL, "NULL argument");
+    CU(cudaStreamSynchronize(b->user));
+    double t = 0.0;
+    for (size_t k = 0; k + 1 < b->ev_used; k += 2) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, b->ev[k], b->ev[k + 1]));
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = (long long)(b->ev_used / 2);
+    return LBIB_OK;
+}
+
+int lb_batch_destroy(lbib_batch *b) {
+    if (!b) return LBIB_OK;
+    cudaStreamSynchronize(b->user);
+    if (b->ib) cudaStreamSynchronize(b->ib);
+    for (lbib_ctx *c : b->ctx)
+        if (c && c->batch == b) c->batch = nullptr;
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap_ib) cudaStreamDestroy(b->cap_ib);
+    if (b->ib) cudaStreamDestroy(b->ib);
+    if (b->e_fork) cudaEventDestroy(b->e_fork);
+    if (b->e_main) cudaEventDestroy(b->e_main);
+    if (b->e_ib) cudaEventDestroy(b->e_ib);
+    if (b->dev) cudaFree(b->dev);
+    delete b;
     return LBIB_OK;
 }
 

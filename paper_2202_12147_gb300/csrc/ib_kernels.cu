@@ -146,17 +146,19 @@ __device__ void triangle_forces(const DevCtx &c, int t) {
     o[2] = make_float4(-w2x, -w2y, -w2z, 0.f);
 }
 
-__global__ void __launch_bounds__(PREP_TPB) k_ib_prepare(const DevCtx c) {
+__device__ __forceinline__ void prepare_body(const DevCtx &c, int bid) {
     // the other parity's tile list (the previous step's) is consumed: empty it
     // for the marks of the next step
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.tile_count[(c.ctl->step + 1) & 1] = 0;
-    if ((int)blockIdx.x < c.n_swimmers) {
-        swimmer_forces(c, blockIdx.x);
+    if (bid == 0 && threadIdx.x == 0) c.tile_count[(c.ctl->step + 1) & 1] = 0;
+    if (bid < c.n_swimmers) {
+        swimmer_forces(c, bid);
         return;
     }
-    const int t = (blockIdx.x - c.n_swimmers) * PREP_TPB + threadIdx.x;
+    const int t = (bid - c.n_swimmers) * PREP_TPB + threadIdx.x;
     if (t < c.n_tris) triangle_forces(c, t);
 }
+
+__global__ void __launch_bounds__(PREP_TPB) k_ib_prepare(const DevCtx c) { prepare_body(c, blockIdx.x); }
 
 // Bead centres from the positions (FP64 mean, fixed order); clears the
 // pending advection marks.
@@ -180,11 +182,11 @@ __global__ void __launch_bounds__(PREP_TPB) k_bead_init(const DevCtx c) {
 }
 
 template <int KW, bool DET>
-__global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
+__device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid) {
     __shared__ float4 sf[GS_NODES];
     __shared__ int so[GS_NODES][3];
     __shared__ float sw[GS_NODES][3][KW];
-    const int j0 = blockIdx.x * GS_NODES;
+    const int j0 = bid * GS_NODES;
     const int nloc = min(GS_NODES, c.n_nodes - j0);
     if ((int)threadIdx.x < nloc) {
         const int j = j0 + threadIdx.x;
@@ -254,6 +256,9 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) {
     }
     if (__any_sync(0xffffffffu, unmarked) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_MARK);
 }
+
+template <int KW, bool DET>
+__global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) { gather_spread_body<KW, DET>(c, blockIdx.x); }
 
 // Fold an advection into the bead centres: R_b += mean_j v_j (the mean is
 // linear, so this keeps R_b the centre of mass of its nodes, Fig. 1 caption).
@@ -329,8 +334,8 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_mark(const DevCtx c) {
 // order.  With ADVECT, lane 0 moves the node (FP64) and, if mark_parity >= 0,
 // the lanes mark the tiles of the moved node's stencil for the next step.
 template <int KW, bool ADVECT>
-__global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *vel_out, int mark_parity) {
-    const int gt = blockIdx.x * INT_TPB + threadIdx.x;
+__device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, float *vel_out, int mark_parity) {
+    const int gt = bid * INT_TPB + threadIdx.x;
     const int j = gt / KW, l = gt % KW;
     const bool active = j < c.n_nodes;
     const int nx = c.nx, ny = c.ny, nz = c.nz;
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
         __shared__ int s_last;
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(&c.ctl->done, 1) == (int)gridDim.x - 1;
+        if (threadIdx.x == 0) s_last = atomicAdd(&c.ctl->done, 1) == nblk - 1;
         __syncthreads();
         if (s_last) {
             __threadfence();
@@ -421,6 +426,11 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
             }
         }
     }
+}
+
+template <int KW, bool ADVECT>
+__global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *vel_out, int mark_parity) {
+    interp_body<KW, ADVECT>(c, blockIdx.x, gridDim.x, vel_out, mark_parity);
 }
 
 // Observables: one block per swimmer, FP64 reductions in a fixed order.
@@ -490,6 +500,66 @@ __global__ void __launch_bounds__(PREP_TPB) k_swimmer_state(const DevCtx c, int 
             st->disp[a] = x - c.xcm0[3 * s + a];
         }
     }
+}
+
+// ---------------------------------------------------------------- batches
+// One launch serves every box of a batch: block b of the launch belongs to the
+// box whose prefix range [off[box], off[box + 1]) holds b, and runs that box's
+// code with its local block index.
+__device__ __forceinline__ int batch_box(const int *off, int n, int b) {
+    int lo = 0, hi = n;  // off[lo] <= b < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(PREP_TPB) k_ib_prepare_batch(const BatchDev bt) {
+    const int b = batch_box(bt.off_prep, bt.n_boxes, blockIdx.x);
+    prepare_body(bt.boxes[b], blockIdx.x - bt.off_prep[b]);
+}
+
+template <int KW, bool DET>
+__global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread_batch(const BatchDev bt) {
+    const int b = batch_box(bt.off_gs, bt.n_boxes, blockIdx.x);
+    gather_spread_body<KW, DET>(bt.boxes[b], blockIdx.x - bt.off_gs[b]);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(INT_TPB) k_ib_interp_batch(const BatchDev bt) {
+    const int b = batch_box(bt.off_int, bt.n_boxes, blockIdx.x);
+    const DevCtx &c = bt.boxes[b];
+    interp_body<KW, true>(c, blockIdx.x - bt.off_int[b], bt.off_int[b + 1] - bt.off_int[b], nullptr,
+                          (int)((c.ctl->step + 1) & 1));
+}
+
+cudaError_t launch_ib_batch(const BatchDev &bt, int kernel, int deterministic, int phase, cudaStream_t s) {
+    if (phase == 0) {
+        if (bt.blocks_prep) k_ib_prepare_batch<<<bt.blocks_prep, PREP_TPB, 0, s>>>(bt);
+    } else if (phase == 1) {
+        if (!bt.blocks_gs) return cudaSuccess;
+        if (kernel == LBIB_LINEAR2) {
+            if (deterministic) k_ib_gather_spread_batch<2, true><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
+            else k_ib_gather_spread_batch<2, false><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
+        } else {
+            if (deterministic) k_ib_gather_spread_batch<4, true><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
+            else k_ib_gather_spread_batch<4, false><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
+        }
+    } else {
+        if (!bt.blocks_int) return cudaSuccess;
+        if (kernel == LBIB_LINEAR2) k_ib_interp_batch<2><<<bt.blocks_int, INT_TPB, 0, s>>>(bt);
+        else k_ib_interp_batch<4><<<bt.blocks_int, INT_TPB, 0, s>>>(bt);
+    }
+    return cudaGetLastError();
+}
+
+int ib_blocks_prepare(const DevCtx &c) { return c.n_swimmers + (c.n_tris + PREP_TPB - 1) / PREP_TPB; }
+int ib_blocks_spread(const DevCtx &c) { return (c.n_nodes + GS_NODES - 1) / GS_NODES; }
+int ib_blocks_interp(const DevCtx &c, int kernel) {
+    const int lanes = kernel == LBIB_LINEAR2 ? 2 : 4;
+    return (int)(((long long)c.n_nodes * lanes + INT_TPB - 1) / INT_TPB);
 }
 
 cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s) {

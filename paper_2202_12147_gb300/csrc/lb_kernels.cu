@@ -500,30 +500,35 @@ __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
 #define LBIB_LB_BOUNDS(CPT) \
     __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? 4 : LBIB_LB_QUAD_MINB))
 template <int ST, bool ODD, int FORCING, int CPT>
-__global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
-    const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+__device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, unsigned tx, unsigned y, unsigned z) {
     // tiles stamped with this step's number are updated by k_lb_marked; gen[p]
     // is written before this launch and not again until it has finished
     if (c.marks[(ODD ? c.n_tiles : 0) + tile] == c.ctl->gen[ODD ? 1 : 0]) return;
-    const unsigned x = blockIdx.x * c.tile_x + CPT * threadIdx.x;
+    const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
     bool ok = true;
     if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
-        if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, blockIdx.y, blockIdx.z);
-        else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, blockIdx.y, blockIdx.z);
-        else ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, blockIdx.y, blockIdx.z);
+        if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, y, z);
+        else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, y, z);
+        else ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, y, z);
     }
     report_bad(c, !ok);
     if (c.n_nodes == 0 && tile == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
 }
 
+template <int ST, bool ODD, int FORCING, int CPT>
+__global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
+    const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // The marked tiles of this parity's list: a persistent grid walks the list.
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
-__global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked(const DevCtx c) {
+__device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nblk) {
     const int p = ODD ? 1 : 0;
     const int n = c.tile_count[p];
     const int *list = c.tile_list + (size_t)p * c.n_tiles;
     bool ok = true;
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    for (int k = bid; k < n; k += nblk) {
         const int tile = list[k];
         const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
         const unsigned y = yz % c.ny, z = yz / c.ny;
@@ -535,6 +540,65 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked(const DevCtx c) {
         }
     }
     report_bad(c, !ok);
+}
+
+template <int ST, bool ODD, int FORCING, bool DET, int CPT>
+__global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked(const DevCtx c) {
+    lb_marked_body<ST, ODD, FORCING, DET, CPT>(c, blockIdx.x, gridDim.x);
+}
+
+// Batches: one launch over the tiles of every box (block -> box by prefix
+// search), and one persistent launch over every box's marked-tile list.
+template <int ST, bool ODD, int FORCING, int CPT>
+__global__ void LBIB_LB_BOUNDS(CPT) k_lb_main_batch(const BatchDev bt) {
+    int lo = 0, hi = bt.n_boxes;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bt.off_main[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    const DevCtx &c = bt.boxes[lo];
+    const unsigned tile = blockIdx.x - bt.off_main[lo];
+    const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
+    lb_main_body<ST, ODD, FORCING, CPT>(c, tile, tx, yz % c.ny, yz / c.ny);
+}
+
+// The marked tiles of every box form one flat work list: the per-box list
+// lengths are prefix-summed in shared memory, and a persistent grid walks it.
+template <int ST, bool ODD, int FORCING, bool DET, int CPT>
+__global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked_batch(const BatchDev bt) {
+    __shared__ int s_pref[LBIB_MAX_BATCH + 1];
+    const int p = ODD ? 1 : 0;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < bt.n_boxes; ++b) {
+            s_pref[b] = acc;
+            acc += bt.boxes[b].tile_count[p];
+        }
+        s_pref[bt.n_boxes] = acc;
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int k = blockIdx.x; k < s_pref[bt.n_boxes]; k += gridDim.x) {
+        int lo = 0, hi = bt.n_boxes;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_pref[mid] <= k) lo = mid;
+            else hi = mid;
+        }
+        const DevCtx &c = bt.boxes[lo];
+        const int tile = c.tile_list[(size_t)p * c.n_tiles + (k - s_pref[lo])];
+        const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
+        const unsigned y = yz % c.ny, z = yz / c.ny;
+        const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
+        if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+            if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
+        }
+        if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_NONFINITE);
+        ok = true;
+    }
 }
 
 template <int ST, bool ODD>
@@ -623,6 +687,33 @@ static void marked_dispatch(const DevCtx &c, bool odd, cudaStream_t s) {
             else fn<LBIB_F32, LBIB_GUO>(__VA_ARGS__);                                   \
         }                                                                               \
     } while (0)
+
+template <int ST, int FORCING, int CPT>
+static void batch_dispatch_cpt(const BatchDev &bt, bool marked, int det, bool odd, cudaStream_t s) {
+    const unsigned threads = (unsigned)((bt.max_tile_threads + 31) / 32 * 32);
+    if (!marked) {
+        if (odd) k_lb_main_batch<ST, true, FORCING, CPT><<<bt.blocks_main, threads, 0, s>>>(bt);
+        else k_lb_main_batch<ST, false, FORCING, CPT><<<bt.blocks_main, threads, 0, s>>>(bt);
+    } else if (det) {
+        if (odd) k_lb_marked_batch<ST, true, FORCING, true, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
+        else k_lb_marked_batch<ST, false, FORCING, true, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
+    } else {
+        if (odd) k_lb_marked_batch<ST, true, FORCING, false, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
+        else k_lb_marked_batch<ST, false, FORCING, false, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
+    }
+}
+
+template <int ST, int FORCING>
+static void batch_dispatch(const BatchDev &bt, bool marked, int det, bool odd, cudaStream_t s) {
+    if (ST != LBIB_F32 && bt.cells_per_thread == 4) batch_dispatch_cpt<ST, FORCING, ST == LBIB_F32 ? 2 : 4>(bt, marked, det, odd, s);
+    else if (bt.cells_per_thread >= 2) batch_dispatch_cpt<ST, FORCING, 2>(bt, marked, det, odd, s);
+    else batch_dispatch_cpt<ST, FORCING, 1>(bt, marked, det, odd, s);
+}
+
+cudaError_t launch_lb_batch(const BatchDev &bt, int storage, int forcing, int det, bool marked, bool odd, cudaStream_t s) {
+    LBIB_DISPATCH(batch_dispatch, storage, forcing, bt, marked, det, odd, s);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s) {
     LBIB_DISPATCH(main_dispatch, storage, forcing, c, odd, s);

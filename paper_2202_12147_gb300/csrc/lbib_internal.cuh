@@ -124,6 +124,20 @@ struct DevCtx {
     double *xcm0;              // x_cm at init, 3 per swimmer
 };
 
+// most boxes one batch holds
+constexpr int LBIB_MAX_BATCH = 1024;
+
+// A batch of boxes advanced by shared launches: the per-box descriptors in
+// device memory and, per kernel, prefix sums of each box's block count.
+struct BatchDev {
+    int n_boxes;
+    const DevCtx *boxes;
+    const int *off_main, *off_prep, *off_gs, *off_int;  // [n_boxes + 1]
+    int blocks_main, blocks_prep, blocks_gs, blocks_int, blocks_marked;
+    int max_tile_threads;  // widest tile of any box, in threads
+    int cells_per_thread;  // common to every box of the batch
+};
+
 // fixed-point scale of deterministic spreading: 2^48 units per force unit
 // (resolution 3.6e-15, range +-32768 per cell)
 constexpr double FIX_SCALE = 281474976710656.0;
@@ -166,6 +180,7 @@ void set_last_error(const char *msg);
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
 cudaError_t launch_lb_marked(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
 cudaError_t launch_lb_macros(const DevCtx &c, int storage, bool odd, float *rho, float *u, cudaStream_t s);
+cudaError_t launch_lb_batch(const BatchDev &bt, int storage, int forcing, int det, bool marked, bool odd, cudaStream_t s);
 // IB (ib_kernels.cu)
 cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s);
 cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s);
@@ -173,5 +188,10 @@ cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *ve
 cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s);
 cudaError_t launch_bead_init(const DevCtx &c, cudaStream_t s);
 cudaError_t launch_ib_mark(const DevCtx &c, int kernel, cudaStream_t s);
+// phase 0: prepare, 1: gather/spread, 2: advecting interpolation, for every box
+cudaError_t launch_ib_batch(const BatchDev &bt, int kernel, int deterministic, int phase, cudaStream_t s);
+int ib_blocks_prepare(const DevCtx &c);
+int ib_blocks_spread(const DevCtx &c);
+int ib_blocks_interp(const DevCtx &c, int kernel);
 
 }  // namespace lbib

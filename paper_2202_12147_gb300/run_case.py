@@ -1,0 +1,55 @@
+"""Run one synthetic swimmer box for a number of coupled steps and print the
+swimmers' displacement (a command-line runner, also used to drive profilers
+on a single box).
+
+    python -m paper_2202_12147_gb300.run_case --case pair_side_3 --steps 4 --storage f32
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _box(name):
+    from workloads import adjoint_single_96, pair_side_256cube, single_swimmer_48, swimmer_pair
+    if name == "single_48":
+        return single_swimmer_48()
+    if name == "pair_side_256cube":
+        return pair_side_256cube()
+    if name == "single_96":
+        return adjoint_single_96()
+    arr, gap = name.split("_")[1], int(name.split("_")[2])
+    return swimmer_pair(arr, gap)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="pair_side_3",
+                    help="single_48 | single_96 | pair_side_256cube | pair_{inline,side}_{3,5,8} (256x128x128)")
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--deterministic", action="store_true")
+    ap.add_argument("--kernel-by-kernel", action="store_true",
+                    help="launch kernels one by one instead of replaying CUDA graphs")
+    a = ap.parse_args(argv)
+    from paper_2202_12147_gb300 import Simulation
+    from workloads import assemble
+    box = _box(a.case)
+    sim = Simulation(box.dims, assemble(box), tau=box.tau, rho0=box.rho0, storage=a.storage,
+                     deterministic=a.deterministic, forcing=box.forcing, kernel=box.kernel)
+    if a.kernel_by_kernel:
+        sim.profile(True)
+    sim.lb_step(a.steps)
+    for k in range(sim.n_swimmers):
+        st = sim.swimmer_state(k)
+        print(f"{box.name} swimmer {k}: step {st['step']} displacement {st['disp'].tolist()}")
+    sim.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -213,3 +213,40 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Independent boxes advanced together by one set of launches per step.
+
+    The simulations keep their own buffers and accessors; while batched they
+    are stepped only through the batch."""
+
+    def __init__(self, sims):
+        self.L = _lib.load()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*(s.ctx.value for s in self.sims))
+        self.b = ctypes.c_void_p()
+        check(self.L.lb_batch_create(arr, len(self.sims), ctypes.byref(self.b)))
+
+    def lb_step(self, n=1):
+        check(self.L.lb_batch_step(self.b, int(n)))
+
+    def profile(self, on=True):
+        check(self.L.lb_batch_profile(self.b, 1 if on else 0))
+
+    def profile_read(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        check(self.L.lb_batch_profile_read(self.b, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if self.b:
+            self.L.lb_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -183,3 +183,54 @@ def random_populations(n_cells, weights, seed=0, rho_amp=1e-3, u_amp=1e-3):
 def perturbed_nodes(nodes, seed=0, amp=0.05):
     rng = np.random.default_rng(seed)
     return nodes + amp * rng.uniform(-1.0, 1.0, size=nodes.shape)
+
+
+ENSEMBLE_SIZES = [(48, 48, 48), (64, 64, 64), (96, 96, 96), (192, 128, 128)]
+
+
+def ensemble_boxes(n=64, seed=0, period=2000.0):
+    """Independent boxes for batched runs, drawn with numpy default_rng(seed):
+    sizes uniformly from 48^3, 64^3, 96^3 and 128x128x192 (stored with the
+    long side along x); one or two swimmers (radius 6 at subdivision 3,
+    spacing 18) with drive amplitude A = B drawn from [5e-4, 2e-3], phase
+    shift from [pi/4, 3pi/4], pairs in-line or side by side with a surface
+    gap of 2-8 radii.  Fit rules: a 48^3 box holds one smaller swimmer
+    (radius 4, subdivision 2, spacing 12); every swimmer keeps a clearance of
+    two radii to the periodic images, so an in-line pair that does not fit
+    becomes side by side, a side-by-side gap is clamped to fit, and a pair
+    that still does not fit keeps one swimmer."""
+    rng = np.random.default_rng(seed)
+    boxes = []
+    for b in range(n):
+        dims = ENSEMBLE_SIZES[int(rng.integers(len(ENSEMBLE_SIZES)))]
+        n_sw = 1 + int(rng.integers(2))
+        arr = "inline" if rng.random() < 0.5 else "side"
+        gap_r = float(rng.uniform(2.0, 8.0))
+        alpha = float(rng.uniform(math.pi / 4, 3 * math.pi / 4))
+        amp = float(rng.uniform(5e-4, 2e-3))
+        nx, ny, nz = dims
+        cx, cy, cz = (float(d // 2) for d in dims)
+        if dims == (48, 48, 48):
+            a, L, sub, n_sw = 4.0, 12.0, 2, 1
+        else:
+            a, L, sub = 6.0, 18.0, 3
+        gap = gap_r * a
+        ext = 2 * L + 2 * a
+        clear = 2 * a
+        if n_sw == 2 and arr == "inline" and 2 * ext + gap + clear > nx:
+            arr = "side"
+        if n_sw == 2 and arr == "side" and 4 * a + gap + clear > ny:
+            gap = ny - 4 * a - clear
+            if gap < 2 * a:
+                n_sw = 1
+        spec = dict(radius=a, subdiv=sub, spacing=L, k_spring=0.005, Gs=0.01, period=period)
+        if n_sw == 1:
+            sw = (SwimmerSpec(center=(cx, cy, cz), **spec).with_drive(amp, amp, alpha),)
+        elif arr == "inline":
+            h = (ext + gap) / 2.0
+            sw = tuple(SwimmerSpec(center=(cx + s * h, cy, cz), **spec).with_drive(amp, amp, alpha) for s in (-1, 1))
+        else:
+            h = (2 * a + gap) / 2.0
+            sw = tuple(SwimmerSpec(center=(cx, cy + s * h, cz), **spec).with_drive(amp, amp, alpha) for s in (-1, 1))
+        boxes.append(BoxSpec(dims=dims, swimmers=sw, name=f"ensemble_{b}_{nx}x{ny}x{nz}_{len(sw)}sw"))
+    return boxes
