@@ -209,6 +209,7 @@ struct lbib_ctx {
 struct lbib_batch {
     std::vector<lbib_ctx *> ctx;
     BatchDev bt;
+    std::vector<ClassArgs> classes;  // boxes grouped by size for the main fluid launches
     void *dev = nullptr;           // device copy of the descriptors and prefix tables
     int storage = 0, forcing = 0, kernel = 0, det = 0;
     bool any_nodes = false;
@@ -852,16 +853,17 @@ cudaError_t batch_fork(lbib_batch *b, cudaStream_t sm, cudaStream_t sib) {
 cudaError_t batch_enqueue_step(lbib_batch *b, bool odd, cudaStream_t sm, cudaStream_t sib, bool timed) {
     cudaError_t e;
     const BatchDev &bt = b->bt;
-    if (!b->any_nodes) {
-        if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
-        if ((e = launch_lb_batch(bt, b->storage, b->forcing, b->det, false, odd, sm)) != cudaSuccess) return e;
-        if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
+    auto main_fluid = [&]() -> cudaError_t {
+        cudaError_t r;
+        if (timed && (r = batch_timed_event(b, sm)) != cudaSuccess) return r;
+        for (const ClassArgs &ca : b->classes)
+            if ((r = launch_lb_class(ca, b->storage, b->forcing, bt.cells_per_thread, odd, sm)) != cudaSuccess) return r;
+        if (timed && (r = batch_timed_event(b, sm)) != cudaSuccess) return r;
         return cudaSuccess;
-    }
+    };
+    if (!b->any_nodes) return main_fluid();
     if ((e = cudaStreamWaitEvent(sm, b->e_ib, 0)) != cudaSuccess) return e;
-    if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
-    if ((e = launch_lb_batch(bt, b->storage, b->forcing, b->det, false, odd, sm)) != cudaSuccess) return e;
-    if (timed && (e = batch_timed_event(b, sm)) != cudaSuccess) return e;
+    if ((e = main_fluid()) != cudaSuccess) return e;
     if ((e = launch_ib_batch(bt, b->kernel, b->det, 0, sib)) != cudaSuccess) return e;
     if ((e = launch_ib_batch(bt, b->kernel, b->det, 1, sib)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(sib, b->e_main, 0)) != cudaSuccess) return e;
@@ -934,6 +936,20 @@ int lb_batch_create(lbib_ctx *const *ctxs, int n, lbib_batch **out) {
         offs[k] = (int *)(dp + sizeof(DevCtx) * n + k * sizeof(int) * (n + 1));
         if (cudaMemcpy(offs[k], src[k]->data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(LBIB_ECUDA, "uploading the batch tables failed"));
+    }
+    // size classes for the main fluid launches (at most LBIB_CLASS_BOXES boxes per launch)
+    for (int i = 0; i < n; ++i) {
+        ClassArgs *hit = nullptr;
+        for (ClassArgs &ca : b->classes)
+            if (ca.n < LBIB_CLASS_BOXES && ca.box[0].nx == boxes[i].nx && ca.box[0].ny == boxes[i].ny &&
+                ca.box[0].nz == boxes[i].nz)
+                hit = &ca;
+        if (!hit) {
+            b->classes.emplace_back();
+            hit = &b->classes.back();
+            memset(hit, 0, sizeof(ClassArgs));
+        }
+        hit->box[hit->n++] = boxes[i];
     }
     BatchDev &bt = b->bt;
     bt.n_boxes = n;

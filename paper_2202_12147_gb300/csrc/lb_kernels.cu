@@ -565,6 +565,16 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_main_batch(const BatchDev bt) {
 
 // The marked tiles of every box form one flat work list: the per-box list
 // lengths are prefix-summed in shared memory, and a persistent grid walks it.
+template <int ST, bool ODD, int FORCING, int CPT>
+__global__ void LBIB_LB_BOUNDS(CPT) k_lb_main_class(const __grid_constant__ ClassArgs ca) {
+    const int nz = ca.box[0].nz;
+    const int b = blockIdx.z / nz;
+    const unsigned z = blockIdx.z - b * nz;
+    const DevCtx &c = ca.box[b];
+    const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * z);
+    lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, z);
+}
+
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked_batch(const BatchDev bt) {
     __shared__ int s_pref[LBIB_MAX_BATCH + 1];
@@ -712,6 +722,27 @@ static void batch_dispatch(const BatchDev &bt, bool marked, int det, bool odd, c
 
 cudaError_t launch_lb_batch(const BatchDev &bt, int storage, int forcing, int det, bool marked, bool odd, cudaStream_t s) {
     LBIB_DISPATCH(batch_dispatch, storage, forcing, bt, marked, det, odd, s);
+    return cudaGetLastError();
+}
+
+template <int ST, int FORCING, int CPT>
+static void class_dispatch_cpt(const ClassArgs &ca, bool odd, cudaStream_t s) {
+    const DevCtx &c = ca.box[0];
+    const dim3 blocks((unsigned)c.tiles_x, (unsigned)c.ny, (unsigned)(c.nz * ca.n));
+    const unsigned threads = (unsigned)((c.tile_x / CPT + 31) / 32 * 32);
+    if (odd) k_lb_main_class<ST, true, FORCING, CPT><<<blocks, threads, 0, s>>>(ca);
+    else k_lb_main_class<ST, false, FORCING, CPT><<<blocks, threads, 0, s>>>(ca);
+}
+
+template <int ST, int FORCING>
+static void class_dispatch(const ClassArgs &ca, int cpt, bool odd, cudaStream_t s) {
+    if (ST != LBIB_F32 && cpt == 4) class_dispatch_cpt<ST, FORCING, ST == LBIB_F32 ? 2 : 4>(ca, odd, s);
+    else if (cpt >= 2) class_dispatch_cpt<ST, FORCING, 2>(ca, odd, s);
+    else class_dispatch_cpt<ST, FORCING, 1>(ca, odd, s);
+}
+
+cudaError_t launch_lb_class(const ClassArgs &ca, int storage, int forcing, int cpt, bool odd, cudaStream_t s) {
+    LBIB_DISPATCH(class_dispatch, storage, forcing, ca, cpt, odd, s);
     return cudaGetLastError();
 }
 

@@ -138,6 +138,14 @@ struct BatchDev {
     int cells_per_thread;  // common to every box of the batch
 };
 
+// Boxes of one size passed by value to one launch of the main fluid kernel
+// (grid (tiles_x, ny, nz * n)); the descriptors sit in the parameter bank.
+constexpr int LBIB_CLASS_BOXES = 64;
+struct ClassArgs {
+    int n;
+    DevCtx box[LBIB_CLASS_BOXES];
+};
+
 // fixed-point scale of deterministic spreading: 2^48 units per force unit
 // (resolution 3.6e-15, range +-32768 per cell)
 constexpr double FIX_SCALE = 281474976710656.0;
@@ -181,6 +189,7 @@ cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, 
 cudaError_t launch_lb_marked(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
 cudaError_t launch_lb_macros(const DevCtx &c, int storage, bool odd, float *rho, float *u, cudaStream_t s);
 cudaError_t launch_lb_batch(const BatchDev &bt, int storage, int forcing, int det, bool marked, bool odd, cudaStream_t s);
+cudaError_t launch_lb_class(const ClassArgs &ca, int storage, int forcing, int cpt, bool odd, cudaStream_t s);
 // IB (ib_kernels.cu)
 cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s);
 cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s);

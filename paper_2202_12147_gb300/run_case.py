@@ -30,15 +30,29 @@ def _box(name):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="pair_side_3",
-                    help="single_48 | single_96 | pair_side_256cube | pair_{inline,side}_{3,5,8} (256x128x128)")
+                    help="single_48 | single_96 | pair_side_256cube | pair_{inline,side}_{3,5,8} (256x128x128) | ensemble")
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--deterministic", action="store_true")
     ap.add_argument("--kernel-by-kernel", action="store_true",
                     help="launch kernels one by one instead of replaying CUDA graphs")
     a = ap.parse_args(argv)
-    from paper_2202_12147_gb300 import Simulation
-    from workloads import assemble
+    from paper_2202_12147_gb300 import Batch, Simulation
+    from workloads import assemble, ensemble_boxes
+    if a.case == "ensemble":
+        boxes = ensemble_boxes(64, seed=0)
+        sims = [Simulation(b.dims, assemble(b), tau=b.tau, rho0=b.rho0, storage=a.storage,
+                           deterministic=a.deterministic) for b in boxes]
+        batch = Batch(sims)
+        if a.kernel_by_kernel:
+            batch.profile(True)
+        batch.lb_step(a.steps)
+        st = sims[0].swimmer_state(0)
+        print(f"ensemble of {len(sims)} boxes: step {st['step']}, box 0 swimmer 0 displacement {st['disp'].tolist()}")
+        batch.close()
+        for s in sims:
+            s.close()
+        return
     box = _box(a.case)
     sim = Simulation(box.dims, assemble(box), tau=box.tau, rho0=box.rho0, storage=a.storage,
                      deterministic=a.deterministic, forcing=box.forcing, kernel=box.kernel)
