@@ -31,6 +31,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS incl. IBM and % of HBM roofline (FP32 vs FP16-storage vs batched) at stated error"
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per launch of the FP32 main fluid kernel on one
+# 256x128x128 two-swimmer box, from the ncu capture summarised in
+# profiles/k_lb_main_pair_side_3_256x128x128.md (mean of both AA parities).
+# Reported as roofline.traffic only for FP32 storage.
+K_LB_MAIN_F32_DRAM_BYTES = 560.2e6
 WORKLOAD = "two_swimmer_boxes_256x128x128_x6"
 
 
@@ -387,7 +392,8 @@ def run_ours(a):
                        "l2": "inputs larger than L2 (populations 318 MB per box in FP32)",
                        "timing": "kernels launched one by one (two streams) with CUDA events around every main fluid-kernel launch"},
             "roofline": {"bound": "hbm", "kernel": "k_lb_main", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": K_LB_MAIN_F32_DRAM_BYTES if a.storage == "f32" else None,
                          "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
                          "launches": lb_n, "cells_per_launch": N - marked},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
