@@ -24,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbib_oracle.c")
+_INC = os.path.join(_HERE, "lbib_oracle_step.inc")
 _LIB = os.path.join(_HERE, "liblbib_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -35,7 +36,8 @@ NEOHOOKE, SKALAK = 0, 1
 
 def build(force=False):
     """Compile the oracle with gcc (FMA contraction off so x86 and Arm agree)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_INC))
+    if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=gnu99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                _SRC, "-o", tmp, "-lm"])
@@ -64,6 +66,16 @@ def lib():
             L.orc_membrane_energy.argtypes = [i, d, d, i, P, P, P]
             L.orc_membrane_energy.restype = d
             L.orc_membrane_forces.argtypes = [i, d, d, i, P, P, P, P]
+            # complex-step twins (double complex arguments as complex128 arrays)
+            L.orc_lb_step_cs.argtypes = [i, i, i, d, i, P, P, P, P, P, P]
+            L.orc_phi_cs.argtypes = [i, P, P]
+            L.orc_spread_cs.argtypes = [i, i, i, i, i, P, P, P]
+            L.orc_interpolate_cs.argtypes = [i, i, i, i, i, P, P, P]
+            L.orc_bead_centres_cs.argtypes = [i, P, P, P]
+            L.orc_drive_cs.argtypes = [P, P, i, d, d, P]
+            L.orc_springs_cs.argtypes = [d, d, P, P]
+            L.orc_membrane_energy_v_cs.argtypes = [i, d, d, i, P, P, P, P]
+            L.orc_membrane_forces_cs.argtypes = [i, d, d, i, P, P, P, P]
             _lib = L
     return _lib
 
@@ -74,6 +86,20 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _is_c(*arrays):
+    """True if any argument is complex: the call then runs the complex-step
+    twin of the C function on complex128 copies of every array."""
+    return any(np.iscomplexobj(a) for a in arrays if a is not None)
+
+
+def _fn(name, cplx):
+    return getattr(lib(), name + "_cs" if cplx else name)
 
 
 def lattice():
@@ -91,22 +117,30 @@ def equilibrium(rho, u):
 
 
 def phi(r, kernel=PESKIN4):
+    if _is_c(np.asarray(r)):
+        x = np.array([r], dtype=np.complex128)
+        out = np.zeros(1, dtype=np.complex128)
+        lib().orc_phi_cs(kernel, _p(x), _p(out))
+        return complex(out[0])
     return lib().orc_phi(kernel, float(r))
 
 
 def lb_step(f, dims, tau, F=None, g=(0.0, 0.0, 0.0), forcing=GUO):
-    """One collide+stream of raw populations f (N,19). Returns (fnew, rho, u)."""
+    """One collide+stream of raw populations f (N,19). Returns (fnew, rho, u).
+    Complex inputs run the complex-step twin."""
     nx, ny, nz = dims
-    f = _f64(f)
+    cplx = _is_c(f, F, np.asarray(g))
+    cv = _c128 if cplx else _f64
+    f = cv(f)
     fnew = np.empty_like(f)
-    rho = np.empty(f.shape[0])
-    u = np.empty((f.shape[0], 3))
-    g = _f64(g)
-    Fp = _p(_f64(F)) if F is not None else None
+    rho = np.empty(f.shape[0], dtype=f.dtype)
+    u = np.empty((f.shape[0], 3), dtype=f.dtype)
+    g = cv(g)
+    Fp = None
     if F is not None:
-        F = _f64(F)
+        F = cv(F)
         Fp = _p(F)
-    lib().orc_lb_step(nx, ny, nz, float(tau), forcing, Fp, _p(g), _p(f), _p(fnew), _p(rho), _p(u))
+    _fn("orc_lb_step", cplx)(nx, ny, nz, float(tau), forcing, Fp, _p(g), _p(f), _p(fnew), _p(rho), _p(u))
     return fnew, rho, u
 
 
@@ -120,51 +154,72 @@ def macros(f):
 
 def spread(r, fn, dims, kernel=PESKIN4, F=None):
     nx, ny, nz = dims
-    r, fn = _f64(r), _f64(fn)
+    cplx = _is_c(r, fn, F)
+    cv = _c128 if cplx else _f64
+    r, fn = cv(r), cv(fn)
     if F is None:
-        F = np.zeros((nx * ny * nz, 3))
-    lib().orc_spread(kernel, nx, ny, nz, r.shape[0], _p(r), _p(fn), _p(F))
+        F = np.zeros((nx * ny * nz, 3), dtype=r.dtype)
+    elif F.dtype != r.dtype or not F.flags.c_contiguous:
+        raise TypeError("F must be a C-contiguous array of the arguments' dtype")
+    _fn("orc_spread", cplx)(kernel, nx, ny, nz, r.shape[0], _p(r), _p(fn), _p(F))
     return F
 
 
 def interpolate(r, u, dims, kernel=PESKIN4):
     nx, ny, nz = dims
-    r, u = _f64(r), _f64(u)
-    v = np.zeros((r.shape[0], 3))
-    lib().orc_interpolate(kernel, nx, ny, nz, r.shape[0], _p(r), _p(u), _p(v))
+    cplx = _is_c(r, u)
+    cv = _c128 if cplx else _f64
+    r, u = cv(r), cv(u)
+    v = np.zeros((r.shape[0], 3), dtype=r.dtype)
+    _fn("orc_interpolate", cplx)(kernel, nx, ny, nz, r.shape[0], _p(r), _p(u), _p(v))
     return v
 
 
 def bead_centres(r, beads):
     beads = np.ascontiguousarray(beads, dtype=np.int32)
-    R = np.zeros((beads.shape[0], 3))
-    lib().orc_bead_centres(beads.shape[0], _p(beads), _p(_f64(r)), _p(R))
+    cplx = _is_c(r)
+    r = (_c128 if cplx else _f64)(r)
+    R = np.zeros((beads.shape[0], 3), dtype=r.dtype)
+    _fn("orc_bead_centres", cplx)(beads.shape[0], _p(beads), _p(r), _p(R))
     return R
 
 
 def drive(amp, phase, balance, period, t):
-    out = np.zeros((3, 3))
-    lib().orc_drive(_p(_f64(amp)), _p(_f64(phase)), int(balance), float(period), float(t), _p(out))
+    cplx = _is_c(np.asarray(amp), np.asarray(phase))
+    cv = _c128 if cplx else _f64
+    out = np.zeros((3, 3), dtype=np.complex128 if cplx else np.float64)
+    _fn("orc_drive", cplx)(_p(cv(amp)), _p(cv(phase)), int(balance), float(period), float(t), _p(out))
     return out
 
 
 def springs(k, L, R):
-    out = np.zeros((3, 3))
-    lib().orc_springs(float(k), float(L), _p(_f64(R)), _p(out))
+    cplx = _is_c(R)
+    R = (_c128 if cplx else _f64)(R)
+    out = np.zeros((3, 3), dtype=R.dtype)
+    _fn("orc_springs", cplx)(float(k), float(L), _p(R), _p(out))
     return out
 
 
 def membrane_energy(X, x, tris, p1, p2=0.0, law=NEOHOOKE):
     tris = np.ascontiguousarray(tris, dtype=np.int32)
+    if _is_c(X, x):
+        W = np.zeros(1, dtype=np.complex128)
+        lib().orc_membrane_energy_v_cs(law, float(p1), float(p2), tris.shape[0], _p(tris), _p(_c128(X)),
+                                       _p(_c128(x)), _p(W))
+        return complex(W[0])
     return lib().orc_membrane_energy(law, float(p1), float(p2), tris.shape[0], _p(tris), _p(_f64(X)), _p(_f64(x)))
 
 
 def membrane_forces(X, x, tris, p1, p2=0.0, law=NEOHOOKE, out=None):
     tris = np.ascontiguousarray(tris, dtype=np.int32)
-    x = _f64(x)
+    cplx = _is_c(X, x, out)
+    cv = _c128 if cplx else _f64
+    x = cv(x)
     if out is None:
         out = np.zeros_like(x)
-    lib().orc_membrane_forces(law, float(p1), float(p2), tris.shape[0], _p(tris), _p(_f64(X)), _p(x), _p(out))
+    elif out.dtype != x.dtype or not out.flags.c_contiguous:
+        raise TypeError("out must be a C-contiguous array of the positions' dtype")
+    _fn("orc_membrane_forces", cplx)(law, float(p1), float(p2), tris.shape[0], _p(tris), _p(cv(X)), _p(x), _p(out))
     return out
 
 
@@ -174,23 +229,31 @@ class OracleSim:
     State: raw populations f (N,19) in the oracle's lattice order, node
     positions (M,3) unwrapped, step counter t.  The rest shape of every
     membrane is the node set given at construction.
+
+    dtype=np.complex128 runs the complex-step twin of every function; `drive`
+    optionally replaces each swimmer's drive parameters by an (n_swimmers, 6)
+    array (A1, A2, A3, phi1, phi2, phi3), complex for complex-step
+    derivatives.  For a swimmer with `balance`, A2 and phi2 are unused.
     """
 
-    def __init__(self, box, asm=None, f=None):
+    def __init__(self, box, asm=None, f=None, dtype=np.float64, drive=None):
         from workloads import assemble
         self.box = box
         self.dims = tuple(box.dims)
         self.N = box.n_cells
+        self.dtype = np.dtype(dtype)
         self.asm = asm if asm is not None else assemble(box)
         self.c, self.w = lattice()
-        self.f = np.tile(self.w * box.rho0, (self.N, 1)) if f is None else _f64(f).copy()
-        self.rest = self.asm["nodes"].copy()
-        self.r = self.asm["nodes"].copy()
+        self.f = (np.tile(self.w * box.rho0, (self.N, 1)) if f is None else np.array(f)).astype(self.dtype)
+        self.rest = self.asm["nodes"].astype(self.dtype)
+        self.r = self.asm["nodes"].astype(self.dtype)
         self.t = 0
         self.forcing = SHAN_CHEN if box.forcing == "shan_chen" else GUO
         self.kernel = LINEAR2 if box.kernel == "linear2" else PESKIN4
-        self.u = np.zeros((self.N, 3))
-        self.rho = np.full(self.N, box.rho0)
+        self.drive = drive_parameters(self.asm) if drive is None else np.array(drive)
+        self.drive = self.drive.astype(np.result_type(self.drive.dtype, np.float64))
+        self.u = np.zeros((self.N, 3), dtype=self.dtype)
+        self.rho = np.full(self.N, box.rho0, dtype=self.dtype)
         self.v = np.zeros_like(self.r)
         self.node_force = np.zeros_like(self.r)
         self.F = None
@@ -200,13 +263,14 @@ class OracleSim:
         a = self.asm
         beads = a["beads"]
         R = bead_centres(self.r, beads)
-        fn = np.zeros_like(self.r)
+        fn = np.zeros(self.r.shape, dtype=np.result_type(self.r.dtype, self.drive.dtype))
         for b in range(beads.shape[0]):
             n0, nn, t0, nt = beads[b]
-            membrane_forces(self.rest, self.r, a["tris"][t0:t0 + nt], a["bead_Gs"][b], out=fn)
-        for s in a["swimmers"]:
+            membrane_forces(self.rest.astype(fn.dtype), self.r.astype(fn.dtype), a["tris"][t0:t0 + nt],
+                            a["bead_Gs"][b], out=fn)
+        for k, s in enumerate(a["swimmers"]):
             ids = s["beads"]
-            fd = drive(s["amp"], s["phase"], s["balance"], s["period"], self.t)
+            fd = drive(self.drive[k, 0:3], self.drive[k, 3:6], s["balance"], s["period"], self.t)
             fs = springs(s["k"], s["L"], R[ids])
             for q, b in enumerate(ids):
                 n0, nn = beads[b][0], beads[b][1]
@@ -231,3 +295,55 @@ class OracleSim:
         """x_cm of every swimmer: the mean of its three bead centres (Sec. 3, Eq. vel_swim)."""
         R = bead_centres(self.r, self.asm["beads"])
         return np.array([R[s["beads"]].mean(axis=0) for s in self.asm["swimmers"]])
+
+
+# ----------------------------------------------------------------------------
+# Net displacement and its derivatives with respect to the drive parameters
+# ----------------------------------------------------------------------------
+
+def drive_parameters(asm):
+    """(n_swimmers, 6) array of each swimmer's drive (A1, A2, A3, phi1, phi2, phi3)."""
+    return np.array([list(s["amp"]) + list(s["phase"]) for s in asm["swimmers"]], dtype=np.float64).reshape(-1, 6)
+
+
+def displacement(box, steps, drive=None, asm=None, dtype=np.float64):
+    """Net displacement x_cm(steps) - x_cm(0) of every swimmer, (n_swimmers, 3),
+    starting from rest (Sec. 3: the swimmer's displacement over its stroke)."""
+    sim = OracleSim(box, asm, dtype=dtype, drive=drive)
+    x0 = sim.swimmer_centres()
+    sim.step(steps)
+    return sim.swimmer_centres() - x0
+
+
+def displacement_jacobian_cs(box, steps, params, drive=None, asm=None, h=1e-30):
+    """Exact derivative of the discrete map: d disp / d theta_p for each
+    parameter p = (swimmer, index into the 6 drive entries), by the complex
+    step theta_p + i h (Squire & Trapp 1998).  Returns (len(params), n_sw, 3)."""
+    from workloads import assemble
+    asm = asm if asm is not None else assemble(box)
+    base = drive_parameters(asm) if drive is None else np.asarray(drive, dtype=np.float64)
+    out = []
+    for (s, k) in params:
+        th = base.astype(np.complex128)
+        th[s, k] += 1j * h
+        d = displacement(box, steps, th, asm, dtype=np.complex128)
+        out.append(d.imag / h)
+    return np.array(out)
+
+
+def displacement_jacobian_fd(box, steps, params, drive=None, asm=None, rel_h=1e-6):
+    """Central finite differences of the FP64 displacement with step
+    h = rel_h * |theta_p|.  Returns (len(params), n_sw, 3)."""
+    from workloads import assemble
+    asm = asm if asm is not None else assemble(box)
+    base = drive_parameters(asm) if drive is None else np.asarray(drive, dtype=np.float64)
+    out = []
+    for (s, k) in params:
+        h = rel_h * abs(base[s, k])
+        tp, tm = base.copy(), base.copy()
+        tp[s, k] += h
+        tm[s, k] -= h
+        dp = displacement(box, steps, tp, asm)
+        dm = displacement(box, steps, tm, asm)
+        out.append((dp - dm) / (2.0 * h))
+    return np.array(out)

@@ -156,10 +156,38 @@ def pair_side_256cube():
     return swimmer_pair("side", 3, dims=(256, 256, 256))
 
 
+def balanced_drive(A=1e-3, B=1e-3, alpha=math.pi / 2):
+    """Per-bead drive (A1, A2, A3, phi1, phi2, phi3) whose middle bead carries
+    minus the sum of the outer two: f1 + f3 = A sin(wt) + B sin(wt + alpha)
+    = C sin(wt + beta) with C = sqrt(A^2 + B^2 + 2AB cos alpha) and
+    beta = atan2(B sin alpha, A + B cos alpha), so f2 = C sin(wt + beta + pi).
+    For A = B = 1e-3, alpha = pi/2: A2 = sqrt(2) 1e-3, phi2 = 5 pi/4."""
+    C = math.sqrt(A * A + B * B + 2.0 * A * B * math.cos(alpha))
+    beta = math.atan2(B * math.sin(alpha), A + B * math.cos(alpha))
+    return (A, C, B, 0.0, beta + math.pi, alpha)
+
+
+def free_drive(spec: SwimmerSpec, theta):
+    """The swimmer with independent per-bead drives theta = (A1, A2, A3, phi1, phi2, phi3)."""
+    return replace(spec, amp=tuple(float(v) for v in theta[:3]), phase=tuple(float(v) for v in theta[3:6]),
+                   balance=False)
+
+
 def adjoint_single_96(period=1000.0):
-    """Single swimmer (radius 6, subdivision 3, spacing 18) in 96^3, period 1000."""
-    s = _pair_swimmer((48.0, 48.0, 48.0), period)
+    """Single swimmer (radius 6, subdivision 3, spacing 18) in 96^3, period
+    1000, with independent per-bead drives at the base point that reproduces
+    the paper's protocol (A = B = 1e-3, alpha = pi/2, see `balanced_drive`)."""
+    s = free_drive(_pair_swimmer((48.0, 48.0, 48.0), period), balanced_drive())
     return BoxSpec(dims=(96, 96, 96), swimmers=(s,), name="adjoint_single_96")
+
+
+def adjoint_small(dims=(32, 24, 24), period=100.0):
+    """Small adjoint test box: one swimmer of radius 3 (subdivision 1, 42
+    nodes per bead), spacing 9, period 100, free per-bead drives at the
+    balanced base point."""
+    c = tuple(float(d // 2) for d in dims)
+    s = SwimmerSpec(center=c, radius=3.0, subdiv=1, spacing=9.0, k_spring=0.005, Gs=0.01, period=period)
+    return BoxSpec(dims=dims, swimmers=(free_drive(s, balanced_drive()),), name=f"adjoint_small_{dims[0]}x{dims[1]}x{dims[2]}")
 
 
 def fluid_box(dims, tau=1.0, g=(0.0, 0.0, 0.0), forcing="guo"):
