@@ -54,6 +54,9 @@ def _args():
     ap.add_argument("--no-ensemble", dest="ensemble", action="store_false",
                     help="skip the batched 64-box ensemble line")
     ap.add_argument("--ensemble-steps", type=int, default=32)
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
+                    help="skip the adjoint (drive-gradient) line")
+    ap.add_argument("--adjoint-precision", default="f32", choices=["f32", "f64"])
     return ap.parse_args()
 
 
@@ -239,6 +242,52 @@ def _run_ensemble(a, barrier, stream, ws):
             "round_robin_means": "every step, each box launched on its own (one coupled step per call), box after box"}
 
 
+def _run_adjoint(a, barrier, stream):
+    """Gradient of a swimmer's net x displacement over one drive period with
+    respect to its per-bead amplitudes and phases: one swimmer in 96^3, 1000
+    steps, checkpoints every 100 steps.  Device time of the engine's forward
+    and backward sweeps (CUDA events inside the library), next to the plain
+    coupled step (lb_step) over the same 1000 steps."""
+    import numpy as np
+    import torch
+    from paper_2202_12147_gb300 import Adjoint, Simulation
+    from workloads import adjoint_single_96, assemble
+    box = adjoint_single_96()
+    asm = assemble(box)
+    steps, K = 1000, 100
+    eng = Adjoint(box.dims, asm, n_steps=steps, K=K, precision=a.adjoint_precision)
+    eng.forward()  # warm-up sweep
+    eng.backward(np.array([[1.0, 0.0, 0.0]]))
+    barrier()
+    d = eng.forward()
+    g = eng.backward(np.array([[1.0, 0.0, 0.0]]))
+    t = eng.timing()
+    ws_bytes = eng.workspace_bytes
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
+    sim = Simulation(box.dims, asm, tau=box.tau, rho0=box.rho0)
+    sim.lb_step(32)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.lb_step(steps)
+    e1.record(stream)
+    barrier()
+    fwd_ms = e0.elapsed_time(e1)
+    sim.sync()
+    sim.close()
+    return {"workload": "one swimmer (beads radius 6, 642 nodes), 96^3, one drive period of 1000 steps, "
+                        "checkpoint every 100 steps", "precision": a.adjoint_precision,
+            "objective": "x_cm(T) - x_cm(0)", "displacement": float(d[0, 0]),
+            "gradient": {"A1": g[0, 0], "A2": g[0, 1], "A3": g[0, 2], "phi2": g[0, 4], "phi3": g[0, 5]},
+            "engine_forward_ms": t["forward_ms"], "engine_backward_ms": t["backward_ms"],
+            "lb_step_1000_ms": fwd_ms, "backward_over_lb_step": t["backward_ms"] / fwd_ms,
+            "forward_plus_backward_over_lb_step": (t["forward_ms"] + t["backward_ms"]) / fwd_ms,
+            "launches": {"forward": t["forward_launches"], "backward": t["backward_launches"]},
+            "workspace_GB": ws_bytes / 1e9}
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -341,6 +390,10 @@ def run_ours(a):
     if a.ensemble and a.storage == "f32":
         ensemble = _run_ensemble(a, barrier, stream, ws)
 
+    adjoint = None
+    if a.adjoint and a.storage == "f32" and rank == 0:
+        adjoint = _run_adjoint(a, torch.cuda.synchronize, stream)  # rank 0 only: no collective barrier
+
     e2e = None
     if not a.no_e2e:
         # End to end through the public API: structure upload from host arrays
@@ -397,7 +450,7 @@ def run_ours(a):
                          "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
                          "launches": lb_n, "cells_per_launch": N - marked},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-            "variants": variants, "ensemble": ensemble,
+            "variants": variants, "ensemble": ensemble, "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

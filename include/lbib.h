@@ -280,6 +280,73 @@ int lb_batch_destroy(lbib_batch *b);
  * LBIB_EINVAL while the context belongs to a batch. */
 int lb_destroy(lbib_ctx *ctx);
 
+/* ---- adjoint: gradients with respect to the drive --------------------
+ * Reverse-mode derivative of the coupled step (the one of the header comment,
+ * Sec. 2.1-2.3) over n_steps steps, for gradients of swimmer displacements
+ * x_cm(T) - x_cm(0) (Sec. 3, Eq. vel_swim) with respect to every bead's drive
+ * amplitude and phase (Sec. 2.2, driving-force equation, generalised to
+ * f_b = A_b sin(2 pi t / period + phi_b) on each bead b).
+ *
+ * The engine runs its own forward step on a plain layout (two population
+ * arrays, push streaming, full per-step records) in FP32 or FP64 fluid
+ * precision; node positions, forces and every node-level derivative are
+ * FP64.  It keeps a checkpoint (populations + node positions) every K steps
+ * and, sweeping backward, recomputes each K-step segment from its checkpoint
+ * before reversing it, so memory grows with n_steps / K + K states rather
+ * than n_steps.  Only Guo forcing and the 4-point kernel (differentiable; the
+ * 2-point kernel is not) are supported.  The drive parameter vector of
+ * swimmer s is theta[6 s .. 6 s + 5] = (A_1, A_2, A_3, phi_1, phi_2, phi_3)
+ * in the order of lbib_swimmer.bead; for a swimmer with balance = 1 the
+ * middle bead carries -(f_1 + f_3) and its entries A_2, phi_2 are unused
+ * (their gradient is 0). */
+#define LBIB_F64 3 /* adjoint engine only: FP64 fluid state */
+
+typedef struct lbib_adjoint lbib_adjoint;
+
+/* Bytes of device workspace an engine needs: params as for lb_init with
+ * storage LBIB_F32 or LBIB_F64, forcing LBIB_GUO, kernel LBIB_PESKIN4;
+ * n_steps >= 1 steps per sweep; a checkpoint every K >= 1 steps. */
+int lb_adjoint_required_bytes(const lb_params *params, const lbib_structure *structure, long long n_steps, int K,
+                              size_t *bytes);
+/* Create an engine on a caller-owned DEVICE workspace of at least
+ * lb_adjoint_required_bytes (256-byte aligned; borrowed, must outlive the
+ * engine).  The initial state is the rest state (f_i = w_i rho0, nodes at the
+ * rest shape) and theta is taken from the structure's swimmers.  Work is
+ * queued on `stream`.  Synchronous. */
+int lb_adjoint_create(const lb_params *params, const lbib_structure *structure, long long n_steps, int K,
+                      void *workspace, size_t workspace_bytes, void *stream, lbib_adjoint **out);
+/* Replace the drive parameters: HOST theta, n_swimmers x 6.  Invalidates the
+ * last forward sweep. */
+int lb_adjoint_set_drive(lbib_adjoint *a, const double *theta);
+/* Replace the initial state: HOST populations f (19 x n_cells, raw f_i in the
+ * order of lbib_lattice, cell = x + nx*(y + ny*z)) and/or node positions r
+ * (n_nodes x 3); NULL keeps that part.  Invalidates the last forward sweep. */
+int lb_adjoint_set_initial(lbib_adjoint *a, const double *f, const double *r);
+/* Forward sweep: n_steps coupled steps from the initial state, storing the
+ * checkpoints.  disp (HOST, n_swimmers x 3, may be NULL) receives every
+ * swimmer's x_cm(T) - x_cm(0).  Synchronous; LBIB_ENONFINITE or
+ * LBIB_EUNSTABLE if the run blew up. */
+int lb_adjoint_forward(lbib_adjoint *a, double *disp);
+/* Reverse sweep of the last forward sweep for the objective
+ *   L = sum_s seed_disp[s] . disp_s + <seed_f, f(T)> + <seed_r, r(T)>
+ * (HOST seeds: seed_disp n_swimmers x 3, required; seed_f 19 x n_cells and
+ * seed_r n_nodes x 3 optional, NULL = 0).  Writes HOST outputs
+ * grad_theta (n_swimmers x 6, required) = dL/dtheta and, if not NULL,
+ * grad_f0 (19 x n_cells) = dL/df(0) and grad_r0 (n_nodes x 3) = dL/dr(0).
+ * Synchronous.  LBIB_EINVAL without a valid forward sweep. */
+int lb_adjoint_backward(lbib_adjoint *a, const double *seed_disp, const double *seed_f, const double *seed_r,
+                        double *grad_theta, double *grad_f0, double *grad_r0);
+/* State after the last forward sweep (HOST, layouts as lb_adjoint_set_initial;
+ * either pointer may be NULL).  Synchronous. */
+int lb_adjoint_get_final(lbib_adjoint *a, double *f, double *r);
+/* Device time of the last forward and backward sweeps, milliseconds (CUDA
+ * events on the engine's stream), and the number of kernel launches each
+ * made. */
+int lb_adjoint_timing(lbib_adjoint *a, double *forward_ms, double *backward_ms, long long *forward_launches,
+                      long long *backward_launches);
+/* Release the engine (not the workspace).  Synchronises. */
+int lb_adjoint_destroy(lbib_adjoint *a);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,4 +13,7 @@ def __getattr__(name):
     if name in ("Simulation", "Batch", "lattice", "required_sizes"):
         from . import sim
         return getattr(sim, name)
+    if name in ("Adjoint", "DisplacementFn", "displacement"):
+        from . import adjoint
+        return getattr(adjoint, name)
     raise AttributeError(name)

@@ -13,7 +13,7 @@ _lock = threading.Lock()
 _lib = None
 
 LBIB_OK, LBIB_EINVAL, LBIB_ECUDA, LBIB_ENONFINITE, LBIB_EUNSTABLE, LBIB_ETIMEOUT, LBIB_ESIZE = 0, -1, -2, -3, -4, -5, -6
-F32, F16, BF16 = 0, 1, 2
+F32, F16, BF16, F64 = 0, 1, 2, 3
 GUO, SHAN_CHEN = 0, 1
 PESKIN4, LINEAR2 = 0, 1
 NBUF = 3
@@ -24,7 +24,9 @@ EXPORTS = [
     "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces", "lb_get_force_field",
     "lb_set_velocity", "lb_profile", "lb_profile_read", "lb_marked_cells", "ib_spread_fixed_noalloc",
     "lb_batch_create", "lb_batch_step", "lb_batch_profile", "lb_batch_profile_read", "lb_batch_destroy",
-    "lb_destroy",
+    "lb_destroy", "lb_adjoint_required_bytes", "lb_adjoint_create", "lb_adjoint_set_drive",
+    "lb_adjoint_set_initial", "lb_adjoint_forward", "lb_adjoint_backward", "lb_adjoint_get_final",
+    "lb_adjoint_timing", "lb_adjoint_destroy",
 ]
 
 
@@ -114,6 +116,17 @@ def load(build_if_missing: bool = True):
         L.lb_batch_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)]
         L.lb_batch_destroy.argtypes = [P]
         L.lb_destroy.argtypes = [P]
+        L.lb_adjoint_required_bytes.argtypes = [ctypes.POINTER(LbParams), ctypes.POINTER(Structure), LL, I, P]
+        L.lb_adjoint_create.argtypes = [ctypes.POINTER(LbParams), ctypes.POINTER(Structure), LL, I, P,
+                                        ctypes.c_size_t, P, ctypes.POINTER(P)]
+        L.lb_adjoint_set_drive.argtypes = [P, P]
+        L.lb_adjoint_set_initial.argtypes = [P, P, P]
+        L.lb_adjoint_forward.argtypes = [P, P]
+        L.lb_adjoint_backward.argtypes = [P, P, P, P, P, P, P]
+        L.lb_adjoint_get_final.argtypes = [P, P, P]
+        L.lb_adjoint_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(LL), ctypes.POINTER(LL)]
+        L.lb_adjoint_destroy.argtypes = [P]
         for n in EXPORTS:
             if n not in ("lbib_version", "lbib_strerror", "lbib_last_error"):
                 getattr(L, n).restype = I

@@ -1,0 +1,1161 @@
+// Reverse-mode derivative of the coupled lattice-Boltzmann / immersed-
+// boundary step (Sec. 2.1-2.3) for gradients of swimmer displacements with
+// respect to the per-bead drive parameters (Sec. 2.2, driving-force equation).
+//
+// The engine keeps its own forward step on a plain layout so that every
+// intermediate the reverse sweep needs is a stored array: per step k of a
+// segment, slot k holds the populations f^k (shifted deviations, 19 planes),
+// the force field F^k, the velocity u^k (3 planes each), node positions r^k,
+// nodal forces f_j^k, bead centres R^k and the external bead forces.  Forward
+// step k reads slot k and writes the populations, positions and a cleared
+// force field of slot k + 1 (push streaming into a second array).  A
+// checkpoint (populations + positions) is kept every K steps; the reverse
+// sweep recomputes each segment from its checkpoint, then walks it backward.
+//
+// Forward step (the order the oracle and lb_step use):
+//   R_b = mean_j r_j;  e_b = f^d_b(t) x + f^s_b(R)                (Sec. 2.2)
+//   f_j = sum_triangles -dW/dr_j + e_b / N_b                        (Sec. 2.2)
+//   F(x) = sum_j f_j Delta(x - r_j)                                 (Sec. 2.3)
+//   rho, u = (sum f c + F/2)/rho; f* = f - (f - f^eq)/tau + Guo source; push (Sec. 2.1)
+//   r_j += sum_x u(x) Delta(x - r_j)                                (Sec. 2.3)
+// Reverse step, with adjoints lam_f (populations), lam_r (positions):
+//   lam_U = lam_r;  lam_u(x) += Delta lam_U;  lam_r += grad_r <u, lam_U> Delta
+//   per cell: lam*_i(x) = lam_f_i(x + c_i); the collision's Jacobian is
+//     (1 - omega) I plus a rank-4 term through rho and rho u, so
+//     lam_f_i = (1 - omega) lam*_i + lam_rho + c_i . lam_m, and lam_F
+//   lam_fj = sum_x lam_F(x) Delta;  lam_r += grad_r <lam_F, f_j> Delta
+//   lam_r += (d f_mem / d r) lam_f  (symmetric: minus the membrane Hessian)
+//   lam_e_b = mean over the bead of lam_fj -> drive gradient, spring Jacobian
+//     -> lam_R_b -> lam_r += lam_R_b / N_b
+// Fluid arrays are FP32 or FP64 (template T); everything node-level is FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbib_internal.cuh"
+
+using namespace lbib;
+
+namespace {
+
+constexpr size_t AL = 256;
+size_t up(size_t v) { return (v + AL - 1) / AL * AL; }
+
+struct Dims {
+    int nx, ny, nz;
+    long long N, Npad;
+};
+
+// Structure tables (device pointers)
+struct Mesh {
+    int M, T, B, S;
+    const int *tris;        // T x 3 node ids
+    const double *G;        // T x 3 rest metric G00, G01, G11
+    const double *A0Gs;     // T: rest area x shear modulus
+    const int *csr_ptr;     // M + 1
+    const int *csr_ent;     // 3T entries 3 t + q
+    const int *node_bead;   // M
+    const int *bead_start;  // B
+    const int *bead_count;  // B
+    const int *bead_swim;   // B
+};
+
+struct Swim {
+    int bead[3];
+    int balance;
+    double k, L, period;
+};
+
+__device__ __forceinline__ int wrapi(long long a, int n) {
+    long long r = a % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+// Peskin's 4-point weight of stencil cell q (of floor(p) - 1 .. floor(p) + 2)
+// at fractional offset f, and its derivative with respect to p: with
+// s = sqrt(1 + 4f - 4f^2) the weights are (3 - 2f - s)/8, (3 - 2f + s)/8,
+// (1 + 2f + s)/8, (1 + 2f - s)/8, and ds/df = (2 - 4f)/s.
+__device__ __forceinline__ void peskin_q(double f, double s, double ds, int q, double &w, double &dw) {
+    const double A = q < 2 ? 3.0 - 2.0 * f : 1.0 + 2.0 * f, dA = q < 2 ? -2.0 : 2.0;
+    const double sg = (q == 1 || q == 2) ? 1.0 : -1.0;
+    w = (A + sg * s) * 0.125;
+    dw = (dA + sg * ds) * 0.125;
+}
+
+// The two stencil cells of a lane (numbers lane and lane + 32 of the 64,
+// x fastest: they differ in z only), their weights Delta(x - r) and
+// gradients d Delta / d r.
+__device__ __forceinline__ void lane_cells(const Dims &d, const double *r, int lane, long long cell[2], double w[2],
+                                           double g[2][3]) {
+    const int qx = lane & 3, qy = (lane >> 2) & 3, qz = lane >> 4;
+    const double fx = floor(r[0]), fy = floor(r[1]), fz = floor(r[2]);
+    const double ax = r[0] - fx, ay = r[1] - fy, az = r[2] - fz;
+    const double sx = sqrt(1.0 + 4.0 * ax - 4.0 * ax * ax), sy = sqrt(1.0 + 4.0 * ay - 4.0 * ay * ay),
+                 sz = sqrt(1.0 + 4.0 * az - 4.0 * az * az);
+    double wx, dx, wy, dy;
+    peskin_q(ax, sx, (2.0 - 4.0 * ax) / sx, qx, wx, dx);
+    peskin_q(ay, sy, (2.0 - 4.0 * ay) / sy, qy, wy, dy);
+    const int X = wrapi((long long)fx - 1 + qx, d.nx), Y = wrapi((long long)fy - 1 + qy, d.ny);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        double wz, dz;
+        peskin_q(az, sz, (2.0 - 4.0 * az) / sz, qz + 2 * h, wz, dz);
+        const int Z = wrapi((long long)fz - 1 + qz + 2 * h, d.nz);
+        cell[h] = X + (long long)d.nx * (Y + (long long)d.ny * Z);
+        w[h] = wx * wy * wz;
+        g[h][0] = dx * wy * wz;
+        g[h][1] = wx * dy * wz;
+        g[h][2] = wx * wy * dz;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum of three doubles; the result is valid in thread 0
+__device__ __forceinline__ void block_sum3(double v[3], double (*sh)[3]) {
+    for (int a = 0; a < 3; ++a) v[a] = warp_sum(v[a]);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int a = 0; a < 3; ++a) sh[w][a] = v[a];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) v[a] = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+            for (int a = 0; a < 3; ++a) v[a] += sh[k][a];
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- membrane
+// Neo-Hookean linear FEM triangle (Sec. 2.2): with edge vectors d = [d1 d2],
+// rest metric G, E = (d^T d - G)/2 (FP64, small near rest),
+// I2 = 2 tr(G^-1 E) + 4 det E / det G, J^4 = (1 + I2)^2:
+//   dW/dd = s d M,  s = A0 Gs / (det G J^4),
+//   M = (J^4 - 1) adj G - 2 adj E,  adj [[a, b], [b, c]] = [[c, -b], [-b, a]],
+// and the corner forces are f1 = -P[:,0], f2 = -P[:,1], f0 = P[:,0] + P[:,1].
+struct TriState {
+    double d1[3], d2[3];
+    double E00, E01, E11, detG, I2, J2, J4, s, M00, M01, M11;
+};
+
+__device__ __forceinline__ void tri_state(const double *G, double A0Gs, const double *x0, const double *x1,
+                                          const double *x2, TriState &S) {
+    for (int a = 0; a < 3; ++a) {
+        S.d1[a] = x1[a] - x0[a];
+        S.d2[a] = x2[a] - x0[a];
+    }
+    const double g00 = S.d1[0] * S.d1[0] + S.d1[1] * S.d1[1] + S.d1[2] * S.d1[2];
+    const double g01 = S.d1[0] * S.d2[0] + S.d1[1] * S.d2[1] + S.d1[2] * S.d2[2];
+    const double g11 = S.d2[0] * S.d2[0] + S.d2[1] * S.d2[1] + S.d2[2] * S.d2[2];
+    S.E00 = 0.5 * (g00 - G[0]);
+    S.E01 = 0.5 * (g01 - G[1]);
+    S.E11 = 0.5 * (g11 - G[2]);
+    S.detG = G[0] * G[2] - G[1] * G[1];
+    const double trGiE = (G[2] * S.E00 - 2.0 * G[1] * S.E01 + G[0] * S.E11) / S.detG;
+    const double detE = S.E00 * S.E11 - S.E01 * S.E01;
+    S.I2 = 2.0 * trGiE + 4.0 * detE / S.detG;
+    S.J2 = 1.0 + S.I2;
+    S.J4 = S.J2 * S.J2;
+    S.s = A0Gs / (S.detG * S.J4);
+    const double c = S.I2 * (S.I2 + 2.0);  // J^4 - 1
+    S.M00 = c * G[2] - 2.0 * S.E11;
+    S.M01 = -c * G[1] + 2.0 * S.E01;
+    S.M11 = c * G[0] - 2.0 * S.E00;
+}
+
+// directional derivative of the corner forces along node displacements
+// v0, v1, v2 (the force Jacobian is minus the energy Hessian: symmetric, so
+// this is also the transposed product the reverse sweep needs)
+__device__ __forceinline__ void tri_force_jvp(const double *G, const TriState &S, const double *v0, const double *v1,
+                                              const double *v2, double df[3][3]) {
+    double e1[3], e2[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = v1[a] - v0[a];
+        e2[a] = v2[a] - v0[a];
+    }
+    const double dE00 = S.d1[0] * e1[0] + S.d1[1] * e1[1] + S.d1[2] * e1[2];
+    const double dE11 = S.d2[0] * e2[0] + S.d2[1] * e2[1] + S.d2[2] * e2[2];
+    const double dE01 = 0.5 * (S.d1[0] * e2[0] + S.d1[1] * e2[1] + S.d1[2] * e2[2] + e1[0] * S.d2[0] +
+                               e1[1] * S.d2[1] + e1[2] * S.d2[2]);
+    const double dtr = (G[2] * dE00 - 2.0 * G[1] * dE01 + G[0] * dE11) / S.detG;
+    const double ddetE = dE00 * S.E11 + S.E00 * dE11 - 2.0 * S.E01 * dE01;
+    const double dI2 = 2.0 * dtr + 4.0 * ddetE / S.detG;
+    const double dJ4 = 2.0 * S.J2 * dI2;
+    const double ds = -S.s * dJ4 / S.J4;
+    const double dM00 = dJ4 * G[2] - 2.0 * dE11;
+    const double dM01 = -dJ4 * G[1] + 2.0 * dE01;
+    const double dM11 = dJ4 * G[0] - 2.0 * dE00;
+    for (int a = 0; a < 3; ++a) {
+        const double P0 = S.d1[a] * S.M00 + S.d2[a] * S.M01;
+        const double P1 = S.d1[a] * S.M01 + S.d2[a] * S.M11;
+        const double dP0 = ds * P0 + S.s * (e1[a] * S.M00 + e2[a] * S.M01 + S.d1[a] * dM00 + S.d2[a] * dM01);
+        const double dP1 = ds * P1 + S.s * (e1[a] * S.M01 + e2[a] * S.M11 + S.d1[a] * dM01 + S.d2[a] * dM11);
+        df[0][a] = dP0 + dP1;
+        df[1][a] = -dP0;
+        df[2][a] = -dP1;
+    }
+}
+
+// ---------------------------------------------------------------- forward kernels
+
+// one block per swimmer: bead centres (FP64), drive and spring forces
+__global__ void k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta, const double *r, double t, double *R,
+                              double *ext) {
+    __shared__ double sh[32][3];
+    __shared__ double Rs[3][3];
+    const int s = blockIdx.x;
+    const Swim w = sw[s];
+    for (int q = 0; q < 3; ++q) {
+        const int b = w.bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int j = n0 + threadIdx.x; j < n0 + nn; j += blockDim.x)
+            for (int a = 0; a < 3; ++a) acc[a] += r[3 * j + a];
+        block_sum3(acc, sh);
+        if (threadIdx.x == 0)
+            for (int a = 0; a < 3; ++a) {
+                Rs[q][a] = acc[a] / nn;
+                R[3 * b + a] = Rs[q][a];
+            }
+    }
+    if (threadIdx.x != 0) return;
+    const double om = 2.0 * 3.14159265358979323846 / w.period;
+    const double *th = theta + 6 * s;
+    double fd[3];
+    fd[0] = th[0] * sin(om * t + th[3]);
+    fd[2] = th[2] * sin(om * t + th[5]);
+    fd[1] = w.balance ? -fd[0] - fd[2] : th[1] * sin(om * t + th[4]);
+    double fs[3][3];
+    for (int side = 0; side < 2; ++side) {
+        const int q = side ? 2 : 0;
+        double dd[3], n2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            dd[a] = Rs[q][a] - Rs[1][a];
+            n2 += dd[a] * dd[a];
+        }
+        const double n = sqrt(n2);
+        for (int a = 0; a < 3; ++a) fs[q][a] = -w.k * (n - w.L) * dd[a] / n;
+    }
+    for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
+    for (int q = 0; q < 3; ++q)
+        for (int a = 0; a < 3; ++a) ext[3 * w.bead[q] + a] = fs[q][a] + (a == 0 ? fd[q] : 0.0);
+}
+
+// one thread per triangle: corner forces -dW/dr
+__global__ void k_fwd_tri(Mesh m, const double *r, double *tri_f) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const int *v = m.tris + 3 * t;
+    TriState S;
+    tri_state(m.G + 3 * t, m.A0Gs[t], r + 3 * v[0], r + 3 * v[1], r + 3 * v[2], S);
+    for (int a = 0; a < 3; ++a) {
+        const double P0 = S.s * (S.d1[a] * S.M00 + S.d2[a] * S.M01);
+        const double P1 = S.s * (S.d1[a] * S.M01 + S.d2[a] * S.M11);
+        tri_f[9 * t + a] = P0 + P1;
+        tri_f[9 * t + 3 + a] = -P0;
+        tri_f[9 * t + 6 + a] = -P1;
+    }
+}
+
+// one thread per node: f_j = sum of its corner forces + e_b / N_b
+__global__ void k_fwd_node(Mesh m, const double *tri_f, const double *ext, double *fn) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m.M) return;
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int e = m.csr_ptr[j]; e < m.csr_ptr[j + 1]; ++e) {
+        const int k = m.csr_ent[e];
+        for (int a = 0; a < 3; ++a) f[a] += tri_f[3 * k + a];
+    }
+    const int b = m.node_bead[j];
+    const double inv = 1.0 / m.bead_count[b];
+    for (int a = 0; a < 3; ++a) fn[3 * j + a] = f[a] + ext[3 * b + a] * inv;
+}
+
+// one warp per node: F(x) += f_j Delta(x - r_j)
+template <typename T>
+__global__ void k_fwd_spread(Dims d, int M, const double *r, const double *fn, T *F) {
+    const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= M) return;
+    long long cell[2];
+    double w[2], g[2][3];
+    lane_cells(d, r + 3 * j, lane, cell, w, g);
+    const double f0 = fn[3 * j], f1 = fn[3 * j + 1], f2 = fn[3 * j + 2];
+    for (int h = 0; h < 2; ++h) {
+        atomicAdd(F + cell[h], (T)(f0 * w[h]));
+        atomicAdd(F + d.Npad + cell[h], (T)(f1 * w[h]));
+        atomicAdd(F + 2 * d.Npad + cell[h], (T)(f2 * w[h]));
+    }
+}
+
+// per-cell moments of the shifted deviations: drho = sum d, m = sum d c
+template <typename T>
+__device__ __forceinline__ void moments(const T *dv, T &drho, T m[3]) {
+    drho = 0;
+    m[0] = m[1] = m[2] = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += dv[i];
+        if (cx(i)) m[0] += cx(i) > 0 ? dv[i] : -dv[i];
+        if (cy(i)) m[1] += cy(i) > 0 ? dv[i] : -dv[i];
+        if (cz(i)) m[2] += cz(i) > 0 ? dv[i] : -dv[i];
+    }
+}
+
+__device__ __forceinline__ void cell_xyz(const Dims &d, long long cell, int &x, int &y, int &z) {
+    x = (int)(cell % d.nx);
+    const long long yz = cell / d.nx;
+    y = (int)(yz % d.ny);
+    z = (int)(yz / d.ny);
+}
+
+// one thread per cell: BGK collision with Guo forcing (Sec. 2.1, Eq. lbe),
+// push into the next slot, the velocity u^k, and a cleared force field of the
+// next slot
+template <typename T>
+__global__ void k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F, T *out,
+                         T *u_out, T *F_next) {
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= d.N) return;
+    int x, y, z;
+    cell_xyz(d, cell, x, y, z);
+    T dv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dv[i] = pops[i * d.Npad + cell];
+    const T Fx = F[cell] + (T)gx, Fy = F[d.Npad + cell] + (T)gy, Fz = F[2 * d.Npad + cell] + (T)gz;
+    T drho, m[3];
+    moments(dv, drho, m);
+    const T rho = rho0 + drho;
+    const T ux = (m[0] + (T)0.5 * Fx) / rho, uy = (m[1] + (T)0.5 * Fy) / rho, uz = (m[2] + (T)0.5 * Fz) / rho;
+    const T uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+    const T src = (T)1 - (T)0.5 * omega;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T cu = (T)cx(i) * ux + (T)cy(i) * uy + (T)cz(i) * uz;
+        const T cF = (T)cx(i) * Fx + (T)cy(i) * Fy + (T)cz(i) * Fz;
+        const T w = (T)wgt_d(i);
+        const T deq = w * (drho + rho * ((T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * uu));
+        const T S = w * ((T)3 * (cF - uF) + (T)9 * cu * cF);
+        const T post = ((T)1 - omega) * dv[i] + omega * deq + src * S;
+        const long long dst = wrapi(x + cx(i), d.nx) + (long long)d.nx * (wrapi(y + cy(i), d.ny) +
+                                                                          (long long)d.ny * wrapi(z + cz(i), d.nz));
+        out[i * d.Npad + dst] = post;
+    }
+    u_out[cell] = ux;
+    u_out[d.Npad + cell] = uy;
+    u_out[2 * d.Npad + cell] = uz;
+    F_next[cell] = 0;
+    F_next[d.Npad + cell] = 0;
+    F_next[2 * d.Npad + cell] = 0;
+}
+
+// one warp per node: r_j^{k+1} = r_j^k + sum_x u(x) Delta(x - r_j)
+template <typename T>
+__global__ void k_fwd_interp(Dims d, int M, const double *r, const T *u, double *r_next, int *err) {
+    const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= M) return;
+    long long cell[2];
+    double w[2], g[2][3];
+    lane_cells(d, r + 3 * j, lane, cell, w, g);
+    double U[3] = {0.0, 0.0, 0.0};
+    for (int h = 0; h < 2; ++h)
+        for (int a = 0; a < 3; ++a) U[a] += w[h] * (double)u[a * d.Npad + cell[h]];
+    for (int a = 0; a < 3; ++a) U[a] = warp_sum(U[a]);
+    if (lane == 0) {
+        bool bad = false, fast = false;
+        for (int a = 0; a < 3; ++a) {
+            r_next[3 * j + a] = r[3 * j + a] + U[a];
+            bad |= !isfinite(U[a]);
+            fast |= fabs(U[a]) > 0.1;
+        }
+        if (bad) atomicOr(err, ERR_NONFINITE);
+        else if (fast) atomicOr(err, ERR_UNSTABLE);
+    }
+}
+
+// one block per swimmer: disp_s = x_cm(final) - x_cm(initial)
+__global__ void k_disp(Mesh m, const Swim *sw, const double *rf, const double *ri, double *disp) {
+    __shared__ double sh[32][3];
+    const int s = blockIdx.x;
+    double tot[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < 3; ++q) {
+        const int b = sw[s].bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int j = n0 + threadIdx.x; j < n0 + nn; j += blockDim.x)
+            for (int a = 0; a < 3; ++a) acc[a] += rf[3 * j + a] - ri[3 * j + a];
+        block_sum3(acc, sh);
+        for (int a = 0; a < 3; ++a) tot[a] += acc[a] / nn;
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) disp[3 * s + a] = tot[a] / 3.0;
+}
+
+// ---------------------------------------------------------------- reverse kernels
+
+// lam_r_j (+)= sign * seed_s / (3 N_b): the derivative of x_cm of swimmer s
+// (mean of its three bead centres, each the mean of N_b nodes)
+__global__ void k_adj_seed(Mesh m, const double *seed_disp, double sign, int add, double *lam_r) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m.M) return;
+    const int b = m.node_bead[j], s = m.bead_swim[b];
+    const double f = sign / (3.0 * m.bead_count[b]);
+    for (int a = 0; a < 3; ++a) {
+        const double v = f * seed_disp[3 * s + a];
+        lam_r[3 * j + a] = add ? lam_r[3 * j + a] + v : v;
+    }
+}
+
+// one warp per node: transpose of r^{k+1} = r^k + interp(u^k, r^k)
+template <typename T>
+__global__ void k_adj_interp(Dims d, int M, const double *r, const T *u, double *lam_r, T *lam_u) {
+    const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= M) return;
+    long long cell[2];
+    double w[2], g[2][3];
+    lane_cells(d, r + 3 * j, lane, cell, w, g);
+    const double L0 = lam_r[3 * j], L1 = lam_r[3 * j + 1], L2 = lam_r[3 * j + 2];
+    double G[3] = {0.0, 0.0, 0.0};
+    for (int h = 0; h < 2; ++h) {
+        const double u0 = (double)u[cell[h]], u1 = (double)u[d.Npad + cell[h]], u2 = (double)u[2 * d.Npad + cell[h]];
+        atomicAdd(lam_u + cell[h], (T)(w[h] * L0));
+        atomicAdd(lam_u + d.Npad + cell[h], (T)(w[h] * L1));
+        atomicAdd(lam_u + 2 * d.Npad + cell[h], (T)(w[h] * L2));
+        const double dot = L0 * u0 + L1 * u1 + L2 * u2;
+        for (int a = 0; a < 3; ++a) G[a] += dot * g[h][a];
+    }
+    for (int a = 0; a < 3; ++a) G[a] = warp_sum(G[a]);
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) lam_r[3 * j + a] += G[a];
+}
+
+// one thread per cell: transpose of stream + collide (+ the velocity output)
+template <typename T>
+__global__ void k_adj_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F,
+                         const T *lam_next, T *lam_u, T *lam_cur, T *lam_F) {
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= d.N) return;
+    int x, y, z;
+    cell_xyz(d, cell, x, y, z);
+    T ls[Q], dv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const long long src = wrapi(x + cx(i), d.nx) + (long long)d.nx * (wrapi(y + cy(i), d.ny) +
+                                                                          (long long)d.ny * wrapi(z + cz(i), d.nz));
+        ls[i] = lam_next[i * d.Npad + src];
+        dv[i] = pops[i * d.Npad + cell];
+    }
+    const T Fx = F[cell] + (T)gx, Fy = F[d.Npad + cell] + (T)gy, Fz = F[2 * d.Npad + cell] + (T)gz;
+    T drho, m[3];
+    moments(dv, drho, m);
+    const T rho = rho0 + drho, ir = (T)1 / rho;
+    const T u[3] = {(m[0] + (T)0.5 * Fx) * ir, (m[1] + (T)0.5 * Fy) * ir, (m[2] + (T)0.5 * Fz) * ir};
+    const T Fv[3] = {Fx, Fy, Fz};
+    const T lu[3] = {lam_u[cell], lam_u[d.Npad + cell], lam_u[2 * d.Npad + cell]};
+    lam_u[cell] = 0;
+    lam_u[d.Npad + cell] = 0;
+    lam_u[2 * d.Npad + cell] = 0;
+    // weighted moments of lam*: s0 = sum w l, s1 = sum w l c, s2 = sum w l c c
+    T s0 = 0, s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T wl = (T)wgt_d(i) * ls[i];
+        const int c[3] = {cx(i), cy(i), cz(i)};
+        s0 += wl;
+        for (int a = 0; a < 3; ++a) {
+            if (c[a]) s1[a] += c[a] > 0 ? wl : -wl;
+            for (int b = 0; b < 3; ++b)
+                if (c[a] && c[b]) s2[a][b] += c[a] * c[b] > 0 ? wl : -wl;
+        }
+    }
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T s2u[3], s2F[3], Pq = s0 * ((T)1 - (T)1.5 * uu);
+    for (int a = 0; a < 3; ++a) {
+        s2u[a] = s2[a][0] * u[0] + s2[a][1] * u[1] + s2[a][2] * u[2];
+        s2F[a] = s2[a][0] * Fv[0] + s2[a][1] * Fv[1] + s2[a][2] * Fv[2];
+        Pq += (T)3 * s1[a] * u[a] + (T)4.5 * u[a] * s2u[a];
+    }
+    const T src = (T)1 - (T)0.5 * omega;
+    T au[3], lm[3], lF[3], au_u = 0;
+    for (int a = 0; a < 3; ++a) {
+        const T Qa = (T)3 * s1[a] - (T)3 * s0 * u[a] + (T)9 * s2u[a];
+        au[a] = omega * rho * Qa + src * ((T)9 * s2F[a] - (T)3 * s0 * Fv[a]) + lu[a];
+        lF[a] = src * Qa + (T)0.5 * au[a] * ir;
+        lm[a] = au[a] * ir;
+        au_u += au[a] * u[a];
+    }
+    const T lrho = omega * Pq - au_u * ir;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T v = ((T)1 - omega) * ls[i] + lrho;
+        if (cx(i)) v += cx(i) > 0 ? lm[0] : -lm[0];
+        if (cy(i)) v += cy(i) > 0 ? lm[1] : -lm[1];
+        if (cz(i)) v += cz(i) > 0 ? lm[2] : -lm[2];
+        lam_cur[i * d.Npad + cell] = v;
+    }
+    lam_F[cell] = lF[0];
+    lam_F[d.Npad + cell] = lF[1];
+    lam_F[2 * d.Npad + cell] = lF[2];
+}
+
+// one warp per node: transpose of spreading
+template <typename T>
+__global__ void k_adj_spread(Dims d, int M, const double *r, const double *fn, const T *lam_F, double *lam_r,
+                             double *lam_fn) {
+    const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= M) return;
+    long long cell[2];
+    double w[2], g[2][3];
+    lane_cells(d, r + 3 * j, lane, cell, w, g);
+    const double f0 = fn[3 * j], f1 = fn[3 * j + 1], f2 = fn[3 * j + 2];
+    double lf[3] = {0.0, 0.0, 0.0}, G[3] = {0.0, 0.0, 0.0};
+    for (int h = 0; h < 2; ++h) {
+        const double l0 = (double)lam_F[cell[h]], l1 = (double)lam_F[d.Npad + cell[h]],
+                     l2 = (double)lam_F[2 * d.Npad + cell[h]];
+        lf[0] += w[h] * l0;
+        lf[1] += w[h] * l1;
+        lf[2] += w[h] * l2;
+        const double dot = l0 * f0 + l1 * f1 + l2 * f2;
+        for (int a = 0; a < 3; ++a) G[a] += dot * g[h][a];
+    }
+    for (int a = 0; a < 3; ++a) {
+        lf[a] = warp_sum(lf[a]);
+        G[a] = warp_sum(G[a]);
+    }
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            lam_fn[3 * j + a] = lf[a];
+            lam_r[3 * j + a] += G[a];
+        }
+}
+
+// one thread per triangle: membrane force Jacobian times lam_f at its corners
+__global__ void k_adj_tri(Mesh m, const double *r, const double *lam_fn, double *tri_adj) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const int *v = m.tris + 3 * t;
+    TriState S;
+    tri_state(m.G + 3 * t, m.A0Gs[t], r + 3 * v[0], r + 3 * v[1], r + 3 * v[2], S);
+    double df[3][3];
+    tri_force_jvp(m.G + 3 * t, S, lam_fn + 3 * v[0], lam_fn + 3 * v[1], lam_fn + 3 * v[2], df);
+    for (int q = 0; q < 3; ++q)
+        for (int a = 0; a < 3; ++a) tri_adj[9 * t + 3 * q + a] = df[q][a];
+}
+
+// one block per swimmer: lam_e_b = mean over bead b of lam_fj; drive-parameter
+// gradient; transpose of the spring forces -> lam_R
+__global__ void k_adj_swimmer(Mesh m, const Swim *sw, const double *theta, const double *R, const double *lam_fn,
+                              double t, double *lam_R, double *grad) {
+    __shared__ double sh[32][3];
+    __shared__ double le[3][3];
+    const int s = blockIdx.x;
+    const Swim w = sw[s];
+    for (int q = 0; q < 3; ++q) {
+        const int b = w.bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int j = n0 + threadIdx.x; j < n0 + nn; j += blockDim.x)
+            for (int a = 0; a < 3; ++a) acc[a] += lam_fn[3 * j + a];
+        block_sum3(acc, sh);
+        if (threadIdx.x == 0)
+            for (int a = 0; a < 3; ++a) le[q][a] = acc[a] / nn;
+    }
+    if (threadIdx.x != 0) return;
+    // drive: f_q = A_q sin(om t + phi_q) along x (balance: f_1 = -f_0 - f_2)
+    const double om = 2.0 * 3.14159265358979323846 / w.period;
+    const double *th = theta + 6 * s;
+    double sens[3];
+    if (w.balance) {
+        sens[0] = le[0][0] - le[1][0];
+        sens[1] = 0.0;
+        sens[2] = le[2][0] - le[1][0];
+    } else {
+        for (int q = 0; q < 3; ++q) sens[q] = le[q][0];
+    }
+    for (int q = 0; q < 3; ++q) {
+        if (w.balance && q == 1) continue;
+        const double arg = om * t + th[3 + q];
+        grad[6 * s + q] += sin(arg) * sens[q];
+        grad[6 * s + 3 + q] += th[q] * cos(arg) * sens[q];
+    }
+    // springs: f_0 = h(R_0 - R_1), f_2 = h(R_2 - R_1), f_1 = -f_0 - f_2 with
+    // h(d) = -k (|d| - L) d/|d|, dh/dd = -k [(1 - L/|d|) I + (L/|d|) dhat dhat^T]
+    double lR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int side = 0; side < 2; ++side) {
+        const int q = side ? 2 : 0;
+        double dd[3], n2 = 0.0, lv[3];
+        for (int a = 0; a < 3; ++a) {
+            dd[a] = R[3 * w.bead[q] + a] - R[3 * w.bead[1] + a];
+            n2 += dd[a] * dd[a];
+            lv[a] = le[q][a] - le[1][a];
+        }
+        const double n = sqrt(n2), c1 = 1.0 - w.L / n, c2 = w.L / (n * n2);
+        const double dl = dd[0] * lv[0] + dd[1] * lv[1] + dd[2] * lv[2];
+        for (int a = 0; a < 3; ++a) {
+            const double ld = -w.k * (c1 * lv[a] + c2 * dd[a] * dl);
+            lR[q][a] += ld;
+            lR[1][a] -= ld;
+        }
+    }
+    for (int q = 0; q < 3; ++q)
+        for (int a = 0; a < 3; ++a) lam_R[3 * w.bead[q] + a] = lR[q][a];
+}
+
+// one thread per node: lam_r_j += sum of its corners' membrane terms + lam_R_b / N_b
+__global__ void k_adj_node(Mesh m, const double *tri_adj, const double *lam_R, double *lam_r) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m.M) return;
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int e = m.csr_ptr[j]; e < m.csr_ptr[j + 1]; ++e) {
+        const int k = m.csr_ent[e];
+        for (int a = 0; a < 3; ++a) f[a] += tri_adj[3 * k + a];
+    }
+    const int b = m.node_bead[j];
+    const double inv = 1.0 / m.bead_count[b];
+    for (int a = 0; a < 3; ++a) lam_r[3 * j + a] += f[a] + lam_R[3 * b + a] * inv;
+}
+
+// ---------------------------------------------------------------- host side
+
+int fail(int code, const std::string &msg) {
+    set_last_error(msg.c_str());
+    return code;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(LBIB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+struct Plan {
+    Dims d;
+    size_t esize;
+    int M, T, B, S;
+    long long n_steps;
+    int K, n_seg;
+    // per-slot offsets
+    size_t s_pops, s_F, s_u, s_r, s_fn, s_R, s_ext, slot_bytes;
+    // per-checkpoint offsets
+    size_t c_pops, c_r, ck_bytes;
+    // workspace offsets
+    size_t o_tris, o_G, o_A0, o_cptr, o_cent, o_nb, o_bs, o_bc, o_bw, o_swim, o_theta, o_grad, o_disp, o_err,
+        o_seed, o_lf0, o_lf1, o_lu, o_lF, o_lr, o_lfn, o_trif, o_tria, o_lR, o_ck, o_slots, total;
+};
+
+Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, int K) {
+    Plan P;
+    P.d.nx = p->nx;
+    P.d.ny = p->ny;
+    P.d.nz = p->nz;
+    P.d.N = (long long)p->nx * p->ny * p->nz;
+    P.d.Npad = (P.d.N + 63) / 64 * 64;
+    P.esize = p->storage == LBIB_F64 ? 8 : 4;
+    P.M = s ? s->n_nodes : 0;
+    P.T = s ? s->n_tris : 0;
+    P.B = s ? s->n_beads : 0;
+    P.S = s ? s->n_swimmers : 0;
+    P.n_steps = n_steps;
+    P.K = K;
+    P.n_seg = (int)((n_steps + K - 1) / K);
+    const size_t fp = (size_t)P.d.Npad * P.esize, nd = 3 * (size_t)std::max(P.M, 1) * 8,
+                 bd = 3 * (size_t)std::max(P.B, 1) * 8;
+    size_t o = 0;
+    P.s_pops = o; o += up(Q * fp);
+    P.s_F = o; o += up(3 * fp);
+    P.s_u = o; o += up(3 * fp);
+    P.s_r = o; o += up(nd);
+    P.s_fn = o; o += up(nd);
+    P.s_R = o; o += up(bd);
+    P.s_ext = o; o += up(bd);
+    P.slot_bytes = o;
+    o = 0;
+    P.c_pops = o; o += up(Q * fp);
+    P.c_r = o; o += up(nd);
+    P.ck_bytes = o;
+    const size_t Tn = std::max(P.T, 1), Mn = std::max(P.M, 1), Bn = std::max(P.B, 1), Sn = std::max(P.S, 1);
+    o = 0;
+    P.o_tris = o; o += up(3 * Tn * 4);
+    P.o_G = o; o += up(3 * Tn * 8);
+    P.o_A0 = o; o += up(Tn * 8);
+    P.o_cptr = o; o += up((Mn + 1) * 4);
+    P.o_cent = o; o += up(3 * Tn * 4);
+    P.o_nb = o; o += up(Mn * 4);
+    P.o_bs = o; o += up(Bn * 4);
+    P.o_bc = o; o += up(Bn * 4);
+    P.o_bw = o; o += up(Bn * 4);
+    P.o_swim = o; o += up(Sn * sizeof(Swim));
+    P.o_theta = o; o += up(6 * Sn * 8);
+    P.o_grad = o; o += up(6 * Sn * 8);
+    P.o_disp = o; o += up(3 * Sn * 8);
+    P.o_err = o; o += up(4);
+    P.o_seed = o; o += up(3 * Sn * 8);
+    P.o_lf0 = o; o += up(Q * fp);
+    P.o_lf1 = o; o += up(Q * fp);
+    P.o_lu = o; o += up(3 * fp);
+    P.o_lF = o; o += up(3 * fp);
+    P.o_lr = o; o += up(nd);
+    P.o_lfn = o; o += up(nd);
+    P.o_trif = o; o += up(9 * Tn * 8);
+    P.o_tria = o; o += up(9 * Tn * 8);
+    P.o_lR = o; o += up(bd);
+    P.o_ck = o; o += (size_t)(P.n_seg + 1) * P.ck_bytes;  // + the final state
+    P.o_slots = o; o += (size_t)(K + 1) * P.slot_bytes;
+    P.total = o;
+    return P;
+}
+
+bool check(const lb_params *p, const lbib_structure *s, long long n_steps, int K, std::string &why) {
+    if (!p) { why = "params is NULL"; return false; }
+    if (p->storage != LBIB_F32 && p->storage != LBIB_F64) {
+        why = "the adjoint engine stores populations as LBIB_F32 or LBIB_F64";
+        return false;
+    }
+    lb_params q = *p;
+    q.storage = LBIB_F32;
+    if (!check_params(&q, why) || !check_structure(&q, s, why)) return false;
+    if (p->forcing != LBIB_GUO) { why = "the adjoint engine supports Guo forcing only"; return false; }
+    if (p->kernel != LBIB_PESKIN4) {
+        why = "the adjoint engine needs the differentiable 4-point kernel";
+        return false;
+    }
+    if (n_steps < 1 || K < 1) { why = "n_steps and K must be >= 1"; return false; }
+    if (n_steps > (1ll << 40)) { why = "n_steps too large"; return false; }
+    return true;
+}
+
+}  // namespace
+
+struct lbib_adjoint {
+    lb_params p;
+    Plan P;
+    cudaStream_t s;
+    char *ws;
+    Mesh m;
+    std::vector<double> rest;  // rest node positions (host)
+    int slots_seg = -1;        // segment whose steps the slots currently hold
+    bool have_fwd = false;
+    cudaEvent_t ev[4];
+    float fwd_ms = 0.f, bwd_ms = 0.f;
+    long long fwd_launches = 0, bwd_launches = 0, launches = 0;
+
+    template <typename X> X *at(size_t off) const { return (X *)(ws + off); }
+    char *slot(int k) const { return ws + P.o_slots + (size_t)k * P.slot_bytes; }
+    char *ck(int c) const { return ws + P.o_ck + (size_t)c * P.ck_bytes; }
+    int seg_len(int g) const { return (int)std::min<long long>(P.K, P.n_steps - (long long)g * P.K); }
+};
+
+namespace {
+
+template <typename T>
+cudaError_t fwd_step(lbib_adjoint *a, int k, long long t) {
+    const Plan &P = a->P;
+    char *sl = a->slot(k), *sn = a->slot(k + 1);
+    const double *r = (const double *)(sl + P.s_r);
+    double *fn = (double *)(sl + P.s_fn), *R = (double *)(sl + P.s_R), *ext = (double *)(sl + P.s_ext);
+    T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
+    const int M = P.M;
+    if (M > 0) {
+        k_fwd_swimmer<<<P.S, 256, 0, a->s>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), r, (double)t, R, ext);
+        k_fwd_tri<<<(P.T + 127) / 128, 128, 0, a->s>>>(a->m, r, a->at<double>(P.o_trif));
+        k_fwd_node<<<(M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_trif), ext, fn);
+        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, fn, F);
+        a->launches += 4;
+    }
+    const unsigned nb = (unsigned)((P.d.N + 255) / 256);
+    k_fwd_lb<T><<<nb, 256, 0, a->s>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                       (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F));
+    a->launches += 1;
+    if (M > 0) {
+        k_fwd_interp<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
+        a->launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adj_step(lbib_adjoint *a, int k, long long t, T *lam_next, T *lam_cur) {
+    const Plan &P = a->P;
+    char *sl = a->slot(k);
+    const double *r = (const double *)(sl + P.s_r), *fn = (const double *)(sl + P.s_fn),
+                 *R = (const double *)(sl + P.s_R);
+    const T *F = (const T *)(sl + P.s_F), *u = (const T *)(sl + P.s_u);
+    T *lam_u = a->at<T>(P.o_lu), *lam_F = a->at<T>(P.o_lF);
+    double *lam_r = a->at<double>(P.o_lr), *lam_fn = a->at<double>(P.o_lfn);
+    const int M = P.M;
+    if (M > 0) {
+        k_adj_interp<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, u, lam_r, lam_u);
+        a->launches += 1;
+    }
+    const unsigned nb = (unsigned)((P.d.N + 255) / 256);
+    k_adj_lb<T><<<nb, 256, 0, a->s>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                       (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F);
+    a->launches += 1;
+    if (M > 0) {
+        k_adj_spread<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
+        k_adj_tri<<<(P.T + 127) / 128, 128, 0, a->s>>>(a->m, r, lam_fn, a->at<double>(P.o_tria));
+        k_adj_swimmer<<<P.S, 256, 0, a->s>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), R, lam_fn,
+                                             (double)t, a->at<double>(P.o_lR), a->at<double>(P.o_grad));
+        k_adj_node<<<(M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_tria), a->at<double>(P.o_lR), lam_r);
+        a->launches += 4;
+    }
+    return cudaGetLastError();
+}
+
+// run segment g forward from its checkpoint, filling slots 0..len
+template <typename T>
+cudaError_t run_segment(lbib_adjoint *a, int g) {
+    const Plan &P = a->P;
+    char *s0 = a->slot(0), *c = a->ck(g);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(s0 + P.s_pops, c + P.c_pops, Q * (size_t)P.d.Npad * P.esize, cudaMemcpyDeviceToDevice,
+                             a->s)) != cudaSuccess)
+        return e;
+    if (P.M > 0 &&
+        (e = cudaMemcpyAsync(s0 + P.s_r, c + P.c_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToDevice, a->s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(s0 + P.s_F, 0, 3 * (size_t)P.d.Npad * P.esize, a->s)) != cudaSuccess) return e;
+    const int len = a->seg_len(g);
+    for (int k = 0; k < len; ++k)
+        if ((e = fwd_step<T>(a, k, (long long)g * P.K + k)) != cudaSuccess) return e;
+    a->slots_seg = g;
+    return cudaSuccess;
+}
+
+// copy the populations and positions of slot k into checkpoint c
+cudaError_t save_ck(lbib_adjoint *a, int k, int c) {
+    const Plan &P = a->P;
+    cudaError_t e = cudaMemcpyAsync(a->ck(c) + P.c_pops, a->slot(k) + P.s_pops, Q * (size_t)P.d.Npad * P.esize,
+                                    cudaMemcpyDeviceToDevice, a->s);
+    if (e == cudaSuccess && P.M > 0)
+        e = cudaMemcpyAsync(a->ck(c) + P.c_r, a->slot(k) + P.s_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToDevice, a->s);
+    return e;
+}
+
+template <typename T>
+int forward_impl(lbib_adjoint *a, double *disp) {
+    const Plan &P = a->P;
+    CU(cudaMemsetAsync(a->at<int>(P.o_err), 0, 4, a->s));
+    CU(cudaEventRecord(a->ev[0], a->s));
+    a->launches = 0;
+    for (int g = 0; g < P.n_seg; ++g) {
+        CU(run_segment<T>(a, g));
+        CU(save_ck(a, a->seg_len(g), g + 1));  // the next checkpoint (the last one: the final state)
+    }
+    if (P.S > 0) {
+        k_disp<<<P.S, 256, 0, a->s>>>(a->m, a->at<Swim>(P.o_swim), (const double *)(a->ck(P.n_seg) + P.c_r),
+                                      (const double *)(a->ck(0) + P.c_r), a->at<double>(P.o_disp));
+        a->launches += 1;
+        CU(cudaGetLastError());
+    }
+    CU(cudaEventRecord(a->ev[1], a->s));
+    int err = 0;
+    CU(cudaMemcpyAsync(&err, a->at<int>(P.o_err), 4, cudaMemcpyDeviceToHost, a->s));
+    CU(cudaStreamSynchronize(a->s));
+    CU(cudaEventElapsedTime(&a->fwd_ms, a->ev[0], a->ev[1]));
+    a->fwd_launches = a->launches;
+    if (err & ERR_NONFINITE) return fail(LBIB_ENONFINITE, "a node velocity became non-finite");
+    if (err & ERR_UNSTABLE) return fail(LBIB_EUNSTABLE, "a node moved faster than 0.1 lattice units per step");
+    if (disp && P.S > 0) {
+        CU(cudaMemcpy(disp, a->at<double>(P.o_disp), 3 * (size_t)P.S * 8, cudaMemcpyDeviceToHost));
+    }
+    a->have_fwd = true;
+    return LBIB_OK;
+}
+
+// host [19][N] raw populations <-> device deviations (lattice order of this
+// library, planes Npad apart)
+template <typename T>
+void to_dev_layout(const lbib_adjoint *a, const double *hf, bool shift, std::vector<T> &out) {
+    const Plan &P = a->P;
+    out.assign(Q * (size_t)P.d.Npad, (T)0);
+    for (int i = 0; i < Q; ++i) {
+        const double base = shift ? wgt_d(i) * a->p.rho0 : 0.0;
+        for (long long c = 0; c < P.d.N; ++c) out[i * P.d.Npad + c] = (T)(hf[i * P.d.N + c] - base);
+    }
+}
+
+template <typename T>
+int from_dev(const lbib_adjoint *a, const void *dev, bool shift, double *hf) {
+    const Plan &P = a->P;
+    std::vector<T> h(Q * (size_t)P.d.Npad);
+    CU(cudaMemcpyAsync(h.data(), dev, h.size() * sizeof(T), cudaMemcpyDeviceToHost, a->s));
+    CU(cudaStreamSynchronize(a->s));
+    for (int i = 0; i < Q; ++i) {
+        const double base = shift ? wgt_d(i) * a->p.rho0 : 0.0;
+        for (long long c = 0; c < P.d.N; ++c) hf[i * P.d.N + c] = base + (double)h[i * P.d.Npad + c];
+    }
+    return LBIB_OK;
+}
+
+template <typename T>
+int upload_pops(lbib_adjoint *a, const double *hf, bool shift, void *dev) {
+    std::vector<T> h;
+    to_dev_layout<T>(a, hf, shift, h);
+    CU(cudaMemcpyAsync(dev, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, a->s));
+    CU(cudaStreamSynchronize(a->s));
+    return LBIB_OK;
+}
+
+template <typename T>
+int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f, const double *seed_r,
+                  double *grad_theta, double *grad_f0, double *grad_r0) {
+    const Plan &P = a->P;
+    const size_t fp = (size_t)P.d.Npad * sizeof(T);
+    T *lam[2] = {a->at<T>(P.o_lf0), a->at<T>(P.o_lf1)};
+    int nxt = 0;
+    // seeds
+    if (seed_f) {
+        int st = upload_pops<T>(a, seed_f, false, lam[nxt]);
+        if (st) return st;
+    } else {
+        CU(cudaMemsetAsync(lam[nxt], 0, Q * fp, a->s));
+    }
+    double *lam_r = a->at<double>(P.o_lr);
+    if (P.M > 0) {
+        if (seed_r) CU(cudaMemcpyAsync(lam_r, seed_r, 3 * (size_t)P.M * 8, cudaMemcpyHostToDevice, a->s));
+        CU(cudaMemcpyAsync(a->at<double>(P.o_seed), seed_disp, 3 * (size_t)P.S * 8, cudaMemcpyHostToDevice, a->s));
+    }
+    CU(cudaMemsetAsync(a->at<T>(P.o_lu), 0, 3 * fp, a->s));
+    CU(cudaMemsetAsync(a->at<double>(P.o_grad), 0, 6 * (size_t)std::max(P.S, 1) * 8, a->s));
+    CU(cudaEventRecord(a->ev[2], a->s));
+    a->launches = 0;
+    if (P.M > 0) {
+        k_adj_seed<<<(P.M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_seed), 1.0, seed_r ? 1 : 0, lam_r);
+        a->launches += 1;
+        CU(cudaGetLastError());
+    }
+    for (int g = P.n_seg - 1; g >= 0; --g) {
+        if (a->slots_seg != g) CU(run_segment<T>(a, g));
+        for (int k = a->seg_len(g) - 1; k >= 0; --k) {
+            CU(adj_step<T>(a, k, (long long)g * P.K + k, lam[nxt], lam[1 - nxt]));
+            nxt = 1 - nxt;
+        }
+    }
+    if (P.M > 0) {  // x_cm(0) enters the displacement with a minus sign
+        k_adj_seed<<<(P.M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_seed), -1.0, 1, lam_r);
+        a->launches += 1;
+        CU(cudaGetLastError());
+    }
+    CU(cudaEventRecord(a->ev[3], a->s));
+    CU(cudaStreamSynchronize(a->s));
+    CU(cudaEventElapsedTime(&a->bwd_ms, a->ev[2], a->ev[3]));
+    a->bwd_launches = a->launches;
+    if (P.S > 0) CU(cudaMemcpy(grad_theta, a->at<double>(P.o_grad), 6 * (size_t)P.S * 8, cudaMemcpyDeviceToHost));
+    if (grad_f0) {
+        int st = from_dev<T>(a, lam[nxt], false, grad_f0);
+        if (st) return st;
+    }
+    if (grad_r0 && P.M > 0) CU(cudaMemcpy(grad_r0, lam_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToHost));
+    return LBIB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_adjoint_required_bytes(const lb_params *p, const lbib_structure *s, long long n_steps, int K, size_t *bytes) {
+    std::string why;
+    if (!bytes) return fail(LBIB_EINVAL, "bytes is NULL");
+    if (!check(p, s, n_steps, K, why)) return fail(LBIB_EINVAL, why);
+    *bytes = make_plan(p, s, n_steps, K).total;
+    return LBIB_OK;
+}
+
+int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_steps, int K, void *workspace,
+                      size_t workspace_bytes, void *stream, lbib_adjoint **out) {
+    std::string why;
+    if (!out) return fail(LBIB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!check(p, s, n_steps, K, why)) return fail(LBIB_EINVAL, why);
+    const Plan P = make_plan(p, s, n_steps, K);
+    if (!workspace) return fail(LBIB_EINVAL, "workspace is NULL");
+    if ((uintptr_t)workspace % AL) return fail(LBIB_EINVAL, "workspace must be 256-byte aligned");
+    if (workspace_bytes < P.total) return fail(LBIB_ESIZE, "workspace smaller than lb_adjoint_required_bytes");
+    const int M = P.M, T = P.T, B = P.B, S = P.S;
+    // host tables
+    std::vector<int> tris(3 * (size_t)T), cptr(M + 1, 0), cent(3 * (size_t)T), nb(M), bs(B), bc(B), bw(B, 0);
+    std::vector<double> G(3 * (size_t)T), A0(T), theta(6 * (size_t)S);
+    std::vector<Swim> sw(S);
+    for (int b = 0; b < B; ++b) {
+        const lbib_bead &bd = s->beads[b];
+        bs[b] = bd.node_start;
+        bc[b] = bd.node_count;
+        for (int j = bd.node_start; j < bd.node_start + bd.node_count; ++j) nb[j] = b;
+        for (int t = bd.tri_start; t < bd.tri_start + bd.tri_count; ++t) {
+            const int *v = s->tris + 3 * t;
+            const double *X = s->rest_nodes;
+            double e1[3], e2[3];
+            for (int a = 0; a < 3; ++a) {
+                e1[a] = X[3 * v[1] + a] - X[3 * v[0] + a];
+                e2[a] = X[3 * v[2] + a] - X[3 * v[0] + a];
+                tris[3 * t + a] = v[a];
+            }
+            G[3 * t] = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+            G[3 * t + 1] = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+            G[3 * t + 2] = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+            const double det = G[3 * t] * G[3 * t + 2] - G[3 * t + 1] * G[3 * t + 1];
+            if (!(det > 0.0)) return fail(LBIB_EINVAL, "degenerate rest triangle");
+            A0[t] = 0.5 * std::sqrt(det) * bd.Gs;
+        }
+    }
+    for (int t = 0; t < T; ++t)
+        for (int q = 0; q < 3; ++q) cptr[s->tris[3 * t + q] + 1]++;
+    for (int j = 0; j < M; ++j) cptr[j + 1] += cptr[j];
+    {
+        std::vector<int> fill(cptr.begin(), cptr.end() - 1);
+        for (int t = 0; t < T; ++t)
+            for (int q = 0; q < 3; ++q) cent[fill[s->tris[3 * t + q]]++] = 3 * t + q;
+    }
+    for (int k = 0; k < S; ++k) {
+        const lbib_swimmer &w = s->swimmers[k];
+        for (int q = 0; q < 3; ++q) {
+            sw[k].bead[q] = w.bead[q];
+            bw[w.bead[q]] = k;
+            theta[6 * k + q] = w.amp[q];
+            theta[6 * k + 3 + q] = w.phase[q];
+        }
+        sw[k].balance = w.balance;
+        sw[k].k = w.k_spring;
+        sw[k].L = w.L_spring;
+        sw[k].period = w.period;
+    }
+
+    lbib_adjoint *a = new lbib_adjoint();
+    a->p = *p;
+    a->P = P;
+    a->s = (cudaStream_t)stream;
+    a->ws = (char *)workspace;
+    a->rest.assign(s && M ? s->rest_nodes : nullptr, s && M ? s->rest_nodes + 3 * (size_t)M : nullptr);
+    Mesh &m = a->m;
+    m.M = M;
+    m.T = T;
+    m.B = B;
+    m.S = S;
+    m.tris = a->at<int>(P.o_tris);
+    m.G = a->at<double>(P.o_G);
+    m.A0Gs = a->at<double>(P.o_A0);
+    m.csr_ptr = a->at<int>(P.o_cptr);
+    m.csr_ent = a->at<int>(P.o_cent);
+    m.node_bead = a->at<int>(P.o_nb);
+    m.bead_start = a->at<int>(P.o_bs);
+    m.bead_count = a->at<int>(P.o_bc);
+    m.bead_swim = a->at<int>(P.o_bw);
+    auto cleanup = [&](int code) {
+        delete a;
+        return code;
+    };
+#define CUA(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return cleanup(fail(LBIB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+    } while (0)
+    for (int k = 0; k < 4; ++k) CUA(cudaEventCreate(&a->ev[k]));
+    auto put = [&](size_t off, const void *src, size_t n) {
+        return n ? cudaMemcpyAsync(a->ws + off, src, n, cudaMemcpyHostToDevice, a->s) : cudaSuccess;
+    };
+    CUA(put(P.o_tris, tris.data(), tris.size() * 4));
+    CUA(put(P.o_G, G.data(), G.size() * 8));
+    CUA(put(P.o_A0, A0.data(), A0.size() * 8));
+    CUA(put(P.o_cptr, cptr.data(), cptr.size() * 4));
+    CUA(put(P.o_cent, cent.data(), cent.size() * 4));
+    CUA(put(P.o_nb, nb.data(), nb.size() * 4));
+    CUA(put(P.o_bs, bs.data(), bs.size() * 4));
+    CUA(put(P.o_bc, bc.data(), bc.size() * 4));
+    CUA(put(P.o_bw, bw.data(), bw.size() * 4));
+    CUA(put(P.o_swim, sw.data(), sw.size() * sizeof(Swim)));
+    CUA(put(P.o_theta, theta.data(), theta.size() * 8));
+    // rest initial state: zero deviations, nodes at the rest shape
+    CUA(cudaMemsetAsync(a->ck(0) + P.c_pops, 0, Q * (size_t)P.d.Npad * P.esize, a->s));
+    CUA(put(P.o_ck + P.c_r, a->rest.data(), a->rest.size() * 8));
+    CUA(cudaStreamSynchronize(a->s));
+#undef CUA
+    *out = a;
+    return LBIB_OK;
+}
+
+int lb_adjoint_set_drive(lbib_adjoint *a, const double *theta) {
+    if (!a || (!theta && a->P.S)) return fail(LBIB_EINVAL, "NULL argument");
+    for (long long k = 0; k < 6ll * a->P.S; ++k)
+        if (!std::isfinite(theta[k])) return fail(LBIB_EINVAL, "non-finite drive parameter");
+    if (a->P.S) {
+        CU(cudaMemcpyAsync(a->at<double>(a->P.o_theta), theta, 6 * (size_t)a->P.S * 8, cudaMemcpyHostToDevice, a->s));
+        CU(cudaStreamSynchronize(a->s));
+    }
+    a->have_fwd = false;
+    a->slots_seg = -1;
+    return LBIB_OK;
+}
+
+int lb_adjoint_set_initial(lbib_adjoint *a, const double *f, const double *r) {
+    if (!a) return fail(LBIB_EINVAL, "NULL argument");
+    const Plan &P = a->P;
+    if (f) {
+        for (long long k = 0; k < Q * P.d.N; ++k)
+            if (!std::isfinite(f[k])) return fail(LBIB_EINVAL, "non-finite population");
+        const int st = P.esize == 8 ? upload_pops<double>(a, f, true, a->ck(0) + P.c_pops)
+                                    : upload_pops<float>(a, f, true, a->ck(0) + P.c_pops);
+        if (st) return st;
+    }
+    if (r && P.M) {
+        for (long long k = 0; k < 3ll * P.M; ++k)
+            if (!std::isfinite(r[k])) return fail(LBIB_EINVAL, "non-finite node position");
+        CU(cudaMemcpyAsync(a->ck(0) + P.c_r, r, 3 * (size_t)P.M * 8, cudaMemcpyHostToDevice, a->s));
+        CU(cudaStreamSynchronize(a->s));
+    }
+    a->have_fwd = false;
+    a->slots_seg = -1;
+    return LBIB_OK;
+}
+
+int lb_adjoint_forward(lbib_adjoint *a, double *disp) {
+    if (!a) return fail(LBIB_EINVAL, "NULL argument");
+    a->have_fwd = false;
+    return a->P.esize == 8 ? forward_impl<double>(a, disp) : forward_impl<float>(a, disp);
+}
+
+int lb_adjoint_backward(lbib_adjoint *a, const double *seed_disp, const double *seed_f, const double *seed_r,
+                        double *grad_theta, double *grad_f0, double *grad_r0) {
+    if (!a || (a->P.S && (!seed_disp || !grad_theta))) return fail(LBIB_EINVAL, "NULL argument");
+    if (!a->have_fwd) return fail(LBIB_EINVAL, "no forward sweep with the current drive and initial state");
+    return a->P.esize == 8 ? backward_impl<double>(a, seed_disp, seed_f, seed_r, grad_theta, grad_f0, grad_r0)
+                           : backward_impl<float>(a, seed_disp, seed_f, seed_r, grad_theta, grad_f0, grad_r0);
+}
+
+int lb_adjoint_get_final(lbib_adjoint *a, double *f, double *r) {
+    if (!a) return fail(LBIB_EINVAL, "NULL argument");
+    if (!a->have_fwd) return fail(LBIB_EINVAL, "no forward sweep");
+    const Plan &P = a->P;
+    const char *c = a->ck(P.n_seg);
+    if (f) {
+        const int st = P.esize == 8 ? from_dev<double>(a, c + P.c_pops, true, f) : from_dev<float>(a, c + P.c_pops, true, f);
+        if (st) return st;
+    }
+    if (r && P.M) CU(cudaMemcpy(r, c + P.c_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToHost));
+    return LBIB_OK;
+}
+
+int lb_adjoint_timing(lbib_adjoint *a, double *forward_ms, double *backward_ms, long long *forward_launches,
+                      long long *backward_launches) {
+    if (!a) return fail(LBIB_EINVAL, "NULL argument");
+    if (forward_ms) *forward_ms = a->fwd_ms;
+    if (backward_ms) *backward_ms = a->bwd_ms;
+    if (forward_launches) *forward_launches = a->fwd_launches;
+    if (backward_launches) *backward_launches = a->bwd_launches;
+    return LBIB_OK;
+}
+
+int lb_adjoint_destroy(lbib_adjoint *a) {
+    if (!a) return fail(LBIB_EINVAL, "NULL argument");
+    cudaError_t e = cudaStreamSynchronize(a->s);
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(a->ev[k]);
+    delete a;
+    if (e != cudaSuccess) return fail(LBIB_ECUDA, cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
+}  // extern "C"

@@ -186,6 +186,11 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
 
 }  // namespace
 
+bool lbib::check_params(const lb_params *p, std::string &why) { return valid_params(p, why); }
+bool lbib::check_structure(const lb_params *p, const lbib_structure *s, std::string &why) {
+    return valid_structure(p, s, why);
+}
+
 struct lbib_ctx {
     lb_params p;
     Layout L;

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "lbib.h"
 
 namespace lbib {
@@ -182,6 +184,9 @@ __device__ __forceinline__ int stencil_axis(double p, int n, int kw, float &frac
 
 // message returned by lbib_last_error() on this thread
 void set_last_error(const char *msg);
+// argument checks of lb_init (api.cu), shared with the adjoint engine
+bool check_params(const lb_params *p, std::string &why);
+bool check_structure(const lb_params *p, const lbib_structure *s, std::string &why);
 
 // ---------------------------------------------------------------- launchers
 // LB (lb_kernels.cu)

@@ -36,6 +36,11 @@ def main(argv=None):
     ap.add_argument("--deterministic", action="store_true")
     ap.add_argument("--kernel-by-kernel", action="store_true",
                     help="launch kernels one by one instead of replaying CUDA graphs")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="run the adjoint engine: forward and backward sweeps over --steps steps, "
+                         "gradient of swimmer 0's x displacement w.r.t. its drive")
+    ap.add_argument("--K", type=int, default=100, help="adjoint checkpoint interval")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"], help="adjoint fluid precision")
     a = ap.parse_args(argv)
     from paper_2202_12147_gb300 import Batch, Simulation
     from workloads import assemble, ensemble_boxes
@@ -54,6 +59,19 @@ def main(argv=None):
             s.close()
         return
     box = _box(a.case)
+    if a.adjoint:
+        import numpy as np
+        from paper_2202_12147_gb300 import Adjoint
+        eng = Adjoint(box.dims, assemble(box), n_steps=a.steps, K=a.K, precision=a.precision, tau=box.tau,
+                      rho0=box.rho0, g=box.g)
+        d = eng.forward()
+        seed = np.zeros((eng.n_swimmers, 3))
+        seed[0, 0] = 1.0
+        g = eng.backward(seed)
+        print(f"{box.name}: displacement {d[0].tolist()}, gradient (A1 A2 A3 phi1 phi2 phi3) {g[0].tolist()}, "
+              f"timing {eng.timing()}")
+        eng.close()
+        return
     sim = Simulation(box.dims, assemble(box), tau=box.tau, rho0=box.rho0, storage=a.storage,
                      deterministic=a.deterministic, forcing=box.forcing, kernel=box.kernel)
     if a.kernel_by_kernel:

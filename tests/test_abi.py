@@ -71,3 +71,47 @@ def test_structure_validation():
     a["nodes"][3, 1] = np.nan
     with pytest.raises(_lib.LbibError, match="non-finite"):
         required_sizes((48, 48, 48), a)
+
+
+def _adjoint_bytes(dims, structure, n_steps, K, storage=3, forcing=0, kernel=0):
+    from paper_2202_12147_gb300 import _lib
+    from paper_2202_12147_gb300.sim import _HostStructure
+    L = _lib.load()
+    p = _lib.LbParams()
+    p.nx, p.ny, p.nz = dims
+    p.tau, p.rho0 = 1.0, 1.0
+    p.storage, p.forcing, p.kernel = storage, forcing, kernel
+    hs = _HostStructure(structure)
+    out = ctypes.c_size_t()
+    _lib.check(L.lb_adjoint_required_bytes(ctypes.byref(p), ctypes.byref(hs.c), n_steps, K, ctypes.byref(out)))
+    return out.value
+
+
+def test_adjoint_workspace_sizes_without_gpu():
+    """Checkpoint-and-recompute memory: K + 1 step records plus one checkpoint
+    per segment (and the final state), not one record per step."""
+    from workloads import adjoint_single_96, assemble
+    box = adjoint_single_96()
+    asm = assemble(box)
+    n = 96 ** 3
+    b64 = _adjoint_bytes(box.dims, asm, 1000, 100)
+    b32 = _adjoint_bytes(box.dims, asm, 1000, 100, storage=0)
+    rec64 = 25 * n * 8       # populations, F and u of one step, FP64
+    ck64 = 19 * n * 8
+    assert 101 * rec64 + 11 * ck64 < b64 < 101 * rec64 + 11 * ck64 + 2 * 19 * n * 8 + 8 * n * 8 + (64 << 20)
+    assert b32 < 0.55 * b64
+    # ten periods cost ten more checkpoints, not ten times the records
+    b10 = _adjoint_bytes(box.dims, asm, 10000, 100)
+    assert b10 - b64 == pytest.approx(90 * ck64, rel=0.01)
+
+
+@pytest.mark.parametrize("bad", [dict(storage=1), dict(storage=0, forcing=1), dict(kernel=1), dict(K=0),
+                                 dict(n_steps=0)])
+def test_adjoint_invalid_arguments_rejected(bad):
+    from paper_2202_12147_gb300 import _lib
+    from workloads import adjoint_small, assemble
+    box = adjoint_small()
+    kw = dict(n_steps=10, K=5)
+    kw.update(bad)
+    with pytest.raises(_lib.LbibError):
+        _adjoint_bytes(box.dims, assemble(box), **kw)
