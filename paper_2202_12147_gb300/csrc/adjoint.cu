@@ -76,34 +76,39 @@ __device__ __forceinline__ int wrapi(long long a, int n) {
 // Peskin's 4-point weight of stencil cell q (of floor(p) - 1 .. floor(p) + 2)
 // at fractional offset f, and its derivative with respect to p: with
 // s = sqrt(1 + 4f - 4f^2) the weights are (3 - 2f - s)/8, (3 - 2f + s)/8,
-// (1 + 2f + s)/8, (1 + 2f - s)/8, and ds/df = (2 - 4f)/s.
-__device__ __forceinline__ void peskin_q(double f, double s, double ds, int q, double &w, double &dw) {
-    const double A = q < 2 ? 3.0 - 2.0 * f : 1.0 + 2.0 * f, dA = q < 2 ? -2.0 : 2.0;
-    const double sg = (q == 1 || q == 2) ? 1.0 : -1.0;
-    w = (A + sg * s) * 0.125;
-    dw = (dA + sg * ds) * 0.125;
+// (1 + 2f + s)/8, (1 + 2f - s)/8, and ds/df = (2 - 4f)/s.  W is the
+// precision of the weights (that of the fluid state).
+template <typename W>
+__device__ __forceinline__ void peskin_q(W f, W s, W ds, int q, W &w, W &dw) {
+    const W A = q < 2 ? (W)3 - (W)2 * f : (W)1 + (W)2 * f, dA = q < 2 ? (W)-2 : (W)2;
+    const W sg = (q == 1 || q == 2) ? (W)1 : (W)-1;
+    w = (A + sg * s) * (W)0.125;
+    dw = (dA + sg * ds) * (W)0.125;
 }
 
 // The two stencil cells of a lane (numbers lane and lane + 32 of the 64,
 // x fastest: they differ in z only), their weights Delta(x - r) and
-// gradients d Delta / d r.
-__device__ __forceinline__ void lane_cells(const Dims &d, const double *r, int lane, long long cell[2], double w[2],
-                                           double g[2][3]) {
+// gradients d Delta / d r.  The fractional offsets are taken in FP64 from
+// the FP64 positions.
+template <typename W>
+__device__ __forceinline__ void lane_cells(const Dims &d, const double *r, int lane, int cell[2], W w[2],
+                                           W g[2][3]) {
     const int qx = lane & 3, qy = (lane >> 2) & 3, qz = lane >> 4;
     const double fx = floor(r[0]), fy = floor(r[1]), fz = floor(r[2]);
-    const double ax = r[0] - fx, ay = r[1] - fy, az = r[2] - fz;
-    const double sx = sqrt(1.0 + 4.0 * ax - 4.0 * ax * ax), sy = sqrt(1.0 + 4.0 * ay - 4.0 * ay * ay),
-                 sz = sqrt(1.0 + 4.0 * az - 4.0 * az * az);
-    double wx, dx, wy, dy;
-    peskin_q(ax, sx, (2.0 - 4.0 * ax) / sx, qx, wx, dx);
-    peskin_q(ay, sy, (2.0 - 4.0 * ay) / sy, qy, wy, dy);
+    const W ax = (W)(r[0] - fx), ay = (W)(r[1] - fy), az = (W)(r[2] - fz);
+    const W sx = sqrt((W)1 + (W)4 * ax - (W)4 * ax * ax), sy = sqrt((W)1 + (W)4 * ay - (W)4 * ay * ay),
+            sz = sqrt((W)1 + (W)4 * az - (W)4 * az * az);
+    W wx, dx, wy, dy;
+    peskin_q<W>(ax, sx, ((W)2 - (W)4 * ax) / sx, qx, wx, dx);
+    peskin_q<W>(ay, sy, ((W)2 - (W)4 * ay) / sy, qy, wy, dy);
     const int X = wrapi((long long)fx - 1 + qx, d.nx), Y = wrapi((long long)fy - 1 + qy, d.ny);
+    const W dsz = ((W)2 - (W)4 * az) / sz;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        double wz, dz;
-        peskin_q(az, sz, (2.0 - 4.0 * az) / sz, qz + 2 * h, wz, dz);
+        W wz, dz;
+        peskin_q<W>(az, sz, dsz, qz + 2 * h, wz, dz);
         const int Z = wrapi((long long)fz - 1 + qz + 2 * h, d.nz);
-        cell[h] = X + (long long)d.nx * (Y + (long long)d.ny * Z);
+        cell[h] = X + d.nx * (Y + d.ny * Z);
         w[h] = wx * wy * wz;
         g[h][0] = dx * wy * wz;
         g[h][1] = wx * dy * wz;
@@ -117,20 +122,26 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// block-wide sum of three doubles; the result is valid in thread 0
-__device__ __forceinline__ void block_sum3(double v[3], double (*sh)[3]) {
+// Sum of three doubles over each 256-thread group of a 768-thread block (one
+// group per bead of a swimmer); the group's sum is written to out[group].
+__device__ __forceinline__ void group_sum3(double v[3], double (*sh)[3], double (*out)[3]) {
     for (int a = 0; a < 3; ++a) v[a] = warp_sum(v[a]);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0)
         for (int a = 0; a < 3; ++a) sh[w][a] = v[a];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int a = 0; a < 3; ++a) v[a] = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
-            for (int a = 0; a < 3; ++a) v[a] += sh[k][a];
+    if (threadIdx.x < 3 * 32) {  // warp q adds the 8 warp sums of group q
+        const int q = threadIdx.x >> 5;
+        for (int a = 0; a < 3; ++a) {
+            double x = l < 8 ? sh[8 * q + l][a] : 0.0;
+            x = warp_sum(x);
+            if (l == 0) out[q][a] = x;
+        }
     }
     __syncthreads();
 }
+
+constexpr int SWIM_THREADS = 768;  // three groups of 256: one per bead
 
 // ---------------------------------------------------------------- membrane
 // Neo-Hookean linear FEM triangle (Sec. 2.2): with edge vectors d = [d1 d2],
@@ -204,25 +215,29 @@ __device__ __forceinline__ void tri_force_jvp(const double *G, const TriState &S
 
 // ---------------------------------------------------------------- forward kernels
 
-// one block per swimmer: bead centres (FP64), drive and spring forces
-__global__ void k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta, const double *r, double t, double *R,
-                              double *ext) {
-    __shared__ double sh[32][3];
+// one block per swimmer, one 256-thread group per bead: bead centres (FP64),
+// then drive and spring forces (thread 0)
+__global__ void __launch_bounds__(SWIM_THREADS) k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta,
+                                                              const double *r, const long long *t_base, int k,
+                                                              double *R, double *ext) {
+    __shared__ double sh[SWIM_THREADS / 32][3];
     __shared__ double Rs[3][3];
-    const int s = blockIdx.x;
+    const double t = (double)(*t_base + k);
+    const int s = blockIdx.x, q = threadIdx.x >> 8, tq = threadIdx.x & 255;
     const Swim w = sw[s];
-    for (int q = 0; q < 3; ++q) {
+    {
         const int b = w.bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
         double acc[3] = {0.0, 0.0, 0.0};
-        for (int j = n0 + threadIdx.x; j < n0 + nn; j += blockDim.x)
+        for (int j = n0 + tq; j < n0 + nn; j += 256)
             for (int a = 0; a < 3; ++a) acc[a] += r[3 * j + a];
-        block_sum3(acc, sh);
-        if (threadIdx.x == 0)
-            for (int a = 0; a < 3; ++a) {
-                Rs[q][a] = acc[a] / nn;
-                R[3 * b + a] = Rs[q][a];
-            }
+        group_sum3(acc, sh, Rs);
     }
+    if (threadIdx.x < 9) {
+        const int qq = threadIdx.x / 3, a = threadIdx.x % 3, b = w.bead[qq];
+        Rs[qq][a] /= m.bead_count[b];
+        R[3 * b + a] = Rs[qq][a];
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     const double om = 2.0 * 3.14159265358979323846 / w.period;
     const double *th = theta + 6 * s;
@@ -232,18 +247,18 @@ __global__ void k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta, const
     fd[1] = w.balance ? -fd[0] - fd[2] : th[1] * sin(om * t + th[4]);
     double fs[3][3];
     for (int side = 0; side < 2; ++side) {
-        const int q = side ? 2 : 0;
+        const int qq = side ? 2 : 0;
         double dd[3], n2 = 0.0;
         for (int a = 0; a < 3; ++a) {
-            dd[a] = Rs[q][a] - Rs[1][a];
+            dd[a] = Rs[qq][a] - Rs[1][a];
             n2 += dd[a] * dd[a];
         }
         const double n = sqrt(n2);
-        for (int a = 0; a < 3; ++a) fs[q][a] = -w.k * (n - w.L) * dd[a] / n;
+        for (int a = 0; a < 3; ++a) fs[qq][a] = -w.k * (n - w.L) * dd[a] / n;
     }
     for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
-    for (int q = 0; q < 3; ++q)
-        for (int a = 0; a < 3; ++a) ext[3 * w.bead[q] + a] = fs[q][a] + (a == 0 ? fd[q] : 0.0);
+    for (int qq = 0; qq < 3; ++qq)
+        for (int a = 0; a < 3; ++a) ext[3 * w.bead[qq] + a] = fs[qq][a] + (a == 0 ? fd[qq] : 0.0);
 }
 
 // one thread per triangle: corner forces -dW/dr
@@ -262,33 +277,31 @@ __global__ void k_fwd_tri(Mesh m, const double *r, double *tri_f) {
     }
 }
 
-// one thread per node: f_j = sum of its corner forces + e_b / N_b
-__global__ void k_fwd_node(Mesh m, const double *tri_f, const double *ext, double *fn) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per node: f_j = sum of its corner forces + e_b / N_b (lanes gather
+// the corners, fixed order), recorded, then F(x) += f_j Delta(x - r_j)
+template <typename T>
+__global__ void k_fwd_spread(Dims d, Mesh m, const double *r, const double *tri_f, const double *ext, double *fn,
+                             T *F) {
+    const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= m.M) return;
+    const int e0 = m.csr_ptr[j], e1 = m.csr_ptr[j + 1];
     double f[3] = {0.0, 0.0, 0.0};
-    for (int e = m.csr_ptr[j]; e < m.csr_ptr[j + 1]; ++e) {
+    for (int e = e0 + lane; e < e1; e += 32) {
         const int k = m.csr_ent[e];
         for (int a = 0; a < 3; ++a) f[a] += tri_f[3 * k + a];
     }
     const int b = m.node_bead[j];
     const double inv = 1.0 / m.bead_count[b];
-    for (int a = 0; a < 3; ++a) fn[3 * j + a] = f[a] + ext[3 * b + a] * inv;
-}
-
-// one warp per node: F(x) += f_j Delta(x - r_j)
-template <typename T>
-__global__ void k_fwd_spread(Dims d, int M, const double *r, const double *fn, T *F) {
-    const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (j >= M) return;
-    long long cell[2];
-    double w[2], g[2][3];
-    lane_cells(d, r + 3 * j, lane, cell, w, g);
-    const double f0 = fn[3 * j], f1 = fn[3 * j + 1], f2 = fn[3 * j + 2];
+    for (int a = 0; a < 3; ++a) f[a] = warp_sum(f[a]) + ext[3 * b + a] * inv;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) fn[3 * j + a] = f[a];
+    int cell[2];
+    T w[2], g[2][3];
+    lane_cells<T>(d, r + 3 * j, lane, cell, w, g);
     for (int h = 0; h < 2; ++h) {
-        atomicAdd(F + cell[h], (T)(f0 * w[h]));
-        atomicAdd(F + d.Npad + cell[h], (T)(f1 * w[h]));
-        atomicAdd(F + 2 * d.Npad + cell[h], (T)(f2 * w[h]));
+        atomicAdd(F + cell[h], (T)f[0] * w[h]);
+        atomicAdd(F + d.Npad + cell[h], (T)f[1] * w[h]);
+        atomicAdd(F + 2 * d.Npad + cell[h], (T)f[2] * w[h]);
     }
 }
 
@@ -306,11 +319,21 @@ __device__ __forceinline__ void moments(const T *dv, T &drho, T m[3]) {
     }
 }
 
-__device__ __forceinline__ void cell_xyz(const Dims &d, long long cell, int &x, int &y, int &z) {
-    x = (int)(cell % d.nx);
-    const long long yz = cell / d.nx;
-    y = (int)(yz % d.ny);
-    z = (int)(yz / d.ny);
+// cell = x + nx (y + ny z) < 2^31
+__device__ __forceinline__ void cell_xyz(const Dims &d, int cell, int &x, int &y, int &z) {
+    const int yz = cell / d.nx;
+    x = cell - yz * d.nx;
+    z = yz / d.ny;
+    y = yz - z * d.ny;
+}
+
+// neighbour cell x + c of a periodic box (c in {-1, 0, 1} per axis)
+__device__ __forceinline__ int nbr(const Dims &d, int x, int y, int z, int ccx, int ccy, int ccz) {
+    int X = x + ccx, Y = y + ccy, Z = z + ccz;
+    X = X < 0 ? X + d.nx : (X >= d.nx ? X - d.nx : X);
+    Y = Y < 0 ? Y + d.ny : (Y >= d.ny ? Y - d.ny : Y);
+    Z = Z < 0 ? Z + d.nz : (Z >= d.nz ? Z - d.nz : Z);
+    return X + d.nx * (Y + d.ny * Z);
 }
 
 // one thread per cell: BGK collision with Guo forcing (Sec. 2.1, Eq. lbe),
@@ -319,7 +342,7 @@ __device__ __forceinline__ void cell_xyz(const Dims &d, long long cell, int &x, 
 template <typename T>
 __global__ void k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F, T *out,
                          T *u_out, T *F_next) {
-    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= d.N) return;
     int x, y, z;
     cell_xyz(d, cell, x, y, z);
@@ -341,9 +364,7 @@ __global__ void k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double g
         const T deq = w * (drho + rho * ((T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * uu));
         const T S = w * ((T)3 * (cF - uF) + (T)9 * cu * cF);
         const T post = ((T)1 - omega) * dv[i] + omega * deq + src * S;
-        const long long dst = wrapi(x + cx(i), d.nx) + (long long)d.nx * (wrapi(y + cy(i), d.ny) +
-                                                                          (long long)d.ny * wrapi(z + cz(i), d.nz));
-        out[i * d.Npad + dst] = post;
+        out[i * d.Npad + nbr(d, x, y, z, cx(i), cy(i), cz(i))] = post;
     }
     u_out[cell] = ux;
     u_out[d.Npad + cell] = uy;
@@ -358,12 +379,12 @@ template <typename T>
 __global__ void k_fwd_interp(Dims d, int M, const double *r, const T *u, double *r_next, int *err) {
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= M) return;
-    long long cell[2];
-    double w[2], g[2][3];
-    lane_cells(d, r + 3 * j, lane, cell, w, g);
+    int cell[2];
+    T w[2], g[2][3];
+    lane_cells<T>(d, r + 3 * j, lane, cell, w, g);
     double U[3] = {0.0, 0.0, 0.0};
     for (int h = 0; h < 2; ++h)
-        for (int a = 0; a < 3; ++a) U[a] += w[h] * (double)u[a * d.Npad + cell[h]];
+        for (int a = 0; a < 3; ++a) U[a] += (double)(w[h] * u[a * d.Npad + cell[h]]);
     for (int a = 0; a < 3; ++a) U[a] = warp_sum(U[a]);
     if (lane == 0) {
         bool bad = false, fast = false;
@@ -377,21 +398,23 @@ __global__ void k_fwd_interp(Dims d, int M, const double *r, const T *u, double 
     }
 }
 
-// one block per swimmer: disp_s = x_cm(final) - x_cm(initial)
-__global__ void k_disp(Mesh m, const Swim *sw, const double *rf, const double *ri, double *disp) {
-    __shared__ double sh[32][3];
-    const int s = blockIdx.x;
-    double tot[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < 3; ++q) {
-        const int b = sw[s].bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int j = n0 + threadIdx.x; j < n0 + nn; j += blockDim.x)
-            for (int a = 0; a < 3; ++a) acc[a] += rf[3 * j + a] - ri[3 * j + a];
-        block_sum3(acc, sh);
-        for (int a = 0; a < 3; ++a) tot[a] += acc[a] / nn;
+// one block per swimmer (a group per bead): disp_s = x_cm(final) - x_cm(initial)
+__global__ void __launch_bounds__(SWIM_THREADS) k_disp(Mesh m, const Swim *sw, const double *rf, const double *ri,
+                                                       double *disp) {
+    __shared__ double sh[SWIM_THREADS / 32][3];
+    __shared__ double tot[3][3];
+    const int s = blockIdx.x, q = threadIdx.x >> 8, tq = threadIdx.x & 255;
+    const int b = sw[s].bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int j = n0 + tq; j < n0 + nn; j += 256)
+        for (int a = 0; a < 3; ++a) acc[a] += rf[3 * j + a] - ri[3 * j + a];
+    group_sum3(acc, sh, tot);
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        double x = 0.0;
+        for (int qq = 0; qq < 3; ++qq) x += tot[qq][a] / m.bead_count[sw[s].bead[qq]];
+        disp[3 * s + a] = x / 3.0;
     }
-    if (threadIdx.x == 0)
-        for (int a = 0; a < 3; ++a) disp[3 * s + a] = tot[a] / 3.0;
 }
 
 // ---------------------------------------------------------------- reverse kernels
@@ -414,18 +437,18 @@ template <typename T>
 __global__ void k_adj_interp(Dims d, int M, const double *r, const T *u, double *lam_r, T *lam_u) {
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= M) return;
-    long long cell[2];
-    double w[2], g[2][3];
-    lane_cells(d, r + 3 * j, lane, cell, w, g);
+    int cell[2];
+    T w[2], g[2][3];
+    lane_cells<T>(d, r + 3 * j, lane, cell, w, g);
     const double L0 = lam_r[3 * j], L1 = lam_r[3 * j + 1], L2 = lam_r[3 * j + 2];
     double G[3] = {0.0, 0.0, 0.0};
     for (int h = 0; h < 2; ++h) {
         const double u0 = (double)u[cell[h]], u1 = (double)u[d.Npad + cell[h]], u2 = (double)u[2 * d.Npad + cell[h]];
-        atomicAdd(lam_u + cell[h], (T)(w[h] * L0));
-        atomicAdd(lam_u + d.Npad + cell[h], (T)(w[h] * L1));
-        atomicAdd(lam_u + 2 * d.Npad + cell[h], (T)(w[h] * L2));
+        atomicAdd(lam_u + cell[h], w[h] * (T)L0);
+        atomicAdd(lam_u + d.Npad + cell[h], w[h] * (T)L1);
+        atomicAdd(lam_u + 2 * d.Npad + cell[h], w[h] * (T)L2);
         const double dot = L0 * u0 + L1 * u1 + L2 * u2;
-        for (int a = 0; a < 3; ++a) G[a] += dot * g[h][a];
+        for (int a = 0; a < 3; ++a) G[a] += dot * (double)g[h][a];
     }
     for (int a = 0; a < 3; ++a) G[a] = warp_sum(G[a]);
     if (lane == 0)
@@ -436,16 +459,14 @@ __global__ void k_adj_interp(Dims d, int M, const double *r, const T *u, double 
 template <typename T>
 __global__ void k_adj_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F,
                          const T *lam_next, T *lam_u, T *lam_cur, T *lam_F) {
-    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= d.N) return;
     int x, y, z;
     cell_xyz(d, cell, x, y, z);
     T ls[Q], dv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const long long src = wrapi(x + cx(i), d.nx) + (long long)d.nx * (wrapi(y + cy(i), d.ny) +
-                                                                          (long long)d.ny * wrapi(z + cz(i), d.nz));
-        ls[i] = lam_next[i * d.Npad + src];
+        ls[i] = lam_next[i * d.Npad + nbr(d, x, y, z, cx(i), cy(i), cz(i))];
         dv[i] = pops[i * d.Npad + cell];
     }
     const T Fx = F[cell] + (T)gx, Fy = F[d.Npad + cell] + (T)gy, Fz = F[2 * d.Npad + cell] + (T)gz;
@@ -507,19 +528,19 @@ __global__ void k_adj_spread(Dims d, int M, const double *r, const double *fn, c
                              double *lam_fn) {
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= M) return;
-    long long cell[2];
-    double w[2], g[2][3];
-    lane_cells(d, r + 3 * j, lane, cell, w, g);
+    int cell[2];
+    T w[2], g[2][3];
+    lane_cells<T>(d, r + 3 * j, lane, cell, w, g);
     const double f0 = fn[3 * j], f1 = fn[3 * j + 1], f2 = fn[3 * j + 2];
     double lf[3] = {0.0, 0.0, 0.0}, G[3] = {0.0, 0.0, 0.0};
     for (int h = 0; h < 2; ++h) {
         const double l0 = (double)lam_F[cell[h]], l1 = (double)lam_F[d.Npad + cell[h]],
                      l2 = (double)lam_F[2 * d.Npad + cell[h]];
-        lf[0] += w[h] * l0;
-        lf[1] += w[h] * l1;
-        lf[2] += w[h] * l2;
+        lf[0] += (double)w[h] * l0;
+        lf[1] += (double)w[h] * l1;
+        lf[2] += (double)w[h] * l2;
         const double dot = l0 * f0 + l1 * f1 + l2 * f2;
-        for (int a = 0; a < 3; ++a) G[a] += dot * g[h][a];
+        for (int a = 0; a < 3; ++a) G[a] += dot * (double)g[h][a];
     }
     for (int a = 0; a < 3; ++a) {
         lf[a] = warp_sum(lf[a]);
@@ -545,24 +566,28 @@ __global__ void k_adj_tri(Mesh m, const double *r, const double *lam_fn, double 
         for (int a = 0; a < 3; ++a) tri_adj[9 * t + 3 * q + a] = df[q][a];
 }
 
-// one block per swimmer: lam_e_b = mean over bead b of lam_fj; drive-parameter
-// gradient; transpose of the spring forces -> lam_R
-__global__ void k_adj_swimmer(Mesh m, const Swim *sw, const double *theta, const double *R, const double *lam_fn,
-                              double t, double *lam_R, double *grad) {
-    __shared__ double sh[32][3];
+// one block per swimmer, one 256-thread group per bead: lam_e_b = mean over
+// bead b of lam_fj; then (thread 0) the drive-parameter gradient and the
+// transpose of the spring forces -> lam_R
+__global__ void __launch_bounds__(SWIM_THREADS) k_adj_swimmer(Mesh m, const Swim *sw, const double *theta,
+                                                              const double *R, const double *lam_fn,
+                                                              const long long *t_base, int k, double *lam_R,
+                                                              double *grad) {
+    __shared__ double sh[SWIM_THREADS / 32][3];
     __shared__ double le[3][3];
-    const int s = blockIdx.x;
+    const double t = (double)(*t_base + k);
+    const int s = blockIdx.x, q = threadIdx.x >> 8, tq = threadIdx.x & 255;
     const Swim w = sw[s];
-    for (int q = 0; q < 3; ++q) {
+    {
         const int b = w.bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
         double acc[3] = {0.0, 0.0, 0.0};
-        for (int j = n0 + threadIdx.x; j < n0 + nn; j += blockDim.x)
+        for (int j = n0 + tq; j < n0 + nn; j += 256)
             for (int a = 0; a < 3; ++a) acc[a] += lam_fn[3 * j + a];
-        block_sum3(acc, sh);
-        if (threadIdx.x == 0)
-            for (int a = 0; a < 3; ++a) le[q][a] = acc[a] / nn;
+        group_sum3(acc, sh, le);
     }
     if (threadIdx.x != 0) return;
+    for (int qq = 0; qq < 3; ++qq)
+        for (int a = 0; a < 3; ++a) le[qq][a] /= m.bead_count[w.bead[qq]];
     // drive: f_q = A_q sin(om t + phi_q) along x (balance: f_1 = -f_0 - f_2)
     const double om = 2.0 * 3.14159265358979323846 / w.period;
     const double *th = theta + 6 * s;
@@ -572,35 +597,35 @@ __global__ void k_adj_swimmer(Mesh m, const Swim *sw, const double *theta, const
         sens[1] = 0.0;
         sens[2] = le[2][0] - le[1][0];
     } else {
-        for (int q = 0; q < 3; ++q) sens[q] = le[q][0];
+        for (int qq = 0; qq < 3; ++qq) sens[qq] = le[qq][0];
     }
-    for (int q = 0; q < 3; ++q) {
-        if (w.balance && q == 1) continue;
-        const double arg = om * t + th[3 + q];
-        grad[6 * s + q] += sin(arg) * sens[q];
-        grad[6 * s + 3 + q] += th[q] * cos(arg) * sens[q];
+    for (int qq = 0; qq < 3; ++qq) {
+        if (w.balance && qq == 1) continue;
+        const double arg = om * t + th[3 + qq];
+        grad[6 * s + qq] += sin(arg) * sens[qq];
+        grad[6 * s + 3 + qq] += th[qq] * cos(arg) * sens[qq];
     }
     // springs: f_0 = h(R_0 - R_1), f_2 = h(R_2 - R_1), f_1 = -f_0 - f_2 with
     // h(d) = -k (|d| - L) d/|d|, dh/dd = -k [(1 - L/|d|) I + (L/|d|) dhat dhat^T]
     double lR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int side = 0; side < 2; ++side) {
-        const int q = side ? 2 : 0;
+        const int qq = side ? 2 : 0;
         double dd[3], n2 = 0.0, lv[3];
         for (int a = 0; a < 3; ++a) {
-            dd[a] = R[3 * w.bead[q] + a] - R[3 * w.bead[1] + a];
+            dd[a] = R[3 * w.bead[qq] + a] - R[3 * w.bead[1] + a];
             n2 += dd[a] * dd[a];
-            lv[a] = le[q][a] - le[1][a];
+            lv[a] = le[qq][a] - le[1][a];
         }
         const double n = sqrt(n2), c1 = 1.0 - w.L / n, c2 = w.L / (n * n2);
         const double dl = dd[0] * lv[0] + dd[1] * lv[1] + dd[2] * lv[2];
         for (int a = 0; a < 3; ++a) {
             const double ld = -w.k * (c1 * lv[a] + c2 * dd[a] * dl);
-            lR[q][a] += ld;
+            lR[qq][a] += ld;
             lR[1][a] -= ld;
         }
     }
-    for (int q = 0; q < 3; ++q)
-        for (int a = 0; a < 3; ++a) lam_R[3 * w.bead[q] + a] = lR[q][a];
+    for (int qq = 0; qq < 3; ++qq)
+        for (int a = 0; a < 3; ++a) lam_R[3 * w.bead[qq] + a] = lR[qq][a];
 }
 
 // one thread per node: lam_r_j += sum of its corners' membrane terms + lam_R_b / N_b
@@ -643,7 +668,7 @@ struct Plan {
     size_t c_pops, c_r, ck_bytes;
     // workspace offsets
     size_t o_tris, o_G, o_A0, o_cptr, o_cent, o_nb, o_bs, o_bc, o_bw, o_swim, o_theta, o_grad, o_disp, o_err,
-        o_seed, o_lf0, o_lf1, o_lu, o_lF, o_lr, o_lfn, o_trif, o_tria, o_lR, o_ck, o_slots, total;
+        o_seed, o_lf0, o_lf1, o_lu, o_lF, o_lr, o_lfn, o_trif, o_tria, o_lR, o_tb, o_tbt, o_ck, o_slots, total;
 };
 
 Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, int K) {
@@ -702,6 +727,8 @@ Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, i
     P.o_trif = o; o += up(9 * Tn * 8);
     P.o_tria = o; o += up(9 * Tn * 8);
     P.o_lR = o; o += up(bd);
+    P.o_tb = o; o += up(8);                          // first step of the running segment
+    P.o_tbt = o; o += up((size_t)P.n_seg * 8);       // g K for every segment g
     P.o_ck = o; o += (size_t)(P.n_seg + 1) * P.ck_bytes;  // + the final state
     P.o_slots = o; o += (size_t)(K + 1) * P.slot_bytes;
     P.total = o;
@@ -738,10 +765,23 @@ struct lbib_adjoint {
     std::vector<double> rest;  // rest node positions (host)
     int slots_seg = -1;        // segment whose steps the slots currently hold
     bool have_fwd = false;
-    cudaEvent_t ev[4];
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     float fwd_ms = 0.f, bwd_ms = 0.f;
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
+    // CUDA graphs of one full K-step segment: the forward steps, and the
+    // reverse steps for either parity of the adjoint population buffers
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t g_fwd = nullptr, g_rev[2] = {nullptr, nullptr};
+    long long n_fwd = 0, n_rev[2] = {0, 0};
 
+    ~lbib_adjoint() {
+        if (g_fwd) cudaGraphExecDestroy(g_fwd);
+        for (cudaGraphExec_t g : g_rev)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap) cudaStreamDestroy(cap);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
     template <typename X> X *at(size_t off) const { return (X *)(ws + off); }
     char *slot(int k) const { return ws + P.o_slots + (size_t)k * P.slot_bytes; }
     char *ck(int c) const { return ws + P.o_ck + (size_t)c * P.ck_bytes; }
@@ -751,7 +791,7 @@ struct lbib_adjoint {
 namespace {
 
 template <typename T>
-cudaError_t fwd_step(lbib_adjoint *a, int k, long long t) {
+cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
     const Plan &P = a->P;
     char *sl = a->slot(k), *sn = a->slot(k + 1);
     const double *r = (const double *)(sl + P.s_r);
@@ -759,25 +799,25 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, long long t) {
     T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
     const int M = P.M;
     if (M > 0) {
-        k_fwd_swimmer<<<P.S, 256, 0, a->s>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), r, (double)t, R, ext);
-        k_fwd_tri<<<(P.T + 127) / 128, 128, 0, a->s>>>(a->m, r, a->at<double>(P.o_trif));
-        k_fwd_node<<<(M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_trif), ext, fn);
-        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, fn, F);
-        a->launches += 4;
+        k_fwd_swimmer<<<P.S, SWIM_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), r,
+                                           a->at<long long>(P.o_tb), k, R, ext);
+        k_fwd_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
+        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F);
+        a->launches += 3;
     }
     const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-    k_fwd_lb<T><<<nb, 256, 0, a->s>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                       (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F));
+    k_fwd_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                     (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F));
     a->launches += 1;
     if (M > 0) {
-        k_fwd_interp<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
+        k_fwd_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
         a->launches += 1;
     }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t adj_step(lbib_adjoint *a, int k, long long t, T *lam_next, T *lam_cur) {
+cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st) {
     const Plan &P = a->P;
     char *sl = a->slot(k);
     const double *r = (const double *)(sl + P.s_r), *fn = (const double *)(sl + P.s_fn),
@@ -787,22 +827,58 @@ cudaError_t adj_step(lbib_adjoint *a, int k, long long t, T *lam_next, T *lam_cu
     double *lam_r = a->at<double>(P.o_lr), *lam_fn = a->at<double>(P.o_lfn);
     const int M = P.M;
     if (M > 0) {
-        k_adj_interp<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, u, lam_r, lam_u);
+        k_adj_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, lam_r, lam_u);
         a->launches += 1;
     }
     const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-    k_adj_lb<T><<<nb, 256, 0, a->s>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                       (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F);
+    k_adj_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                     (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F);
     a->launches += 1;
     if (M > 0) {
-        k_adj_spread<T><<<(M + 3) / 4, 128, 0, a->s>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
-        k_adj_tri<<<(P.T + 127) / 128, 128, 0, a->s>>>(a->m, r, lam_fn, a->at<double>(P.o_tria));
-        k_adj_swimmer<<<P.S, 256, 0, a->s>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), R, lam_fn,
-                                             (double)t, a->at<double>(P.o_lR), a->at<double>(P.o_grad));
-        k_adj_node<<<(M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_tria), a->at<double>(P.o_lR), lam_r);
+        k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
+        k_adj_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, lam_fn, a->at<double>(P.o_tria));
+        k_adj_swimmer<<<P.S, SWIM_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), R, lam_fn,
+                                           a->at<long long>(P.o_tb), k, a->at<double>(P.o_lR),
+                                           a->at<double>(P.o_grad));
+        k_adj_node<<<(M + 127) / 128, 128, 0, st>>>(a->m, a->at<double>(P.o_tria), a->at<double>(P.o_lR), lam_r);
         a->launches += 4;
     }
     return cudaGetLastError();
+}
+
+// capture the K forward steps of a full segment (slots 0 -> K), or its K
+// reverse steps starting on adjoint buffer `par`, into a graph
+template <typename T>
+cudaError_t capture(lbib_adjoint *a, bool reverse, int par) {
+    const Plan &P = a->P;
+    const long long n0 = a->launches;
+    cudaError_t e = cudaStreamBeginCapture(a->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    T *lam[2] = {a->at<T>(P.o_lf0), a->at<T>(P.o_lf1)};
+    int nxt = par;
+    for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
+        if (reverse) {
+            const int kk = P.K - 1 - k;
+            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap);
+            nxt = 1 - nxt;
+        } else {
+            e = fwd_step<T>(a, k, a->cap);
+        }
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(a->cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(reverse ? &a->g_rev[par] : &a->g_fwd, g, 0);
+    if (g) cudaGraphDestroy(g);
+    (reverse ? a->n_rev[par] : a->n_fwd) = a->launches - n0;
+    a->launches = n0;
+    return e;
+}
+
+// set the device step counter to the first step of segment g
+cudaError_t set_tbase(lbib_adjoint *a, int g) {
+    return cudaMemcpyAsync(a->at<long long>(a->P.o_tb), a->at<long long>(a->P.o_tbt) + g, 8, cudaMemcpyDeviceToDevice,
+                           a->s);
 }
 
 // run segment g forward from its checkpoint, filling slots 0..len
@@ -818,9 +894,16 @@ cudaError_t run_segment(lbib_adjoint *a, int g) {
         (e = cudaMemcpyAsync(s0 + P.s_r, c + P.c_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToDevice, a->s)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(s0 + P.s_F, 0, 3 * (size_t)P.d.Npad * P.esize, a->s)) != cudaSuccess) return e;
+    if ((e = set_tbase(a, g)) != cudaSuccess) return e;
     const int len = a->seg_len(g);
-    for (int k = 0; k < len; ++k)
-        if ((e = fwd_step<T>(a, k, (long long)g * P.K + k)) != cudaSuccess) return e;
+    if (len == P.K) {
+        if (!a->g_fwd && (e = capture<T>(a, false, 0)) != cudaSuccess) return e;
+        if ((e = cudaGraphLaunch(a->g_fwd, a->s)) != cudaSuccess) return e;
+        a->launches += a->n_fwd;
+    } else {
+        for (int k = 0; k < len; ++k)
+            if ((e = fwd_step<T>(a, k, a->s)) != cudaSuccess) return e;
+    }
     a->slots_seg = g;
     return cudaSuccess;
 }
@@ -846,7 +929,7 @@ int forward_impl(lbib_adjoint *a, double *disp) {
         CU(save_ck(a, a->seg_len(g), g + 1));  // the next checkpoint (the last one: the final state)
     }
     if (P.S > 0) {
-        k_disp<<<P.S, 256, 0, a->s>>>(a->m, a->at<Swim>(P.o_swim), (const double *)(a->ck(P.n_seg) + P.c_r),
+        k_disp<<<P.S, SWIM_THREADS, 0, a->s>>>(a->m, a->at<Swim>(P.o_swim), (const double *)(a->ck(P.n_seg) + P.c_r),
                                       (const double *)(a->ck(0) + P.c_r), a->at<double>(P.o_disp));
         a->launches += 1;
         CU(cudaGetLastError());
@@ -930,9 +1013,18 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
     }
     for (int g = P.n_seg - 1; g >= 0; --g) {
         if (a->slots_seg != g) CU(run_segment<T>(a, g));
-        for (int k = a->seg_len(g) - 1; k >= 0; --k) {
-            CU(adj_step<T>(a, k, (long long)g * P.K + k, lam[nxt], lam[1 - nxt]));
-            nxt = 1 - nxt;
+        CU(set_tbase(a, g));
+        const int len = a->seg_len(g);
+        if (len == P.K) {
+            if (!a->g_rev[nxt]) CU(capture<T>(a, true, nxt));
+            CU(cudaGraphLaunch(a->g_rev[nxt], a->s));
+            a->launches += a->n_rev[nxt];
+            if (P.K & 1) nxt = 1 - nxt;
+        } else {
+            for (int k = len - 1; k >= 0; --k) {
+                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], a->s));
+                nxt = 1 - nxt;
+            }
         }
     }
     if (P.M > 0) {  // x_cm(0) enters the displacement with a minus sign
@@ -1055,6 +1147,9 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
             return cleanup(fail(LBIB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
     } while (0)
     for (int k = 0; k < 4; ++k) CUA(cudaEventCreate(&a->ev[k]));
+    CUA(cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking));
+    std::vector<long long> tb(P.n_seg);
+    for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
     auto put = [&](size_t off, const void *src, size_t n) {
         return n ? cudaMemcpyAsync(a->ws + off, src, n, cudaMemcpyHostToDevice, a->s) : cudaSuccess;
     };
@@ -1069,6 +1164,7 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     CUA(put(P.o_bw, bw.data(), bw.size() * 4));
     CUA(put(P.o_swim, sw.data(), sw.size() * sizeof(Swim)));
     CUA(put(P.o_theta, theta.data(), theta.size() * 8));
+    CUA(put(P.o_tbt, tb.data(), tb.size() * 8));
     // rest initial state: zero deviations, nodes at the rest shape
     CUA(cudaMemsetAsync(a->ck(0) + P.c_pops, 0, Q * (size_t)P.d.Npad * P.esize, a->s));
     CUA(put(P.o_ck + P.c_r, a->rest.data(), a->rest.size() * 8));
@@ -1152,7 +1248,6 @@ int lb_adjoint_timing(lbib_adjoint *a, double *forward_ms, double *backward_ms, 
 int lb_adjoint_destroy(lbib_adjoint *a) {
     if (!a) return fail(LBIB_EINVAL, "NULL argument");
     cudaError_t e = cudaStreamSynchronize(a->s);
-    for (int k = 0; k < 4; ++k) cudaEventDestroy(a->ev[k]);
     delete a;
     if (e != cudaSuccess) return fail(LBIB_ECUDA, cudaGetErrorString(e));
     return LBIB_OK;
