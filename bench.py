@@ -222,6 +222,7 @@ def _run_ensemble(a, barrier, stream, ws):
     barrier()
     rr_ms = e0.elapsed_time(e1) * K / K1
     batch = Batch(sims)
+    tuning = batch.autotune(steps_per_trial=4)  # launch shapes timed on real steps
     batch.lb_step(16)
     barrier()
     e0.record(stream)
@@ -239,7 +240,8 @@ def _run_ensemble(a, barrier, stream, ws):
             "batched_ms_per_step": bat_ms / K, "sequential_ms_per_step": seq_ms / K, "speedup": seq_ms / bat_ms,
             "sequential_means": "each box advanced on its own (its captured 16-step graphs), one box after another",
             "round_robin": ws * cells * K / (rr_ms / 1e3) / 1e6, "speedup_vs_round_robin": rr_ms / bat_ms,
-            "round_robin_means": "every step, each box launched on its own (one coupled step per call), box after box"}
+            "round_robin_means": "every step, each box launched on its own (one coupled step per call), box after box",
+            "autotune": tuning}
 
 
 def _run_adjoint(a, barrier, stream):

@@ -273,6 +273,32 @@ int lb_batch_step(lbib_batch *b, long long n_steps);
  * batched main fluid launch with CUDA events. */
 int lb_batch_profile(lbib_batch *b, int on);
 int lb_batch_profile_read(lbib_batch *b, double *total_ms, long long *launches);
+/* Launch-shape autotuner of a batch.  The main fluid update of every box-size
+ * class can run one, two or four adjacent cells per thread (four for 16-bit
+ * storage only; the count must divide the row length), which sets its block
+ * shape; the marked-tile launch walks its flat work list with a grid of
+ * blocks whose size trades load balance for launch width.  lb_batch_autotune
+ * times real steps of the batch with CUDA events: first `steps_per_trial`
+ * steps (rounded up to an even number, >= 2) per cells-per-thread candidate,
+ * timing each class's launches, then as many per marked-grid candidate,
+ * timing whole steps; it keeps the fastest choice of each, re-captures the
+ * batch's CUDA graph and fills `report` (may be NULL).  The tuning steps are
+ * ordinary steps of every box (the candidates differ in launch shape only),
+ * so the batch advances by report->steps_taken steps.  Synchronous. */
+#define LBIB_TUNE_MAX_CLASSES 32
+typedef struct {
+    int n_classes;                                /* box-size classes (first 32 reported) */
+    int class_dims[LBIB_TUNE_MAX_CLASSES][3];     /* nx, ny, nz of the class */
+    int class_boxes[LBIB_TUNE_MAX_CLASSES];       /* boxes in the class */
+    int class_cells_per_thread[LBIB_TUNE_MAX_CLASSES]; /* chosen */
+    double class_us[LBIB_TUNE_MAX_CLASSES][3];    /* mean main-fluid launch time for 1, 2, 4 cells per
+                                                     thread, microseconds (0: not a candidate) */
+    int marked_candidates[4];                     /* marked-tile grid sizes tried */
+    double marked_step_us[4];                     /* mean step time for each, microseconds */
+    int marked_blocks;                            /* chosen */
+    long long steps_taken;                        /* steps the tuning advanced the batch by */
+} lbib_batch_tuning;
+int lb_batch_autotune(lbib_batch *b, int steps_per_trial, lbib_batch_tuning *report);
 /* Release the batch (not the contexts).  Synchronises. */
 int lb_batch_destroy(lbib_batch *b);
 

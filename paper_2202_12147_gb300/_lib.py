@@ -26,7 +26,7 @@ EXPORTS = [
     "lb_batch_create", "lb_batch_step", "lb_batch_profile", "lb_batch_profile_read", "lb_batch_destroy",
     "lb_destroy", "lb_adjoint_required_bytes", "lb_adjoint_create", "lb_adjoint_set_drive",
     "lb_adjoint_set_initial", "lb_adjoint_forward", "lb_adjoint_backward", "lb_adjoint_get_final",
-    "lb_adjoint_timing", "lb_adjoint_destroy",
+    "lb_adjoint_timing", "lb_adjoint_destroy", "lb_batch_autotune",
 ]
 
 
@@ -62,6 +62,18 @@ class SwimmerState(ctypes.Structure):
     _fields_ = [("step", ctypes.c_longlong), ("R", (ctypes.c_double * 3) * 3), ("V", (ctypes.c_double * 3) * 3),
                 ("F", (ctypes.c_double * 3) * 3), ("T", (ctypes.c_double * 3) * 3), ("x_cm", ctypes.c_double * 3),
                 ("disp", ctypes.c_double * 3)]
+
+
+TUNE_MAX_CLASSES = 32
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int), ("class_dims", (ctypes.c_int * 3) * TUNE_MAX_CLASSES),
+                ("class_boxes", ctypes.c_int * TUNE_MAX_CLASSES),
+                ("class_cells_per_thread", ctypes.c_int * TUNE_MAX_CLASSES),
+                ("class_us", (ctypes.c_double * 3) * TUNE_MAX_CLASSES), ("marked_candidates", ctypes.c_int * 4),
+                ("marked_step_us", ctypes.c_double * 4), ("marked_blocks", ctypes.c_int),
+                ("steps_taken", ctypes.c_longlong)]
 
 
 class LbibError(RuntimeError):
@@ -115,6 +127,7 @@ def load(build_if_missing: bool = True):
         L.lb_batch_profile.argtypes = [P, I]
         L.lb_batch_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)]
         L.lb_batch_destroy.argtypes = [P]
+        L.lb_batch_autotune.argtypes = [P, I, ctypes.POINTER(BatchTuning)]
         L.lb_destroy.argtypes = [P]
         L.lb_adjoint_required_bytes.argtypes = [ctypes.POINTER(LbParams), ctypes.POINTER(Structure), LL, I, P]
         L.lb_adjoint_create.argtypes = [ctypes.POINTER(LbParams), ctypes.POINTER(Structure), LL, I, P,

@@ -327,25 +327,37 @@ __device__ __forceinline__ void cell_xyz(const Dims &d, int cell, int &x, int &y
     y = yz - z * d.ny;
 }
 
-// neighbour cell x + c of a periodic box (c in {-1, 0, 1} per axis)
-__device__ __forceinline__ int nbr(const Dims &d, int x, int y, int z, int ccx, int ccy, int ccz) {
-    int X = x + ccx, Y = y + ccy, Z = z + ccz;
-    X = X < 0 ? X + d.nx : (X >= d.nx ? X - d.nx : X);
-    Y = Y < 0 ? Y + d.ny : (Y >= d.ny ? Y - d.ny : Y);
-    Z = Z < 0 ? Z + d.nz : (Z >= d.nz ? Z - d.nz : Z);
-    return X + d.nx * (Y + d.ny * Z);
-}
+// Offsets from a cell to its periodic neighbours along +-x, +-y, +-z.
+struct Nbr {
+    int xp, xm, yp, ym, zp, zm;
+    __device__ __forceinline__ Nbr(const Dims &d, int x, int y, int z) {
+        const int sy = d.nx, sz = d.nx * d.ny;
+        xp = x == d.nx - 1 ? 1 - d.nx : 1;
+        xm = x == 0 ? d.nx - 1 : -1;
+        yp = y == d.ny - 1 ? (1 - d.ny) * sy : sy;
+        ym = y == 0 ? (d.ny - 1) * sy : -sy;
+        zp = z == d.nz - 1 ? (1 - d.nz) * sz : sz;
+        zm = z == 0 ? (d.nz - 1) * sz : -sz;
+    }
+    // offset of the neighbour at x + c_i
+    __device__ __forceinline__ int off(int i) const {
+        return (cx(i) > 0 ? xp : cx(i) < 0 ? xm : 0) + (cy(i) > 0 ? yp : cy(i) < 0 ? ym : 0) +
+               (cz(i) > 0 ? zp : cz(i) < 0 ? zm : 0);
+    }
+};
 
 // one thread per cell: BGK collision with Guo forcing (Sec. 2.1, Eq. lbe),
 // push into the next slot, the velocity u^k, and a cleared force field of the
-// next slot
+// next slot.  Opposite directions i, i+1 (c_{i+1} = -c_i) share the even and
+// odd parts of the equilibrium and of the source term.
 template <typename T>
-__global__ void k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F, T *out,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F, T *out,
                          T *u_out, T *F_next) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= d.N) return;
     int x, y, z;
     cell_xyz(d, cell, x, y, z);
+    const Nbr nb(d, x, y, z);
     T dv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) dv[i] = pops[i * d.Npad + cell];
@@ -355,16 +367,21 @@ __global__ void k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double g
     const T rho = rho0 + drho;
     const T ux = (m[0] + (T)0.5 * Fx) / rho, uy = (m[1] + (T)0.5 * Fy) / rho, uz = (m[2] + (T)0.5 * Fz) / rho;
     const T uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
-    const T src = (T)1 - (T)0.5 * omega;
+    const T src = (T)1 - (T)0.5 * omega, keep = (T)1 - omega;
+    {
+        const T w = (T)wgt_d(0);
+        out[cell] = keep * dv[0] + omega * w * (drho - rho * (T)1.5 * uu) + src * w * ((T)-3 * uF);
+    }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; i += 2) {
         const T cu = (T)cx(i) * ux + (T)cy(i) * uy + (T)cz(i) * uz;
         const T cF = (T)cx(i) * Fx + (T)cy(i) * Fy + (T)cz(i) * Fz;
         const T w = (T)wgt_d(i);
-        const T deq = w * (drho + rho * ((T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * uu));
-        const T S = w * ((T)3 * (cF - uF) + (T)9 * cu * cF);
-        const T post = ((T)1 - omega) * dv[i] + omega * deq + src * S;
-        out[i * d.Npad + nbr(d, x, y, z, cx(i), cy(i), cz(i))] = post;
+        const T eq_e = w * (drho + rho * ((T)4.5 * cu * cu - (T)1.5 * uu)), eq_o = w * rho * (T)3 * cu;
+        const T S_e = w * ((T)9 * cu * cF - (T)3 * uF), S_o = w * (T)3 * cF;
+        const T e = omega * eq_e + src * S_e, o = omega * eq_o + src * S_o;
+        out[i * d.Npad + cell + nb.off(i)] = keep * dv[i] + e + o;
+        out[(i + 1) * d.Npad + cell + nb.off(i + 1)] = keep * dv[i + 1] + e - o;
     }
     u_out[cell] = ux;
     u_out[d.Npad + cell] = uy;
@@ -455,18 +472,27 @@ __global__ void k_adj_interp(Dims d, int M, const double *r, const T *u, double 
         for (int a = 0; a < 3; ++a) lam_r[3 * j + a] += G[a];
 }
 
-// one thread per cell: transpose of stream + collide (+ the velocity output)
+// One thread per cell: transpose of stream + collide (+ the velocity output).
+// Pulled adjoints lam*_i(x) = lam_i^{n+1}(x + c_i); with
+// s0 = sum w l, s1 = sum w l c, s2 = sum w l c c (over opposite pairs: even
+// parts l_i + l_{i+1} feed s0 and s2, odd parts l_i - l_{i+1} feed s1):
+//   P = s0 (1 - 3/2 u.u) + 3 s1.u + 9/2 u.s2.u,  Q = 3 s1 - 3 s0 u + 9 s2 u,
+//   a_u = omega rho Q + (1 - omega/2)(9 s2 F - 3 s0 F) + lam_u,
+//   lam_F = (1 - omega/2) Q + a_u / (2 rho),  lam_m = a_u / rho,
+//   lam_rho = omega P - a_u.u / rho,
+//   lam_i = (1 - omega) lam*_i + lam_rho + c_i . lam_m.
 template <typename T>
-__global__ void k_adj_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_adj_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F,
                          const T *lam_next, T *lam_u, T *lam_cur, T *lam_F) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= d.N) return;
     int x, y, z;
     cell_xyz(d, cell, x, y, z);
+    const Nbr nb(d, x, y, z);
     T ls[Q], dv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        ls[i] = lam_next[i * d.Npad + nbr(d, x, y, z, cx(i), cy(i), cz(i))];
+        ls[i] = lam_next[i * d.Npad + cell + nb.off(i)];
         dv[i] = pops[i * d.Npad + cell];
     }
     const T Fx = F[cell] + (T)gx, Fy = F[d.Npad + cell] + (T)gy, Fz = F[2 * d.Npad + cell] + (T)gz;
@@ -479,19 +505,22 @@ __global__ void k_adj_lb(Dims d, T omega, T rho0, double gx, double gy, double g
     lam_u[cell] = 0;
     lam_u[d.Npad + cell] = 0;
     lam_u[2 * d.Npad + cell] = 0;
-    // weighted moments of lam*: s0 = sum w l, s1 = sum w l c, s2 = sum w l c c
-    T s0 = 0, s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    T s0 = (T)wgt_d(0) * ls[0], s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const T wl = (T)wgt_d(i) * ls[i];
+    for (int i = 1; i < Q; i += 2) {
+        const T w = (T)wgt_d(i);
+        const T ev = w * (ls[i] + ls[i + 1]), od = w * (ls[i] - ls[i + 1]);
         const int c[3] = {cx(i), cy(i), cz(i)};
-        s0 += wl;
+        s0 += ev;
         for (int a = 0; a < 3; ++a) {
-            if (c[a]) s1[a] += c[a] > 0 ? wl : -wl;
-            for (int b = 0; b < 3; ++b)
-                if (c[a] && c[b]) s2[a][b] += c[a] * c[b] > 0 ? wl : -wl;
+            if (c[a]) s1[a] += c[a] > 0 ? od : -od;
+            for (int b = a; b < 3; ++b)
+                if (c[a] && c[b]) s2[a][b] += c[a] * c[b] > 0 ? ev : -ev;
         }
     }
+    s2[1][0] = s2[0][1];
+    s2[2][0] = s2[0][2];
+    s2[2][1] = s2[1][2];
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     T s2u[3], s2F[3], Pq = s0 * ((T)1 - (T)1.5 * uu);
     for (int a = 0; a < 3; ++a) {
@@ -499,23 +528,22 @@ __global__ void k_adj_lb(Dims d, T omega, T rho0, double gx, double gy, double g
         s2F[a] = s2[a][0] * Fv[0] + s2[a][1] * Fv[1] + s2[a][2] * Fv[2];
         Pq += (T)3 * s1[a] * u[a] + (T)4.5 * u[a] * s2u[a];
     }
-    const T src = (T)1 - (T)0.5 * omega;
-    T au[3], lm[3], lF[3], au_u = 0;
+    const T src = (T)1 - (T)0.5 * omega, keep = (T)1 - omega;
+    T lm[3], lF[3], au_u = 0;
     for (int a = 0; a < 3; ++a) {
         const T Qa = (T)3 * s1[a] - (T)3 * s0 * u[a] + (T)9 * s2u[a];
-        au[a] = omega * rho * Qa + src * ((T)9 * s2F[a] - (T)3 * s0 * Fv[a]) + lu[a];
-        lF[a] = src * Qa + (T)0.5 * au[a] * ir;
-        lm[a] = au[a] * ir;
-        au_u += au[a] * u[a];
+        const T au = omega * rho * Qa + src * ((T)9 * s2F[a] - (T)3 * s0 * Fv[a]) + lu[a];
+        lF[a] = src * Qa + (T)0.5 * au * ir;
+        lm[a] = au * ir;
+        au_u += au * u[a];
     }
     const T lrho = omega * Pq - au_u * ir;
+    lam_cur[cell] = keep * ls[0] + lrho;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        T v = ((T)1 - omega) * ls[i] + lrho;
-        if (cx(i)) v += cx(i) > 0 ? lm[0] : -lm[0];
-        if (cy(i)) v += cy(i) > 0 ? lm[1] : -lm[1];
-        if (cz(i)) v += cz(i) > 0 ? lm[2] : -lm[2];
-        lam_cur[i * d.Npad + cell] = v;
+    for (int i = 1; i < Q; i += 2) {
+        const T cm = (T)cx(i) * lm[0] + (T)cy(i) * lm[1] + (T)cz(i) * lm[2];
+        lam_cur[i * d.Npad + cell] = keep * ls[i] + lrho + cm;
+        lam_cur[(i + 1) * d.Npad + cell] = keep * ls[i + 1] + lrho - cm;
     }
     lam_F[cell] = lF[0];
     lam_F[d.Npad + cell] = lF[1];

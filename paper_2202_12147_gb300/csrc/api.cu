@@ -2,6 +2,7 @@
 // of the caller buffers, mesh preprocessing, CUDA-graph capture of the step
 // and the host-side accessors.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstddef>
 #include <cstdlib>
@@ -225,6 +226,12 @@ struct lbib_batch {
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
+    std::vector<int> class_cpt;    // cells per thread of each class's main fluid launch
+    // autotuning: events around every class launch (class index, start, end)
+    bool class_timing = false;
+    std::vector<cudaEvent_t> tev;
+    std::vector<int> tev_class;
+    size_t tev_used = 0;
 };
 
 namespace {
@@ -846,6 +853,20 @@ cudaError_t batch_timed_event(lbib_batch *b, cudaStream_t s) {
     return cudaSuccess;
 }
 
+cudaError_t class_event(lbib_batch *b, int cls, cudaStream_t s) {
+    cudaError_t e;
+    while (b->tev.size() < b->tev_used + 1) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+        b->tev.push_back(ev);
+        b->tev_class.push_back(-1);
+    }
+    if ((e = cudaEventRecord(b->tev[b->tev_used], s)) != cudaSuccess) return e;
+    b->tev_class[b->tev_used] = cls;
+    b->tev_used += 1;
+    return cudaSuccess;
+}
+
 cudaError_t batch_fork(lbib_batch *b, cudaStream_t sm, cudaStream_t sib) {
     cudaError_t e;
     if ((e = cudaEventRecord(b->e_fork, sm)) != cudaSuccess) return e;
@@ -861,8 +882,12 @@ cudaError_t batch_enqueue_step(lbib_batch *b, bool odd, cudaStream_t sm, cudaStr
     auto main_fluid = [&]() -> cudaError_t {
         cudaError_t r;
         if (timed && (r = batch_timed_event(b, sm)) != cudaSuccess) return r;
-        for (const ClassArgs &ca : b->classes)
-            if ((r = launch_lb_class(ca, b->storage, b->forcing, bt.cells_per_thread, odd, sm)) != cudaSuccess) return r;
+        for (size_t k = 0; k < b->classes.size(); ++k) {
+            if (b->class_timing && (r = class_event(b, (int)k, sm)) != cudaSuccess) return r;
+            if ((r = launch_lb_class(b->classes[k], b->storage, b->forcing, b->class_cpt[k], odd, sm)) != cudaSuccess)
+                return r;
+            if (b->class_timing && (r = class_event(b, (int)k, sm)) != cudaSuccess) return r;
+        }
         if (timed && (r = batch_timed_event(b, sm)) != cudaSuccess) return r;
         return cudaSuccess;
     };
@@ -876,6 +901,34 @@ cudaError_t batch_enqueue_step(lbib_batch *b, bool odd, cudaStream_t sm, cudaStr
     if ((e = launch_lb_batch(bt, b->storage, b->forcing, b->det, true, odd, sib)) != cudaSuccess) return e;
     if ((e = launch_ib_batch(bt, b->kernel, b->det, 2, sib)) != cudaSuccess) return e;
     return cudaEventRecord(b->e_ib, sib);
+}
+
+// capture GRAPH_STEPS batch steps, starting at the parity of the current step
+cudaError_t capture_batch_graph(lbib_batch *b) {
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->step = b->ctx[0]->step;
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return ce;
+    ce = batch_fork(b, b->cap, b->cap_ib);
+    for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k)
+        ce = batch_enqueue_step(b, ((b->step + k) & 1) != 0, b->cap, b->cap_ib, false);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->e_ib, 0);
+    const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return ce;
+}
+
+// a cells-per-thread count the main fluid kernel of class k can use
+bool cpt_valid(const lbib_batch *b, size_t k, int cpt) {
+    const DevCtx &c = b->classes[k].box[0];
+    if (b->storage == LBIB_F32 && cpt > 2) return false;
+    return c.tile_x % cpt == 0 && c.nx % cpt == 0;
 }
 
 }  // namespace
@@ -979,19 +1032,10 @@ int lb_batch_create(lbib_ctx *const *ctxs, int n, lbib_batch **out) {
         cudaEventCreateWithFlags(&b->e_main, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->e_ib, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "creating batch streams or events failed"));
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return bail(fail(LBIB_ECUDA, "cudaStreamBeginCapture failed"));
-    cudaError_t ce = batch_fork(b, b->cap, b->cap_ib);
-    for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k)
-        ce = batch_enqueue_step(b, ((b->step + k) & 1) != 0, b->cap, b->cap_ib, false);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->e_ib, 0);
-    cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
-    if (ce != cudaSuccess || ee != cudaSuccess)
-        return bail(fail(LBIB_ECUDA, std::string("batch graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee)));
-    ce = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (ce != cudaSuccess) return bail(fail(LBIB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce)));
+    b->class_cpt.assign(b->classes.size(), cpt);
+    const cudaError_t ce = capture_batch_graph(b);
+    if (ce != cudaSuccess)
+        return bail(fail(LBIB_ECUDA, std::string("batch graph capture failed: ") + cudaGetErrorString(ce)));
     for (lbib_ctx *c : b->ctx) c->batch = b;
     *out = b;
     return LBIB_OK;
@@ -1048,6 +1092,119 @@ int lb_batch_profile_read(lbib_batch *b, double *total_ms, long long *launches) 
     return LBIB_OK;
 }
 
+int lb_batch_autotune(lbib_batch *b, int steps_per_trial, lbib_batch_tuning *report) {
+    if (!b) return fail(LBIB_EINVAL, "batch is NULL");
+    if (steps_per_trial < 1) return fail(LBIB_EINVAL, "steps_per_trial < 1");
+    const int n_trial = (steps_per_trial + 1) / 2 * 2;
+    const bool was_profiling = b->profiling;
+    const long long step0 = b->ctx[0]->step;
+    const size_t nc = b->classes.size();
+    std::vector<std::array<double, 3>> us(nc, std::array<double, 3>{0.0, 0.0, 0.0});
+    CU(cudaStreamSynchronize(b->user));
+    b->profiling = true;  // kernel by kernel
+    b->ev_used = 0;
+    // 1. cells per thread of each class's main fluid launch
+    const int cands[3] = {1, 2, 4};
+    const std::vector<int> best0 = b->class_cpt;
+    for (int ci = 0; ci < 3; ++ci) {
+        const int cand = cands[ci];
+        bool any = false;
+        for (size_t k = 0; k < nc; ++k) {
+            const bool ok = cpt_valid(b, k, cand);
+            b->class_cpt[k] = ok ? cand : best0[k];
+            any |= ok;
+        }
+        if (!any) continue;
+        b->class_timing = true;
+        b->tev_used = 0;
+        const int st = lb_batch_step(b, n_trial);
+        b->class_timing = false;
+        if (st != LBIB_OK) return st;
+        CU(cudaStreamSynchronize(b->user));
+        std::vector<double> sum(nc, 0.0);
+        std::vector<int> cnt(nc, 0);
+        for (size_t e = 0; e + 1 < b->tev_used; e += 2) {
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, b->tev[e], b->tev[e + 1]));
+            const int k = b->tev_class[e];
+            sum[k] += ms * 1e3;
+            cnt[k] += 1;
+        }
+        for (size_t k = 0; k < nc; ++k)
+            if (cpt_valid(b, k, cand) && cnt[k]) us[k][ci] = sum[k] / cnt[k];
+    }
+    for (size_t k = 0; k < nc; ++k) {
+        int best = best0[k];
+        double t_best = 1e300;
+        for (int ci = 0; ci < 3; ++ci)
+            if (us[k][ci] > 0.0 && us[k][ci] < t_best) {
+                t_best = us[k][ci];
+                best = cands[ci];
+            }
+        b->class_cpt[k] = best;
+    }
+    // 2. grid of the marked-tile launch (whole-step timing)
+    int mc[4] = {0, 0, 0, 0};
+    double mus[4] = {0.0, 0.0, 0.0, 0.0};
+    int n_mc = 0;
+    if (b->any_nodes) {
+        int sms = 0, dev = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int base = b->bt.blocks_marked;
+        const int cand_m[4] = {base, std::max(1, base / 2), std::min(65535, 2 * base), std::max(1, 2 * sms)};
+        for (int c : cand_m) {
+            bool dup = false;
+            for (int q = 0; q < n_mc; ++q) dup |= mc[q] == c;
+            if (!dup) mc[n_mc++] = c;
+        }
+        cudaEvent_t t0, t1;
+        CU(cudaEventCreate(&t0));
+        CU(cudaEventCreate(&t1));
+        for (int q = 0; q < n_mc; ++q) {
+            b->bt.blocks_marked = mc[q];
+            CU(cudaEventRecord(t0, b->user));
+            const int st = lb_batch_step(b, n_trial);
+            if (st != LBIB_OK) return st;
+            CU(cudaEventRecord(t1, b->user));
+            CU(cudaEventSynchronize(t1));
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, t0, t1));
+            mus[q] = ms * 1e3 / n_trial;
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        int qb = 0;
+        for (int q = 1; q < n_mc; ++q)
+            if (mus[q] < mus[qb]) qb = q;
+        b->bt.blocks_marked = mc[qb];
+    }
+    b->profiling = was_profiling;
+    b->ev_used = 0;
+    const cudaError_t ce = capture_batch_graph(b);
+    if (ce != cudaSuccess) return fail(LBIB_ECUDA, std::string("batch graph capture failed: ") + cudaGetErrorString(ce));
+    if (report) {
+        memset(report, 0, sizeof(*report));
+        report->n_classes = (int)nc;
+        for (size_t k = 0; k < nc && k < LBIB_TUNE_MAX_CLASSES; ++k) {
+            const DevCtx &c = b->classes[k].box[0];
+            report->class_dims[k][0] = c.nx;
+            report->class_dims[k][1] = c.ny;
+            report->class_dims[k][2] = c.nz;
+            report->class_boxes[k] = b->classes[k].n;
+            report->class_cells_per_thread[k] = b->class_cpt[k];
+            for (int ci = 0; ci < 3; ++ci) report->class_us[k][ci] = us[k][ci];
+        }
+        for (int q = 0; q < n_mc; ++q) {
+            report->marked_candidates[q] = mc[q];
+            report->marked_step_us[q] = mus[q];
+        }
+        report->marked_blocks = b->bt.blocks_marked;
+        report->steps_taken = b->ctx[0]->step - step0;
+    }
+    return LBIB_OK;
+}
+
 int lb_batch_destroy(lbib_batch *b) {
     if (!b) return LBIB_OK;
     cudaStreamSynchronize(b->user);
@@ -1055,6 +1212,7 @@ int lb_batch_destroy(lbib_batch *b) {
     for (lbib_ctx *c : b->ctx)
         if (c && c->batch == b) c->batch = nullptr;
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->tev) cudaEventDestroy(e);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->cap_ib) cudaStreamDestroy(b->cap_ib);

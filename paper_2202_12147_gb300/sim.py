@@ -240,6 +240,23 @@ class Batch:
         check(self.L.lb_batch_profile_read(self.b, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def autotune(self, steps_per_trial=4):
+        """Time the launch-shape candidates on real steps and keep the fastest
+        (lb_batch_autotune); returns the tuning report as a dict."""
+        r = _lib.BatchTuning()
+        check(self.L.lb_batch_autotune(self.b, int(steps_per_trial), ctypes.byref(r)))
+        n = min(r.n_classes, _lib.TUNE_MAX_CLASSES)
+        cands = [c for c in r.marked_candidates if c > 0]
+        return {
+            "classes": [{"dims": list(r.class_dims[k]), "boxes": r.class_boxes[k],
+                         "cells_per_thread": r.class_cells_per_thread[k],
+                         "us_by_cells_per_thread": {str(c): r.class_us[k][i] for i, c in enumerate((1, 2, 4))
+                                                    if r.class_us[k][i] > 0}} for k in range(n)],
+            "marked_blocks": r.marked_blocks,
+            "marked_step_us": {str(c): r.marked_step_us[i] for i, c in enumerate(cands)},
+            "steps_taken": r.steps_taken,
+        }
+
     def close(self):
         if self.b:
             self.L.lb_batch_destroy(self.b)

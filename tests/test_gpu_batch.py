@@ -84,3 +84,36 @@ def test_batched_box_against_oracle(perm):
     batch.close()
     for s in sims:
         s.close()
+
+
+def test_autotuned_batch_against_oracle(perm):
+    """lb_batch_autotune times the launch-shape candidates on real steps, keeps
+    the fastest and re-captures the graph; the tuning steps are ordinary steps,
+    and the tuned batch still matches the oracle."""
+    from paper_2202_12147_gb300 import Batch
+    boxes = _boxes()
+    asms = [assemble(b) for b in boxes]
+    sims = [gpu_sim(b, a) for b, a in zip(boxes, asms)]
+    batch = Batch(sims)
+    rep = batch.autotune(steps_per_trial=2)
+    assert len(rep["classes"]) == 4
+    assert rep["steps_taken"] >= 4 and rep["steps_taken"] % 2 == 0
+    for c in rep["classes"]:
+        assert c["cells_per_thread"] in (1, 2)
+        assert str(c["cells_per_thread"]) in c["us_by_cells_per_thread"]
+        assert c["dims"][0] % c["cells_per_thread"] == 0
+    assert rep["marked_blocks"] >= 1
+    n = 40 - rep["steps_taken"] % 16
+    batch.lb_step(n)  # graph replays from the tuned capture plus single steps
+    total = rep["steps_taken"] + n
+    k = 1
+    assert sims[k].swimmer_state(0)["step"] == total
+    fg = gpu_f_to_oracle(sims[k].get_populations(), perm)
+    osim = oracle.OracleSim(boxes[k], asms[k]).step(total)
+    _, ug = oracle.macros(fg)
+    _, uo = oracle.macros(osim.f)
+    assert rel_l2(ug, uo) < 1e-5
+    assert np.abs(sims[k].get_nodes() - osim.r).max() < 1e-7
+    batch.close()
+    for s in sims:
+        s.close()
