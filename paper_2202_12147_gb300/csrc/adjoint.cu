@@ -351,7 +351,7 @@ struct Nbr {
 // next slot.  Opposite directions i, i+1 (c_{i+1} = -c_i) share the even and
 // odd parts of the equilibrium and of the source term.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F, T *out,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F, T *out,
                          T *u_out, T *F_next) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= d.N) return;
