@@ -209,6 +209,7 @@ struct lbib_ctx {
     Control *h_ctl = nullptr;      // pinned
     lbib_swimmer_state *h_sws = nullptr;  // pinned
     int n_nodes = 0, n_swimmers = 0;
+    int rows_grid = 0;  // > 0: main fluid update by the TMA-staged row kernel with this grid
     lbib_batch *batch = nullptr;   // set while the context belongs to a batch
 };
 
@@ -235,6 +236,12 @@ struct lbib_batch {
 };
 
 namespace {
+
+// the update of every unmarked tile: TMA-staged rows or the tile kernel
+cudaError_t main_fluid(lbib_ctx *c, bool odd, cudaStream_t s) {
+    if (c->rows_grid > 0) return launch_lb_rows(c->d, c->p.storage, c->p.forcing, odd, c->rows_grid, s);
+    return launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, s);
+}
 
 cudaError_t timed_event(lbib_ctx *c, cudaStream_t s) {
     cudaError_t e;
@@ -272,13 +279,13 @@ cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t sm, cudaStream_t si
     const int p = odd ? 1 : 0;
     if (c->n_nodes == 0) {
         if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
-        if ((e = launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, sm)) != cudaSuccess) return e;
+        if ((e = main_fluid(c, odd, sm)) != cudaSuccess) return e;
         if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
         return cudaSuccess;
     }
     if ((e = cudaStreamWaitEvent(sm, c->e_ib, 0)) != cudaSuccess) return e;
     if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
-    if ((e = launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, sm)) != cudaSuccess) return e;
+    if ((e = main_fluid(c, odd, sm)) != cudaSuccess) return e;
     if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
     if ((e = launch_ib_prepare(c->d, sib)) != cudaSuccess) return e;
     if ((e = launch_ib_gather_spread(c->d, c->p.kernel, sib)) != cudaSuccess) return e;
@@ -559,6 +566,13 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         if (cudaMemcpy(&cnt, d.tile_count, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return bail(fail(LBIB_ECUDA, "reading the marked-tile count failed"));
         d.marked_grid = env_int("LBIB_MARKED_GRID", std::min(L.n_tiles, std::max(32, cnt + cnt / 4 + 16)));
+    }
+
+    // main fluid kernel: TMA-staged rows (LBIB_MAIN_KERNEL=rows) or tiles
+    {
+        const char *mk = getenv("LBIB_MAIN_KERNEL");
+        const bool want_rows = mk && std::string(mk) == "rows";
+        c->rows_grid = want_rows && lb_rows_supported(d, p->storage) ? lb_rows_grid(d, p->storage) : 0;
     }
 
     // streams and events of the two-stream step; the IB stream gets the

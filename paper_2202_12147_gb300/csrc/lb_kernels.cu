@@ -29,6 +29,8 @@
 // there, writes the physical velocity u for the interpolation and clears F.
 // The two kernels cover disjoint cells, so k_lb_main can run while the
 // immersed-boundary kernels of the same step run on another stream.
+#include <algorithm>
+
 #include "lbib_internal.cuh"
 
 namespace lbib {
@@ -521,6 +523,206 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// ---------------------------------------------------------------- TMA-staged rows
+// Main fluid update of the unmarked rows (tile = whole row, nx <= 256) with
+// the populations staged through shared memory by the bulk-copy (TMA) engine.
+// A persistent block walks its rows (blockIdx.x, + gridDim.x, ..., skipping
+// stamped ones) through a ring of ROW_STAGES stages; each stage holds the 19
+// row-planes a row reads (even step: plane i of the row; odd step: plane
+// opp(i) of row (y - c_iy, z - c_iz), so the x shift becomes a shared-memory
+// index).  One thread issues the copies, which complete on the stage's
+// mbarrier; the block collides two adjacent cells per thread from shared
+// memory, writes the results back into the same stage at their destination
+// positions (the x shift of odd steps wraps inside the row), and the issuing
+// thread sends each row-plane to its destination row with a bulk store.
+// Every stage is refilled with the next row once the stores that read it
+// have finished, so up to ROW_STAGES - 1 rows of loads are in flight while a
+// row computes.  The AA pattern makes this race-free: the row-planes a row
+// reads are exactly the ones it writes, and no other row touches them.
+constexpr int ROW_STAGES = 3;
+constexpr long long ROW_WAIT_LIMIT = 1ll << 26;  // bounded mbarrier polls
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// bytes of dynamic shared memory of k_lb_rows for a box
+__host__ __device__ inline size_t rows_smem_bytes(int nx, int esize) {
+    return (size_t)ROW_STAGES * Q * nx * esize + ROW_STAGES * (sizeof(unsigned long long) + sizeof(int));
+}
+
+template <int ST, bool ODD, int FORCING>
+__global__ void __launch_bounds__(LB_TPB / 2) k_lb_rows(const DevCtx c) {
+    using S = Store<ST>;
+    using T = typename S::T;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nx = c.nx, ny = c.ny, nz = c.nz;
+    const int n_rows = ny * nz;
+    const unsigned rowbytes = (unsigned)(nx * sizeof(T));
+    T *stage0 = reinterpret_cast<T *>(smem);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + (size_t)ROW_STAGES * Q * rowbytes);
+    int *rowid = reinterpret_cast<int *>(bar + ROW_STAGES);
+    T *P = reinterpret_cast<T *>(c.pops);
+    const size_t Np = (size_t)c.Npad, nxy = (size_t)nx * ny;
+    const int p = ODD ? 1 : 0;
+    const int *marks = c.marks + (ODD ? c.n_tiles : 0);
+    const int gen = c.ctl->gen[p];
+    auto buf = [&](int st, int i) { return stage0 + ((size_t)st * Q + i) * nx; };
+    // row (yy, zz) of the periodic box, shifted by (dy, dz)
+    auto row_off = [&](int r, int dy, int dz) {
+        int yy = r % ny + dy, zz = r / ny + dz;
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        return (size_t)yy * nx + (size_t)zz * nxy;
+    };
+    auto next_row = [&](int r) {
+        while (r < n_rows && marks[r] == gen) r += gridDim.x;
+        return r;
+    };
+    auto issue = [&](int st, int r) {  // thread 0: the 19 row-planes of row r into stage st
+        mbar_expect_tx(&bar[st], Q * rowbytes);
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+            const T *src = ODD ? P + opp(i) * Np + row_off(r, -cy(i), -cz(i)) : P + i * Np + row_off(r, 0, 0);
+            bulk_load(buf(st, i), src, rowbytes, &bar[st]);
+        }
+        rowid[st] = r;
+    };
+    int next = 0;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < ROW_STAGES; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        next = next_row(blockIdx.x);
+        for (int st = 0; st < ROW_STAGES; ++st) {
+            if (st < ROW_STAGES - 1 && next < n_rows) {
+                issue(st, next);
+                next = next_row(next + gridDim.x);
+            } else {
+                rowid[st] = -1;
+            }
+        }
+    }
+    __syncthreads();
+    const int x0 = 2 * threadIdx.x;
+    const bool active = x0 < nx;
+    const bool forced = c.has_g != 0;
+    bool ok = true, timed_out = false;
+    for (int j = 0;; ++j) {
+        const int st = j % ROW_STAGES;
+        const int r = rowid[st];
+        if (r < 0) break;
+        {
+            const unsigned parity = (unsigned)(j / ROW_STAGES) & 1u;
+            long long it = 0;
+            bool late = false;
+            while (!mbar_try_wait(&bar[st], parity))
+                if (++it > ROW_WAIT_LIMIT) {
+                    late = true;
+                    break;
+                }
+            if (__syncthreads_or(late)) {  // leave together
+                timed_out = true;
+                break;
+            }
+        }
+        float2 d[Q];
+        if (active) {
+            const int xm = x0 ? x0 - 1 : nx - 1, x1 = x0 + 1, xp = x0 + 2 == nx ? 0 : x0 + 2;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float m = S::scaled ? wgt(i) * c.st_inv_scale : 1.0f;
+                const T *b = buf(st, i);
+                if (!ODD || cx(i) == 0) d[i] = S::ld2(b + x0, m);
+                else if (cx(i) > 0) d[i] = make_float2(S::ld(b + xm, m), S::ld(b + x0, m));
+                else d[i] = make_float2(S::ld(b + x1, m), S::ld(b + xp, m));
+            }
+        }
+        __syncthreads();  // every thread has read the stage
+        if (active) {
+            float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
+            if (forced) {
+                Fx = sp2(c.g[0]);
+                Fy = sp2(c.g[1]);
+                Fz = sp2(c.g[2]);
+            }
+            float2 ux, uy, uz, rho;
+            collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
+            ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
+            const int xm = x0 ? x0 - 1 : nx - 1, x1 = x0 + 1, xp = x0 + 2 == nx ? 0 : x0 + 2;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float m = S::scaled ? c.st_scale / wgt(i) : 1.0f;
+                if (!ODD) {
+                    S::st2(buf(st, opp(i)) + x0, d[i], m);  // slot opp(i) of the same cell
+                } else {
+                    T *b = buf(st, i);                       // slot i of cell x + c_i
+                    if (cx(i) == 0) {
+                        S::st2(b + x0, d[i], m);
+                    } else if (cx(i) > 0) {
+                        S::st(b + x1, d[i].x, m);
+                        S::st(b + xp, d[i].y, m);
+                    } else {
+                        S::st(b + xm, d[i].x, m);
+                        S::st(b + x0, d[i].y, m);
+                    }
+                }
+            }
+        }
+        fence_async_smem();
+        __syncthreads();  // the stage holds the row's results
+        if (threadIdx.x == 0) {
+#pragma unroll 1
+            for (int i = 0; i < Q; ++i) {
+                T *dst = ODD ? P + i * Np + row_off(r, cy(i), cz(i)) : P + i * Np + row_off(r, 0, 0);
+                bulk_store(dst, buf(st, i), rowbytes);
+            }
+            bulk_commit();
+            // refill the stage used one row earlier once its stores have read it
+            const int sr = (j + ROW_STAGES - 1) % ROW_STAGES;
+            bulk_wait_read1();
+            if (next < n_rows) {
+                issue(sr, next);
+                next = next_row(next + gridDim.x);
+            } else {
+                rowid[sr] = -1;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        bulk_wait_all();  // the stores have left shared memory and reached global memory
+        if (c.n_nodes == 0 && blockIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
+    }
+    if (timed_out && threadIdx.x == 0) atomicOr(&c.ctl->err, ERR_TIMEOUT);
+    report_bad(c, !ok);
+}
+
 // The marked tiles of this parity's list: a persistent grid walks the list.
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nblk) {
@@ -744,6 +946,62 @@ static void class_dispatch(const ClassArgs &ca, int cpt, bool odd, cudaStream_t 
 cudaError_t launch_lb_class(const ClassArgs &ca, int storage, int forcing, int cpt, bool odd, cudaStream_t s) {
     LBIB_DISPATCH(class_dispatch, storage, forcing, ca, cpt, odd, s);
     return cudaGetLastError();
+}
+
+template <int ST, int FORCING>
+static cudaError_t rows_dispatch(const DevCtx &c, bool odd, int grid, cudaStream_t s) {
+    using T = typename Store<ST>::T;
+    const size_t sm = rows_smem_bytes(c.nx, (int)sizeof(T));
+    const unsigned threads = (unsigned)((c.nx / 2 + 31) / 32 * 32);
+    if (odd) k_lb_rows<ST, true, FORCING><<<grid, threads, sm, s>>>(c);
+    else k_lb_rows<ST, false, FORCING><<<grid, threads, sm, s>>>(c);
+    return cudaGetLastError();
+}
+
+template <int ST, int FORCING>
+static void rows_dispatch_v(const DevCtx &c, bool odd, int grid, cudaStream_t s, cudaError_t *e) {
+    *e = rows_dispatch<ST, FORCING>(c, odd, grid, s);
+}
+
+// allow the row kernels of one storage format more than 48 KB of dynamic shared memory
+template <int ST>
+static cudaError_t rows_set_attr() {
+    constexpr int A = cudaFuncAttributeMaxDynamicSharedMemorySize, B = 160 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_lb_rows<ST, false, LBIB_GUO>, (cudaFuncAttribute)A, B)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lb_rows<ST, true, LBIB_GUO>, (cudaFuncAttribute)A, B)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lb_rows<ST, false, LBIB_SHAN_CHEN>, (cudaFuncAttribute)A, B)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_lb_rows<ST, true, LBIB_SHAN_CHEN>, (cudaFuncAttribute)A, B);
+}
+
+bool lb_rows_supported(const DevCtx &c, int storage) {
+    const int es = storage == LBIB_F32 ? 4 : 2;
+    return c.tile_x == c.nx && c.tiles_x == 1 && c.nx <= LB_TPB && (c.nx * es) % 16 == 0 && c.nx % 2 == 0 &&
+           rows_smem_bytes(c.nx, es) <= 160 * 1024;
+}
+
+cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int grid, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    LBIB_DISPATCH(rows_dispatch_v, storage, forcing, c, odd, grid, s, &e);
+    return e;
+}
+
+int lb_rows_grid(const DevCtx &c, int storage) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    const int es = storage == LBIB_F32 ? 4 : 2;
+    const size_t sm = rows_smem_bytes(c.nx, es);
+    const int threads = (c.nx / 2 + 31) / 32 * 32;
+    cudaError_t e = storage == LBIB_F16 ? rows_set_attr<LBIB_F16>()
+                    : storage == LBIB_BF16 ? rows_set_attr<LBIB_BF16>() : rows_set_attr<LBIB_F32>();
+    if (e != cudaSuccess) return 0;
+    if (storage == LBIB_F16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_rows<LBIB_F16, false, LBIB_GUO>, threads, sm);
+    else if (storage == LBIB_BF16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_rows<LBIB_BF16, false, LBIB_GUO>, threads, sm);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_rows<LBIB_F32, false, LBIB_GUO>, threads, sm);
+    if (e != cudaSuccess || per < 1) return 0;
+    const int rows = c.ny * c.nz;
+    return std::min(rows, sms * per);
 }
 
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s) {
