@@ -278,6 +278,76 @@ __device__ __forceinline__ void collide_pair(float2 (&d)[Q], const DevCtx &c, bo
     }
 }
 
+// collide_pair on values kept in the 16-bit storage scale, e_i = d_i S / w_i.
+// The weights cancel from the update: with drho = sum w_i e_i / S and
+// rho j = sum w_i e_i c_i / S, the equilibrium of direction i in this scale is
+// S (drho + rho (4.5 (c.u)^2 - 1.5 u.u +- 3 c.u)) for every i, and Guo's
+// source term S gu (9 (c.u)(c.F) - 3 u.F +- 3 c.F); so the values load and
+// store without rescaling.
+template <int FORCING>
+__device__ __forceinline__ void collide_pair_scaled(float2 (&e)[Q], const DevCtx &c, bool forced, float2 Fx, float2 Fy,
+                                                    float2 Fz, float2 &ux, float2 &uy, float2 &uz, float2 &rho) {
+    const float is = c.st_inv_scale, S = c.st_scale;
+    float2 drho = mul2(sp2(wgt(0) * is), e[0]), jx = sp2(0.f), jy = sp2(0.f), jz = sp2(0.f);
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) {
+        const float wk = wgt(k) * is;
+        const float2 sm = add2(e[k], e[k + 1]), df = sub2(e[k], e[k + 1]);
+        drho = fma2(sp2(wk), sm, drho);
+        if (cx(k)) jx = fma2(sp2(cx(k) > 0 ? wk : -wk), df, jx);
+        if (cy(k)) jy = fma2(sp2(cy(k) > 0 ? wk : -wk), df, jy);
+        if (cz(k)) jz = fma2(sp2(cz(k) > 0 ? wk : -wk), df, jz);
+    }
+    rho = add2(sp2(c.rho0), drho);
+    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    ux = mul2(fma2(sp2(0.5f), Fx, jx), irho);
+    uy = mul2(fma2(sp2(0.5f), Fy, jy), irho);
+    uz = mul2(fma2(sp2(0.5f), Fz, jz), irho);
+    float2 ex = ux, ey = uy, ez = uz;
+    if (FORCING == LBIB_SHAN_CHEN) {
+        ex = mul2(fma2(sp2(c.tau), Fx, jx), irho);
+        ey = mul2(fma2(sp2(c.tau), Fy, jy), irho);
+        ez = mul2(fma2(sp2(c.tau), Fz, jz), irho);
+    }
+    const float2 om = sp2(c.omega);
+    const float2 usq = fma2(ex, ex, fma2(ey, ey, mul2(ez, ez)));
+    const float2 base = mul2(sp2(S), sub2(drho, mul2(mul2(sp2(1.5f), rho), usq)));
+    const bool guo = FORCING == LBIB_GUO && forced;
+    const float gus = guo ? 1.0f - 0.5f * c.omega : 0.f;
+    const float2 uF3 = guo ? mul2(sp2(3.0f), fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)))) : sp2(0.f);
+    const float2 rho45 = mul2(sp2(4.5f * S), rho), rho3 = mul2(sp2(3.0f * S), rho);
+    {
+        float2 post = fma2(om, sub2(base, e[0]), e[0]);
+        if (guo) post = fma2(sp2(-gus * S), uF3, post);
+        e[0] = post;
+    }
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) {
+        float2 cu = sp2(0.f);
+        bool first = true;
+        if (cx(k)) { cu = first ? (cx(k) > 0 ? ex : sub2(cu, ex)) : (cx(k) > 0 ? add2(cu, ex) : sub2(cu, ex)); first = false; }
+        if (cy(k)) { cu = first ? (cy(k) > 0 ? ey : sub2(cu, ey)) : (cy(k) > 0 ? add2(cu, ey) : sub2(cu, ey)); first = false; }
+        if (cz(k)) { cu = first ? (cz(k) > 0 ? ez : sub2(cu, ez)) : (cz(k) > 0 ? add2(cu, ez) : sub2(cu, ez)); first = false; }
+        const float2 ev = fma2(mul2(rho45, cu), cu, base);
+        const float2 od = mul2(rho3, cu);
+        float2 p0 = fma2(om, sub2(add2(ev, od), e[k]), e[k]);
+        float2 p1 = fma2(om, sub2(sub2(ev, od), e[k + 1]), e[k + 1]);
+        if (guo) {
+            float2 cF = sp2(0.f);
+            bool f1 = true;
+            if (cx(k)) { cF = f1 ? (cx(k) > 0 ? Fx : sub2(cF, Fx)) : (cx(k) > 0 ? add2(cF, Fx) : sub2(cF, Fx)); f1 = false; }
+            if (cy(k)) { cF = f1 ? (cy(k) > 0 ? Fy : sub2(cF, Fy)) : (cy(k) > 0 ? add2(cF, Fy) : sub2(cF, Fy)); f1 = false; }
+            if (cz(k)) { cF = f1 ? (cz(k) > 0 ? Fz : sub2(cF, Fz)) : (cz(k) > 0 ? add2(cF, Fz) : sub2(cF, Fz)); f1 = false; }
+            const float2 sev = mul2(sp2(gus * S), fma2(mul2(sp2(9.0f), cu), cF, make_float2(-uF3.x, -uF3.y)));
+            const float2 sod = mul2(sp2(3.0f * gus * S), cF);
+            p0 = add2(p0, add2(sev, sod));
+            p1 = add2(p1, sub2(sev, sod));
+        }
+        e[k] = p0;
+        e[k + 1] = p1;
+    }
+}
+
 // Update of the two cells (x0, y, z), (x0 + 1, y, z), x0 even.  Populations
 // whose source or destination keeps the pair adjacent (even steps, and
 // directions with c_x = 0 on odd steps) move as one pair-aligned vector; the
@@ -359,17 +429,14 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
     return isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
 }
 
-// 16-bit formats: convert a packed pair of stored values to scaled FP32 and back.
+// 16-bit formats: a packed pair of stored values to FP32 and back (no rescaling).
 template <int ST>
-__device__ __forceinline__ float2 unpack2(unsigned v, float m) {
-    float2 f;
-    if (ST == LBIB_F16) f = __half22float2(*reinterpret_cast<const __half2 *>(&v));
-    else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
-    return __fmul2_rn(f, make_float2(m, m));
+__device__ __forceinline__ float2 unpack2_raw(unsigned v) {
+    if (ST == LBIB_F16) return __half22float2(*reinterpret_cast<const __half2 *>(&v));
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
 }
 template <int ST>
-__device__ __forceinline__ unsigned pack2(float2 v, float m) {
-    v = __fmul2_rn(v, make_float2(m, m));
+__device__ __forceinline__ unsigned pack2_raw(float2 v) {
     unsigned r;
     if (ST == LBIB_F16) {
         const __half2 h = __float22half2_rn(v);
@@ -426,7 +493,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
     for (int h = 0; h < 2; ++h) {
         float2 d[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = unpack2<ST>(h ? raw[i].y : raw[i].x, wgt(i) * c.st_inv_scale);
+        for (int i = 0; i < Q; ++i) d[i] = unpack2_raw<ST>(h ? raw[i].y : raw[i].x);  // storage scale
         const unsigned cl = cell + 2 * h;
         float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
         if (MARKED) {
@@ -446,7 +513,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
             Fz = add2(Fz, sp2(c.g[2]));
         }
         float2 ux, uy, uz, rho;
-        collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
+        collide_pair_scaled<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
         if (MARKED) {
             c.U[cl] = make_float4(ux.x, uy.x, uz.x, rho.x);
             c.U[cl + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
@@ -454,7 +521,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
         ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const unsigned e = pack2<ST>(d[i], c.st_scale / wgt(i));  // this pair's cells (x0 + 2h, x0 + 2h + 1)
+            const unsigned e = pack2_raw<ST>(d[i]);  // this pair's cells (x0 + 2h, x0 + 2h + 1)
             if (ODD) {
                 // direction i of cell x goes to slot i of cell x + c_i
                 const int dy = cy(i), dz = cz(i);
