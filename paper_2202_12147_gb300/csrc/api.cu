@@ -209,7 +209,7 @@ struct lbib_ctx {
     Control *h_ctl = nullptr;      // pinned
     lbib_swimmer_state *h_sws = nullptr;  // pinned
     int n_nodes = 0, n_swimmers = 0;
-    int rows_grid = 0;  // > 0: main fluid update by the TMA-staged row kernel with this grid
+    int slab_grid = 0;  // > 0: main fluid update by the TMA-staged slab kernel with this grid
     lbib_batch *batch = nullptr;   // set while the context belongs to a batch
 };
 
@@ -239,7 +239,7 @@ namespace {
 
 // the update of every unmarked tile: TMA-staged rows or the tile kernel
 cudaError_t main_fluid(lbib_ctx *c, bool odd, cudaStream_t s) {
-    if (c->rows_grid > 0) return launch_lb_rows(c->d, c->p.storage, c->p.forcing, odd, c->rows_grid, s);
+    if (c->slab_grid > 0) return launch_lb_slab(c->d, c->p.storage, c->p.forcing, odd, c->slab_grid, s);
     return launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, s);
 }
 
@@ -568,11 +568,11 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         d.marked_grid = env_int("LBIB_MARKED_GRID", std::min(L.n_tiles, std::max(32, cnt + cnt / 4 + 16)));
     }
 
-    // main fluid kernel: TMA-staged rows (LBIB_MAIN_KERNEL=rows) or tiles
+    // main fluid kernel: TMA-staged slabs (LBIB_MAIN_KERNEL=slabs) or tiles
     {
         const char *mk = getenv("LBIB_MAIN_KERNEL");
-        const bool want_rows = mk && std::string(mk) == "rows";
-        c->rows_grid = want_rows && lb_rows_supported(d, p->storage) ? lb_rows_grid(d, p->storage) : 0;
+        const bool want = mk && std::string(mk) == "slabs";
+        c->slab_grid = want && lb_slab_supported(d, p->storage) ? lb_slab_grid(d, p->storage) : 0;
     }
 
     // streams and events of the two-stream step; the IB stream gets the

@@ -590,24 +590,32 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// ---------------------------------------------------------------- TMA-staged rows
-// Main fluid update of the unmarked rows (tile = whole row, nx <= 256) with
-// the populations staged through shared memory by the bulk-copy (TMA) engine.
-// A persistent block walks its rows (blockIdx.x, + gridDim.x, ..., skipping
-// stamped ones) through a ring of ROW_STAGES stages; each stage holds the 19
-// row-planes a row reads (even step: plane i of the row; odd step: plane
-// opp(i) of row (y - c_iy, z - c_iz), so the x shift becomes a shared-memory
-// index).  One thread issues the copies, which complete on the stage's
-// mbarrier; the block collides two adjacent cells per thread from shared
-// memory, writes the results back into the same stage at their destination
-// positions (the x shift of odd steps wraps inside the row), and the issuing
-// thread sends each row-plane to its destination row with a bulk store.
-// Every stage is refilled with the next row once the stores that read it
-// have finished, so up to ROW_STAGES - 1 rows of loads are in flight while a
-// row computes.  The AA pattern makes this race-free: the row-planes a row
-// reads are exactly the ones it writes, and no other row touches them.
-constexpr int ROW_STAGES = 3;
-constexpr long long ROW_WAIT_LIMIT = 1ll << 26;  // bounded mbarrier polls
+// ---------------------------------------------------------------- TMA-staged slabs
+// Main fluid update of the unmarked rows with the populations staged through
+// shared memory by the bulk-copy (TMA) engine, for boxes whose rows are 64,
+// 128 or 256 cells long.  A slab is R consecutive rows (in y, at one z) with
+// R x nx x (bytes per value) = 4 KB per plane, so every bulk copy moves 4 KB
+// (2 KB at a periodic y seam).  Each persistent block (one per SM) has one
+// producer thread and 256 consumer threads and a double buffer of two slab
+// stages (2 x 19 x 4 KB):
+//   producer: loads the 19 plane slabs a slab reads (even step: plane i of
+//     its rows; odd step: plane opp(i) of rows y - c_iy at z - c_iz, so the x
+//     shift becomes a shared-memory index) on the stage's `full` mbarrier;
+//     when the consumers have marked the stage `done`, it sends each plane
+//     slab to its destination rows with bulk stores (skipping stamped rows,
+//     which the marked-tile kernel updates) and, once the stores have read
+//     the stage, refills it with the block's next slab;
+//   consumers: collide two adjacent cells per thread from shared memory,
+//     group by group of whole rows, and write the results back into the
+//     stage at their destination positions (the odd step's x shift wraps
+//     inside the row).
+// While the consumers work on one stage the other one is in flight.  The AA
+// pattern makes this race-free: the row-planes a row reads are exactly the
+// ones it writes, and no other row touches them.
+constexpr int SLAB_PLANE_BYTES = 4096;
+constexpr int SLAB_CONSUMERS = 256;
+constexpr int SLAB_THREADS = SLAB_CONSUMERS + 32;
+constexpr long long SLAB_WAIT_LIMIT = 1ll << 26;  // bounded mbarrier polls
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
@@ -636,157 +644,206 @@ __device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned 
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// bytes of dynamic shared memory of k_lb_rows for a box
-__host__ __device__ inline size_t rows_smem_bytes(int nx, int esize) {
-    return (size_t)ROW_STAGES * Q * nx * esize + ROW_STAGES * (sizeof(unsigned long long) + sizeof(int));
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar)) : "memory");
+}
+// bounded wait for the phase of the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
+    for (long long it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__host__ __device__ inline size_t slab_smem_bytes() {
+    return 2 * (size_t)Q * SLAB_PLANE_BYTES + 4 * sizeof(unsigned long long) + 4 * sizeof(int);
+}
+
+// rows per slab (0: the slab kernel does not handle this box)
+__host__ __device__ inline int slab_rows(int nx, int ny, int esize) {
+    const int rowbytes = nx * esize;
+    if (nx < 2 || 512 % nx || SLAB_PLANE_BYTES % rowbytes) return 0;
+    const int R = SLAB_PLANE_BYTES / rowbytes;
+    return (R <= 32 && ny % R == 0) ? R : 0;
 }
 
 template <int ST, bool ODD, int FORCING>
-__global__ void __launch_bounds__(LB_TPB / 2) k_lb_rows(const DevCtx c) {
+__global__ void __launch_bounds__(SLAB_THREADS, 1) k_lb_slab(const DevCtx c, int R) {
     using S = Store<ST>;
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem[];
     const int nx = c.nx, ny = c.ny, nz = c.nz;
-    const int n_rows = ny * nz;
+    const int slabs_y = ny / R, n_slabs = slabs_y * nz;
     const unsigned rowbytes = (unsigned)(nx * sizeof(T));
-    T *stage0 = reinterpret_cast<T *>(smem);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + (size_t)ROW_STAGES * Q * rowbytes);
-    int *rowid = reinterpret_cast<int *>(bar + ROW_STAGES);
+    T *const sbuf = reinterpret_cast<T *>(smem);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + 2 * (size_t)Q * SLAB_PLANE_BYTES);
+    unsigned long long *done = full + 2;
+    int *slab_id = reinterpret_cast<int *>(done + 2);
+    unsigned *slab_mask = reinterpret_cast<unsigned *>(slab_id + 2);
     T *P = reinterpret_cast<T *>(c.pops);
     const size_t Np = (size_t)c.Npad, nxy = (size_t)nx * ny;
-    const int p = ODD ? 1 : 0;
-    const int *marks = c.marks + (ODD ? c.n_tiles : 0);
-    const int gen = c.ctl->gen[p];
-    auto buf = [&](int st, int i) { return stage0 + ((size_t)st * Q + i) * nx; };
-    // row (yy, zz) of the periodic box, shifted by (dy, dz)
-    auto row_off = [&](int r, int dy, int dz) {
-        int yy = r % ny + dy, zz = r / ny + dz;
-        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-        return (size_t)yy * nx + (size_t)zz * nxy;
-    };
-    auto next_row = [&](int r) {
-        while (r < n_rows && marks[r] == gen) r += gridDim.x;
-        return r;
-    };
-    auto issue = [&](int st, int r) {  // thread 0: the 19 row-planes of row r into stage st
-        mbar_expect_tx(&bar[st], Q * rowbytes);
-#pragma unroll 1
-        for (int i = 0; i < Q; ++i) {
-            const T *src = ODD ? P + opp(i) * Np + row_off(r, -cy(i), -cz(i)) : P + i * Np + row_off(r, 0, 0);
-            bulk_load(buf(st, i), src, rowbytes, &bar[st]);
-        }
-        rowid[st] = r;
-    };
-    int next = 0;
+    auto buf = [&](int st, int i) { return sbuf + ((size_t)st * Q + i) * R * nx; };
+    auto wrapy = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
+    auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
     if (threadIdx.x == 0) {
-        for (int st = 0; st < ROW_STAGES; ++st) mbar_init(&bar[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        next = next_row(blockIdx.x);
-        for (int st = 0; st < ROW_STAGES; ++st) {
-            if (st < ROW_STAGES - 1 && next < n_rows) {
-                issue(st, next);
-                next = next_row(next + gridDim.x);
-            } else {
-                rowid[st] = -1;
-            }
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&done[st], SLAB_CONSUMERS);
         }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int x0 = 2 * threadIdx.x;
-    const bool active = x0 < nx;
-    const bool forced = c.has_g != 0;
-    bool ok = true, timed_out = false;
-    for (int j = 0;; ++j) {
-        const int st = j % ROW_STAGES;
-        const int r = rowid[st];
-        if (r < 0) break;
-        {
-            const unsigned parity = (unsigned)(j / ROW_STAGES) & 1u;
-            long long it = 0;
-            bool late = false;
-            while (!mbar_try_wait(&bar[st], parity))
-                if (++it > ROW_WAIT_LIMIT) {
-                    late = true;
-                    break;
+
+    if (threadIdx.x >= SLAB_CONSUMERS) {
+        // ------------------------------------------------ producer
+        if (threadIdx.x != SLAB_CONSUMERS) return;
+        const int *marks = c.marks + (ODD ? c.n_tiles : 0);
+        const int gen = c.ctl->gen[ODD ? 1 : 0];
+        const unsigned all = R == 32 ? 0xffffffffu : ((1u << R) - 1u);
+        auto marked_rows = [&](int s) {  // bit rr: row y0 + rr of slab s is stamped
+            const int y0 = (s % slabs_y) * R, z = s / slabs_y;
+            unsigned m = 0;
+            for (int rr = 0; rr < R; ++rr) m |= (marks[y0 + rr + ny * z] == gen ? 1u : 0u) << rr;
+            return m;
+        };
+        auto next_slab = [&](int s) {
+            while (s < n_slabs && marked_rows(s) == all) s += gridDim.x;
+            return s;
+        };
+        auto load = [&](int st, int s) {  // publish slab s (or the end) in stage st
+            if (s >= n_slabs) {
+                slab_id[st] = -1;
+                mbar_arrive(&full[st]);
+                return;
+            }
+            slab_id[st] = s;
+            slab_mask[st] = marked_rows(s);
+            mbar_expect_tx(&full[st], Q * R * rowbytes);
+            const int y0 = (s % slabs_y) * R, z = s / slabs_y;
+#pragma unroll 1
+            for (int i = 0; i < Q; ++i) {
+                const int pl = ODD ? opp(i) : i, dy = ODD ? -cy(i) : 0;
+                const size_t zo = (size_t)wrapz(z + (ODD ? -cz(i) : 0)) * nxy;
+                for (int rr = 0; rr < R;) {
+                    const int yy = wrapy(y0 + rr + dy);
+                    const int len = min(R - rr, ny - yy);
+                    bulk_load(buf(st, i) + (size_t)rr * nx, P + pl * Np + zo + (size_t)yy * nx, len * rowbytes, &full[st]);
+                    rr += len;
                 }
-            if (__syncthreads_or(late)) {  // leave together
-                timed_out = true;
+            }
+        };
+        int s = next_slab(blockIdx.x);
+        for (int st = 0; st < 2; ++st) {
+            load(st, s);
+            if (s < n_slabs) s = next_slab(s + gridDim.x);
+        }
+        for (int j = 0;; ++j) {
+            const int st = j & 1;
+            const int cur = slab_id[st];
+            if (cur < 0) break;
+            if (!mbar_wait(&done[st], (unsigned)(j >> 1) & 1u, SLAB_WAIT_LIMIT)) {
+                atomicOr(&c.ctl->err, ERR_TIMEOUT);
                 break;
             }
-        }
-        float2 d[Q];
-        if (active) {
-            const int xm = x0 ? x0 - 1 : nx - 1, x1 = x0 + 1, xp = x0 + 2 == nx ? 0 : x0 + 2;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float m = S::scaled ? wgt(i) * c.st_inv_scale : 1.0f;
-                const T *b = buf(st, i);
-                if (!ODD || cx(i) == 0) d[i] = S::ld2(b + x0, m);
-                else if (cx(i) > 0) d[i] = make_float2(S::ld(b + xm, m), S::ld(b + x0, m));
-                else d[i] = make_float2(S::ld(b + x1, m), S::ld(b + xp, m));
+            const unsigned mask = slab_mask[st];
+            const int y0 = (cur % slabs_y) * R, z = cur / slabs_y;
+#pragma unroll 1
+            for (int k = 0; k < Q; ++k) {  // plane k of the stage -> plane k of the destination rows
+                const int dy = ODD ? cy(k) : 0;
+                const size_t zo = (size_t)wrapz(z + (ODD ? cz(k) : 0)) * nxy;
+                for (int rr = 0; rr < R;) {
+                    if ((mask >> rr) & 1u) {
+                        ++rr;
+                        continue;
+                    }
+                    const int yy = wrapy(y0 + rr + dy);
+                    int len = 1;
+                    while (rr + len < R && !((mask >> (rr + len)) & 1u) && yy + len < ny) ++len;
+                    bulk_store(P + k * Np + zo + (size_t)yy * nx, buf(st, k) + (size_t)rr * nx, len * rowbytes);
+                    rr += len;
+                }
             }
+            bulk_commit();
+            bulk_wait_read0();  // the stage may be overwritten
+            load(st, s);
+            if (s < n_slabs) s = next_slab(s + gridDim.x);
         }
-        __syncthreads();  // every thread has read the stage
-        if (active) {
-            float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
-            if (forced) {
-                Fx = sp2(c.g[0]);
-                Fy = sp2(c.g[1]);
-                Fz = sp2(c.g[2]);
-            }
-            float2 ux, uy, uz, rho;
-            collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
-            ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
-            const int xm = x0 ? x0 - 1 : nx - 1, x1 = x0 + 1, xp = x0 + 2 == nx ? 0 : x0 + 2;
+        bulk_wait_all();  // every store has reached global memory
+        if (c.n_nodes == 0 && blockIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
+        return;
+    }
+
+    // ---------------------------------------------------- consumers
+    const int half = nx / 2, G = SLAB_CONSUMERS / half;  // rows per group
+    const int gr = threadIdx.x / half, x0 = 2 * (threadIdx.x % half);
+    const int xm = x0 ? x0 - 1 : nx - 1, x1 = x0 + 1, xp = x0 + 2 == nx ? 0 : x0 + 2;
+    const bool forced = c.has_g != 0;
+    bool ok = true;
+    for (int j = 0;; ++j) {
+        const int st = j & 1;
+        const bool late = !mbar_wait(&full[st], (unsigned)(j >> 1) & 1u, SLAB_WAIT_LIMIT);
+        unsigned any_late;
+        asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(any_late)
+                     : "r"((unsigned)late), "n"(SLAB_CONSUMERS)
+                     : "memory");
+        if (any_late) {
+            if (threadIdx.x == 0) atomicOr(&c.ctl->err, ERR_TIMEOUT);
+            break;
+        }
+        if (slab_id[st] < 0) break;
+        const unsigned mask = slab_mask[st];
+        for (int g0 = 0; g0 < R; g0 += G) {
+            const int rr = g0 + gr;
+            const bool act = rr < R && !((mask >> rr) & 1u);
+            float2 d[Q];
+            if (act) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float m = S::scaled ? c.st_scale / wgt(i) : 1.0f;
-                if (!ODD) {
-                    S::st2(buf(st, opp(i)) + x0, d[i], m);  // slot opp(i) of the same cell
-                } else {
-                    T *b = buf(st, i);                       // slot i of cell x + c_i
-                    if (cx(i) == 0) {
-                        S::st2(b + x0, d[i], m);
-                    } else if (cx(i) > 0) {
-                        S::st(b + x1, d[i].x, m);
-                        S::st(b + xp, d[i].y, m);
+                for (int i = 0; i < Q; ++i) {
+                    const float m = S::scaled ? wgt(i) * c.st_inv_scale : 1.0f;
+                    const T *b = buf(st, i) + (size_t)rr * nx;
+                    if (!ODD || cx(i) == 0) d[i] = S::ld2(b + x0, m);
+                    else if (cx(i) > 0) d[i] = make_float2(S::ld(b + xm, m), S::ld(b + x0, m));
+                    else d[i] = make_float2(S::ld(b + x1, m), S::ld(b + xp, m));
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(SLAB_CONSUMERS) : "memory");  // the group's rows are read
+            if (act) {
+                float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
+                if (forced) {
+                    Fx = sp2(c.g[0]);
+                    Fy = sp2(c.g[1]);
+                    Fz = sp2(c.g[2]);
+                }
+                float2 ux, uy, uz, rho;
+                collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
+                ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const float m = S::scaled ? c.st_scale / wgt(i) : 1.0f;
+                    if (!ODD) {
+                        S::st2(buf(st, opp(i)) + (size_t)rr * nx + x0, d[i], m);  // slot opp(i) of the same cell
                     } else {
-                        S::st(b + xm, d[i].x, m);
-                        S::st(b + x0, d[i].y, m);
+                        T *b = buf(st, i) + (size_t)rr * nx;                     // slot i of cell x + c_i
+                        if (cx(i) == 0) {
+                            S::st2(b + x0, d[i], m);
+                        } else if (cx(i) > 0) {
+                            S::st(b + x1, d[i].x, m);
+                            S::st(b + xp, d[i].y, m);
+                        } else {
+                            S::st(b + xm, d[i].x, m);
+                            S::st(b + x0, d[i].y, m);
+                        }
                     }
                 }
             }
         }
         fence_async_smem();
-        __syncthreads();  // the stage holds the row's results
-        if (threadIdx.x == 0) {
-#pragma unroll 1
-            for (int i = 0; i < Q; ++i) {
-                T *dst = ODD ? P + i * Np + row_off(r, cy(i), cz(i)) : P + i * Np + row_off(r, 0, 0);
-                bulk_store(dst, buf(st, i), rowbytes);
-            }
-            bulk_commit();
-            // refill the stage used one row earlier once its stores have read it
-            const int sr = (j + ROW_STAGES - 1) % ROW_STAGES;
-            bulk_wait_read1();
-            if (next < n_rows) {
-                issue(sr, next);
-                next = next_row(next + gridDim.x);
-            } else {
-                rowid[sr] = -1;
-            }
-        }
+        mbar_arrive(&done[st]);
     }
-    if (threadIdx.x == 0) {
-        bulk_wait_all();  // the stores have left shared memory and reached global memory
-        if (c.n_nodes == 0 && blockIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
-    }
-    if (timed_out && threadIdx.x == 0) atomicOr(&c.ctl->err, ERR_TIMEOUT);
     report_bad(c, !ok);
 }
 
@@ -1016,59 +1073,52 @@ cudaError_t launch_lb_class(const ClassArgs &ca, int storage, int forcing, int c
 }
 
 template <int ST, int FORCING>
-static cudaError_t rows_dispatch(const DevCtx &c, bool odd, int grid, cudaStream_t s) {
+static void slab_dispatch(const DevCtx &c, bool odd, int grid, cudaStream_t s, cudaError_t *e) {
     using T = typename Store<ST>::T;
-    const size_t sm = rows_smem_bytes(c.nx, (int)sizeof(T));
-    const unsigned threads = (unsigned)((c.nx / 2 + 31) / 32 * 32);
-    if (odd) k_lb_rows<ST, true, FORCING><<<grid, threads, sm, s>>>(c);
-    else k_lb_rows<ST, false, FORCING><<<grid, threads, sm, s>>>(c);
-    return cudaGetLastError();
+    const int R = slab_rows(c.nx, c.ny, (int)sizeof(T));
+    if (odd) k_lb_slab<ST, true, FORCING><<<grid, SLAB_THREADS, slab_smem_bytes(), s>>>(c, R);
+    else k_lb_slab<ST, false, FORCING><<<grid, SLAB_THREADS, slab_smem_bytes(), s>>>(c, R);
+    *e = cudaGetLastError();
 }
 
-template <int ST, int FORCING>
-static void rows_dispatch_v(const DevCtx &c, bool odd, int grid, cudaStream_t s, cudaError_t *e) {
-    *e = rows_dispatch<ST, FORCING>(c, odd, grid, s);
-}
-
-// allow the row kernels of one storage format more than 48 KB of dynamic shared memory
+// allow the slab kernels of one storage format their dynamic shared memory
 template <int ST>
-static cudaError_t rows_set_attr() {
-    constexpr int A = cudaFuncAttributeMaxDynamicSharedMemorySize, B = 160 * 1024;
+static cudaError_t slab_set_attr() {
+    const int B = (int)slab_smem_bytes();
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_lb_rows<ST, false, LBIB_GUO>, (cudaFuncAttribute)A, B)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_lb_rows<ST, true, LBIB_GUO>, (cudaFuncAttribute)A, B)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_lb_rows<ST, false, LBIB_SHAN_CHEN>, (cudaFuncAttribute)A, B)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_lb_rows<ST, true, LBIB_SHAN_CHEN>, (cudaFuncAttribute)A, B);
+    if ((e = cudaFuncSetAttribute(k_lb_slab<ST, false, LBIB_GUO>, A, B)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lb_slab<ST, true, LBIB_GUO>, A, B)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lb_slab<ST, false, LBIB_SHAN_CHEN>, A, B)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_lb_slab<ST, true, LBIB_SHAN_CHEN>, A, B);
 }
 
-bool lb_rows_supported(const DevCtx &c, int storage) {
+bool lb_slab_supported(const DevCtx &c, int storage) {
     const int es = storage == LBIB_F32 ? 4 : 2;
-    return c.tile_x == c.nx && c.tiles_x == 1 && c.nx <= LB_TPB && (c.nx * es) % 16 == 0 && c.nx % 2 == 0 &&
-           rows_smem_bytes(c.nx, es) <= 160 * 1024;
+    return c.tile_x == c.nx && c.tiles_x == 1 && slab_rows(c.nx, c.ny, es) > 0;
 }
 
-cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int grid, cudaStream_t s) {
+cudaError_t launch_lb_slab(const DevCtx &c, int storage, int forcing, bool odd, int grid, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    LBIB_DISPATCH(rows_dispatch_v, storage, forcing, c, odd, grid, s, &e);
+    LBIB_DISPATCH(slab_dispatch, storage, forcing, c, odd, grid, s, &e);
     return e;
 }
 
-int lb_rows_grid(const DevCtx &c, int storage) {
+int lb_slab_grid(const DevCtx &c, int storage) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    const int es = storage == LBIB_F32 ? 4 : 2;
-    const size_t sm = rows_smem_bytes(c.nx, es);
-    const int threads = (c.nx / 2 + 31) / 32 * 32;
-    cudaError_t e = storage == LBIB_F16 ? rows_set_attr<LBIB_F16>()
-                    : storage == LBIB_BF16 ? rows_set_attr<LBIB_BF16>() : rows_set_attr<LBIB_F32>();
+    cudaError_t e = storage == LBIB_F16 ? slab_set_attr<LBIB_F16>()
+                    : storage == LBIB_BF16 ? slab_set_attr<LBIB_BF16>() : slab_set_attr<LBIB_F32>();
     if (e != cudaSuccess) return 0;
-    if (storage == LBIB_F16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_rows<LBIB_F16, false, LBIB_GUO>, threads, sm);
-    else if (storage == LBIB_BF16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_rows<LBIB_BF16, false, LBIB_GUO>, threads, sm);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_rows<LBIB_F32, false, LBIB_GUO>, threads, sm);
+    if (storage == LBIB_F16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_slab<LBIB_F16, false, LBIB_GUO>, SLAB_THREADS, slab_smem_bytes());
+    else if (storage == LBIB_BF16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_slab<LBIB_BF16, false, LBIB_GUO>, SLAB_THREADS, slab_smem_bytes());
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_slab<LBIB_F32, false, LBIB_GUO>, SLAB_THREADS, slab_smem_bytes());
     if (e != cudaSuccess || per < 1) return 0;
-    const int rows = c.ny * c.nz;
-    return std::min(rows, sms * per);
+    const int es = storage == LBIB_F32 ? 4 : 2;
+    const int R = slab_rows(c.nx, c.ny, es);
+    const int slabs = R ? (c.ny / R) * c.nz : 0;
+    return std::min(slabs, sms * per);
 }
 
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s) {
