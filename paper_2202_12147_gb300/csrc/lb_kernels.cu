@@ -594,10 +594,10 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
 // Main fluid update of the unmarked rows with the populations staged through
 // shared memory by the bulk-copy (TMA) engine, for boxes whose rows are 64,
 // 128 or 256 cells long.  A slab is R consecutive rows (in y, at one z) with
-// R x nx x (bytes per value) = 4 KB per plane, so every bulk copy moves 4 KB
-// (2 KB at a periodic y seam).  Each persistent block (one per SM) has one
+// R x nx x (bytes per value) = SLAB_PLANE_BYTES per plane, so every bulk copy
+// moves that much (less at a periodic y seam).  Each persistent block has one
 // producer thread and 256 consumer threads and a double buffer of two slab
-// stages (2 x 19 x 4 KB):
+// stages (2 x 19 x SLAB_PLANE_BYTES):
 //   producer: loads the 19 plane slabs a slab reads (even step: plane i of
 //     its rows; odd step: plane opp(i) of rows y - c_iy at z - c_iz, so the x
 //     shift becomes a shared-memory index) on the stage's `full` mbarrier;
@@ -612,7 +612,13 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
 // While the consumers work on one stage the other one is in flight.  The AA
 // pattern makes this race-free: the row-planes a row reads are exactly the
 // ones it writes, and no other row touches them.
-constexpr int SLAB_PLANE_BYTES = 4096;
+#ifndef LBIB_SLAB_PLANE_BYTES
+#define LBIB_SLAB_PLANE_BYTES 4096
+#endif
+#ifndef LBIB_SLAB_MINB
+#define LBIB_SLAB_MINB 1
+#endif
+constexpr int SLAB_PLANE_BYTES = LBIB_SLAB_PLANE_BYTES;
 constexpr int SLAB_CONSUMERS = 256;
 constexpr int SLAB_THREADS = SLAB_CONSUMERS + 32;
 constexpr long long SLAB_WAIT_LIMIT = 1ll << 26;  // bounded mbarrier polls
@@ -671,7 +677,7 @@ __host__ __device__ inline int slab_rows(int nx, int ny, int esize) {
 }
 
 template <int ST, bool ODD, int FORCING>
-__global__ void __launch_bounds__(SLAB_THREADS, 1) k_lb_slab(const DevCtx c, int R) {
+__global__ void __launch_bounds__(SLAB_THREADS, LBIB_SLAB_MINB) k_lb_slab(const DevCtx c, int R) {
     using S = Store<ST>;
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem[];
