@@ -180,6 +180,13 @@ int ib_interpolate(lbib_ctx *ctx, float *node_vel_out);
 /* Copy one swimmer's observables to host memory.  Synchronises the context
  * stream and reports latched device errors. */
 int swimmer_state(lbib_ctx *ctx, int swimmer, lbib_swimmer_state *out);
+/* Asynchronous form: queues the evaluation of every swimmer's observables and
+ * a copy of the n_swimmers records into HOST memory `out` on the context
+ * stream, and returns.  The records are valid after the next synchronising
+ * call (lb_sync); `out` should be page-locked for the copy to overlap the
+ * following steps, and must not be reused before then.  Device errors
+ * surface at that synchronising call. */
+int swimmer_state_async(lbib_ctx *ctx, lbib_swimmer_state *out);
 
 /* Wait for queued work and report latched device errors. */
 int lb_sync(lbib_ctx *ctx);

@@ -26,7 +26,7 @@ EXPORTS = [
     "lb_batch_create", "lb_batch_step", "lb_batch_profile", "lb_batch_profile_read", "lb_batch_destroy",
     "lb_destroy", "lb_adjoint_required_bytes", "lb_adjoint_create", "lb_adjoint_set_drive",
     "lb_adjoint_set_initial", "lb_adjoint_forward", "lb_adjoint_backward", "lb_adjoint_get_final",
-    "lb_adjoint_timing", "lb_adjoint_destroy", "lb_batch_autotune",
+    "lb_adjoint_timing", "lb_adjoint_destroy", "lb_batch_autotune", "swimmer_state_async",
 ]
 
 
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
         L.ib_spread.argtypes = [P]
         L.ib_interpolate.argtypes = [P, P]
         L.swimmer_state.argtypes = [P, I, ctypes.POINTER(SwimmerState)]
+        L.swimmer_state_async.argtypes = [P, P]
         L.lb_sync.argtypes = [P]
         L.lb_get_macros.argtypes = [P, P, P]
         for n in ("lb_get_populations", "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces",

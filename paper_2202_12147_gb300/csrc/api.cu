@@ -658,6 +658,14 @@ int swimmer_state(lbib_ctx *c, int s, lbib_swimmer_state *out) {
     return st;
 }
 
+int swimmer_state_async(lbib_ctx *c, lbib_swimmer_state *out) {
+    if (!c || (!out && c->n_swimmers)) return fail(LBIB_EINVAL, "NULL argument");
+    if (c->n_swimmers == 0) return LBIB_OK;
+    CU(launch_swimmer_state(c->d, false, c->user));
+    CU(cudaMemcpyAsync(out, c->d.sw_state, sizeof(lbib_swimmer_state) * c->n_swimmers, cudaMemcpyDeviceToHost, c->user));
+    return LBIB_OK;
+}
+
 int lb_sync(lbib_ctx *c) {
     if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
     return check_device_errors(c);

@@ -77,7 +77,17 @@ struct Store<LBIB_BF16> {
 
 // Packed FP32 arithmetic on pairs of cells (two lanes per instruction).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+#ifndef LBIB_SUB2_FMA
+#define LBIB_SUB2_FMA 1
+#endif
+// a - b as one packed multiply-add, b * (-1) + a (exact: the product is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+#if LBIB_SUB2_FMA
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+#else
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+#endif
+}
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sp2(float s) { return make_float2(s, s); }
@@ -365,10 +375,11 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
     const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
     const unsigned cell = x0 + r0 + s0;
     const size_t Np = (size_t)c.Npad;
+    // 16-bit storage: the values stay in the storage scale (collide_pair_scaled)
     float2 d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float m = S::scaled ? wgt(i) * c.st_inv_scale : 1.0f;
+        const float m = 1.0f;
         if (ODD) {
             // direction i of cell x sits in slot opp(i) of cell x - c_i
             const int dy = -cy(i), dz = -cz(i);
@@ -400,14 +411,15 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
         Fz = add2(Fz, sp2(c.g[2]));
     }
     float2 ux, uy, uz, rho;
-    collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
+    if (S::scaled) collide_pair_scaled<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
+    else collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
     if (MARKED) {
         c.U[cell] = make_float4(ux.x, uy.x, uz.x, rho.x);
         c.U[cell + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float m = S::scaled ? c.st_scale / wgt(i) : 1.0f;
+        const float m = 1.0f;
         if (ODD) {
             // direction i of cell x goes to slot i of cell x + c_i
             const int dy = cy(i), dz = cz(i);
@@ -566,8 +578,15 @@ __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
 #ifndef LBIB_LB_QUAD_MINB
 #define LBIB_LB_QUAD_MINB 8
 #endif
+#ifndef LBIB_LB_PAIR16_MINB
+#define LBIB_LB_PAIR16_MINB 4
+#endif
 #define LBIB_LB_BOUNDS(CPT) \
     __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? 4 : LBIB_LB_QUAD_MINB))
+// the same with the storage format: 16-bit two-cell threads need fewer registers
+#define LBIB_LB_BOUNDS_ST(ST, CPT) \
+    __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), \
+                      (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? ((ST) == LBIB_F32 ? 4 : LBIB_LB_PAIR16_MINB) : LBIB_LB_QUAD_MINB))
 template <int ST, bool ODD, int FORCING, int CPT>
 __device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, unsigned tx, unsigned y, unsigned z) {
     // tiles stamped with this step's number are updated by k_lb_marked; gen[p]
@@ -585,7 +604,7 @@ __device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, uns
 }
 
 template <int ST, bool ODD, int FORCING, int CPT>
-__global__ void LBIB_LB_BOUNDS(CPT) k_lb_main(const DevCtx c) {
+__global__ void LBIB_LB_BOUNDS_ST(ST, CPT) k_lb_main(const DevCtx c) {
     const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
 }

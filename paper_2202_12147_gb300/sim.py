@@ -136,6 +136,13 @@ class Simulation:
         check(self.L.ib_interpolate(self.ctx, ctypes.c_void_p(out.data_ptr())))
         return out
 
+    def swimmer_state_async(self, out):
+        """Queue every swimmer's observables into `out` (host memory of at least
+        n_swimmers records, e.g. a pinned uint8 tensor, or an array of
+        _lib.SwimmerState); valid after sync()."""
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else ctypes.addressof(out)
+        check(self.L.swimmer_state_async(self.ctx, ctypes.c_void_p(ptr)))
+
     def swimmer_state(self, s=0):
         st = _lib.SwimmerState()
         check(self.L.swimmer_state(self.ctx, int(s), ctypes.byref(st)))

@@ -185,3 +185,30 @@ def test_empty_structure_and_tiny_box(perm):
     fg = gpu_f_to_oracle(sim.get_populations(), perm)
     assert rel_l2(_dev(fg, w), _dev(fo, w)) < 1e-6
     sim.close()
+
+
+def test_swimmer_state_async_matches_sync(gpu_lib):
+    """swimmer_state_async queues the same records swimmer_state returns."""
+    import ctypes
+
+    import torch
+
+    from paper_2202_12147_gb300 import _lib
+    from workloads import BoxSpec, SwimmerSpec
+    sw = tuple(SwimmerSpec(center=(24.0, y, 12.0), radius=3.0, subdiv=1, spacing=9.0, period=40.0).with_drive(
+        1e-3, 1e-3, 1.0) for y in (8.0, 20.0))
+    box = BoxSpec(dims=(48, 28, 24), swimmers=sw)
+    s = gpu_sim(box)
+    rec = ctypes.sizeof(_lib.SwimmerState)
+    ring = torch.zeros((3, 2 * rec), dtype=torch.uint8, pin_memory=True)
+    for k in range(3):
+        s.lb_step(5)
+        s.swimmer_state_async(ring[k])
+    s.sync()
+    last = _lib.SwimmerState.from_buffer_copy(bytes(ring[2, rec:2 * rec].numpy()))
+    ref = s.swimmer_state(1)
+    assert last.step == ref["step"] == 15
+    assert list(last.x_cm) == list(ref["x_cm"])
+    first = _lib.SwimmerState.from_buffer_copy(bytes(ring[0, :rec].numpy()))
+    assert first.step == 5
+    s.close()
