@@ -77,17 +77,10 @@ struct Store<LBIB_BF16> {
 
 // Packed FP32 arithmetic on pairs of cells (two lanes per instruction).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-#ifndef LBIB_SUB2_FMA
-#define LBIB_SUB2_FMA 1
-#endif
-// a - b as one packed multiply-add, b * (-1) + a (exact: the product is exact)
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-#if LBIB_SUB2_FMA
-    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
-#else
-    return __fadd2_rn(a, make_float2(-b.x, -b.y));
-#endif
-}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a - b as one packed multiply-add, b * (-1) + a (exact: the product is exact);
+// fewer instructions in the issue-bound 16-bit kernel, a register more
+__device__ __forceinline__ float2 sub2f(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sp2(float s) { return make_float2(s, s); }
@@ -302,7 +295,7 @@ __device__ __forceinline__ void collide_pair_scaled(float2 (&e)[Q], const DevCtx
 #pragma unroll
     for (int k = 1; k < Q; k += 2) {
         const float wk = wgt(k) * is;
-        const float2 sm = add2(e[k], e[k + 1]), df = sub2(e[k], e[k + 1]);
+        const float2 sm = add2(e[k], e[k + 1]), df = sub2f(e[k], e[k + 1]);
         drho = fma2(sp2(wk), sm, drho);
         if (cx(k)) jx = fma2(sp2(cx(k) > 0 ? wk : -wk), df, jx);
         if (cy(k)) jy = fma2(sp2(cy(k) > 0 ? wk : -wk), df, jy);
@@ -321,13 +314,13 @@ __device__ __forceinline__ void collide_pair_scaled(float2 (&e)[Q], const DevCtx
     }
     const float2 om = sp2(c.omega);
     const float2 usq = fma2(ex, ex, fma2(ey, ey, mul2(ez, ez)));
-    const float2 base = mul2(sp2(S), sub2(drho, mul2(mul2(sp2(1.5f), rho), usq)));
+    const float2 base = mul2(sp2(S), sub2f(drho, mul2(mul2(sp2(1.5f), rho), usq)));
     const bool guo = FORCING == LBIB_GUO && forced;
     const float gus = guo ? 1.0f - 0.5f * c.omega : 0.f;
     const float2 uF3 = guo ? mul2(sp2(3.0f), fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)))) : sp2(0.f);
     const float2 rho45 = mul2(sp2(4.5f * S), rho), rho3 = mul2(sp2(3.0f * S), rho);
     {
-        float2 post = fma2(om, sub2(base, e[0]), e[0]);
+        float2 post = fma2(om, sub2f(base, e[0]), e[0]);
         if (guo) post = fma2(sp2(-gus * S), uF3, post);
         e[0] = post;
     }
@@ -335,23 +328,23 @@ __device__ __forceinline__ void collide_pair_scaled(float2 (&e)[Q], const DevCtx
     for (int k = 1; k < Q; k += 2) {
         float2 cu = sp2(0.f);
         bool first = true;
-        if (cx(k)) { cu = first ? (cx(k) > 0 ? ex : sub2(cu, ex)) : (cx(k) > 0 ? add2(cu, ex) : sub2(cu, ex)); first = false; }
-        if (cy(k)) { cu = first ? (cy(k) > 0 ? ey : sub2(cu, ey)) : (cy(k) > 0 ? add2(cu, ey) : sub2(cu, ey)); first = false; }
-        if (cz(k)) { cu = first ? (cz(k) > 0 ? ez : sub2(cu, ez)) : (cz(k) > 0 ? add2(cu, ez) : sub2(cu, ez)); first = false; }
+        if (cx(k)) { cu = first ? (cx(k) > 0 ? ex : sub2f(cu, ex)) : (cx(k) > 0 ? add2(cu, ex) : sub2f(cu, ex)); first = false; }
+        if (cy(k)) { cu = first ? (cy(k) > 0 ? ey : sub2f(cu, ey)) : (cy(k) > 0 ? add2(cu, ey) : sub2f(cu, ey)); first = false; }
+        if (cz(k)) { cu = first ? (cz(k) > 0 ? ez : sub2f(cu, ez)) : (cz(k) > 0 ? add2(cu, ez) : sub2f(cu, ez)); first = false; }
         const float2 ev = fma2(mul2(rho45, cu), cu, base);
         const float2 od = mul2(rho3, cu);
-        float2 p0 = fma2(om, sub2(add2(ev, od), e[k]), e[k]);
-        float2 p1 = fma2(om, sub2(sub2(ev, od), e[k + 1]), e[k + 1]);
+        float2 p0 = fma2(om, sub2f(add2(ev, od), e[k]), e[k]);
+        float2 p1 = fma2(om, sub2f(sub2f(ev, od), e[k + 1]), e[k + 1]);
         if (guo) {
             float2 cF = sp2(0.f);
             bool f1 = true;
-            if (cx(k)) { cF = f1 ? (cx(k) > 0 ? Fx : sub2(cF, Fx)) : (cx(k) > 0 ? add2(cF, Fx) : sub2(cF, Fx)); f1 = false; }
-            if (cy(k)) { cF = f1 ? (cy(k) > 0 ? Fy : sub2(cF, Fy)) : (cy(k) > 0 ? add2(cF, Fy) : sub2(cF, Fy)); f1 = false; }
-            if (cz(k)) { cF = f1 ? (cz(k) > 0 ? Fz : sub2(cF, Fz)) : (cz(k) > 0 ? add2(cF, Fz) : sub2(cF, Fz)); f1 = false; }
+            if (cx(k)) { cF = f1 ? (cx(k) > 0 ? Fx : sub2f(cF, Fx)) : (cx(k) > 0 ? add2(cF, Fx) : sub2f(cF, Fx)); f1 = false; }
+            if (cy(k)) { cF = f1 ? (cy(k) > 0 ? Fy : sub2f(cF, Fy)) : (cy(k) > 0 ? add2(cF, Fy) : sub2f(cF, Fy)); f1 = false; }
+            if (cz(k)) { cF = f1 ? (cz(k) > 0 ? Fz : sub2f(cF, Fz)) : (cz(k) > 0 ? add2(cF, Fz) : sub2f(cF, Fz)); f1 = false; }
             const float2 sev = mul2(sp2(gus * S), fma2(mul2(sp2(9.0f), cu), cF, make_float2(-uF3.x, -uF3.y)));
             const float2 sod = mul2(sp2(3.0f * gus * S), cF);
             p0 = add2(p0, add2(sev, sod));
-            p1 = add2(p1, sub2(sev, sod));
+            p1 = add2(p1, sub2f(sev, sod));
         }
         e[k] = p0;
         e[k + 1] = p1;

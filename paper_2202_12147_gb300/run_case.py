@@ -19,6 +19,9 @@ def _box(name):
     from workloads import adjoint_single_96, pair_side_256cube, single_swimmer_48, swimmer_pair
     if name == "single_48":
         return single_swimmer_48()
+    if name.startswith("ensemble_"):  # one box of the 64-box ensemble, by index
+        from workloads import ensemble_boxes
+        return ensemble_boxes(64, seed=0)[int(name.split("_")[1])]
     if name == "pair_side_256cube":
         return pair_side_256cube()
     if name == "single_96":
@@ -41,6 +44,7 @@ def main(argv=None):
                          "gradient of swimmer 0's x displacement w.r.t. its drive")
     ap.add_argument("--K", type=int, default=100, help="adjoint checkpoint interval")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"], help="adjoint fluid precision")
+    ap.add_argument("--batch", type=int, default=0, help="advance this many copies of the box as one batch")
     a = ap.parse_args(argv)
     from paper_2202_12147_gb300 import Batch, Simulation
     from workloads import assemble, ensemble_boxes
@@ -71,6 +75,20 @@ def main(argv=None):
         print(f"{box.name}: displacement {d[0].tolist()}, gradient (A1 A2 A3 phi1 phi2 phi3) {g[0].tolist()}, "
               f"timing {eng.timing()}")
         eng.close()
+        return
+    if a.batch > 0:
+        asm = assemble(box)
+        sims = [Simulation(box.dims, asm, tau=box.tau, rho0=box.rho0, storage=a.storage,
+                           deterministic=a.deterministic, forcing=box.forcing, kernel=box.kernel) for _ in range(a.batch)]
+        batch = Batch(sims)
+        if a.kernel_by_kernel:
+            batch.profile(True)
+        batch.lb_step(a.steps)
+        st = sims[0].swimmer_state(0) if sims[0].n_swimmers else None
+        print(f"batch of {a.batch} x {box.name}: step {a.steps}" + (f", box 0 swimmer 0 displacement {st['disp'].tolist()}" if st else ""))
+        batch.close()
+        for s in sims:
+            s.close()
         return
     sim = Simulation(box.dims, assemble(box), tau=box.tau, rho0=box.rho0, storage=a.storage,
                      deterministic=a.deterministic, forcing=box.forcing, kernel=box.kernel)
