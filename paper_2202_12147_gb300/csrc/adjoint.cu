@@ -346,22 +346,12 @@ struct Nbr {
     }
 };
 
-// one thread per cell: BGK collision with Guo forcing (Sec. 2.1, Eq. lbe),
-// push into the next slot, the velocity u^k, and a cleared force field of the
-// next slot.  Opposite directions i, i+1 (c_{i+1} = -c_i) share the even and
+// BGK collision with Guo forcing (Sec. 2.1, Eq. lbe) of one cell's shifted
+// deviations dv: post-collision values (before streaming) and the physical
+// velocity u.  Opposite directions i, i+1 (c_{i+1} = -c_i) share the even and
 // odd parts of the equilibrium and of the source term.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F, T *out,
-                         T *u_out, T *F_next) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= d.N) return;
-    int x, y, z;
-    cell_xyz(d, cell, x, y, z);
-    const Nbr nb(d, x, y, z);
-    T dv[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) dv[i] = pops[i * d.Npad + cell];
-    const T Fx = F[cell] + (T)gx, Fy = F[d.Npad + cell] + (T)gy, Fz = F[2 * d.Npad + cell] + (T)gz;
+__device__ __forceinline__ void fwd_cell(const T (&dv)[Q], T Fx, T Fy, T Fz, T omega, T rho0, T (&post)[Q], T (&u)[3]) {
     T drho, m[3];
     moments(dv, drho, m);
     const T rho = rho0 + drho;
@@ -370,7 +360,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd_lb(Dims d, 
     const T src = (T)1 - (T)0.5 * omega, keep = (T)1 - omega;
     {
         const T w = (T)wgt_d(0);
-        out[cell] = keep * dv[0] + omega * w * (drho - rho * (T)1.5 * uu) + src * w * ((T)-3 * uF);
+        post[0] = keep * dv[0] + omega * w * (drho - rho * (T)1.5 * uu) + src * w * ((T)-3 * uF);
     }
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
@@ -380,15 +370,73 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd_lb(Dims d, 
         const T eq_e = w * (drho + rho * ((T)4.5 * cu * cu - (T)1.5 * uu)), eq_o = w * rho * (T)3 * cu;
         const T S_e = w * ((T)9 * cu * cF - (T)3 * uF), S_o = w * (T)3 * cF;
         const T e = omega * eq_e + src * S_e, o = omega * eq_o + src * S_o;
-        out[i * d.Npad + cell + nb.off(i)] = keep * dv[i] + e + o;
-        out[(i + 1) * d.Npad + cell + nb.off(i + 1)] = keep * dv[i + 1] + e - o;
+        post[i] = keep * dv[i] + e + o;
+        post[i + 1] = keep * dv[i + 1] + e - o;
     }
-    u_out[cell] = ux;
-    u_out[d.Npad + cell] = uy;
-    u_out[2 * d.Npad + cell] = uz;
-    F_next[cell] = 0;
-    F_next[d.Npad + cell] = 0;
-    F_next[2 * d.Npad + cell] = 0;
+    u[0] = ux;
+    u[1] = uy;
+    u[2] = uz;
+}
+
+// one thread per cell: collide, push into the next slot, the velocity u^k, and
+// a cleared force field of the next slot
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy,
+                                                                       double gz, const T *pops, const T *F, T *out,
+                                                                       T *u_out, T *F_next) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= d.N) return;
+    int x, y, z;
+    cell_xyz(d, cell, x, y, z);
+    const Nbr nb(d, x, y, z);
+    T dv[Q], post[Q], u[3];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dv[i] = pops[i * d.Npad + cell];
+    fwd_cell(dv, F[cell] + (T)gx, F[d.Npad + cell] + (T)gy, F[2 * d.Npad + cell] + (T)gz, omega, rho0, post, u);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i * d.Npad + cell + nb.off(i)] = post[i];
+    for (int a = 0; a < 3; ++a) {
+        u_out[a * d.Npad + cell] = u[a];
+        F_next[a * d.Npad + cell] = 0;
+    }
+}
+
+// FP32, rows of even length: two adjacent cells per thread, with 8-byte
+// vector loads and stores wherever both cells' values stay adjacent (every
+// load, and the stores of directions with c_x = 0)
+__global__ void __launch_bounds__(128, 4) k_fwd_lb2(Dims d, float omega, float rho0, double gx, double gy, double gz,
+                                                    const float *pops, const float *F, float *out, float *u_out,
+                                                    float *F_next) {
+    const int cell = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (cell >= d.N) return;
+    int x, y, z;
+    cell_xyz(d, cell, x, y, z);
+    const Nbr n0(d, x, y, z), n1(d, x + 1, y, z);
+    float dv0[Q], dv1[Q], p0[Q], p1[Q], u0[3], u1[3];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
+        dv0[i] = v.x;
+        dv1[i] = v.y;
+    }
+    float2 Fv[3];
+    for (int a = 0; a < 3; ++a) Fv[a] = *reinterpret_cast<const float2 *>(F + a * d.Npad + cell);
+    fwd_cell(dv0, Fv[0].x + (float)gx, Fv[1].x + (float)gy, Fv[2].x + (float)gz, omega, rho0, p0, u0);
+    fwd_cell(dv1, Fv[0].y + (float)gx, Fv[1].y + (float)gy, Fv[2].y + (float)gz, omega, rho0, p1, u1);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float *pl = out + i * d.Npad;
+        if (cx(i) == 0) {
+            *reinterpret_cast<float2 *>(pl + cell + n0.off(i)) = make_float2(p0[i], p1[i]);
+        } else {
+            pl[cell + n0.off(i)] = p0[i];
+            pl[cell + 1 + n1.off(i)] = p1[i];
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        *reinterpret_cast<float2 *>(u_out + a * d.Npad + cell) = make_float2(u0[a], u1[a]);
+        *reinterpret_cast<float2 *>(F_next + a * d.Npad + cell) = make_float2(0.f, 0.f);
+    }
 }
 
 // one warp per node: r_j^{k+1} = r_j^k + sum_x u(x) Delta(x - r_j)
@@ -472,39 +520,22 @@ __global__ void k_adj_interp(Dims d, int M, const double *r, const T *u, double 
         for (int a = 0; a < 3; ++a) lam_r[3 * j + a] += G[a];
 }
 
-// One thread per cell: transpose of stream + collide (+ the velocity output).
-// Pulled adjoints lam*_i(x) = lam_i^{n+1}(x + c_i); with
-// s0 = sum w l, s1 = sum w l c, s2 = sum w l c c (over opposite pairs: even
-// parts l_i + l_{i+1} feed s0 and s2, odd parts l_i - l_{i+1} feed s1):
+// Transpose of one cell's collision (+ the velocity output).  With the pulled
+// adjoints lam*_i and s0 = sum w l, s1 = sum w l c, s2 = sum w l c c (over
+// opposite pairs: even parts l_i + l_{i+1} feed s0 and s2, odd parts
+// l_i - l_{i+1} feed s1):
 //   P = s0 (1 - 3/2 u.u) + 3 s1.u + 9/2 u.s2.u,  Q = 3 s1 - 3 s0 u + 9 s2 u,
 //   a_u = omega rho Q + (1 - omega/2)(9 s2 F - 3 s0 F) + lam_u,
 //   lam_F = (1 - omega/2) Q + a_u / (2 rho),  lam_m = a_u / rho,
 //   lam_rho = omega P - a_u.u / rho,
 //   lam_i = (1 - omega) lam*_i + lam_rho + c_i . lam_m.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_adj_lb(Dims d, T omega, T rho0, double gx, double gy, double gz, const T *pops, const T *F,
-                         const T *lam_next, T *lam_u, T *lam_cur, T *lam_F) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= d.N) return;
-    int x, y, z;
-    cell_xyz(d, cell, x, y, z);
-    const Nbr nb(d, x, y, z);
-    T ls[Q], dv[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        ls[i] = lam_next[i * d.Npad + cell + nb.off(i)];
-        dv[i] = pops[i * d.Npad + cell];
-    }
-    const T Fx = F[cell] + (T)gx, Fy = F[d.Npad + cell] + (T)gy, Fz = F[2 * d.Npad + cell] + (T)gz;
+__device__ __forceinline__ void adj_cell(const T (&ls)[Q], const T (&dv)[Q], const T (&Fv)[3], const T (&lu)[3], T omega,
+                                         T rho0, T (&lam)[Q], T (&lF)[3]) {
     T drho, m[3];
     moments(dv, drho, m);
     const T rho = rho0 + drho, ir = (T)1 / rho;
-    const T u[3] = {(m[0] + (T)0.5 * Fx) * ir, (m[1] + (T)0.5 * Fy) * ir, (m[2] + (T)0.5 * Fz) * ir};
-    const T Fv[3] = {Fx, Fy, Fz};
-    const T lu[3] = {lam_u[cell], lam_u[d.Npad + cell], lam_u[2 * d.Npad + cell]};
-    lam_u[cell] = 0;
-    lam_u[d.Npad + cell] = 0;
-    lam_u[2 * d.Npad + cell] = 0;
+    const T u[3] = {(m[0] + (T)0.5 * Fv[0]) * ir, (m[1] + (T)0.5 * Fv[1]) * ir, (m[2] + (T)0.5 * Fv[2]) * ir};
     T s0 = (T)wgt_d(0) * ls[0], s1[3] = {0, 0, 0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
@@ -529,7 +560,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_adj_lb(Dims d, 
         Pq += (T)3 * s1[a] * u[a] + (T)4.5 * u[a] * s2u[a];
     }
     const T src = (T)1 - (T)0.5 * omega, keep = (T)1 - omega;
-    T lm[3], lF[3], au_u = 0;
+    T lm[3], au_u = 0;
     for (int a = 0; a < 3; ++a) {
         const T Qa = (T)3 * s1[a] - (T)3 * s0 * u[a] + (T)9 * s2u[a];
         const T au = omega * rho * Qa + src * ((T)9 * s2F[a] - (T)3 * s0 * Fv[a]) + lu[a];
@@ -538,16 +569,93 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_adj_lb(Dims d, 
         au_u += au * u[a];
     }
     const T lrho = omega * Pq - au_u * ir;
-    lam_cur[cell] = keep * ls[0] + lrho;
+    lam[0] = keep * ls[0] + lrho;
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
         const T cm = (T)cx(i) * lm[0] + (T)cy(i) * lm[1] + (T)cz(i) * lm[2];
-        lam_cur[i * d.Npad + cell] = keep * ls[i] + lrho + cm;
-        lam_cur[(i + 1) * d.Npad + cell] = keep * ls[i + 1] + lrho - cm;
+        lam[i] = keep * ls[i] + lrho + cm;
+        lam[i + 1] = keep * ls[i + 1] + lrho - cm;
     }
-    lam_F[cell] = lF[0];
-    lam_F[d.Npad + cell] = lF[1];
-    lam_F[2 * d.Npad + cell] = lF[2];
+}
+
+// one thread per cell: pull lam*_i(x) = lam_i^{n+1}(x + c_i) (the transpose
+// of the push), transpose the collision, clear lam_u
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_adj_lb(Dims d, T omega, T rho0, double gx, double gy,
+                                                                       double gz, const T *pops, const T *F,
+                                                                       const T *lam_next, T *lam_u, T *lam_cur,
+                                                                       T *lam_F) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= d.N) return;
+    int x, y, z;
+    cell_xyz(d, cell, x, y, z);
+    const Nbr nb(d, x, y, z);
+    T ls[Q], dv[Q], lam[Q], lF[3];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        ls[i] = lam_next[i * d.Npad + cell + nb.off(i)];
+        dv[i] = pops[i * d.Npad + cell];
+    }
+    const T Fv[3] = {F[cell] + (T)gx, F[d.Npad + cell] + (T)gy, F[2 * d.Npad + cell] + (T)gz};
+    const T lu[3] = {lam_u[cell], lam_u[d.Npad + cell], lam_u[2 * d.Npad + cell]};
+    adj_cell(ls, dv, Fv, lu, omega, rho0, lam, lF);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lam_cur[i * d.Npad + cell] = lam[i];
+    for (int a = 0; a < 3; ++a) {
+        lam_F[a * d.Npad + cell] = lF[a];
+        lam_u[a * d.Npad + cell] = 0;
+    }
+}
+
+// FP32, rows of even length: two adjacent cells per thread with 8-byte
+// vector loads and stores wherever both cells' values stay adjacent (every
+// access except the pulled adjoints of directions with c_x != 0)
+__global__ void __launch_bounds__(128, 4) k_adj_lb2(Dims d, float omega, float rho0, double gx, double gy, double gz,
+                                                    const float *pops, const float *F, const float *lam_next,
+                                                    float *lam_u, float *lam_cur, float *lam_F) {
+    const int cell = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (cell >= d.N) return;
+    int x, y, z;
+    cell_xyz(d, cell, x, y, z);
+    const Nbr n0(d, x, y, z), n1(d, x + 1, y, z);
+    float ls0[Q], ls1[Q], dv0[Q], dv1[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float *pl = lam_next + i * d.Npad;
+        if (cx(i) == 0) {
+            const float2 v = *reinterpret_cast<const float2 *>(pl + cell + n0.off(i));
+            ls0[i] = v.x;
+            ls1[i] = v.y;
+        } else {
+            ls0[i] = pl[cell + n0.off(i)];
+            ls1[i] = pl[cell + 1 + n1.off(i)];
+        }
+        const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
+        dv0[i] = v.x;
+        dv1[i] = v.y;
+    }
+    float2 Fv[3], lu[3];
+    for (int a = 0; a < 3; ++a) {
+        Fv[a] = *reinterpret_cast<const float2 *>(F + a * d.Npad + cell);
+        lu[a] = *reinterpret_cast<const float2 *>(lam_u + a * d.Npad + cell);
+    }
+    float lam0[Q], lam1[Q], lF0[3], lF1[3];
+    {
+        const float F0[3] = {Fv[0].x + (float)gx, Fv[1].x + (float)gy, Fv[2].x + (float)gz};
+        const float l0[3] = {lu[0].x, lu[1].x, lu[2].x};
+        adj_cell(ls0, dv0, F0, l0, omega, rho0, lam0, lF0);
+    }
+    {
+        const float F1[3] = {Fv[0].y + (float)gx, Fv[1].y + (float)gy, Fv[2].y + (float)gz};
+        const float l1[3] = {lu[0].y, lu[1].y, lu[2].y};
+        adj_cell(ls1, dv1, F1, l1, omega, rho0, lam1, lF1);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) *reinterpret_cast<float2 *>(lam_cur + i * d.Npad + cell) = make_float2(lam0[i], lam1[i]);
+    for (int a = 0; a < 3; ++a) {
+        *reinterpret_cast<float2 *>(lam_F + a * d.Npad + cell) = make_float2(lF0[a], lF1[a]);
+        *reinterpret_cast<float2 *>(lam_u + a * d.Npad + cell) = make_float2(0.f, 0.f);
+    }
 }
 
 // one warp per node: transpose of spreading
@@ -833,9 +941,16 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
         k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F);
         a->launches += 3;
     }
-    const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-    k_fwd_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                     (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F));
+    if (sizeof(T) == 4 && P.d.nx % 2 == 0) {
+        const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
+        k_fwd_lb2<<<nb, 128, 0, st>>>(P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                      (const float *)(sl + P.s_pops), (const float *)F, (float *)(sn + P.s_pops),
+                                      (float *)u, (float *)(sn + P.s_F));
+    } else {
+        const unsigned nb = (unsigned)((P.d.N + 255) / 256);
+        k_fwd_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                         (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F));
+    }
     a->launches += 1;
     if (M > 0) {
         k_fwd_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
@@ -858,9 +973,16 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
         k_adj_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, lam_r, lam_u);
         a->launches += 1;
     }
-    const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-    k_adj_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                     (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F);
+    if (sizeof(T) == 4 && P.d.nx % 2 == 0) {
+        const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
+        k_adj_lb2<<<nb, 128, 0, st>>>(P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                      (const float *)(sl + P.s_pops), (const float *)F, (const float *)lam_next,
+                                      (float *)lam_u, (float *)lam_cur, (float *)lam_F);
+    } else {
+        const unsigned nb = (unsigned)((P.d.N + 255) / 256);
+        k_adj_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                         (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F);
+    }
     a->launches += 1;
     if (M > 0) {
         k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
