@@ -57,6 +57,9 @@ def _args():
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                     help="skip the adjoint (drive-gradient) line")
     ap.add_argument("--adjoint-precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--configs", action="store_true",
+                    help="also measure the single-swimmer 48^3 and the 256^3 precision configurations "
+                         "(throughput, error against the oracle) and the oracle on one core")
     return ap.parse_args()
 
 
@@ -290,6 +293,85 @@ def _run_adjoint(a, barrier, stream):
             "workspace_GB": ws_bytes / 1e9}
 
 
+def _f_dev(f, w, rho0=1.0):
+    return f - w[:, None] * rho0
+
+
+def _run_configs(a, stream):
+    """The other configurations of the problem statement on one GPU, each with
+    its error against the FP64 oracle: one swimmer in 48^3 (radius 4,
+    subdivision 2, period 500) for its full 500 steps, and two side-by-side
+    swimmers in 256^3 (gap 3 radii) for 16 steps (the oracle's share of the
+    budget); throughput of both in FP32 / FP16 / BF16 storage (64 timed
+    steps for 256^3); and the oracle's throughput on one core and on all."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2202_12147_gb300 import Simulation, lattice
+    from workloads import assemble, pair_side_256cube, single_swimmer_48
+    cg, wg = lattice()
+    co, wo = oracle.lattice()
+    perm = [next(k for k in range(19) if (co[k] == cg[i]).all()) for i in range(19)]
+
+    def u_of(f_gpu):
+        fo = np.empty((f_gpu.shape[1], 19))
+        fo[:, perm] = f_gpu.T
+        return oracle.macros(fo)[1]
+
+    def rel(x, y):
+        return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+    out = {}
+    for name, box, n_err, n_time in (("single_swimmer_48", single_swimmer_48(), 500, 500),
+                                     ("pair_side_256cube", pair_side_256cube(), 16, 64)):
+        asm = assemble(box)
+        osim = oracle.OracleSim(box, asm)
+        x0 = osim.swimmer_centres()
+        osim.step(n_err)
+        u_ref = oracle.macros(osim.f)[1]
+        d_ref = osim.swimmer_centres() - x0
+        res = {"cells": box.n_cells, "error_steps": n_err, "timed_steps": n_time}
+        for st in ("f32", "f16", "bf16"):
+            sim = Simulation(box.dims, asm, tau=box.tau, rho0=box.rho0, storage=st)
+            sim.lb_step(n_err)
+            u = u_of(sim.get_populations())
+            disp = np.array([sim.swimmer_state(k)["disp"] for k in range(sim.n_swimmers)])
+            sim.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.lb_step(n_time)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            lb_ms, lb_n = sim.profile_read()
+            marked = sim.marked_cells()
+            sim.sync()
+            sim.close()
+            esize = 4 if st == "f32" else 2
+            bw = (box.n_cells - marked) * 19 * 2 * esize / (lb_ms / lb_n / 1e3) / 1e9
+            res[st] = {"MLUPS": box.n_cells * n_time / (ms / 1e3) / 1e6, "velocity_rel_l2": rel(u, u_ref),
+                       "displacement_rel_err": float(np.abs(disp[:, 0] - d_ref[:, 0]).max() / np.abs(d_ref[:, 0]).max()),
+                       "k_lb_main_GBs": bw, "timing": "kernel by kernel (two streams), CUDA events"}
+        out[name] = res
+    # the oracle on one core and on all (bounded samples of the 48^3 workload)
+    box = single_swimmer_48()
+    all_cores = oracle.set_threads(0)
+    for n_thr in (1, all_cores):
+        oracle.set_threads(n_thr)
+        sim = oracle.OracleSim(box)
+        sim.step(1)
+        t0 = time.perf_counter()
+        n = 0
+        while n < 2 or time.perf_counter() - t0 < 3.0:
+            sim.step(1)
+            n += 1
+        dt = time.perf_counter() - t0
+        out[f"oracle_{n_thr}_cores"] = {"MLUPS": box.n_cells * n / dt / 1e6, "steps": n, "workload": "single_swimmer_48"}
+    oracle.set_threads(all_cores)
+    return out
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -439,6 +521,10 @@ def run_ours(a):
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cpu = _oracle_sample(a.cpu_seconds)
 
+    configs = None
+    if a.configs and rank == 0 and ws == 1:
+        configs = _run_configs(a, torch.cuda.current_stream())
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
@@ -458,6 +544,8 @@ def run_ours(a):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "variants": variants, "ensemble": ensemble, "adjoint": adjoint,
         }
+        if configs is not None:
+            line["configs"] = configs
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

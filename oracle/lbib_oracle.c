@@ -31,6 +31,7 @@
  * giving exact derivatives of the discrete step by the complex-step method.
  */
 #include <complex.h>
+#include <omp.h>
 #include <stddef.h>
 #include <string.h>
 #include <tgmath.h>
@@ -112,6 +113,14 @@ void orc_macros(long n_cells, const double *f, double *rho, double *u)
         rho[cell] = r;
         for (int a = 0; a < 3; ++a) u[3 * cell + a] = j[a] / r;
     }
+}
+
+/* Threads of the OpenMP loops (for single-core timings); returns the count
+ * now in effect. */
+int orc_set_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
 }
 
 /* The 1-D delta kernel at one point (real and complex argument). */

@@ -66,6 +66,8 @@ def lib():
             L.orc_membrane_energy.argtypes = [i, d, d, i, P, P, P]
             L.orc_membrane_energy.restype = d
             L.orc_membrane_forces.argtypes = [i, d, d, i, P, P, P, P]
+            L.orc_set_threads.argtypes = [i]
+            L.orc_set_threads.restype = i
             # complex-step twins (double complex arguments as complex128 arrays)
             L.orc_lb_step_cs.argtypes = [i, i, i, d, i, P, P, P, P, P, P]
             L.orc_phi_cs.argtypes = [i, P, P]
@@ -100,6 +102,11 @@ def _is_c(*arrays):
 
 def _fn(name, cplx):
     return getattr(lib(), name + "_cs" if cplx else name)
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's loops (n <= 0: query); returns the count in effect."""
+    return lib().orc_set_threads(int(n))
 
 
 def lattice():
