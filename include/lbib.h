@@ -309,6 +309,26 @@ int lb_batch_autotune(lbib_batch *b, int steps_per_trial, lbib_batch_tuning *rep
 /* Release the batch (not the contexts).  Synchronises. */
 int lb_batch_destroy(lbib_batch *b);
 
+/* ---- checkpoint / resume ----------------------------------------------
+ * A checkpoint is a versioned binary blob: a header (format version, box,
+ * storage, forcing and kernel, determinism flag, structure counts, buffer
+ * sizes, step, a 64-bit checksum of the payload) followed by the context's
+ * three device buffers as they are (populations in their stored format and
+ * AA parity, force/velocity fields and tile stamps, node positions, bead
+ * centres, mesh tables, control block, swimmer accumulators).  Restoring it
+ * into a context over the same box and structure continues the run exactly:
+ * with deterministic spreading, bitwise as if it had never stopped. */
+/* Bytes of a checkpoint blob of this context. */
+int lb_checkpoint_size(lbib_ctx *ctx, size_t *bytes);
+/* Write the blob into HOST memory of at least lb_checkpoint_size bytes.
+ * Synchronous; reports a latched device error instead of saving. */
+int lb_checkpoint(lbib_ctx *ctx, void *host_buf, size_t bytes);
+/* Load a blob written by lb_checkpoint (HOST memory).  LBIB_EINVAL for a
+ * blob of another format, box, scheme or structure, or with a checksum
+ * mismatch; LBIB_ESIZE if truncated; LBIB_EINVAL while batched.
+ * Synchronous. */
+int lb_restore(lbib_ctx *ctx, const void *host_buf, size_t bytes);
+
 /* Release the context (not the caller's buffers).  Synchronises.  Fails with
  * LBIB_EINVAL while the context belongs to a batch. */
 int lb_destroy(lbib_ctx *ctx);

@@ -27,6 +27,7 @@ EXPORTS = [
     "lb_destroy", "lb_adjoint_required_bytes", "lb_adjoint_create", "lb_adjoint_set_drive",
     "lb_adjoint_set_initial", "lb_adjoint_forward", "lb_adjoint_backward", "lb_adjoint_get_final",
     "lb_adjoint_timing", "lb_adjoint_destroy", "lb_batch_autotune", "swimmer_state_async",
+    "lb_checkpoint_size", "lb_checkpoint", "lb_restore",
 ]
 
 
@@ -114,6 +115,9 @@ def load(build_if_missing: bool = True):
         L.ib_interpolate.argtypes = [P, P]
         L.swimmer_state.argtypes = [P, I, ctypes.POINTER(SwimmerState)]
         L.swimmer_state_async.argtypes = [P, P]
+        L.lb_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.lb_checkpoint.argtypes = [P, P, ctypes.c_size_t]
+        L.lb_restore.argtypes = [P, P, ctypes.c_size_t]
         L.lb_sync.argtypes = [P]
         L.lb_get_macros.argtypes = [P, P, P]
         for n in ("lb_get_populations", "lb_set_populations", "lb_get_nodes", "lb_set_nodes", "ib_get_node_forces",

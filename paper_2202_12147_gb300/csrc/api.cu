@@ -211,6 +211,7 @@ struct lbib_ctx {
     int n_nodes = 0, n_swimmers = 0;
     int slab_grid = 0;  // > 0: main fluid update by the TMA-staged slab kernel with this grid
     lbib_batch *batch = nullptr;   // set while the context belongs to a batch
+    void *buf[LBIB_NBUF] = {nullptr, nullptr, nullptr};  // the caller buffers
 };
 
 struct lbib_batch {
@@ -493,6 +494,9 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.n_swimmers = S;
     d.deterministic = p->deterministic ? 1 : 0;
     char *F = (char *)b->fields, *A = (char *)b->aux;
+    c->buf[0] = b->pops;
+    c->buf[1] = b->fields;
+    c->buf[2] = b->aux;
     d.pops = b->pops;
     d.F = p->deterministic ? nullptr : (float4 *)(F + L.oF);
     d.Fdet = p->deterministic ? (unsigned long long *)(F + L.oFdet) : nullptr;
@@ -838,6 +842,129 @@ int lb_marked_cells(lbib_ctx *c, long long *cells) {
     *cells = n < c->L.N ? n : c->L.N;
     return LBIB_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- checkpoints
+// Blob: header, then the three caller buffers as they are on the device (the
+// populations in their stored format and AA parity; force, velocity and tile
+// stamps; node positions, bead centres, mesh tables, control block and
+// swimmer accumulators).  The buffers hold no pointers, so restoring them into
+// a context over the same box and structure continues the run exactly.
+namespace {
+
+struct CkpHeader {
+    char magic[8];  // "LBIBCKP1"
+    int version;
+    int nx, ny, nz, storage, forcing, kernel, deterministic;
+    int n_nodes, n_tris, n_beads, n_swimmers;
+    unsigned long long bytes[LBIB_NBUF];
+    long long step;
+    unsigned long long checksum;  // over the buffer bytes
+};
+
+// 64-bit FNV-1a over 8-byte words (then the tail bytes)
+unsigned long long checksum64(const unsigned char *p, size_t n, unsigned long long h) {
+    const unsigned long long prime = 1099511628211ull;
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        unsigned long long w;
+        memcpy(&w, p + i, 8);
+        h = (h ^ w) * prime;
+    }
+    for (; i < n; ++i) h = (h ^ p[i]) * prime;
+    return h;
+}
+
+void fill_header(const lbib_ctx *c, CkpHeader &h) {
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "LBIBCKP1", 8);
+    h.version = 1;
+    h.nx = c->p.nx;
+    h.ny = c->p.ny;
+    h.nz = c->p.nz;
+    h.storage = c->p.storage;
+    h.forcing = c->p.forcing;
+    h.kernel = c->p.kernel;
+    h.deterministic = c->p.deterministic;
+    h.n_nodes = c->d.n_nodes;
+    h.n_tris = c->d.n_tris;
+    h.n_beads = c->d.n_beads;
+    h.n_swimmers = c->d.n_swimmers;
+    for (int k = 0; k < LBIB_NBUF; ++k) h.bytes[k] = c->L.bytes[k];
+    h.step = c->step;
+}
+
+size_t ckp_bytes(const lbib_ctx *c) {
+    size_t n = sizeof(CkpHeader);
+    for (int k = 0; k < LBIB_NBUF; ++k) n += c->L.bytes[k];
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_checkpoint_size(lbib_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return fail(LBIB_EINVAL, "NULL argument");
+    *bytes = ckp_bytes(c);
+    return LBIB_OK;
+}
+
+int lb_checkpoint(lbib_ctx *c, void *host, size_t bytes) {
+    if (!c || !host) return fail(LBIB_EINVAL, "NULL argument");
+    if (bytes < ckp_bytes(c)) return fail(LBIB_ESIZE, "checkpoint buffer smaller than lb_checkpoint_size");
+    const int st = check_device_errors(c);  // synchronises; a failed run is not saved
+    if (st != LBIB_OK) return st;
+    CkpHeader h;
+    fill_header(c, h);
+    unsigned char *dst = (unsigned char *)host + sizeof(CkpHeader);
+    unsigned long long sum = 1469598103934665603ull;
+    for (int k = 0; k < LBIB_NBUF; ++k) {
+        CU(cudaMemcpy(dst, c->buf[k], c->L.bytes[k], cudaMemcpyDeviceToHost));
+        sum = checksum64(dst, c->L.bytes[k], sum);
+        dst += c->L.bytes[k];
+    }
+    h.checksum = sum;
+    memcpy(host, &h, sizeof(h));
+    return LBIB_OK;
+}
+
+int lb_restore(lbib_ctx *c, const void *host, size_t bytes) {
+    if (!c || !host) return fail(LBIB_EINVAL, "NULL argument");
+    if (c->batch) return fail(LBIB_EINVAL, "the context belongs to a batch");
+    if (bytes < sizeof(CkpHeader)) return fail(LBIB_EINVAL, "not a checkpoint (too short)");
+    CkpHeader h, mine;
+    memcpy(&h, host, sizeof(h));
+    fill_header(c, mine);
+    if (memcmp(h.magic, "LBIBCKP1", 8) != 0 || h.version != 1) return fail(LBIB_EINVAL, "not a checkpoint of this format");
+    mine.step = h.step;
+    mine.checksum = h.checksum;
+    if (memcmp(&h, &mine, sizeof(h)) != 0)
+        return fail(LBIB_EINVAL, "checkpoint of a different box, storage, scheme or structure");
+    if (bytes < ckp_bytes(c)) return fail(LBIB_ESIZE, "checkpoint truncated");
+    const unsigned char *src = (const unsigned char *)host + sizeof(CkpHeader);
+    unsigned long long sum = 1469598103934665603ull;
+    size_t off = 0;
+    for (int k = 0; k < LBIB_NBUF; ++k) {
+        sum = checksum64(src + off, c->L.bytes[k], sum);
+        off += c->L.bytes[k];
+    }
+    if (sum != h.checksum) return fail(LBIB_EINVAL, "checkpoint checksum mismatch (corrupted)");
+    CU(cudaStreamSynchronize(c->user));
+    if (c->ib) CU(cudaStreamSynchronize(c->ib));
+    off = 0;
+    for (int k = 0; k < LBIB_NBUF; ++k) {
+        CU(cudaMemcpy(c->buf[k], src + off, c->L.bytes[k], cudaMemcpyHostToDevice));
+        off += c->L.bytes[k];
+    }
+    c->step = h.step;
+    return LBIB_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 int lb_destroy(lbib_ctx *c) {
     if (!c) return LBIB_OK;

@@ -136,6 +136,18 @@ class Simulation:
         check(self.L.ib_interpolate(self.ctx, ctypes.c_void_p(out.data_ptr())))
         return out
 
+    def checkpoint(self):
+        """The context's state as a versioned, checksummed blob (numpy uint8)."""
+        n = ctypes.c_size_t()
+        check(self.L.lb_checkpoint_size(self.ctx, ctypes.byref(n)))
+        blob = np.empty(n.value, dtype=np.uint8)
+        check(self.L.lb_checkpoint(self.ctx, blob.ctypes.data_as(ctypes.c_void_p), blob.nbytes))
+        return blob
+
+    def restore(self, blob):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        check(self.L.lb_restore(self.ctx, blob.ctypes.data_as(ctypes.c_void_p), blob.nbytes))
+
     def swimmer_state_async(self, out):
         """Queue every swimmer's observables into `out` (host memory of at least
         n_swimmers records, e.g. a pinned uint8 tensor, or an array of

@@ -117,3 +117,37 @@ def test_autotuned_batch_against_oracle(perm):
     batch.close()
     for s in sims:
         s.close()
+
+
+def test_checkpoint_resume_is_bitwise(perm, tmp_path):
+    """A run checkpointed at step 13 and resumed in a fresh context (from a
+    file) continues bitwise like the uninterrupted run (deterministic
+    spreading); a corrupted or mismatched blob is refused."""
+    from paper_2202_12147_gb300._lib import LbibError
+    box = _boxes()[1]
+    asm = assemble(box)
+    a = gpu_sim(box, asm, deterministic=True)
+    a.lb_step(13)
+    blob = a.checkpoint()
+    path = tmp_path / "state.lbib"
+    blob.tofile(path)
+    a.lb_step(21)
+    ref = (a.get_populations(), a.get_nodes(), a.swimmer_state(1))
+    a.close()
+    b = gpu_sim(box, asm, deterministic=True)
+    b.restore(np.fromfile(path, dtype=np.uint8))
+    assert b.swimmer_state(0)["step"] == 13
+    b.lb_step(21)
+    assert np.array_equal(b.get_populations(), ref[0])
+    assert np.array_equal(b.get_nodes(), ref[1])
+    st = b.swimmer_state(1)
+    assert st["step"] == 34 and np.array_equal(st["disp"], ref[2]["disp"])
+    bad = blob.copy()
+    bad[len(bad) // 2] ^= 1
+    with pytest.raises(LbibError):
+        b.restore(bad)
+    other = gpu_sim(_boxes()[0], assemble(_boxes()[0]), deterministic=True)
+    with pytest.raises(LbibError):
+        other.restore(blob)
+    other.close()
+    b.close()
