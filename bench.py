@@ -74,6 +74,25 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(x, ws, device=None):
+    """The largest x over the ranks of the default process group (x itself on
+    one rank): every timing is the slowest rank's."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = device or ("cuda" if torch.cuda.is_available() else "cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(ws, cells_per_step, steps, ms):
+    """Whole-job throughput: each of the ws ranks advances cells_per_step cells
+    per step (replicas of the same boxes), all done in ms milliseconds."""
+    return ws * cells_per_step * steps / (ms / 1e3) / 1e6
+
+
 def _peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -238,11 +257,12 @@ def _run_ensemble(a, barrier, stream, ws):
     batch.close()
     for s in sims:
         s.close()
+    seq_ms, rr_ms, bat_ms = (max_over_ranks(v, ws) for v in (seq_ms, rr_ms, bat_ms))
     return {"boxes": len(boxes), "cells": cells, "steps": K, "unit": "MLUPS",
-            "batched": ws * cells * K / (bat_ms / 1e3) / 1e6, "sequential": ws * cells * K / (seq_ms / 1e3) / 1e6,
+            "batched": job_mlups(ws, cells, K, bat_ms), "sequential": job_mlups(ws, cells, K, seq_ms),
             "batched_ms_per_step": bat_ms / K, "sequential_ms_per_step": seq_ms / K, "speedup": seq_ms / bat_ms,
             "sequential_means": "each box advanced on its own (its captured 16-step graphs), one box after another",
-            "round_robin": ws * cells * K / (rr_ms / 1e3) / 1e6, "speedup_vs_round_robin": rr_ms / bat_ms,
+            "round_robin": job_mlups(ws, cells, K, rr_ms), "speedup_vs_round_robin": rr_ms / bat_ms,
             "round_robin_means": "every step, each box launched on its own (one coupled step per call), box after box",
             "autotune": tuning}
 
@@ -418,12 +438,9 @@ def run_ours(a):
         s.profile(False)
     for s in sims:
         s.sync()  # latched device errors surface here
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws)
     cells_per_step = N * len(sims)
-    value = ws * cells_per_step * a.steps / (ms / 1e3) / 1e6
+    value = job_mlups(ws, cells_per_step, a.steps, ms)
     esize = {"f32": 4, "f16": 2, "bf16": 2}[a.storage]
     # the timed kernel updates every cell outside the tiles the node stencils mark
     marked = statistics.mean(s.marked_cells() for s in sims)
@@ -452,7 +469,7 @@ def run_ours(a):
                 s.lb_step(a.steps)
             f1.record(stream)
             barrier()
-            vms = f0.elapsed_time(f1)
+            vms = max_over_ranks(f0.elapsed_time(f1), ws)
             t_lb, n_lb = 0.0, 0
             for s in vs:
                 t, n = s.profile_read()
@@ -462,7 +479,7 @@ def run_ours(a):
             vmarked = statistics.mean(s.marked_cells() for s in vs)
             vbytes = (N - vmarked) * 19 * 2 * 2
             vach = vbytes / (t_lb / n_lb / 1e3) / 1e9
-            variants[st] = {"value": ws * cells_per_step * a.steps / (vms / 1e3) / 1e6, "unit": "MLUPS",
+            variants[st] = {"value": job_mlups(ws, cells_per_step, a.steps, vms), "unit": "MLUPS",
                             "ms_per_step": vms / a.steps, "speedup_vs_f32": ms / vms,
                             "roofline": {"achieved": vach, "peak": peak, "frac": vach / peak,
                                          "avg_launch_us": t_lb / n_lb * 1e3, "bytes_per_launch": vbytes}}
@@ -508,11 +525,8 @@ def run_ours(a):
             s.sync()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ws * cells_per_step * a.steps / dt / 1e6, "unit": "MLUPS",
+        dt = max_over_ranks(dt, ws)
+        e2e = {"value": job_mlups(ws, cells_per_step, a.steps, dt * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": int(h2d / a.steps), "d2h_bytes_per_step": int(d2h / a.steps)}
         for s in sims2:
             s.close()
