@@ -225,9 +225,9 @@ int lb_profile_read(lbib_ctx *ctx, double *total_ms, long long *launches);
 
 /* Deterministic force spreading that allocates nothing.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
- * device memory themselves -- code running while a CUDA graph is being
- * captured in global mode, inside a framework whose caching allocator owns
- * all device memory, or in a loop that must not grow its memory after
+ * device memory themselves -- code inside a framework whose caching
+ * allocator owns all device memory (a cudaMalloc there competes with it and
+ * can fail), or a loop that must keep its memory footprint fixed after
  * start-up.  It needs no context and no caller scratch.
  *
  * Computes F(x) = sum_j f_j Delta(x - r_j) on a periodic nx x ny x nz box

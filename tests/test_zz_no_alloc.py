@@ -1,8 +1,8 @@
 """The allocation-free spreading entry point.
 
-Some callers cannot allocate device memory (code running while a CUDA graph
-is captured in global mode, code inside a framework whose caching allocator
-owns all device memory, loops that must not grow memory after start-up).
+Some callers cannot allocate device memory: code inside a framework whose
+caching allocator owns all device memory, or loops that must keep their
+memory footprint fixed after start-up.
 ib_spread_fixed_noalloc serves them with a scratch grid the library owns.
 This file is collected last on purpose: it checks the new entry point
 against the context path's deterministic spreading, on two calls in a row
