@@ -212,3 +212,44 @@ def test_swimmer_state_async_matches_sync(gpu_lib):
     first = _lib.SwimmerState.from_buffer_copy(bytes(ring[0, :rec].numpy()))
     assert first.step == 5
     s.close()
+
+
+def test_coupled_paper_scheme_shan_chen_linear2(perm):
+    """The paper's own choices (Sec. 2.1 Eq. sc velocity shift, Sec. 2.3
+    two-point kernel) in a coupled swimmer run against the oracle."""
+    from workloads import BoxSpec, SwimmerSpec
+    sw = SwimmerSpec(center=(20.0, 14.0, 12.0), radius=3.0, subdiv=2, spacing=9.0, period=60.0).with_drive(
+        2e-3, 2e-3, 1.0)
+    box = BoxSpec(dims=(40, 28, 24), swimmers=(sw,), forcing="shan_chen", kernel="linear2")
+    asm = assemble(box)
+    sim = gpu_sim(box, asm)
+    sim.lb_step(3)
+    sim.lb_step(40)
+    osim = oracle.OracleSim(box, asm).step(43)
+    _, ug = oracle.macros(gpu_f_to_oracle(sim.get_populations(), perm))
+    _, uo = oracle.macros(osim.f)
+    assert rel_l2(ug, uo) < 1e-5
+    assert np.abs(sim.get_nodes() - osim.r).max() < 1e-6
+    np.testing.assert_allclose(sim.swimmer_state(0)["x_cm"], osim.swimmer_centres()[0], atol=1e-6)
+    sim.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 2e-3)])
+def test_benchmark_box_full_size(perm, storage, tol):
+    """One box of the benchmark at its full size (256 x 128 x 128, two
+    side-by-side swimmers of 642-node beads, gap 3 radii), advanced the way
+    bench.py does (two streams, 16-step graph replays), against the oracle's
+    full field after 32 steps."""
+    from workloads import swimmer_pair
+    box = swimmer_pair("side", 3)
+    asm = assemble(box)
+    sim = gpu_sim(box, asm, storage=storage)
+    sim.lb_step(32)
+    osim = oracle.OracleSim(box, asm).step(32)
+    _, ug = oracle.macros(gpu_f_to_oracle(sim.get_populations(), perm))
+    _, uo = oracle.macros(osim.f)
+    err = rel_l2(ug, uo)
+    print(f"{storage}: velocity rel. L2 after 32 steps {err:.2e}")
+    assert err < tol
+    assert np.abs(sim.get_nodes() - osim.r).max() < (1e-6 if storage == "f32" else 1e-5)
+    sim.close()
