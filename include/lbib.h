@@ -125,8 +125,10 @@ typedef struct {
     void *aux;    /* node positions, node forces/velocities, mesh tables, control block */
 } lbib_buffers;
 
-/* Observables of one swimmer (Sec. 3, Eq. vel_swim, Sec. 2.2 Reynolds
- * numbers need the bead velocities).  All FP64. */
+/* Observables of one swimmer (Sec. 3, Eq. vel_swim; the Reynolds numbers of
+ * Sec. 3 with nu = (tau - 1/2)/3 and a the bead's rest radius).  All FP64.
+ * Period boundaries are the steps where floor(t / period) increases; x_cm is
+ * recorded there on the device. */
 typedef struct {
     long long step;        /* time steps taken since lb_init */
     double R[3][3];        /* bead centres, unwrapped */
@@ -135,6 +137,12 @@ typedef struct {
     double T[3][3];        /* torque of those forces about each bead centre */
     double x_cm[3];        /* mean of the three bead centres */
     double disp[3];        /* x_cm minus x_cm at lb_init */
+    long long periods;     /* drive periods completed since lb_init */
+    double v_period[3];    /* mean swimming velocity over the last completed period,
+                              (x_cm(kT) - x_cm((k-1)T)) / T (Sec. 3, Eq. vel_swim);
+                              zero before the first period ends */
+    double re_swim;        /* |v_period| L_swim / nu, L_swim = outer bead distance + 2a */
+    double re_bead;        /* max_b |V_b| a / nu (bead velocities of the last step) */
 } lbib_swimmer_state;
 
 typedef struct lbib_ctx lbib_ctx;

@@ -62,7 +62,8 @@ class Buffers(ctypes.Structure):
 class SwimmerState(ctypes.Structure):
     _fields_ = [("step", ctypes.c_longlong), ("R", (ctypes.c_double * 3) * 3), ("V", (ctypes.c_double * 3) * 3),
                 ("F", (ctypes.c_double * 3) * 3), ("T", (ctypes.c_double * 3) * 3), ("x_cm", ctypes.c_double * 3),
-                ("disp", ctypes.c_double * 3)]
+                ("disp", ctypes.c_double * 3), ("periods", ctypes.c_longlong), ("v_period", ctypes.c_double * 3),
+                ("re_swim", ctypes.c_double), ("re_bead", ctypes.c_double)]
 
 
 TUNE_MAX_CLASSES = 32

@@ -71,7 +71,7 @@ struct Layout {
     size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0;
     // aux
     size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
-           obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0;
+           obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0, oswp = 0;
 };
 
 bool valid_params(const lb_params *p, std::string &why) {
@@ -181,6 +181,7 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     L.octl = o; o += up(sizeof(Control));
     L.osws = o; o += up((size_t)S * sizeof(lbib_swimmer_state) + 16);
     L.oxcm = o; o += up((size_t)S * 24 + 24);
+    L.oswp = o; o += up((size_t)S * 64 + 64);
     L.bytes[2] = o;
     return L;
 }
@@ -453,6 +454,7 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         d.L = w.L_spring;
         d.L2 = w.L_spring * w.L_spring;
         d.inv_period = 1.0 / w.period;
+        d.period = w.period;
         d.pad = 0;
     }
 
@@ -521,6 +523,7 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.ctl = (Control *)(A + L.octl);
     d.sw_state = (lbib_swimmer_state *)(A + L.osws);
     d.xcm0 = (double *)(A + L.oxcm);
+    d.sw_period = (double *)(A + L.oswp);
 
     auto bail = [&](int code) {
         lb_destroy(c);

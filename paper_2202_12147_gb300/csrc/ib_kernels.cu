@@ -419,6 +419,22 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
         if (s_last) {
             __threadfence();
             fold_bead_velocities(c);
+            __syncthreads();
+            // a drive period ends with this step: record x_cm (mean of the
+            // three bead centres) for the period-averaged velocity (Sec. 3)
+            for (int sw = threadIdx.x; sw < c.n_swimmers; sw += blockDim.x) {
+                const SwimDev d = c.swims[sw];
+                if (floor((double)next / d.period) > floor((double)(next - 1) / d.period)) {
+                    double *rec = c.sw_period + 8 * sw;
+                    for (int a = 0; a < 3; ++a) {
+                        const double x = (c.bead_R[4 * d.bead[0] + a] + c.bead_R[4 * d.bead[1] + a] +
+                                          c.bead_R[4 * d.bead[2] + a]) / 3.0;
+                        rec[3 + a] = rec[a];
+                        rec[a] = x;
+                    }
+                    rec[6] += 1.0;
+                }
+            }
             if (threadIdx.x == 0) {
                 c.ctl->done = 0;
                 c.ctl->gen[next & 1] = next;
@@ -493,12 +509,33 @@ __global__ void __launch_bounds__(PREP_TPB) k_swimmer_state(const DevCtx c, int 
     }
     if (threadIdx.x == 0) {
         st->step = c.ctl->step;
+        double *rec = c.sw_period + 8 * s;
         for (int a = 0; a < 3; ++a) {
             const double x = xcm[a] / 3.0;
             st->x_cm[a] = x;
-            if (init) c.xcm0[3 * s + a] = x;
+            if (init) {
+                c.xcm0[3 * s + a] = x;
+                rec[a] = rec[3 + a] = x;  // t = 0 is the first period boundary
+            }
             st->disp[a] = x - c.xcm0[3 * s + a];
         }
+        if (init) rec[6] = 0.0;
+        // period-averaged swimming velocity (Sec. 3, Eq. vel_swim) and the
+        // Reynolds numbers with nu = (tau - 1/2)/3 and a the rest radius
+        st->periods = (long long)rec[6];
+        const double nu = ((double)c.tau - 0.5) / 3.0;
+        double vv = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            st->v_period[a] = rec[6] >= 1.0 ? (rec[a] - rec[3 + a]) / sw.period : 0.0;
+            vv += st->v_period[a] * st->v_period[a];
+        }
+        const double rad = (double)c.beads[sw.bead[0]].reach - 1.0;
+        double ls2 = 0.0, vb = 0.0;
+        for (int a = 0; a < 3; ++a) ls2 += (st->R[2][a] - st->R[0][a]) * (st->R[2][a] - st->R[0][a]);
+        for (int q = 0; q < 3; ++q)
+            vb = fmax(vb, sqrt(st->V[q][0] * st->V[q][0] + st->V[q][1] * st->V[q][1] + st->V[q][2] * st->V[q][2]));
+        st->re_swim = sqrt(vv) * (sqrt(ls2) + 2.0 * rad) / nu;
+        st->re_bead = vb * rad / nu;
     }
 }
 

@@ -82,6 +82,7 @@ struct SwimDev {
     double phase_turns[3];  // phase / (2 pi)
     float amp[3];
     int pad;
+    double period;          // drive period (steps)
 };
 
 // Everything a kernel needs, by value.
@@ -124,6 +125,7 @@ struct DevCtx {
     Control *ctl;
     lbib_swimmer_state *sw_state;
     double *xcm0;              // x_cm at init, 3 per swimmer
+    double *sw_period;         // per swimmer: x_cm at the last two period boundaries, completed periods (8 doubles)
 };
 
 // most boxes one batch holds

@@ -160,7 +160,8 @@ class Simulation:
         check(self.L.swimmer_state(self.ctx, int(s), ctypes.byref(st)))
         m = lambda a: np.array([[a[i][j] for j in range(3)] for i in range(3)])
         return dict(step=st.step, R=m(st.R), V=m(st.V), F=m(st.F), T=m(st.T), x_cm=np.array(list(st.x_cm)),
-                    disp=np.array(list(st.disp)))
+                    disp=np.array(list(st.disp)), periods=st.periods, v_period=np.array(list(st.v_period)),
+                    re_swim=st.re_swim, re_bead=st.re_bead)
 
     def sync(self):
         check(self.L.lb_sync(self.ctx))

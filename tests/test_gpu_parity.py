@@ -253,3 +253,36 @@ def test_benchmark_box_full_size(perm, storage, tol):
     assert err < tol
     assert np.abs(sim.get_nodes() - osim.r).max() < (1e-6 if storage == "f32" else 1e-5)
     sim.close()
+
+
+def test_period_velocity_and_reynolds_numbers(perm):
+    """The mean swimming velocity over each completed drive period (Sec. 3,
+    Eq. vel_swim), recorded on the device at period boundaries, against the
+    oracle's x_cm at the same steps (within 1 %, the net-velocity bound), and
+    the Reynolds numbers against their definitions."""
+    from workloads import BoxSpec, SwimmerSpec
+    T = 40
+    sw = SwimmerSpec(center=(24.0, 14.0, 12.0), radius=3.0, subdiv=1, spacing=9.0, period=float(T)).with_drive(
+        2e-3, 2e-3, math.pi / 2)
+    box = BoxSpec(dims=(48, 28, 24), swimmers=(sw,))
+    asm = assemble(box)
+    sim = gpu_sim(box, asm)
+    assert sim.swimmer_state(0)["periods"] == 0
+    sim.lb_step(T - 1)
+    st = sim.swimmer_state(0)
+    assert st["periods"] == 0 and np.all(st["v_period"] == 0.0)
+    sim.lb_step(T + 5)  # 2T + 4 steps: inside the third period
+    st = sim.swimmer_state(0)
+    assert st["periods"] == 2
+    osim = oracle.OracleSim(box, asm).step(T)
+    x1 = osim.swimmer_centres()[0]
+    osim.step(T)
+    x2 = osim.swimmer_centres()[0]
+    v_ref = (x2 - x1) / T
+    assert abs(st["v_period"][0] - v_ref[0]) < 1e-2 * abs(v_ref[0])
+    nu = (box.tau - 0.5) / 3.0
+    L_swim = np.linalg.norm(st["R"][2] - st["R"][0]) + 2 * 3.0
+    assert st["re_swim"] == pytest.approx(np.linalg.norm(st["v_period"]) * L_swim / nu, rel=1e-6)
+    v_bead = max(np.linalg.norm(st["V"][q]) for q in range(3))
+    assert st["re_bead"] == pytest.approx(v_bead * 3.0 / nu, rel=1e-6)
+    sim.close()
