@@ -574,20 +574,20 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp_batch(const BatchDev bt) 
 
 cudaError_t launch_ib_batch(const BatchDev &bt, int kernel, int deterministic, int phase, cudaStream_t s) {
     if (phase == 0) {
-        if (bt.blocks_prep) k_ib_prepare_batch<<<bt.blocks_prep, PREP_TPB, 0, s>>>(bt);
+        if (bt.blocks_prep) launch_prio(k_ib_prepare_batch, bt.blocks_prep, PREP_TPB, 0, s, bt);
     } else if (phase == 1) {
         if (!bt.blocks_gs) return cudaSuccess;
         if (kernel == LBIB_LINEAR2) {
-            if (deterministic) k_ib_gather_spread_batch<2, true><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
-            else k_ib_gather_spread_batch<2, false><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
+            if (deterministic) launch_prio(k_ib_gather_spread_batch<2, true>, bt.blocks_gs, GS_TPB, 0, s, bt);
+            else launch_prio(k_ib_gather_spread_batch<2, false>, bt.blocks_gs, GS_TPB, 0, s, bt);
         } else {
-            if (deterministic) k_ib_gather_spread_batch<4, true><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
-            else k_ib_gather_spread_batch<4, false><<<bt.blocks_gs, GS_TPB, 0, s>>>(bt);
+            if (deterministic) launch_prio(k_ib_gather_spread_batch<4, true>, bt.blocks_gs, GS_TPB, 0, s, bt);
+            else launch_prio(k_ib_gather_spread_batch<4, false>, bt.blocks_gs, GS_TPB, 0, s, bt);
         }
     } else {
         if (!bt.blocks_int) return cudaSuccess;
-        if (kernel == LBIB_LINEAR2) k_ib_interp_batch<2><<<bt.blocks_int, INT_TPB, 0, s>>>(bt);
-        else k_ib_interp_batch<4><<<bt.blocks_int, INT_TPB, 0, s>>>(bt);
+        if (kernel == LBIB_LINEAR2) launch_prio(k_ib_interp_batch<2>, bt.blocks_int, INT_TPB, 0, s, bt);
+        else launch_prio(k_ib_interp_batch<4>, bt.blocks_int, INT_TPB, 0, s, bt);
     }
     return cudaGetLastError();
 }
@@ -602,7 +602,7 @@ int ib_blocks_interp(const DevCtx &c, int kernel) {
 cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s) {
     const int blocks = c.n_swimmers + (c.n_tris + PREP_TPB - 1) / PREP_TPB;
     if (blocks == 0) return cudaSuccess;
-    k_ib_prepare<<<blocks, PREP_TPB, 0, s>>>(c);
+    launch_prio(k_ib_prepare, blocks, PREP_TPB, 0, s, c);
     return cudaGetLastError();
 }
 
@@ -616,11 +616,11 @@ cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s)
     if (c.n_nodes == 0) return cudaSuccess;
     const int blocks = (c.n_nodes + GS_NODES - 1) / GS_NODES;
     if (kernel == LBIB_LINEAR2) {
-        if (c.deterministic) k_ib_gather_spread<2, true><<<blocks, GS_TPB, 0, s>>>(c);
-        else k_ib_gather_spread<2, false><<<blocks, GS_TPB, 0, s>>>(c);
+        if (c.deterministic) launch_prio(k_ib_gather_spread<2, true>, blocks, GS_TPB, 0, s, c);
+        else launch_prio(k_ib_gather_spread<2, false>, blocks, GS_TPB, 0, s, c);
     } else {
-        if (c.deterministic) k_ib_gather_spread<4, true><<<blocks, GS_TPB, 0, s>>>(c);
-        else k_ib_gather_spread<4, false><<<blocks, GS_TPB, 0, s>>>(c);
+        if (c.deterministic) launch_prio(k_ib_gather_spread<4, true>, blocks, GS_TPB, 0, s, c);
+        else launch_prio(k_ib_gather_spread<4, false>, blocks, GS_TPB, 0, s, c);
     }
     return cudaGetLastError();
 }
@@ -631,11 +631,11 @@ cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *ve
     const long long threads = (long long)c.n_nodes * lanes;
     const int blocks = (int)((threads + INT_TPB - 1) / INT_TPB);
     if (kernel == LBIB_LINEAR2) {
-        if (advect) k_ib_interp<2, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out, mark_parity);
-        else k_ib_interp<2, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out, -1);
+        if (advect) launch_prio(k_ib_interp<2, true>, blocks, INT_TPB, 0, s, c, vel_out, mark_parity);
+        else launch_prio(k_ib_interp<2, false>, blocks, INT_TPB, 0, s, c, vel_out, -1);
     } else {
-        if (advect) k_ib_interp<4, true><<<blocks, INT_TPB, 0, s>>>(c, vel_out, mark_parity);
-        else k_ib_interp<4, false><<<blocks, INT_TPB, 0, s>>>(c, vel_out, -1);
+        if (advect) launch_prio(k_ib_interp<4, true>, blocks, INT_TPB, 0, s, c, vel_out, mark_parity);
+        else launch_prio(k_ib_interp<4, false>, blocks, INT_TPB, 0, s, c, vel_out, -1);
     }
     return cudaGetLastError();
 }

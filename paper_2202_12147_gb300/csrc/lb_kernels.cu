@@ -1014,11 +1014,11 @@ template <int ST, int FORCING, int CPT>
 static void marked_dispatch_cpt(const DevCtx &c, bool odd, cudaStream_t s) {
     const unsigned blocks = (unsigned)(c.n_tiles < c.marked_grid ? c.n_tiles : c.marked_grid);
     if (c.deterministic) {
-        if (odd) k_lb_marked<ST, true, FORCING, true, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
-        else k_lb_marked<ST, false, FORCING, true, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+        if (odd) launch_prio(k_lb_marked<ST, true, FORCING, true, CPT>, blocks, tile_threads(c), 0, s, c);
+        else launch_prio(k_lb_marked<ST, false, FORCING, true, CPT>, blocks, tile_threads(c), 0, s, c);
     } else {
-        if (odd) k_lb_marked<ST, true, FORCING, false, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
-        else k_lb_marked<ST, false, FORCING, false, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+        if (odd) launch_prio(k_lb_marked<ST, true, FORCING, false, CPT>, blocks, tile_threads(c), 0, s, c);
+        else launch_prio(k_lb_marked<ST, false, FORCING, false, CPT>, blocks, tile_threads(c), 0, s, c);
     }
 }
 
@@ -1049,11 +1049,11 @@ static void batch_dispatch_cpt(const BatchDev &bt, bool marked, int det, bool od
         if (odd) k_lb_main_batch<ST, true, FORCING, CPT><<<bt.blocks_main, threads, 0, s>>>(bt);
         else k_lb_main_batch<ST, false, FORCING, CPT><<<bt.blocks_main, threads, 0, s>>>(bt);
     } else if (det) {
-        if (odd) k_lb_marked_batch<ST, true, FORCING, true, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
-        else k_lb_marked_batch<ST, false, FORCING, true, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
+        if (odd) launch_prio(k_lb_marked_batch<ST, true, FORCING, true, CPT>, bt.blocks_marked, threads, 0, s, bt);
+        else launch_prio(k_lb_marked_batch<ST, false, FORCING, true, CPT>, bt.blocks_marked, threads, 0, s, bt);
     } else {
-        if (odd) k_lb_marked_batch<ST, true, FORCING, false, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
-        else k_lb_marked_batch<ST, false, FORCING, false, CPT><<<bt.blocks_marked, threads, 0, s>>>(bt);
+        if (odd) launch_prio(k_lb_marked_batch<ST, true, FORCING, false, CPT>, bt.blocks_marked, threads, 0, s, bt);
+        else launch_prio(k_lb_marked_batch<ST, false, FORCING, false, CPT>, bt.blocks_marked, threads, 0, s, bt);
     }
 }
 

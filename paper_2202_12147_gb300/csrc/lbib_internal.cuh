@@ -184,6 +184,27 @@ __device__ __forceinline__ int stencil_axis(double p, int n, int kw, float &frac
     return (int)o;
 }
 
+// Launch on stream s with s's priority as a launch attribute: a CUDA graph
+// captured from s keeps it on the kernel node (the immersed-boundary chain
+// runs on a high-priority stream beside the main fluid update).
+template <typename... Exp, typename... Act>
+inline cudaError_t launch_prio(void (*k)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Act &&...args) {
+    int prio = 0;
+    cudaError_t e = cudaStreamGetPriority(s, &prio);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributePriority;
+    attr.val.priority = prio;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<Act &&>(args)...);
+}
+
 // message returned by lbib_last_error() on this thread
 void set_last_error(const char *msg);
 // argument checks of lb_init (api.cu), shared with the adjoint engine
