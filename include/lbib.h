@@ -358,7 +358,8 @@ int lb_destroy(lbib_ctx *ctx);
  * FP64.  It keeps a checkpoint (populations + node positions) every K steps
  * and, sweeping backward, recomputes each K-step segment from its checkpoint
  * before reversing it, so memory grows with n_steps / K + K states rather
- * than n_steps.  Only Guo forcing and the 4-point kernel (differentiable; the
+ * than n_steps.  Full K-step segments replay captured CUDA graphs in both
+ * sweeps (LBIB_GRAPHS=0 launches them step by step).  Only Guo forcing and the 4-point kernel (differentiable; the
  * 2-point kernel is not) are supported.  The drive parameter vector of
  * swimmer s is theta[6 s .. 6 s + 5] = (A_1, A_2, A_3, phi_1, phi_2, phi_3)
  * in the order of lbib_swimmer.bead; for a swimmer with balance = 1 the

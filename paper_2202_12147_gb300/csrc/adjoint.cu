@@ -30,6 +30,7 @@
 // Fluid arrays are FP32 or FP64 (template T); everything node-level is FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -908,6 +909,7 @@ struct lbib_adjoint {
     // reverse steps for either parity of the adjoint population buffers
     cudaStream_t cap = nullptr;
     cudaGraphExec_t g_fwd = nullptr, g_rev[2] = {nullptr, nullptr};
+    bool graphs = true;  // replay segment graphs (LBIB_GRAPHS=0: launch directly)
     long long n_fwd = 0, n_rev[2] = {0, 0};
 
     ~lbib_adjoint() {
@@ -1046,7 +1048,7 @@ cudaError_t run_segment(lbib_adjoint *a, int g) {
     if ((e = cudaMemsetAsync(s0 + P.s_F, 0, 3 * (size_t)P.d.Npad * P.esize, a->s)) != cudaSuccess) return e;
     if ((e = set_tbase(a, g)) != cudaSuccess) return e;
     const int len = a->seg_len(g);
-    if (len == P.K) {
+    if (len == P.K && a->graphs) {
         if (!a->g_fwd && (e = capture<T>(a, false, 0)) != cudaSuccess) return e;
         if ((e = cudaGraphLaunch(a->g_fwd, a->s)) != cudaSuccess) return e;
         a->launches += a->n_fwd;
@@ -1165,7 +1167,7 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
         if (a->slots_seg != g) CU(run_segment<T>(a, g));
         CU(set_tbase(a, g));
         const int len = a->seg_len(g);
-        if (len == P.K) {
+        if (len == P.K && a->graphs) {
             if (!a->g_rev[nxt]) CU(capture<T>(a, true, nxt));
             CU(cudaGraphLaunch(a->g_rev[nxt], a->s));
             a->launches += a->n_rev[nxt];
@@ -1271,6 +1273,10 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     a->P = P;
     a->s = (cudaStream_t)stream;
     a->ws = (char *)workspace;
+    {
+        const char *g = getenv("LBIB_GRAPHS");
+        a->graphs = !(g && g[0] == '0');
+    }
     a->rest.assign(s && M ? s->rest_nodes : nullptr, s && M ? s->rest_nodes + 3 * (size_t)M : nullptr);
     Mesh &m = a->m;
     m.M = M;
