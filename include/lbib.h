@@ -171,11 +171,9 @@ int lbib_required_sizes(const lb_params *p, const lbib_structure *s, size_t *out
 int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, void *stream, lbib_ctx **out);
 
 /* Advance n_steps full coupled steps (1-7 above) asynchronously on the
- * context stream.  Boxes below 2^20 cells replay the captured 16-step CUDA
- * graphs (the host's launch cost would dominate their short steps); larger
- * boxes launch each step's kernels directly on the two streams, which
- * measured faster there.  The environment variable LBIB_GRAPHS=0 / 2 forces
- * direct launches / graph replays; the results are the same either way. */
+ * context stream, replaying the captured 16-step CUDA graphs (single steps
+ * for odd remainders).  The environment variable LBIB_GRAPHS=0 launches every
+ * step's kernels directly instead; the results are the same either way. */
 int lb_step(lbib_ctx *ctx, long long n_steps);
 
 /* Steps 1-4 alone at the current positions and time: evaluate f^tot on every
