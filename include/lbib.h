@@ -171,9 +171,10 @@ int lbib_required_sizes(const lb_params *p, const lbib_structure *s, size_t *out
 int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, void *stream, lbib_ctx **out);
 
 /* Advance n_steps full coupled steps (1-7 above) asynchronously on the
- * context stream, replaying the captured 16-step CUDA graphs (single steps
- * for odd remainders).  The environment variable LBIB_GRAPHS=0 launches every
- * step's kernels directly instead; the results are the same either way. */
+ * context stream, replaying the captured CUDA graphs: 16 steps per replay
+ * from an even step, one-step graphs for the rest.  The environment
+ * variable LBIB_GRAPHS=0 launches every step's kernels directly instead; the
+ * results are the same either way. */
 int lb_step(lbib_ctx *ctx, long long n_steps);
 
 /* Steps 1-4 alone at the current positions and time: evaluate f^tot on every
@@ -197,6 +198,29 @@ int swimmer_state(lbib_ctx *ctx, int swimmer, lbib_swimmer_state *out);
  * following steps, and must not be reused before then.  Device errors
  * surface at that synchronising call. */
 int swimmer_state_async(lbib_ctx *ctx, lbib_swimmer_state *out);
+
+/* Trajectory of one swimmer at one step, written on the device by every
+ * coupled step (the last block of step 7, after the bead centres have moved
+ * with the mean velocity of their nodes, Fig. 1 caption).  FP64. */
+typedef struct {
+    long long step;     /* steps taken since lb_init once this step completed */
+    double x_cm[3];     /* mean of the three bead centres */
+    double R[3][3];     /* bead centres, unwrapped */
+    double V[3][3];     /* mean interpolated node velocity of each bead in this step */
+} lbib_track_point;
+
+/* Steps of trajectory points a context keeps on the device (a ring). */
+#define LBIB_TRACK_STEPS 256
+
+/* Queue a copy of the trajectory points of the last n_steps completed steps
+ * into HOST memory out[n_steps][n_swimmers] (oldest step first) on the stream
+ * that advances the context (its own, or its batch's), and return.
+ * 1 <= n_steps <= LBIB_TRACK_STEPS and n_steps <= the steps taken since
+ * lb_init (else LBIB_EINVAL, nothing queued).  Like swimmer_state_async, the
+ * points are valid after the next synchronising call; `out` should be
+ * page-locked.  The ring is part of the checkpoint, so points written before
+ * lb_checkpoint survive lb_restore. */
+int lb_track(lbib_ctx *ctx, long long n_steps, lbib_track_point *out);
 
 /* Wait for queued work and report latched device errors. */
 int lb_sync(lbib_ctx *ctx);

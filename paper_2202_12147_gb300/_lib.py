@@ -27,7 +27,7 @@ EXPORTS = [
     "lb_destroy", "lb_adjoint_required_bytes", "lb_adjoint_create", "lb_adjoint_set_drive",
     "lb_adjoint_set_initial", "lb_adjoint_forward", "lb_adjoint_backward", "lb_adjoint_get_final",
     "lb_adjoint_timing", "lb_adjoint_destroy", "lb_batch_autotune", "swimmer_state_async",
-    "lb_checkpoint_size", "lb_checkpoint", "lb_restore",
+    "lb_checkpoint_size", "lb_checkpoint", "lb_restore", "lb_track",
 ]
 
 
@@ -65,6 +65,17 @@ class SwimmerState(ctypes.Structure):
                 ("disp", ctypes.c_double * 3), ("periods", ctypes.c_longlong), ("v_period", ctypes.c_double * 3),
                 ("re_swim", ctypes.c_double), ("re_bead", ctypes.c_double)]
 
+
+TRACK_STEPS = 256
+
+
+class TrackPoint(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("x_cm", ctypes.c_double * 3), ("R", (ctypes.c_double * 3) * 3),
+                ("V", (ctypes.c_double * 3) * 3)]
+
+
+# the same record as a numpy dtype (176 bytes)
+TRACK_DTYPE = [("step", "<i8"), ("x_cm", "<f8", (3,)), ("R", "<f8", (3, 3)), ("V", "<f8", (3, 3))]
 
 TUNE_MAX_CLASSES = 32
 
@@ -116,6 +127,7 @@ def load(build_if_missing: bool = True):
         L.ib_interpolate.argtypes = [P, P]
         L.swimmer_state.argtypes = [P, I, ctypes.POINTER(SwimmerState)]
         L.swimmer_state_async.argtypes = [P, P]
+        L.lb_track.argtypes = [P, ctypes.c_longlong, P]
         L.lb_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         L.lb_checkpoint.argtypes = [P, P, ctypes.c_size_t]
         L.lb_restore.argtypes = [P, P, ctypes.c_size_t]

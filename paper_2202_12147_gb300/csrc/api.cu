@@ -78,7 +78,7 @@ struct Layout {
     size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0;
     // aux
     size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
-           obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0, oswp = 0;
+           obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0, oswp = 0, obv = 0, otrk = 0;
 };
 
 bool valid_params(const lb_params *p, std::string &why) {
@@ -189,6 +189,8 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     L.osws = o; o += up((size_t)S * sizeof(lbib_swimmer_state) + 16);
     L.oxcm = o; o += up((size_t)S * 24 + 24);
     L.oswp = o; o += up((size_t)S * 64 + 64);
+    L.obv = o; o += up((size_t)B * 16 + 16);
+    L.otrk = o; o += up((size_t)LBIB_TRACK_STEPS * S * sizeof(lbib_track_point) + 16);
     L.bytes[2] = o;
     return L;
 }
@@ -209,7 +211,8 @@ struct lbib_ctx {
     cudaStream_t cap = nullptr;    // private streams used only to capture graphs
     cudaStream_t cap_ib = nullptr;
     cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr;  // step-to-step dependencies
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;                 // GRAPH_STEPS steps from an even step
+    cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // one step from an even / odd step
     long long step = 0;            // host mirror of the device step counter
     bool profiling = false;
     std::vector<cudaEvent_t> ev;   // event pairs around fluid-kernel launches
@@ -303,6 +306,22 @@ cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t sm, cudaStream_t si
     if ((e = launch_lb_marked(c->d, c->p.storage, c->p.forcing, odd, sib)) != cudaSuccess) return e;
     if ((e = launch_ib_interp(c->d, c->p.kernel, true, nullptr, 1 - p, sib)) != cudaSuccess) return e;
     return cudaEventRecord(c->e_ib, sib);
+}
+
+// Capture n coupled steps, the first of parity p0, into an executable graph
+// whose nodes keep the priorities of the streams they were captured on.
+cudaError_t capture_steps(lbib_ctx *c, int p0, int n, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return ce;
+    ce = fork(c, c->cap, c->cap_ib);
+    for (int k = 0; k < n && ce == cudaSuccess; ++k) ce = enqueue_step(c, ((p0 + k) & 1) != 0, c->cap, c->cap_ib);
+    if (ce == cudaSuccess) ce = join(c, c->cap);
+    const cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (g) cudaGraphDestroy(g);
+    return ce;
 }
 
 // Stamp the tiles of the current positions for the current step (after the
@@ -531,6 +550,8 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.sw_state = (lbib_swimmer_state *)(A + L.osws);
     d.xcm0 = (double *)(A + L.oxcm);
     d.sw_period = (double *)(A + L.oswp);
+    d.bead_V = (float4 *)(A + L.obv);
+    d.track = (lbib_track_point *)(A + L.otrk);
 
     auto bail = [&](int code) {
         lb_destroy(c);
@@ -601,19 +622,12 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         cudaEventCreateWithFlags(&c->e_ib, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "creating streams or events failed"));
 
-    // capture GRAPH_STEPS coupled steps (alternating AA parity) into one graph
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return bail(fail(LBIB_ECUDA, "cudaStreamBeginCapture failed"));
-    cudaError_t ce = fork(c, c->cap, c->cap_ib);
-    for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k) ce = enqueue_step(c, (k & 1) != 0, c->cap, c->cap_ib);
-    if (ce == cudaSuccess) ce = join(c, c->cap);
-    cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
-    if (ce != cudaSuccess || ee != cudaSuccess)
-        return bail(fail(LBIB_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee)));
-    ce = cudaGraphInstantiateWithFlags(&c->graph, g, cudaGraphInstantiateFlagUseNodePriority);
-    cudaGraphDestroy(g);
-    if (ce != cudaSuccess) return bail(fail(LBIB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce)));
+    // capture GRAPH_STEPS coupled steps (alternating AA parity) into one
+    // graph, and one step of either parity into two more
+    cudaError_t ce = capture_steps(c, 0, GRAPH_STEPS, &c->graph);
+    if (ce == cudaSuccess) ce = capture_steps(c, 0, 1, &c->graph1[0]);
+    if (ce == cudaSuccess) ce = capture_steps(c, 1, 1, &c->graph1[1]);
+    if (ce != cudaSuccess) return bail(fail(LBIB_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce)));
     *out = c;
     return LBIB_OK;
 }
@@ -625,14 +639,12 @@ int lb_step(lbib_ctx *c, long long n) {
     bool forked = false;
     const bool graphs = use_graphs(c->L.N);
     while (n > 0) {
-        if (graphs && !c->profiling && (c->step & 1) == 0 && n >= GRAPH_STEPS) {
-            if (forked) {
-                CU(join(c, c->user));
-                forked = false;
-            }
-            CU(cudaGraphLaunch(c->graph, c->user));
-            c->step += GRAPH_STEPS;
-            n -= GRAPH_STEPS;
+        if (graphs && !c->profiling) {
+            // every graph forks and joins the two streams itself
+            const bool whole = (c->step & 1) == 0 && n >= GRAPH_STEPS;
+            CU(cudaGraphLaunch(whole ? c->graph : c->graph1[c->step & 1], c->user));
+            c->step += whole ? GRAPH_STEPS : 1;
+            n -= whole ? GRAPH_STEPS : 1;
         } else {
             if (!forked) {
                 CU(fork(c, c->user, c->ib));
@@ -678,6 +690,22 @@ int swimmer_state_async(lbib_ctx *c, lbib_swimmer_state *out) {
     if (c->n_swimmers == 0) return LBIB_OK;
     CU(launch_swimmer_state(c->d, false, c->user));
     CU(cudaMemcpyAsync(out, c->d.sw_state, sizeof(lbib_swimmer_state) * c->n_swimmers, cudaMemcpyDeviceToHost, c->user));
+    return LBIB_OK;
+}
+
+int lb_track(lbib_ctx *c, long long n, lbib_track_point *out) {
+    if (!c || (!out && c->n_swimmers)) return fail(LBIB_EINVAL, "NULL argument");
+    if (n < 1 || n > LBIB_TRACK_STEPS) return fail(LBIB_EINVAL, "n_steps outside [1, LBIB_TRACK_STEPS]");
+    if (n > c->step) return fail(LBIB_EINVAL, "n_steps exceeds the steps taken since lb_init");
+    if (c->n_swimmers == 0) return LBIB_OK;
+    cudaStream_t s = c->batch ? c->batch->user : c->user;
+    const size_t S = (size_t)c->n_swimmers;
+    // step t (1-based) lives in slot (t - 1) mod LBIB_TRACK_STEPS: at most two contiguous runs
+    const long long first = (c->step - n) % LBIB_TRACK_STEPS;
+    const long long run = std::min<long long>(n, LBIB_TRACK_STEPS - first);
+    CU(cudaMemcpyAsync(out, c->d.track + first * S, run * S * sizeof(lbib_track_point), cudaMemcpyDeviceToHost, s));
+    if (run < n)
+        CU(cudaMemcpyAsync(out + run * S, c->d.track, (n - run) * S * sizeof(lbib_track_point), cudaMemcpyDeviceToHost, s));
     return LBIB_OK;
 }
 
@@ -984,6 +1012,8 @@ int lb_destroy(lbib_ctx *c) {
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->ib) cudaStreamSynchronize(c->ib);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaGraphExec_t g : c->graph1)
+        if (g) cudaGraphExecDestroy(g);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->cap_ib) cudaStreamDestroy(c->cap_ib);
     if (c->ib) cudaStreamDestroy(c->ib);

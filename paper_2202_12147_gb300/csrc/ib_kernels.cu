@@ -282,9 +282,11 @@ __device__ void fold_bead_velocities(const DevCtx &c) {
         }
         if (l == 0) {
             double *R = c.bead_R + 4 * b;
-            R[0] += (double)(sx * bd.inv_count);
-            R[1] += (double)(sy * bd.inv_count);
-            R[2] += (double)(sz * bd.inv_count);
+            const float vx = sx * bd.inv_count, vy = sy * bd.inv_count, vz = sz * bd.inv_count;
+            R[0] += (double)vx;
+            R[1] += (double)vy;
+            R[2] += (double)vz;
+            c.bead_V[b] = make_float4(vx, vy, vz, 0.f);
         }
     }
 }
@@ -424,6 +426,22 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
             // three bead centres) for the period-averaged velocity (Sec. 3)
             for (int sw = threadIdx.x; sw < c.n_swimmers; sw += blockDim.x) {
                 const SwimDev d = c.swims[sw];
+                // this step's trajectory point, slot (next - 1) mod LBIB_TRACK_STEPS
+                lbib_track_point *tp = c.track + (size_t)((next - 1) % LBIB_TRACK_STEPS) * c.n_swimmers + sw;
+                tp->step = next;
+                for (int a = 0; a < 3; ++a) {
+                    const double *R = c.bead_R + 4 * d.bead[a];
+                    const float4 V = c.bead_V[d.bead[a]];
+                    tp->R[a][0] = R[0];
+                    tp->R[a][1] = R[1];
+                    tp->R[a][2] = R[2];
+                    tp->V[a][0] = V.x;
+                    tp->V[a][1] = V.y;
+                    tp->V[a][2] = V.z;
+                }
+                for (int a = 0; a < 3; ++a)
+                    tp->x_cm[a] = (c.bead_R[4 * d.bead[0] + a] + c.bead_R[4 * d.bead[1] + a] +
+                                   c.bead_R[4 * d.bead[2] + a]) / 3.0;
                 if (floor((double)next / d.period) > floor((double)(next - 1) / d.period)) {
                     double *rec = c.sw_period + 8 * sw;
                     for (int a = 0; a < 3; ++a) {

@@ -121,6 +121,8 @@ struct DevCtx {
     const SwimDev *swims;
     double *bead_R;            // bead centres, 4 doubles per bead
     float4 *bead_ext;          // (f^d + f^s) / N_v per bead
+    float4 *bead_V;            // mean node velocity of each bead in the last step
+    lbib_track_point *track;   // [LBIB_TRACK_STEPS][n_swimmers] ring of trajectory points
 
     Control *ctl;
     lbib_swimmer_state *sw_state;

@@ -155,6 +155,24 @@ class Simulation:
         ptr = out.data_ptr() if hasattr(out, "data_ptr") else ctypes.addressof(out)
         check(self.L.swimmer_state_async(self.ctx, ctypes.c_void_p(ptr)))
 
+    def track_async(self, n_steps, out):
+        """Queue a copy of the trajectory points of the last n_steps steps into
+        `out` (host memory of n_steps x n_swimmers records of 176 bytes, e.g. a
+        pinned uint8 tensor); valid after sync()."""
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        check(self.L.lb_track(self.ctx, int(n_steps), ctypes.c_void_p(ptr)))
+
+    def track(self, n_steps):
+        """The trajectory points of the last n_steps steps as a structured
+        numpy array [n_steps, n_swimmers] (fields step, x_cm, R, V)."""
+        out = np.zeros((int(n_steps), self.n_swimmers), dtype=_lib.TRACK_DTYPE)
+        if self.n_swimmers:
+            self.track_async(n_steps, out)
+        else:
+            check(self.L.lb_track(self.ctx, int(n_steps), None))
+        self.sync()
+        return out
+
     def swimmer_state(self, s=0):
         st = _lib.SwimmerState()
         check(self.L.swimmer_state(self.ctx, int(s), ctypes.byref(st)))
