@@ -458,8 +458,12 @@ __device__ __forceinline__ unsigned pack2_raw(float2 v) {
 // x-shifted directions of odd steps read the aligned word plus the one value
 // across its edge and reassemble with byte permutes, and write one value, an
 // aligned pair and one value.  The collision runs as two packed pairs.
-template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
-__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
+// STAGED: the 19 source row-planes were copied to shared memory beforehand
+// (`stage`, row i = the row-plane direction i is read from, all nx cells),
+// and the loads come from there; the stores still go to global memory.
+template <int ST, bool ODD, int FORCING, bool DET, bool MARKED, bool STAGED = false>
+__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z,
+                                        const unsigned short *stage = nullptr) {
     using T = unsigned short;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
     const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
@@ -472,7 +476,19 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
     uint2 raw[Q];  // cells x0..x0+3 of each direction, 2 values per word
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (ODD) {
+        if (STAGED) {
+            const T *pl = stage + i * nx;
+            const uint2 w = *reinterpret_cast<const uint2 *>(pl + x0);
+            if (!ODD || cx(i) == 0) {
+                raw[i] = w;
+            } else if (cx(i) > 0) {
+                const unsigned e = pl[xm];
+                raw[i] = make_uint2(__byte_perm(e, w.x, 0x5410), __byte_perm(w.x, w.y, 0x5432));
+            } else {
+                const unsigned e = pl[x4];
+                raw[i] = make_uint2(__byte_perm(w.x, w.y, 0x5432), __byte_perm(w.y, e, 0x5432));
+            }
+        } else if (ODD) {
             // direction i of cell x sits in slot opp(i) of cell x - c_i
             const int dy = -cy(i), dz = -cz(i);
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
@@ -866,6 +882,74 @@ __global__ void __launch_bounds__(SLAB_THREADS, LBIB_SLAB_MINB) k_lb_slab(const 
 }
 
 // The marked tiles of this parity's list: a persistent grid walks the list.
+// ---------------------------------------------------------------- staged rows (16-bit)
+// Whole rows (tile_x == nx, four cells per thread): a block updates R
+// consecutive rows.  While it collides row k it has the 19 source row-planes
+// of row k + 1 in flight as asynchronous 8-byte copies into shared memory
+// (two stages), so every warp keeps loads outstanding during its arithmetic
+// instead of alternating between waiting and computing.  Each thread copies
+// the words of its own four cells; the x-shifted directions of odd steps take
+// one value across the word's edge from a neighbour's copy, visible after the
+// block barrier.  Rows stamped for this step are skipped (k_lb_marked).
+#ifndef LBIB_ROWS_MINB
+#define LBIB_ROWS_MINB 8
+#endif
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// copy the words of cells x0..x0+3 of the 19 row-planes row r reads into stage
+template <bool ODD>
+__device__ __forceinline__ void stage_row(const DevCtx &c, unsigned short *stage, unsigned r, unsigned x0) {
+    const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
+    const unsigned y = r % ny, z = r / ny;
+    const unsigned rm = (y ? y - 1 : ny - 1) * nx, r0 = y * nx, rp = ((y + 1 == ny) ? 0 : y + 1) * nx;
+    const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
+    const unsigned short *P = reinterpret_cast<const unsigned short *>(c.pops);
+    const size_t Np = (size_t)c.Npad;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        // odd steps: direction i of cell x sits in slot opp(i) of cell x - c_i
+        const int dy = ODD ? -cy(i) : 0, dz = ODD ? -cz(i) : 0;
+        const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
+        cp_async8(stage + i * nx + x0, P + (size_t)(ODD ? opp(i) : i) * Np + row + x0);
+    }
+}
+
+template <int ST, bool ODD, int FORCING>
+__global__ void __launch_bounds__(LB_TPB / 4, LBIB_ROWS_MINB) k_lb_rows(const DevCtx c, int R) {
+    extern __shared__ __align__(16) unsigned char rows_smem[];
+    unsigned short *stage = reinterpret_cast<unsigned short *>(rows_smem);
+    const unsigned nx = c.nx, ny = c.ny, rows = c.ny * c.nz;
+    const unsigned x0 = 4 * threadIdx.x;
+    const bool mine = x0 < nx;
+    // tiles stamped with this step's number belong to k_lb_marked; one tile per row
+    const int gen = c.ctl->gen[ODD ? 1 : 0];
+    const int *marks = c.marks + (ODD ? c.n_tiles : 0);
+    const unsigned r_end = min(rows, (unsigned)(blockIdx.x + 1) * (unsigned)R);
+    unsigned r = blockIdx.x * (unsigned)R;
+    while (r < r_end && marks[r] == gen) ++r;
+    if (r < r_end && mine) stage_row<ODD>(c, stage, r, x0);
+    cp_async_commit();
+    bool ok = true;
+    for (unsigned k = 0; r < r_end; ++k) {
+        unsigned rn = r + 1;
+        while (rn < r_end && marks[rn] == gen) ++rn;
+        if (rn < r_end && mine) stage_row<ODD>(c, stage + ((k + 1) & 1) * Q * nx, rn, x0);
+        cp_async_commit();
+        cp_async_wait1();  // this thread's copies of row r have landed
+        __syncthreads();   // and every other thread's
+        if (mine) ok &= lb_quad<ST, ODD, FORCING, false, false, true>(c, x0, r % ny, r / ny, stage + (k & 1) * Q * nx);
+        __syncthreads();   // stage (k & 1) is refilled in the next iteration
+        r = rn;
+    }
+    report_bad(c, !ok);
+    if (c.n_nodes == 0 && blockIdx.x == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
+}
+
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nblk) {
     const int p = ODD ? 1 : 0;
@@ -1137,6 +1221,32 @@ int lb_slab_grid(const DevCtx &c, int storage) {
     const int R = slab_rows(c.nx, c.ny, es);
     const int slabs = R ? (c.ny / R) * c.nz : 0;
     return std::min(slabs, sms * per);
+}
+
+template <int ST, int FORCING>
+static void rows_dispatch(const DevCtx &c, bool odd, int R, cudaStream_t s, cudaError_t *e) {
+    if constexpr (ST == LBIB_F32) {
+        *e = cudaErrorInvalidValue;  // 16-bit storage only
+    } else {
+        const unsigned rows = (unsigned)c.ny * (unsigned)c.nz;
+        const unsigned grid = (rows + (unsigned)R - 1) / (unsigned)R;
+        const size_t smem = 2 * (size_t)Q * (size_t)c.nx * sizeof(unsigned short);
+        if (odd) k_lb_rows<ST, true, FORCING><<<grid, tile_threads(c), smem, s>>>(c, R);
+        else k_lb_rows<ST, false, FORCING><<<grid, tile_threads(c), smem, s>>>(c, R);
+        *e = cudaGetLastError();
+    }
+}
+
+bool lb_rows_supported(const DevCtx &c, int storage) {
+    return storage != LBIB_F32 && c.cells_per_thread == 4 && c.tiles_x == 1 && c.tile_x == c.nx && c.nx % 4 == 0 &&
+           c.nx <= LB_TPB;
+}
+
+cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int R, cudaStream_t s) {
+    if (R < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    LBIB_DISPATCH(rows_dispatch, storage, forcing, c, odd, R, s, &e);
+    return e;
 }
 
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s) {
