@@ -460,10 +460,13 @@ __device__ __forceinline__ unsigned pack2_raw(float2 v) {
 // aligned pair and one value.  The collision runs as two packed pairs.
 // STAGED: the 19 source row-planes were copied to shared memory beforehand
 // (`stage`, row i = the row-plane direction i is read from, all nx cells),
-// and the loads come from there; the stores still go to global memory.
-template <int ST, bool ODD, int FORCING, bool DET, bool MARKED, bool STAGED = false>
+// and the loads come from there.  OSTAGED: the results go to shared memory
+// instead (`ostage`, row j = the row-plane of slot j they are written to, all
+// nx cells, x-shifts applied with the row's periodic wrap), for the block to
+// write out as whole aligned words afterwards (flush_row).
+template <int ST, bool ODD, int FORCING, bool DET, bool MARKED, bool STAGED = false, bool OSTAGED = false>
 __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z,
-                                        const unsigned short *stage = nullptr) {
+                                        const unsigned short *stage = nullptr, unsigned short *ostage = nullptr) {
     using T = unsigned short;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
     const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
@@ -543,7 +546,19 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned e = pack2_raw<ST>(d[i]);  // this pair's cells (x0 + 2h, x0 + 2h + 1)
-            if (ODD) {
+            if (OSTAGED) {
+                if (!ODD) {
+                    *reinterpret_cast<unsigned *>(ostage + opp(i) * nx + x0 + 2 * h) = e;
+                } else if (cx(i) == 0) {
+                    *reinterpret_cast<unsigned *>(ostage + i * nx + x0 + 2 * h) = e;
+                } else if (cx(i) > 0) {  // to cells x0 + 2h + 1, x0 + 2h + 2
+                    ostage[i * nx + x0 + 2 * h + 1] = (T)(e & 0xffffu);
+                    ostage[i * nx + (h ? x4 : x0 + 2)] = (T)(e >> 16);
+                } else {                 // to cells x0 + 2h - 1, x0 + 2h
+                    ostage[i * nx + (h ? x0 + 1 : xm)] = (T)(e & 0xffffu);
+                    ostage[i * nx + x0 + 2 * h] = (T)(e >> 16);
+                }
+            } else if (ODD) {
                 // direction i of cell x goes to slot i of cell x + c_i
                 const int dy = cy(i), dz = cz(i);
                 const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
@@ -919,11 +934,34 @@ __device__ __forceinline__ void stage_row(const DevCtx &c, unsigned short *stage
     }
 }
 
-template <int ST, bool ODD, int FORCING>
+// write the block's staged results of row r (row j = slot j's destination
+// row-plane) to global memory, 8 aligned bytes per thread and slot
+template <bool ODD>
+__device__ __forceinline__ void flush_row(const DevCtx &c, const unsigned short *ostage, unsigned r, unsigned x0) {
+    const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
+    const unsigned y = r % ny, z = r / ny;
+    const unsigned rm = (y ? y - 1 : ny - 1) * nx, r0 = y * nx, rp = ((y + 1 == ny) ? 0 : y + 1) * nx;
+    const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
+    unsigned short *P = reinterpret_cast<unsigned short *>(c.pops);
+    const size_t Np = (size_t)c.Npad;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        // odd steps: slot j of cell x + c_j; even steps: slot j of the cell itself
+        const int dy = ODD ? cy(j) : 0, dz = ODD ? cz(j) : 0;
+        const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
+        *reinterpret_cast<uint2 *>(P + (size_t)j * Np + row + x0) = *reinterpret_cast<const uint2 *>(ostage + j * nx + x0);
+    }
+}
+
+// MODE bit 0: loads staged (cp.async, next row in flight); bit 1: results
+// staged in shared memory and written as whole aligned words
+template <int ST, bool ODD, int FORCING, int MODE>
 __global__ void __launch_bounds__(LB_TPB / 4, LBIB_ROWS_MINB) k_lb_rows(const DevCtx c, int R) {
+    constexpr bool IN = (MODE & 1) != 0, OUT = (MODE & 2) != 0;
     extern __shared__ __align__(16) unsigned char rows_smem[];
     unsigned short *stage = reinterpret_cast<unsigned short *>(rows_smem);
     const unsigned nx = c.nx, ny = c.ny, rows = c.ny * c.nz;
+    unsigned short *ostage = stage + (IN ? 2 : 0) * Q * nx;
     const unsigned x0 = 4 * threadIdx.x;
     const bool mine = x0 < nx;
     // tiles stamped with this step's number belong to k_lb_marked; one tile per row
@@ -932,18 +970,26 @@ __global__ void __launch_bounds__(LB_TPB / 4, LBIB_ROWS_MINB) k_lb_rows(const De
     const unsigned r_end = min(rows, (unsigned)(blockIdx.x + 1) * (unsigned)R);
     unsigned r = blockIdx.x * (unsigned)R;
     while (r < r_end && marks[r] == gen) ++r;
-    if (r < r_end && mine) stage_row<ODD>(c, stage, r, x0);
-    cp_async_commit();
+    if (IN) {
+        if (r < r_end && mine) stage_row<ODD>(c, stage, r, x0);
+        cp_async_commit();
+    }
     bool ok = true;
     for (unsigned k = 0; r < r_end; ++k) {
         unsigned rn = r + 1;
         while (rn < r_end && marks[rn] == gen) ++rn;
-        if (rn < r_end && mine) stage_row<ODD>(c, stage + ((k + 1) & 1) * Q * nx, rn, x0);
-        cp_async_commit();
-        cp_async_wait1();  // this thread's copies of row r have landed
-        __syncthreads();   // and every other thread's
-        if (mine) ok &= lb_quad<ST, ODD, FORCING, false, false, true>(c, x0, r % ny, r / ny, stage + (k & 1) * Q * nx);
-        __syncthreads();   // stage (k & 1) is refilled in the next iteration
+        if (IN) {
+            if (rn < r_end && mine) stage_row<ODD>(c, stage + ((k + 1) & 1) * Q * nx, rn, x0);
+            cp_async_commit();
+            cp_async_wait1();  // this thread's copies of row r have landed
+            __syncthreads();   // and every other thread's
+        }
+        if (mine) ok &= lb_quad<ST, ODD, FORCING, false, false, IN, OUT>(c, x0, r % ny, r / ny, stage + (k & 1) * Q * nx, ostage);
+        if (OUT) {
+            __syncthreads();   // every value of the row's destination words is staged
+            if (mine) flush_row<ODD>(c, ostage, r, x0);
+        }
+        if (IN || OUT) __syncthreads();  // the stages are refilled in the next iteration
         r = rn;
     }
     report_bad(c, !ok);
@@ -1224,15 +1270,28 @@ int lb_slab_grid(const DevCtx &c, int storage) {
 }
 
 template <int ST, int FORCING>
-static void rows_dispatch(const DevCtx &c, bool odd, int R, cudaStream_t s, cudaError_t *e) {
+static void rows_dispatch(const DevCtx &c, bool odd, int R, int mode, cudaStream_t s, cudaError_t *e) {
     if constexpr (ST == LBIB_F32) {
         *e = cudaErrorInvalidValue;  // 16-bit storage only
     } else {
         const unsigned rows = (unsigned)c.ny * (unsigned)c.nz;
         const unsigned grid = (rows + (unsigned)R - 1) / (unsigned)R;
-        const size_t smem = 2 * (size_t)Q * (size_t)c.nx * sizeof(unsigned short);
-        if (odd) k_lb_rows<ST, true, FORCING><<<grid, tile_threads(c), smem, s>>>(c, R);
-        else k_lb_rows<ST, false, FORCING><<<grid, tile_threads(c), smem, s>>>(c, R);
+        const size_t row = (size_t)Q * (size_t)c.nx * sizeof(unsigned short);
+        const size_t smem = ((mode & 1) ? 2 : 0) * row + ((mode & 2) ? 1 : 0) * row;
+        const unsigned T = tile_threads(c);
+        switch (mode) {
+        case 1:
+            if (odd) k_lb_rows<ST, true, FORCING, 1><<<grid, T, smem, s>>>(c, R);
+            else k_lb_rows<ST, false, FORCING, 1><<<grid, T, smem, s>>>(c, R);
+            break;
+        case 2:
+            if (odd) k_lb_rows<ST, true, FORCING, 2><<<grid, T, smem, s>>>(c, R);
+            else k_lb_rows<ST, false, FORCING, 2><<<grid, T, smem, s>>>(c, R);
+            break;
+        default:
+            if (odd) k_lb_rows<ST, true, FORCING, 3><<<grid, T, smem, s>>>(c, R);
+            else k_lb_rows<ST, false, FORCING, 3><<<grid, T, smem, s>>>(c, R);
+        }
         *e = cudaGetLastError();
     }
 }
@@ -1242,10 +1301,10 @@ bool lb_rows_supported(const DevCtx &c, int storage) {
            c.nx <= LB_TPB;
 }
 
-cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int R, cudaStream_t s) {
-    if (R < 1) return cudaErrorInvalidValue;
+cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int R, int mode, cudaStream_t s) {
+    if (R < 1 || mode < 1 || mode > 3) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
-    LBIB_DISPATCH(rows_dispatch, storage, forcing, c, odd, R, s, &e);
+    LBIB_DISPATCH(rows_dispatch, storage, forcing, c, odd, R, mode, s, &e);
     return e;
 }
 

@@ -1,8 +1,9 @@
 """The staged-rows main-fluid kernel for 16-bit storage
 (LBIB_MAIN_KERNEL=rows) against the tile kernel.  Both run the same
-four-cell update on the same stored words (the rows kernel reads them from
-shared-memory copies of the 19 source row-planes), so whole runs agree
-bitwise: both AA parities, rows stamped around a swimmer (skipped and left
+four-cell update on the same stored words (the rows kernel may read them
+from shared-memory copies of the 19 source row-planes, and may stage its
+results in shared memory before writing them as aligned words: modes 1, 2,
+3), so whole runs agree bitwise: both AA parities, rows stamped around a swimmer (skipped and left
 to the marked-tile kernel), periodic seams, and row counts that R does not
 divide."""
 import math
@@ -16,13 +17,15 @@ from workloads import BoxSpec, SwimmerSpec, assemble, fluid_box
 pytestmark = pytest.mark.gpu
 
 
-def _sim(box, asm, kernel, monkeypatch, R=None, **kw):
+def _sim(box, asm, kernel, monkeypatch, R=None, mode=None, **kw):
     monkeypatch.setenv("LBIB_MAIN_KERNEL", kernel)
     if R is not None:
         monkeypatch.setenv("LBIB_ROWS_PER_BLOCK", str(R))
+    if mode is not None:
+        monkeypatch.setenv("LBIB_ROWS_MODE", str(mode))
     s = gpu_sim(box, asm, **kw)
-    monkeypatch.delenv("LBIB_MAIN_KERNEL")
-    monkeypatch.delenv("LBIB_ROWS_PER_BLOCK", raising=False)
+    for v in ("LBIB_MAIN_KERNEL", "LBIB_ROWS_PER_BLOCK", "LBIB_ROWS_MODE"):
+        monkeypatch.delenv(v, raising=False)
     return s
 
 
@@ -32,8 +35,8 @@ def _swimmer_box():
     return BoxSpec(dims=(128, 32, 24), swimmers=(sw,))
 
 
-def _run(box, asm, kernel, monkeypatch, storage, R=None):
-    s = _sim(box, asm, kernel, monkeypatch, R=R, storage=storage, deterministic=True)
+def _run(box, asm, kernel, monkeypatch, storage, R=None, mode=None):
+    s = _sim(box, asm, kernel, monkeypatch, R=R, mode=mode, storage=storage, deterministic=True)
     s.lb_step(3)   # single steps of both parities
     s.lb_step(32)  # graph replays
     out = (s.get_populations(), s.get_nodes(), s.lb_get_macros()[1].cpu().numpy())
@@ -42,22 +45,23 @@ def _run(box, asm, kernel, monkeypatch, storage, R=None):
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-@pytest.mark.parametrize("R", [1, 4, 5])
-def test_rows_kernel_matches_tile_kernel_with_swimmer(gpu_lib, monkeypatch, storage, R):
+@pytest.mark.parametrize("R,mode", [(1, 3), (4, 3), (5, 3), (4, 1), (5, 2), (1, 2)])
+def test_rows_kernel_matches_tile_kernel_with_swimmer(gpu_lib, monkeypatch, storage, R, mode):
     box = _swimmer_box()
     asm = assemble(box)
     ref = _run(box, asm, "tiles", monkeypatch, storage)
-    got = _run(box, asm, "rows", monkeypatch, storage, R=R)
+    got = _run(box, asm, "rows", monkeypatch, storage, R=R, mode=mode)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
 
 
-def test_rows_kernel_matches_tile_kernel_fluid_only(gpu_lib, monkeypatch):
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_rows_kernel_matches_tile_kernel_fluid_only(gpu_lib, monkeypatch, mode):
     """No immersed boundary (the main kernel advances the step counter), a
     uniform body force, 64-cell rows, 7 x 9 rows."""
     box = fluid_box((64, 7, 9), tau=0.7, g=(2e-6, -1e-6, 5e-7))
     ref = _run(box, None, "tiles", monkeypatch, "f16")
-    got = _run(box, None, "rows", monkeypatch, "f16", R=4)
+    got = _run(box, None, "rows", monkeypatch, "f16", R=4, mode=mode)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
 
