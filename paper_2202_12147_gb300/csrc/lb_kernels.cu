@@ -612,25 +612,37 @@ __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
     __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), \
                       (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? ((ST) == LBIB_F32 ? 4 : LBIB_LB_PAIR16_MINB) : LBIB_LB_QUAD_MINB))
 template <int ST, bool ODD, int FORCING, int CPT>
-__device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, unsigned tx, unsigned y, unsigned z) {
+__device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, unsigned tx, unsigned y, unsigned z,
+                                             unsigned t = threadIdx.x) {
     // tiles stamped with this step's number are updated by k_lb_marked; gen[p]
     // is written before this launch and not again until it has finished
     if (c.marks[(ODD ? c.n_tiles : 0) + tile] == c.ctl->gen[ODD ? 1 : 0]) return;
-    const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
+    const unsigned x = tx * c.tile_x + CPT * t;
     bool ok = true;
-    if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+    if (CPT * t < (unsigned)c.tile_x && x < (unsigned)c.nx) {
         if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, y, z);
         else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, y, z);
         else ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, y, z);
     }
     report_bad(c, !ok);
-    if (c.n_nodes == 0 && tile == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
+    if (c.n_nodes == 0 && tile == 0 && t == 0) c.ctl->step += 1;  // no IB chain to advance it
 }
 
 template <int ST, bool ODD, int FORCING, int CPT>
 __global__ void LBIB_LB_BOUNDS_ST(ST, CPT) k_lb_main(const DevCtx c) {
     const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Whole rows of 16-bit storage (tiles_x == 1, four cells per thread), NR
+// adjacent rows (y = NR * blockIdx.y + k) per block: the block's loads and
+// stores of each row-plane cover NR * nx * 2 contiguous bytes.
+template <int ST, bool ODD, int FORCING, int NR>
+__global__ void __launch_bounds__(LB_TPB / 4 * NR, LBIB_LB_QUAD_MINB / NR) k_lb_main_nrows(const DevCtx c) {
+    const unsigned tt = blockDim.x / NR;  // threads per row, a multiple of 32
+    const unsigned k = threadIdx.x / tt, y = NR * blockIdx.y + k, z = blockIdx.z;
+    if (y >= (unsigned)c.ny) return;       // whole warps: tt is a multiple of 32
+    lb_main_body<ST, ODD, FORCING, 4>(c, y + c.ny * z, 0, y, z, threadIdx.x - k * tt);
 }
 
 // ---------------------------------------------------------------- TMA-staged slabs
@@ -1305,6 +1317,32 @@ cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, 
     if (R < 1 || mode < 1 || mode > 3) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     LBIB_DISPATCH(rows_dispatch, storage, forcing, c, odd, R, mode, s, &e);
+    return e;
+}
+
+template <int ST, int FORCING>
+static void nrows_dispatch(const DevCtx &c, bool odd, int nr, cudaStream_t s, cudaError_t *e) {
+    if constexpr (ST == LBIB_F32) {
+        *e = cudaErrorInvalidValue;  // 16-bit storage only
+    } else {
+        const unsigned T = tile_threads(c);
+        if (nr == 4) {
+            const dim3 g(1, ((unsigned)c.ny + 3) / 4, (unsigned)c.nz);
+            if (odd) k_lb_main_nrows<ST, true, FORCING, 4><<<g, 4 * T, 0, s>>>(c);
+            else k_lb_main_nrows<ST, false, FORCING, 4><<<g, 4 * T, 0, s>>>(c);
+        } else {
+            const dim3 g(1, ((unsigned)c.ny + 1) / 2, (unsigned)c.nz);
+            if (odd) k_lb_main_nrows<ST, true, FORCING, 2><<<g, 2 * T, 0, s>>>(c);
+            else k_lb_main_nrows<ST, false, FORCING, 2><<<g, 2 * T, 0, s>>>(c);
+        }
+        *e = cudaGetLastError();
+    }
+}
+
+cudaError_t launch_lb_nrows(const DevCtx &c, int storage, int forcing, bool odd, int nr, cudaStream_t s) {
+    if (nr != 2 && nr != 4) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    LBIB_DISPATCH(nrows_dispatch, storage, forcing, c, odd, nr, s, &e);
     return e;
 }
 

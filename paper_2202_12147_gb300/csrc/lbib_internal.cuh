@@ -224,6 +224,8 @@ cudaError_t launch_lb_slab(const DevCtx &c, int storage, int forcing, bool odd, 
 // loads staged asynchronously in shared memory while the current row
 // collides; bit 1: results staged in shared memory, written as aligned words
 bool lb_rows_supported(const DevCtx &c, int storage);
+// 16-bit storage, whole rows, nr (2 or 4) adjacent rows per block (lb_rows_supported)
+cudaError_t launch_lb_nrows(const DevCtx &c, int storage, int forcing, bool odd, int nr, cudaStream_t s);
 cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int R, int mode, cudaStream_t s);
 cudaError_t launch_lb_marked(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
 cudaError_t launch_lb_macros(const DevCtx &c, int storage, bool odd, float *rho, float *u, cudaStream_t s);

@@ -79,3 +79,18 @@ def test_rows_kernel_on_the_benchmark_box(gpu_lib, monkeypatch):
         s.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("kernel", ["rows2", "rows4"])
+def test_adjacent_rows_kernel_matches_tile_kernel(gpu_lib, monkeypatch, storage, kernel):
+    """Two or four adjacent rows per block (30 rows per plane: the last block
+    of four holds two), rows stamped around a swimmer skipped per row."""
+    sw = SwimmerSpec(center=(64.0, 15.0, 12.0), radius=4.0, subdiv=2, spacing=12.0, period=60.0).with_drive(
+        2e-3, 2e-3, math.pi / 2)
+    box = BoxSpec(dims=(128, 30, 24), swimmers=(sw,))
+    asm = assemble(box)
+    ref = _run(box, asm, "tiles", monkeypatch, storage)
+    got = _run(box, asm, kernel, monkeypatch, storage)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
