@@ -221,9 +221,6 @@ struct lbib_ctx {
     lbib_swimmer_state *h_sws = nullptr;  // pinned
     int n_nodes = 0, n_swimmers = 0;
     int slab_grid = 0;  // > 0: main fluid update by the TMA-staged slab kernel with this grid
-    int rows_R = 0;     // > 0: main fluid update by the staged-rows kernel, this many rows per block
-    int rows_mode = 3;  // its staging: 1 loads, 2 results, 3 both
-    int nrows = 0;      // 2 or 4: main fluid update with that many adjacent rows per block
     lbib_batch *batch = nullptr;   // set while the context belongs to a batch
     void *buf[LBIB_NBUF] = {nullptr, nullptr, nullptr};  // the caller buffers
 };
@@ -255,8 +252,6 @@ namespace {
 // the update of every unmarked tile: TMA-staged rows or the tile kernel
 cudaError_t main_fluid(lbib_ctx *c, bool odd, cudaStream_t s) {
     if (c->slab_grid > 0) return launch_lb_slab(c->d, c->p.storage, c->p.forcing, odd, c->slab_grid, s);
-    if (c->nrows > 0) return launch_lb_nrows(c->d, c->p.storage, c->p.forcing, odd, c->nrows, s);
-    if (c->rows_R > 0) return launch_lb_rows(c->d, c->p.storage, c->p.forcing, odd, c->rows_R, c->rows_mode, s);
     return launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, s);
 }
 
@@ -613,11 +608,6 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         const char *mk = getenv("LBIB_MAIN_KERNEL");
         const bool want = mk && std::string(mk) == "slabs";
         c->slab_grid = want && lb_slab_supported(d, p->storage) ? lb_slab_grid(d, p->storage) : 0;
-        const bool rows = mk && std::string(mk) == "rows";
-        c->rows_R = !want && rows && lb_rows_supported(d, p->storage) ? std::max(1, env_int("LBIB_ROWS_PER_BLOCK", 4)) : 0;
-        c->rows_mode = std::min(3, std::max(1, env_int("LBIB_ROWS_MODE", 3)));
-        const bool nr = mk && (std::string(mk) == "rows2" || std::string(mk) == "rows4");
-        c->nrows = nr && lb_rows_supported(d, p->storage) ? (std::string(mk) == "rows4" ? 4 : 2) : 0;
     }
 
     // streams and events of the two-stream step; the IB stream gets the

@@ -458,15 +458,8 @@ __device__ __forceinline__ unsigned pack2_raw(float2 v) {
 // x-shifted directions of odd steps read the aligned word plus the one value
 // across its edge and reassemble with byte permutes, and write one value, an
 // aligned pair and one value.  The collision runs as two packed pairs.
-// STAGED: the 19 source row-planes were copied to shared memory beforehand
-// (`stage`, row i = the row-plane direction i is read from, all nx cells),
-// and the loads come from there.  OSTAGED: the results go to shared memory
-// instead (`ostage`, row j = the row-plane of slot j they are written to, all
-// nx cells, x-shifts applied with the row's periodic wrap), for the block to
-// write out as whole aligned words afterwards (flush_row).
-template <int ST, bool ODD, int FORCING, bool DET, bool MARKED, bool STAGED = false, bool OSTAGED = false>
-__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z,
-                                        const unsigned short *stage = nullptr, unsigned short *ostage = nullptr) {
+template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
+__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
     using T = unsigned short;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
     const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
@@ -479,19 +472,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
     uint2 raw[Q];  // cells x0..x0+3 of each direction, 2 values per word
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (STAGED) {
-            const T *pl = stage + i * nx;
-            const uint2 w = *reinterpret_cast<const uint2 *>(pl + x0);
-            if (!ODD || cx(i) == 0) {
-                raw[i] = w;
-            } else if (cx(i) > 0) {
-                const unsigned e = pl[xm];
-                raw[i] = make_uint2(__byte_perm(e, w.x, 0x5410), __byte_perm(w.x, w.y, 0x5432));
-            } else {
-                const unsigned e = pl[x4];
-                raw[i] = make_uint2(__byte_perm(w.x, w.y, 0x5432), __byte_perm(w.y, e, 0x5432));
-            }
-        } else if (ODD) {
+        if (ODD) {
             // direction i of cell x sits in slot opp(i) of cell x - c_i
             const int dy = -cy(i), dz = -cz(i);
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
@@ -546,19 +527,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned e = pack2_raw<ST>(d[i]);  // this pair's cells (x0 + 2h, x0 + 2h + 1)
-            if (OSTAGED) {
-                if (!ODD) {
-                    *reinterpret_cast<unsigned *>(ostage + opp(i) * nx + x0 + 2 * h) = e;
-                } else if (cx(i) == 0) {
-                    *reinterpret_cast<unsigned *>(ostage + i * nx + x0 + 2 * h) = e;
-                } else if (cx(i) > 0) {  // to cells x0 + 2h + 1, x0 + 2h + 2
-                    ostage[i * nx + x0 + 2 * h + 1] = (T)(e & 0xffffu);
-                    ostage[i * nx + (h ? x4 : x0 + 2)] = (T)(e >> 16);
-                } else {                 // to cells x0 + 2h - 1, x0 + 2h
-                    ostage[i * nx + (h ? x0 + 1 : xm)] = (T)(e & 0xffffu);
-                    ostage[i * nx + x0 + 2 * h] = (T)(e >> 16);
-                }
-            } else if (ODD) {
+            if (ODD) {
                 // direction i of cell x goes to slot i of cell x + c_i
                 const int dy = cy(i), dz = cz(i);
                 const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
@@ -612,37 +581,25 @@ __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
     __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), \
                       (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? ((ST) == LBIB_F32 ? 4 : LBIB_LB_PAIR16_MINB) : LBIB_LB_QUAD_MINB))
 template <int ST, bool ODD, int FORCING, int CPT>
-__device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, unsigned tx, unsigned y, unsigned z,
-                                             unsigned t = threadIdx.x) {
+__device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, unsigned tx, unsigned y, unsigned z) {
     // tiles stamped with this step's number are updated by k_lb_marked; gen[p]
     // is written before this launch and not again until it has finished
     if (c.marks[(ODD ? c.n_tiles : 0) + tile] == c.ctl->gen[ODD ? 1 : 0]) return;
-    const unsigned x = tx * c.tile_x + CPT * t;
+    const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
     bool ok = true;
-    if (CPT * t < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+    if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
         if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, y, z);
         else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, y, z);
         else ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, y, z);
     }
     report_bad(c, !ok);
-    if (c.n_nodes == 0 && tile == 0 && t == 0) c.ctl->step += 1;  // no IB chain to advance it
+    if (c.n_nodes == 0 && tile == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
 }
 
 template <int ST, bool ODD, int FORCING, int CPT>
 __global__ void LBIB_LB_BOUNDS_ST(ST, CPT) k_lb_main(const DevCtx c) {
     const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
-}
-
-// Whole rows of 16-bit storage (tiles_x == 1, four cells per thread), NR
-// adjacent rows (y = NR * blockIdx.y + k) per block: the block's loads and
-// stores of each row-plane cover NR * nx * 2 contiguous bytes.
-template <int ST, bool ODD, int FORCING, int NR>
-__global__ void __launch_bounds__(LB_TPB / 4 * NR, LBIB_LB_QUAD_MINB / NR) k_lb_main_nrows(const DevCtx c) {
-    const unsigned tt = blockDim.x / NR;  // threads per row, a multiple of 32
-    const unsigned k = threadIdx.x / tt, y = NR * blockIdx.y + k, z = blockIdx.z;
-    if (y >= (unsigned)c.ny) return;       // whole warps: tt is a multiple of 32
-    lb_main_body<ST, ODD, FORCING, 4>(c, y + c.ny * z, 0, y, z, threadIdx.x - k * tt);
 }
 
 // ---------------------------------------------------------------- TMA-staged slabs
@@ -909,105 +866,6 @@ __global__ void __launch_bounds__(SLAB_THREADS, LBIB_SLAB_MINB) k_lb_slab(const 
 }
 
 // The marked tiles of this parity's list: a persistent grid walks the list.
-// ---------------------------------------------------------------- staged rows (16-bit)
-// Whole rows (tile_x == nx, four cells per thread): a block updates R
-// consecutive rows.  While it collides row k it has the 19 source row-planes
-// of row k + 1 in flight as asynchronous 8-byte copies into shared memory
-// (two stages), so every warp keeps loads outstanding during its arithmetic
-// instead of alternating between waiting and computing.  Each thread copies
-// the words of its own four cells; the x-shifted directions of odd steps take
-// one value across the word's edge from a neighbour's copy, visible after the
-// block barrier.  Rows stamped for this step are skipped (k_lb_marked).
-#ifndef LBIB_ROWS_MINB
-#define LBIB_ROWS_MINB 8
-#endif
-
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// copy the words of cells x0..x0+3 of the 19 row-planes row r reads into stage
-template <bool ODD>
-__device__ __forceinline__ void stage_row(const DevCtx &c, unsigned short *stage, unsigned r, unsigned x0) {
-    const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
-    const unsigned y = r % ny, z = r / ny;
-    const unsigned rm = (y ? y - 1 : ny - 1) * nx, r0 = y * nx, rp = ((y + 1 == ny) ? 0 : y + 1) * nx;
-    const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
-    const unsigned short *P = reinterpret_cast<const unsigned short *>(c.pops);
-    const size_t Np = (size_t)c.Npad;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        // odd steps: direction i of cell x sits in slot opp(i) of cell x - c_i
-        const int dy = ODD ? -cy(i) : 0, dz = ODD ? -cz(i) : 0;
-        const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
-        cp_async8(stage + i * nx + x0, P + (size_t)(ODD ? opp(i) : i) * Np + row + x0);
-    }
-}
-
-// write the block's staged results of row r (row j = slot j's destination
-// row-plane) to global memory, 8 aligned bytes per thread and slot
-template <bool ODD>
-__device__ __forceinline__ void flush_row(const DevCtx &c, const unsigned short *ostage, unsigned r, unsigned x0) {
-    const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
-    const unsigned y = r % ny, z = r / ny;
-    const unsigned rm = (y ? y - 1 : ny - 1) * nx, r0 = y * nx, rp = ((y + 1 == ny) ? 0 : y + 1) * nx;
-    const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
-    unsigned short *P = reinterpret_cast<unsigned short *>(c.pops);
-    const size_t Np = (size_t)c.Npad;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        // odd steps: slot j of cell x + c_j; even steps: slot j of the cell itself
-        const int dy = ODD ? cy(j) : 0, dz = ODD ? cz(j) : 0;
-        const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
-        *reinterpret_cast<uint2 *>(P + (size_t)j * Np + row + x0) = *reinterpret_cast<const uint2 *>(ostage + j * nx + x0);
-    }
-}
-
-// MODE bit 0: loads staged (cp.async, next row in flight); bit 1: results
-// staged in shared memory and written as whole aligned words
-template <int ST, bool ODD, int FORCING, int MODE>
-__global__ void __launch_bounds__(LB_TPB / 4, LBIB_ROWS_MINB) k_lb_rows(const DevCtx c, int R) {
-    constexpr bool IN = (MODE & 1) != 0, OUT = (MODE & 2) != 0;
-    extern __shared__ __align__(16) unsigned char rows_smem[];
-    unsigned short *stage = reinterpret_cast<unsigned short *>(rows_smem);
-    const unsigned nx = c.nx, ny = c.ny, rows = c.ny * c.nz;
-    unsigned short *ostage = stage + (IN ? 2 : 0) * Q * nx;
-    const unsigned x0 = 4 * threadIdx.x;
-    const bool mine = x0 < nx;
-    // tiles stamped with this step's number belong to k_lb_marked; one tile per row
-    const int gen = c.ctl->gen[ODD ? 1 : 0];
-    const int *marks = c.marks + (ODD ? c.n_tiles : 0);
-    const unsigned r_end = min(rows, (unsigned)(blockIdx.x + 1) * (unsigned)R);
-    unsigned r = blockIdx.x * (unsigned)R;
-    while (r < r_end && marks[r] == gen) ++r;
-    if (IN) {
-        if (r < r_end && mine) stage_row<ODD>(c, stage, r, x0);
-        cp_async_commit();
-    }
-    bool ok = true;
-    for (unsigned k = 0; r < r_end; ++k) {
-        unsigned rn = r + 1;
-        while (rn < r_end && marks[rn] == gen) ++rn;
-        if (IN) {
-            if (rn < r_end && mine) stage_row<ODD>(c, stage + ((k + 1) & 1) * Q * nx, rn, x0);
-            cp_async_commit();
-            cp_async_wait1();  // this thread's copies of row r have landed
-            __syncthreads();   // and every other thread's
-        }
-        if (mine) ok &= lb_quad<ST, ODD, FORCING, false, false, IN, OUT>(c, x0, r % ny, r / ny, stage + (k & 1) * Q * nx, ostage);
-        if (OUT) {
-            __syncthreads();   // every value of the row's destination words is staged
-            if (mine) flush_row<ODD>(c, ostage, r, x0);
-        }
-        if (IN || OUT) __syncthreads();  // the stages are refilled in the next iteration
-        r = rn;
-    }
-    report_bad(c, !ok);
-    if (c.n_nodes == 0 && blockIdx.x == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
-}
-
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nblk) {
     const int p = ODD ? 1 : 0;
@@ -1279,71 +1137,6 @@ int lb_slab_grid(const DevCtx &c, int storage) {
     const int R = slab_rows(c.nx, c.ny, es);
     const int slabs = R ? (c.ny / R) * c.nz : 0;
     return std::min(slabs, sms * per);
-}
-
-template <int ST, int FORCING>
-static void rows_dispatch(const DevCtx &c, bool odd, int R, int mode, cudaStream_t s, cudaError_t *e) {
-    if constexpr (ST == LBIB_F32) {
-        *e = cudaErrorInvalidValue;  // 16-bit storage only
-    } else {
-        const unsigned rows = (unsigned)c.ny * (unsigned)c.nz;
-        const unsigned grid = (rows + (unsigned)R - 1) / (unsigned)R;
-        const size_t row = (size_t)Q * (size_t)c.nx * sizeof(unsigned short);
-        const size_t smem = ((mode & 1) ? 2 : 0) * row + ((mode & 2) ? 1 : 0) * row;
-        const unsigned T = tile_threads(c);
-        switch (mode) {
-        case 1:
-            if (odd) k_lb_rows<ST, true, FORCING, 1><<<grid, T, smem, s>>>(c, R);
-            else k_lb_rows<ST, false, FORCING, 1><<<grid, T, smem, s>>>(c, R);
-            break;
-        case 2:
-            if (odd) k_lb_rows<ST, true, FORCING, 2><<<grid, T, smem, s>>>(c, R);
-            else k_lb_rows<ST, false, FORCING, 2><<<grid, T, smem, s>>>(c, R);
-            break;
-        default:
-            if (odd) k_lb_rows<ST, true, FORCING, 3><<<grid, T, smem, s>>>(c, R);
-            else k_lb_rows<ST, false, FORCING, 3><<<grid, T, smem, s>>>(c, R);
-        }
-        *e = cudaGetLastError();
-    }
-}
-
-bool lb_rows_supported(const DevCtx &c, int storage) {
-    return storage != LBIB_F32 && c.cells_per_thread == 4 && c.tiles_x == 1 && c.tile_x == c.nx && c.nx % 4 == 0 &&
-           c.nx <= LB_TPB;
-}
-
-cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int R, int mode, cudaStream_t s) {
-    if (R < 1 || mode < 1 || mode > 3) return cudaErrorInvalidValue;
-    cudaError_t e = cudaSuccess;
-    LBIB_DISPATCH(rows_dispatch, storage, forcing, c, odd, R, mode, s, &e);
-    return e;
-}
-
-template <int ST, int FORCING>
-static void nrows_dispatch(const DevCtx &c, bool odd, int nr, cudaStream_t s, cudaError_t *e) {
-    if constexpr (ST == LBIB_F32) {
-        *e = cudaErrorInvalidValue;  // 16-bit storage only
-    } else {
-        const unsigned T = tile_threads(c);
-        if (nr == 4) {
-            const dim3 g(1, ((unsigned)c.ny + 3) / 4, (unsigned)c.nz);
-            if (odd) k_lb_main_nrows<ST, true, FORCING, 4><<<g, 4 * T, 0, s>>>(c);
-            else k_lb_main_nrows<ST, false, FORCING, 4><<<g, 4 * T, 0, s>>>(c);
-        } else {
-            const dim3 g(1, ((unsigned)c.ny + 1) / 2, (unsigned)c.nz);
-            if (odd) k_lb_main_nrows<ST, true, FORCING, 2><<<g, 2 * T, 0, s>>>(c);
-            else k_lb_main_nrows<ST, false, FORCING, 2><<<g, 2 * T, 0, s>>>(c);
-        }
-        *e = cudaGetLastError();
-    }
-}
-
-cudaError_t launch_lb_nrows(const DevCtx &c, int storage, int forcing, bool odd, int nr, cudaStream_t s) {
-    if (nr != 2 && nr != 4) return cudaErrorInvalidValue;
-    cudaError_t e = cudaSuccess;
-    LBIB_DISPATCH(nrows_dispatch, storage, forcing, c, odd, nr, s, &e);
-    return e;
 }
 
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s) {

@@ -220,13 +220,6 @@ cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, 
 bool lb_slab_supported(const DevCtx &c, int storage);
 int lb_slab_grid(const DevCtx &c, int storage);  // persistent grid size (0: cannot run)
 cudaError_t launch_lb_slab(const DevCtx &c, int storage, int forcing, bool odd, int grid, cudaStream_t s);
-// 16-bit storage, whole rows, R rows per block; mode bit 0: the next row's
-// loads staged asynchronously in shared memory while the current row
-// collides; bit 1: results staged in shared memory, written as aligned words
-bool lb_rows_supported(const DevCtx &c, int storage);
-// 16-bit storage, whole rows, nr (2 or 4) adjacent rows per block (lb_rows_supported)
-cudaError_t launch_lb_nrows(const DevCtx &c, int storage, int forcing, bool odd, int nr, cudaStream_t s);
-cudaError_t launch_lb_rows(const DevCtx &c, int storage, int forcing, bool odd, int R, int mode, cudaStream_t s);
 cudaError_t launch_lb_marked(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
 cudaError_t launch_lb_macros(const DevCtx &c, int storage, bool odd, float *rho, float *u, cudaStream_t s);
 cudaError_t launch_lb_batch(const BatchDev &bt, int storage, int forcing, int det, bool marked, bool odd, cudaStream_t s);
