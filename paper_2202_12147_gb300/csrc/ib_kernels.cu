@@ -467,94 +467,95 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
     interp_body<KW, ADVECT>(c, blockIdx.x, gridDim.x, vel_out, mark_parity);
 }
 
-// Observables: one block per swimmer, FP64 reductions in a fixed order.
-__global__ void __launch_bounds__(PREP_TPB) k_swimmer_state(const DevCtx c, int init) {
-    __shared__ double sm[96];
-    const int s = blockIdx.x;
+// Observables, part 1: one block per (swimmer, bead), sums in a fixed order.
+// The centre is the FP64 mean of the node positions; velocities, forces and
+// torques are summed in FP32 like the FP32 node data they come from (the
+// lever arms r_j - R_b are taken in FP64 first).
+__global__ void __launch_bounds__(PREP_TPB) k_swimmer_beads(const DevCtx c) {
+    __shared__ double smd[96];
+    __shared__ float smf[96];
+    const int s = blockIdx.x / 3, q = blockIdx.x % 3;
     const SwimDev sw = c.swims[s];
     lbib_swimmer_state *st = c.sw_state + s;
-    double xcm[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < 3; ++q) {
-        const BeadDev bd = c.beads[sw.bead[q]];
-        const int j0 = bd.node_start, j1 = bd.node_start + bd.node_count;
-        const double inv = 1.0 / bd.node_count;
-        double a = 0.0, b = 0.0, cc = 0.0;
-        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            a += c.rx[j];
-            b += c.ry[j];
-            cc += c.rz[j];
-        }
-        block_sum3(a, b, cc, sm);
-        const double R0 = a * inv, R1 = b * inv, R2 = cc * inv;
-        double va = 0.0, vb = 0.0, vc = 0.0;
-        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            const float4 v = c.node_vel[j];
-            va += v.x;
-            vb += v.y;
-            vc += v.z;
-        }
-        block_sum3(va, vb, vc, sm);
-        double fa = 0.0, fb = 0.0, fc = 0.0, ta = 0.0, tb = 0.0, tc = 0.0;
-        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            const float4 f = c.node_force[j];
-            const double dx = c.rx[j] - R0, dy = c.ry[j] - R1, dz = c.rz[j] - R2;
-            fa += f.x;
-            fb += f.y;
-            fc += f.z;
-            ta += dy * f.z - dz * f.y;
-            tb += dz * f.x - dx * f.z;
-            tc += dx * f.y - dy * f.x;
-        }
-        block_sum3(fa, fb, fc, sm);
-        block_sum3(ta, tb, tc, sm);
-        if (threadIdx.x == 0) {
-            st->R[q][0] = R0;
-            st->R[q][1] = R1;
-            st->R[q][2] = R2;
-            st->V[q][0] = va * inv;
-            st->V[q][1] = vb * inv;
-            st->V[q][2] = vc * inv;
-            st->F[q][0] = fa;
-            st->F[q][1] = fb;
-            st->F[q][2] = fc;
-            st->T[q][0] = ta;
-            st->T[q][1] = tb;
-            st->T[q][2] = tc;
-        }
-        xcm[0] += R0;
-        xcm[1] += R1;
-        xcm[2] += R2;
+    const BeadDev bd = c.beads[sw.bead[q]];
+    const int j0 = bd.node_start, j1 = bd.node_start + bd.node_count;
+    const double inv = 1.0 / bd.node_count;
+    double a = 0.0, b = 0.0, cc = 0.0;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        a += c.rx[j];
+        b += c.ry[j];
+        cc += c.rz[j];
     }
+    block_sum3(a, b, cc, smd);
+    const double R0 = a * inv, R1 = b * inv, R2 = cc * inv;
+    float va = 0.f, vb = 0.f, vc = 0.f, fa = 0.f, fb = 0.f, fc = 0.f, ta = 0.f, tb = 0.f, tc = 0.f;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        const float4 v = c.node_vel[j];
+        const float4 f = c.node_force[j];
+        const float dx = (float)(c.rx[j] - R0), dy = (float)(c.ry[j] - R1), dz = (float)(c.rz[j] - R2);
+        va += v.x;
+        vb += v.y;
+        vc += v.z;
+        fa += f.x;
+        fb += f.y;
+        fc += f.z;
+        ta += dy * f.z - dz * f.y;
+        tb += dz * f.x - dx * f.z;
+        tc += dx * f.y - dy * f.x;
+    }
+    block_sum3(va, vb, vc, smf);
+    block_sum3(fa, fb, fc, smf);
+    block_sum3(ta, tb, tc, smf);
     if (threadIdx.x == 0) {
-        st->step = c.ctl->step;
-        double *rec = c.sw_period + 8 * s;
-        for (int a = 0; a < 3; ++a) {
-            const double x = xcm[a] / 3.0;
-            st->x_cm[a] = x;
-            if (init) {
-                c.xcm0[3 * s + a] = x;
-                rec[a] = rec[3 + a] = x;  // t = 0 is the first period boundary
-            }
-            st->disp[a] = x - c.xcm0[3 * s + a];
-        }
-        if (init) rec[6] = 0.0;
-        // period-averaged swimming velocity (Sec. 3, Eq. vel_swim) and the
-        // Reynolds numbers with nu = (tau - 1/2)/3 and a the rest radius
-        st->periods = (long long)rec[6];
-        const double nu = ((double)c.tau - 0.5) / 3.0;
-        double vv = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            st->v_period[a] = rec[6] >= 1.0 ? (rec[a] - rec[3 + a]) / sw.period : 0.0;
-            vv += st->v_period[a] * st->v_period[a];
-        }
-        const double rad = (double)c.beads[sw.bead[0]].reach - 1.0;
-        double ls2 = 0.0, vb = 0.0;
-        for (int a = 0; a < 3; ++a) ls2 += (st->R[2][a] - st->R[0][a]) * (st->R[2][a] - st->R[0][a]);
-        for (int q = 0; q < 3; ++q)
-            vb = fmax(vb, sqrt(st->V[q][0] * st->V[q][0] + st->V[q][1] * st->V[q][1] + st->V[q][2] * st->V[q][2]));
-        st->re_swim = sqrt(vv) * (sqrt(ls2) + 2.0 * rad) / nu;
-        st->re_bead = vb * rad / nu;
+        st->R[q][0] = R0;
+        st->R[q][1] = R1;
+        st->R[q][2] = R2;
+        st->V[q][0] = va * inv;
+        st->V[q][1] = vb * inv;
+        st->V[q][2] = vc * inv;
+        st->F[q][0] = fa;
+        st->F[q][1] = fb;
+        st->F[q][2] = fc;
+        st->T[q][0] = ta;
+        st->T[q][1] = tb;
+        st->T[q][2] = tc;
     }
+}
+
+// Observables, part 2: one thread per swimmer, from its three bead records.
+__global__ void k_swimmer_finish(const DevCtx c, int init) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.n_swimmers) return;
+    const SwimDev sw = c.swims[s];
+    lbib_swimmer_state *st = c.sw_state + s;
+    st->step = c.ctl->step;
+    double *rec = c.sw_period + 8 * s;
+    for (int a = 0; a < 3; ++a) {
+        const double x = (st->R[0][a] + st->R[1][a] + st->R[2][a]) / 3.0;
+        st->x_cm[a] = x;
+        if (init) {
+            c.xcm0[3 * s + a] = x;
+            rec[a] = rec[3 + a] = x;  // t = 0 is the first period boundary
+        }
+        st->disp[a] = x - c.xcm0[3 * s + a];
+    }
+    if (init) rec[6] = 0.0;
+    // period-averaged swimming velocity (Sec. 3, Eq. vel_swim) and the
+    // Reynolds numbers with nu = (tau - 1/2)/3 and a the rest radius
+    st->periods = (long long)rec[6];
+    const double nu = ((double)c.tau - 0.5) / 3.0;
+    double vv = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        st->v_period[a] = rec[6] >= 1.0 ? (rec[a] - rec[3 + a]) / sw.period : 0.0;
+        vv += st->v_period[a] * st->v_period[a];
+    }
+    const double rad = (double)c.beads[sw.bead[0]].reach - 1.0;
+    double ls2 = 0.0, vb = 0.0;
+    for (int a = 0; a < 3; ++a) ls2 += (st->R[2][a] - st->R[0][a]) * (st->R[2][a] - st->R[0][a]);
+    for (int q = 0; q < 3; ++q)
+        vb = fmax(vb, sqrt(st->V[q][0] * st->V[q][0] + st->V[q][1] * st->V[q][1] + st->V[q][2] * st->V[q][2]));
+    st->re_swim = sqrt(vv) * (sqrt(ls2) + 2.0 * rad) / nu;
+    st->re_bead = vb * rad / nu;
 }
 
 // ---------------------------------------------------------------- batches
@@ -670,7 +671,8 @@ cudaError_t launch_ib_mark(const DevCtx &c, int kernel, cudaStream_t s) {
 
 cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s) {
     if (c.n_swimmers == 0) return cudaSuccess;
-    k_swimmer_state<<<c.n_swimmers, PREP_TPB, 0, s>>>(c, init ? 1 : 0);
+    k_swimmer_beads<<<3 * c.n_swimmers, PREP_TPB, 0, s>>>(c);
+    k_swimmer_finish<<<(c.n_swimmers + 127) / 128, 128, 0, s>>>(c, init ? 1 : 0);
     return cudaGetLastError();
 }
 

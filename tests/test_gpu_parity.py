@@ -108,6 +108,45 @@ def test_node_forces_and_spread(perm, kernel):
     sim.close()
 
 
+def test_swimmer_state_forces_and_torques(perm):
+    """Per-bead observables after ib_spread at perturbed positions (t = 0).
+    F_b is the sum of the oracle's node forces over bead b; the membrane part
+    cancels (translation invariance of the energy), leaving the drive plus the
+    spring force of Sec. 2.2 from the oracle's own drive and springs
+    functions.  T_b = sum_j (r_j - R_b) x f_j vanishes up to rounding
+    (rotation invariance; the drive and spring shares are uniform over the
+    nodes and R_b is their mean)."""
+    box = _perturbed_swimmer_box()
+    asm = assemble(box)
+    sim = gpu_sim(box, asm)
+    r = perturbed_nodes(asm["nodes"], seed=4, amp=0.05)
+    sim.set_nodes(r)
+    sim.ib_spread()
+    st = sim.swimmer_state(0)
+    osim = oracle.OracleSim(box, asm)
+    osim.r = r.copy()
+    fo = osim.node_forces()
+    beads = asm["beads"]
+    sw = asm["swimmers"][0]
+    R = oracle.bead_centres(r, beads)
+    fd = oracle.drive(osim.drive[0, 0:3], osim.drive[0, 3:6], sw["balance"], sw["period"], 0.0)
+    fs = oracle.springs(sw["k"], sw["L"], R[sw["beads"]])
+    for q, b in enumerate(sw["beads"]):
+        n0, nn = beads[b][0], beads[b][1]
+        rj, fj = r[n0:n0 + nn], fo[n0:n0 + nn]
+        F_ref = fj.sum(0)
+        f_scale = np.abs(fj).sum()
+        assert np.abs(F_ref - (fd[q] + fs[q])).max() < 1e-12 * f_scale
+        T_ref = np.cross(rj - R[b], fj).sum(0)
+        t_scale = (np.linalg.norm(rj - R[b], axis=1) * np.linalg.norm(fj, axis=1)).sum()
+        assert np.abs(T_ref).max() < 1e-12 * t_scale
+        assert np.abs(np.asarray(st["R"][q]) - R[b]).max() < 1e-12
+        assert np.abs(np.asarray(st["F"][q]) - F_ref).max() < 1e-5 * f_scale
+        assert np.abs(np.asarray(st["T"][q]) - T_ref).max() < 1e-5 * t_scale
+    np.testing.assert_allclose(st["x_cm"], R[sw["beads"]].mean(0), rtol=0, atol=1e-12)
+    sim.close()
+
+
 @pytest.mark.parametrize("kernel", ["peskin4", "linear2"])
 def test_interpolate(perm, kernel):
     import torch
