@@ -574,12 +574,15 @@ __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
 #ifndef LBIB_LB_PAIR16_MINB
 #define LBIB_LB_PAIR16_MINB 4
 #endif
+#ifndef LBIB_LB_PAIR32_MINB
+#define LBIB_LB_PAIR32_MINB 4
+#endif
 #define LBIB_LB_BOUNDS(CPT) \
     __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? 4 : LBIB_LB_QUAD_MINB))
 // the same with the storage format: 16-bit two-cell threads need fewer registers
 #define LBIB_LB_BOUNDS_ST(ST, CPT) \
     __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), \
-                      (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? ((ST) == LBIB_F32 ? 4 : LBIB_LB_PAIR16_MINB) : LBIB_LB_QUAD_MINB))
+                      (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? ((ST) == LBIB_F32 ? LBIB_LB_PAIR32_MINB : LBIB_LB_PAIR16_MINB) : LBIB_LB_QUAD_MINB))
 template <int ST, bool ODD, int FORCING, int CPT>
 __device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, unsigned tx, unsigned y, unsigned z) {
     // tiles stamped with this step's number are updated by k_lb_marked; gen[p]
