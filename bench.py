@@ -449,7 +449,8 @@ def run_ours(a):
         barrier()
         ms = e0.elapsed_time(e1)
         # the same number of steps with CUDA events around every launch of
-        # the main fluid kernel (direct launches), for its roofline
+        # the main fluid kernel (the same graph schedule with event-record
+        # nodes), for its roofline
         for s in sims:
             s.profile(True)
         for s in sims:
@@ -586,8 +587,9 @@ def run_ours(a):
                        "tau": 1.0, "delta_kernel": "peskin4", "forcing": "guo",
                        "l2": "inputs larger than L2 (populations 318 MB per box in FP32)",
                        "timing": "value: lb_step over the timed steps (16-step CUDA graph replays, two streams); "
-                                 "roofline: the same number of steps right after, kernels launched one by one "
-                                 "with CUDA events around every main fluid-kernel launch"},
+                                 "roofline: the same number of steps right after, replaying the same 16-step graph "
+                                 "captured with an event-record node before and after every main fluid-kernel "
+                                 "launch"},
             "roofline": {"bound": "hbm", "kernel": "k_lb_main", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": K_LB_MAIN_F32_DRAM_BYTES if a.storage == "f32" else None,

@@ -246,10 +246,13 @@ int lb_get_force_field(lbib_ctx *ctx, float *host_F);
 /* Overwrite the velocity field u with HOST n_cells x 3 values. */
 int lb_set_velocity(lbib_ctx *ctx, const float *host_u);
 
-/* Timing hook.  With on = 1, lb_step launches its kernels one by one and
- * brackets every launch of the main fluid kernel (the update of every tile no
- * node stencil touches) with a pair of CUDA events on the context stream;
- * with on = 0 (the default) it replays captured graphs.  Switching on
+/* Timing hook.  With on = 1, every launch of the main fluid kernel (the
+ * update of every tile no node stencil touches) is bracketed by a pair of
+ * CUDA events on the context stream: lb_step replays a 16-step graph captured
+ * with an event-record node before and after each main-kernel launch (fresh
+ * events for every replay), and launches single steps one by one; with on =
+ * 0 (the default) it replays the plain graphs.  Switching on captures that
+ * graph the first time (LBIB_GRAPHS=0: launches one by one throughout) and
  * discards earlier measurements. */
 int lb_profile(lbib_ctx *ctx, int on);
 /* Sum of the bracketed fluid-kernel durations in milliseconds and the

@@ -217,6 +217,13 @@ struct lbib_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> ev;   // event pairs around fluid-kernel launches
     size_t ev_used = 0;
+    // the 16-step graph with an event-record node before and after every main
+    // fluid launch (timed replays of the production schedule); its nodes in
+    // capture order, re-pointed at fresh events for every replay
+    cudaGraph_t tgraph_src = nullptr;
+    cudaGraphExec_t tgraph = nullptr;
+    std::vector<cudaGraphNode_t> tnodes;
+    bool capturing_timed = false;
     Control *h_ctl = nullptr;      // pinned
     lbib_swimmer_state *h_sws = nullptr;  // pinned
     int n_nodes = 0, n_swimmers = 0;
@@ -262,7 +269,10 @@ cudaError_t timed_event(lbib_ctx *c, cudaStream_t s) {
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
         c->ev.push_back(ev);
     }
-    if ((e = cudaEventRecord(c->ev[c->ev_used], s)) != cudaSuccess) return e;
+    // inside the capture of the timed graph: an event-record node
+    if ((e = cudaEventRecordWithFlags(c->ev[c->ev_used], s, c->capturing_timed ? cudaEventRecordExternal : 0)) !=
+        cudaSuccess)
+        return e;
     c->ev_used += 1;
     return cudaSuccess;
 }
@@ -322,6 +332,66 @@ cudaError_t capture_steps(lbib_ctx *c, int p0, int n, cudaGraphExec_t *out) {
     if (ce == cudaSuccess) ce = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
     if (g) cudaGraphDestroy(g);
     return ce;
+}
+
+// Capture the timed 16-step graph (from an even step): the events of the
+// capture are ev[0 .. 2 * GRAPH_STEPS), and tnodes[k] is the node that records ev[k].
+cudaError_t capture_timed(lbib_ctx *c) {
+    cudaGraph_t g = nullptr;
+    c->ev_used = 0;
+    c->capturing_timed = true;
+    cudaError_t ce = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        ce = fork(c, c->cap, c->cap_ib);
+        for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k) ce = enqueue_step(c, (k & 1) != 0, c->cap, c->cap_ib, true);
+        if (ce == cudaSuccess) ce = join(c, c->cap);
+        const cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+        if (ce == cudaSuccess) ce = ee;
+    }
+    c->capturing_timed = false;
+    const size_t n_ev = c->ev_used;
+    c->ev_used = 0;
+    if (ce == cudaSuccess && n_ev == 0) ce = cudaErrorInvalidValue;  // no fluid launch to time
+    size_t n = 0;
+    if (ce == cudaSuccess) ce = cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (ce == cudaSuccess && n) ce = cudaGraphGetNodes(g, nodes.data(), &n);
+    c->tnodes.assign(n_ev, nullptr);
+    for (size_t i = 0; i < n && ce == cudaSuccess; ++i) {
+        cudaGraphNodeType t;
+        if ((ce = cudaGraphNodeGetType(nodes[i], &t)) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        if ((ce = cudaGraphEventRecordNodeGetEvent(nodes[i], &ev)) != cudaSuccess) break;
+        for (size_t k = 0; k < n_ev; ++k)
+            if (c->ev[k] == ev) c->tnodes[k] = nodes[i];
+    }
+    for (size_t k = 0; k < n_ev && ce == cudaSuccess; ++k)
+        if (!c->tnodes[k]) ce = cudaErrorInvalidValue;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiateWithFlags(&c->tgraph, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (ce == cudaSuccess) {
+        c->tgraph_src = g;
+    } else {
+        if (g) cudaGraphDestroy(g);
+        c->tnodes.clear();
+    }
+    return ce;
+}
+
+// Replay the timed graph with fresh events for this replay's launches.
+cudaError_t launch_timed(lbib_ctx *c) {
+    cudaError_t e;
+    const size_t n = c->tnodes.size();
+    while (c->ev.size() < c->ev_used + n) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+        c->ev.push_back(ev);
+    }
+    for (size_t k = 0; k < n; ++k)
+        if ((e = cudaGraphExecEventRecordNodeSetEvent(c->tgraph, c->tnodes[k], c->ev[c->ev_used + k])) != cudaSuccess)
+            return e;
+    if ((e = cudaGraphLaunch(c->tgraph, c->user)) != cudaSuccess) return e;
+    c->ev_used += n;
+    return cudaSuccess;
 }
 
 // Stamp the tiles of the current positions for the current step (after the
@@ -639,7 +709,15 @@ int lb_step(lbib_ctx *c, long long n) {
     bool forked = false;
     const bool graphs = use_graphs(c->L.N);
     while (n > 0) {
-        if (graphs && !c->profiling) {
+        if (graphs && c->profiling && c->tgraph && (c->step & 1) == 0 && n >= GRAPH_STEPS) {
+            if (forked) {
+                CU(join(c, c->user));
+                forked = false;
+            }
+            CU(launch_timed(c));
+            c->step += GRAPH_STEPS;
+            n -= GRAPH_STEPS;
+        } else if (graphs && !c->profiling) {
             // every graph forks and joins the two streams itself
             const bool whole = (c->step & 1) == 0 && n >= GRAPH_STEPS;
             CU(cudaGraphLaunch(whole ? c->graph : c->graph1[c->step & 1], c->user));
@@ -853,6 +931,8 @@ int lb_set_velocity(lbib_ctx *c, const float *h) {
 int lb_profile(lbib_ctx *c, int on) {
     if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
     CU(cudaStreamSynchronize(c->user));
+    // timed replays of the production graph when graphs are in use
+    if (on && !c->tgraph && !c->batch && use_graphs(c->L.N)) CU(capture_timed(c));
     c->profiling = on != 0;
     c->ev_used = 0;
     return LBIB_OK;
@@ -1012,6 +1092,8 @@ int lb_destroy(lbib_ctx *c) {
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->ib) cudaStreamSynchronize(c->ib);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->tgraph) cudaGraphExecDestroy(c->tgraph);
+    if (c->tgraph_src) cudaGraphDestroy(c->tgraph_src);
     for (cudaGraphExec_t g : c->graph1)
         if (g) cudaGraphExecDestroy(g);
     if (c->cap) cudaStreamDestroy(c->cap);

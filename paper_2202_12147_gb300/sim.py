@@ -225,7 +225,7 @@ class Simulation:
         check(self.L.lb_set_velocity(self.ctx, u.ctypes.data_as(ctypes.c_void_p)))
 
     def profile(self, on=True):
-        """Bracket every fluid-kernel launch with CUDA events (direct launches)."""
+        """Bracket every main fluid-kernel launch with CUDA events (lb_profile)."""
         check(self.L.lb_profile(self.ctx, 1 if on else 0))
 
     def profile_read(self):

@@ -121,3 +121,30 @@ def test_track_in_a_batch(gpu_lib):
     batch.close()
     for s in sims:
         s.close()
+
+
+def test_profiled_steps_match_plain_steps(gpu_lib):
+    """The timing hook (lb_profile): 16-step graph replays with event-record
+    nodes around the main fluid kernel, one-by-one launches for the rest.
+    Deterministic spreading: the state equals an unprofiled run's bitwise,
+    and every main-kernel launch is timed once."""
+    box = adjoint_small()
+    asm = assemble(box)
+    ref = gpu_sim(box, asm, deterministic=True)
+    ref.lb_step(37)
+    sim = gpu_sim(box, asm, deterministic=True)
+    sim.profile(True)
+    sim.lb_step(37)  # two timed replays, five single steps
+    ms, n = sim.profile_read()
+    assert n == 37 and ms > 0.0
+    sim.profile(True)  # discards the earlier measurements
+    sim.lb_step(16)
+    ms2, n2 = sim.profile_read()
+    assert n2 == 16 and 0.0 < ms2 < ms
+    sim.profile(False)
+    ref.lb_step(16)
+    assert (sim.get_nodes() == ref.get_nodes()).all()
+    assert (sim.get_populations() == ref.get_populations()).all()
+    assert (sim.track(53) == ref.track(53)).all()
+    ref.close()
+    sim.close()
