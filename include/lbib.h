@@ -171,10 +171,11 @@ int lbib_required_sizes(const lb_params *p, const lbib_structure *s, size_t *out
 int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, void *stream, lbib_ctx **out);
 
 /* Advance n_steps full coupled steps (1-7 above) asynchronously on the
- * context stream, replaying the captured CUDA graphs: 16 steps per replay
- * from an even step, one-step graphs for the rest.  The environment
- * variable LBIB_GRAPHS=0 launches every step's kernels directly instead; the
- * results are the same either way. */
+ * context stream, replaying the captured 16-step CUDA graph from even steps
+ * and launching the kernels of the remaining single steps directly (faster
+ * than a one-step graph replay).  The environment variable LBIB_GRAPHS=0
+ * launches every step's kernels directly; the results are the same either
+ * way. */
 int lb_step(lbib_ctx *ctx, long long n_steps);
 
 /* Steps 1-4 alone at the current positions and time: evaluate f^tot on every

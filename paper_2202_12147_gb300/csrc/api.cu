@@ -211,8 +211,7 @@ struct lbib_ctx {
     cudaStream_t cap = nullptr;    // private streams used only to capture graphs
     cudaStream_t cap_ib = nullptr;
     cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr;  // step-to-step dependencies
-    cudaGraphExec_t graph = nullptr;                 // GRAPH_STEPS steps from an even step
-    cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // one step from an even / odd step
+    cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS steps from an even step
     long long step = 0;            // host mirror of the device step counter
     bool profiling = false;
     std::vector<cudaEvent_t> ev;   // event pairs around fluid-kernel launches
@@ -692,11 +691,8 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         cudaEventCreateWithFlags(&c->e_ib, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "creating streams or events failed"));
 
-    // capture GRAPH_STEPS coupled steps (alternating AA parity) into one
-    // graph, and one step of either parity into two more
+    // capture GRAPH_STEPS coupled steps (alternating AA parity) into one graph
     cudaError_t ce = capture_steps(c, 0, GRAPH_STEPS, &c->graph);
-    if (ce == cudaSuccess) ce = capture_steps(c, 0, 1, &c->graph1[0]);
-    if (ce == cudaSuccess) ce = capture_steps(c, 1, 1, &c->graph1[1]);
     if (ce != cudaSuccess) return bail(fail(LBIB_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce)));
     *out = c;
     return LBIB_OK;
@@ -717,12 +713,14 @@ int lb_step(lbib_ctx *c, long long n) {
             CU(launch_timed(c));
             c->step += GRAPH_STEPS;
             n -= GRAPH_STEPS;
-        } else if (graphs && !c->profiling) {
-            // every graph forks and joins the two streams itself
-            const bool whole = (c->step & 1) == 0 && n >= GRAPH_STEPS;
-            CU(cudaGraphLaunch(whole ? c->graph : c->graph1[c->step & 1], c->user));
-            c->step += whole ? GRAPH_STEPS : 1;
-            n -= whole ? GRAPH_STEPS : 1;
+        } else if (graphs && !c->profiling && (c->step & 1) == 0 && n >= GRAPH_STEPS) {
+            if (forked) {
+                CU(join(c, c->user));
+                forked = false;
+            }
+            CU(cudaGraphLaunch(c->graph, c->user));
+            c->step += GRAPH_STEPS;
+            n -= GRAPH_STEPS;
         } else {
             if (!forked) {
                 CU(fork(c, c->user, c->ib));
@@ -1094,8 +1092,6 @@ int lb_destroy(lbib_ctx *c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->tgraph) cudaGraphExecDestroy(c->tgraph);
     if (c->tgraph_src) cudaGraphDestroy(c->tgraph_src);
-    for (cudaGraphExec_t g : c->graph1)
-        if (g) cudaGraphExecDestroy(g);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->cap_ib) cudaStreamDestroy(c->cap_ib);
     if (c->ib) cudaStreamDestroy(c->ib);

@@ -32,8 +32,8 @@ def _oracle_track(box, asm, steps):
 
 
 def test_track_matches_oracle_every_step(gpu_lib):
-    """24 steps (one 16-step graph, then eight one-step graphs of alternating
-    parity): every step's bead centres, bead velocities and x_cm."""
+    """24 steps (one 16-step graph replay, then eight single steps of
+    alternating parity): every step's bead centres, bead velocities and x_cm."""
     box = adjoint_small()
     asm = assemble(box)
     steps = 24
@@ -58,7 +58,7 @@ def test_track_matches_oracle_every_step(gpu_lib):
 
 def test_track_same_for_every_launch_path(gpu_lib, monkeypatch):
     """Deterministic spreading: one call of 40 steps (graph replays), 40 calls
-    of one step (one-step graphs) and direct launches give bitwise equal
+    of one step (direct launches) and LBIB_GRAPHS=0 give bitwise equal
     trajectories."""
     box = adjoint_small()
     asm = assemble(box)
