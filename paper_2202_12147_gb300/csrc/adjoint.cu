@@ -35,6 +35,8 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "lbib_internal.cuh"
 
 using namespace lbib;
@@ -143,6 +145,25 @@ __device__ __forceinline__ void group_sum3(double v[3], double (*sh)[3], double 
 }
 
 constexpr int SWIM_THREADS = 768;  // three groups of 256: one per bead
+constexpr int BEAD_THREADS = 256;  // one block of a swimmer's three-block cluster: one bead
+
+// The same fixed-order sum as one 256-thread group of group_sum3: warp sums,
+// then warp 0 adds the 8 warp sums in order.  Result in out[3].
+__device__ __forceinline__ void bead_sum3(double v[3], double (*sh)[3], double *out) {
+    for (int a = 0; a < 3; ++a) v[a] = warp_sum(v[a]);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int a = 0; a < 3; ++a) sh[w][a] = v[a];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int a = 0; a < 3; ++a) {
+            double x = l < 8 ? sh[l][a] : 0.0;
+            x = warp_sum(x);
+            if (l == 0) out[a] = x;
+        }
+    }
+    __syncthreads();
+}
 
 // ---------------------------------------------------------------- membrane
 // Neo-Hookean linear FEM triangle (Sec. 2.2): with edge vectors d = [d1 d2],
@@ -216,50 +237,60 @@ __device__ __forceinline__ void tri_force_jvp(const double *G, const TriState &S
 
 // ---------------------------------------------------------------- forward kernels
 
-// one block per swimmer, one 256-thread group per bead: bead centres (FP64),
-// then drive and spring forces (thread 0)
-__global__ void __launch_bounds__(SWIM_THREADS) k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta,
-                                                              const double *r, const long long *t_base, int k,
-                                                              double *R, double *ext) {
-    __shared__ double sh[SWIM_THREADS / 32][3];
-    __shared__ double Rs[3][3];
+// one cluster of three blocks per swimmer, block q summing the positions of
+// bead q (FP64, fixed order); block 0 reads the three centres from the
+// blocks' shared memory (distributed shared memory) and evaluates the drive
+// and spring forces (thread 0)
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
+    k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta, const double *r, const long long *t_base, int k,
+                  double *R, double *ext) {
+    namespace cg = cooperative_groups;
+    __shared__ double sh[BEAD_THREADS / 32][3];
+    __shared__ double Rq[3];
+    cg::cluster_group cl = cg::this_cluster();
     const double t = (double)(*t_base + k);
-    const int s = blockIdx.x, q = threadIdx.x >> 8, tq = threadIdx.x & 255;
+    const int s = blockIdx.x / 3, q = (int)cl.block_rank();
     const Swim w = sw[s];
     {
         const int b = w.bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
         double acc[3] = {0.0, 0.0, 0.0};
-        for (int j = n0 + tq; j < n0 + nn; j += 256)
+        for (int j = n0 + threadIdx.x; j < n0 + nn; j += BEAD_THREADS)
             for (int a = 0; a < 3; ++a) acc[a] += r[3 * j + a];
-        group_sum3(acc, sh, Rs);
-    }
-    if (threadIdx.x < 9) {
-        const int qq = threadIdx.x / 3, a = threadIdx.x % 3, b = w.bead[qq];
-        Rs[qq][a] /= m.bead_count[b];
-        R[3 * b + a] = Rs[qq][a];
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double om = 2.0 * 3.14159265358979323846 / w.period;
-    const double *th = theta + 6 * s;
-    double fd[3];
-    fd[0] = th[0] * sin(om * t + th[3]);
-    fd[2] = th[2] * sin(om * t + th[5]);
-    fd[1] = w.balance ? -fd[0] - fd[2] : th[1] * sin(om * t + th[4]);
-    double fs[3][3];
-    for (int side = 0; side < 2; ++side) {
-        const int qq = side ? 2 : 0;
-        double dd[3], n2 = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            dd[a] = Rs[qq][a] - Rs[1][a];
-            n2 += dd[a] * dd[a];
+        bead_sum3(acc, sh, Rq);
+        if (threadIdx.x < 3) {
+            Rq[threadIdx.x] /= nn;
+            R[3 * b + threadIdx.x] = Rq[threadIdx.x];
         }
-        const double n = sqrt(n2);
-        for (int a = 0; a < 3; ++a) fs[qq][a] = -w.k * (n - w.L) * dd[a] / n;
     }
-    for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
-    for (int qq = 0; qq < 3; ++qq)
-        for (int a = 0; a < 3; ++a) ext[3 * w.bead[qq] + a] = fs[qq][a] + (a == 0 ? fd[qq] : 0.0);
+    cl.sync();
+    if (q == 0 && threadIdx.x == 0) {
+        double Rs[3][3];
+        for (int qq = 0; qq < 3; ++qq) {
+            const double *p = cl.map_shared_rank(Rq, qq);
+            for (int a = 0; a < 3; ++a) Rs[qq][a] = p[a];
+        }
+        const double om = 2.0 * 3.14159265358979323846 / w.period;
+        const double *th = theta + 6 * s;
+        double fd[3];
+        fd[0] = th[0] * sin(om * t + th[3]);
+        fd[2] = th[2] * sin(om * t + th[5]);
+        fd[1] = w.balance ? -fd[0] - fd[2] : th[1] * sin(om * t + th[4]);
+        double fs[3][3];
+        for (int side = 0; side < 2; ++side) {
+            const int qq = side ? 2 : 0;
+            double dd[3], n2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                dd[a] = Rs[qq][a] - Rs[1][a];
+                n2 += dd[a] * dd[a];
+            }
+            const double n = sqrt(n2);
+            for (int a = 0; a < 3; ++a) fs[qq][a] = -w.k * (n - w.L) * dd[a] / n;
+        }
+        for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
+        for (int qq = 0; qq < 3; ++qq)
+            for (int a = 0; a < 3; ++a) ext[3 * w.bead[qq] + a] = fs[qq][a] + (a == 0 ? fd[qq] : 0.0);
+    }
+    cl.sync();  // the blocks' shared memory outlives block 0's reads
 }
 
 // one thread per triangle: corner forces -dW/dr
@@ -703,66 +734,76 @@ __global__ void k_adj_tri(Mesh m, const double *r, const double *lam_fn, double 
         for (int a = 0; a < 3; ++a) tri_adj[9 * t + 3 * q + a] = df[q][a];
 }
 
-// one block per swimmer, one 256-thread group per bead: lam_e_b = mean over
-// bead b of lam_fj; then (thread 0) the drive-parameter gradient and the
-// transpose of the spring forces -> lam_R
-__global__ void __launch_bounds__(SWIM_THREADS) k_adj_swimmer(Mesh m, const Swim *sw, const double *theta,
-                                                              const double *R, const double *lam_fn,
-                                                              const long long *t_base, int k, double *lam_R,
-                                                              double *grad) {
-    __shared__ double sh[SWIM_THREADS / 32][3];
-    __shared__ double le[3][3];
+// one cluster of three blocks per swimmer, block q summing lam_fj over bead
+// q; block 0 reads the three sums from the blocks' shared memory and
+// (thread 0) forms lam_e_b = the mean over bead b, the drive-parameter
+// gradient and the transpose of the spring forces -> lam_R
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
+    k_adj_swimmer(Mesh m, const Swim *sw, const double *theta, const double *R, const double *lam_fn,
+                  const long long *t_base, int k, double *lam_R, double *grad) {
+    namespace cg = cooperative_groups;
+    __shared__ double sh[BEAD_THREADS / 32][3];
+    __shared__ double lq[3];
+    cg::cluster_group cl = cg::this_cluster();
     const double t = (double)(*t_base + k);
-    const int s = blockIdx.x, q = threadIdx.x >> 8, tq = threadIdx.x & 255;
+    const int s = blockIdx.x / 3, q = (int)cl.block_rank();
     const Swim w = sw[s];
     {
         const int b = w.bead[q], n0 = m.bead_start[b], nn = m.bead_count[b];
         double acc[3] = {0.0, 0.0, 0.0};
-        for (int j = n0 + tq; j < n0 + nn; j += 256)
+        for (int j = n0 + threadIdx.x; j < n0 + nn; j += BEAD_THREADS)
             for (int a = 0; a < 3; ++a) acc[a] += lam_fn[3 * j + a];
-        group_sum3(acc, sh, le);
+        bead_sum3(acc, sh, lq);
     }
-    if (threadIdx.x != 0) return;
-    for (int qq = 0; qq < 3; ++qq)
-        for (int a = 0; a < 3; ++a) le[qq][a] /= m.bead_count[w.bead[qq]];
-    // drive: f_q = A_q sin(om t + phi_q) along x (balance: f_1 = -f_0 - f_2)
-    const double om = 2.0 * 3.14159265358979323846 / w.period;
-    const double *th = theta + 6 * s;
-    double sens[3];
-    if (w.balance) {
-        sens[0] = le[0][0] - le[1][0];
-        sens[1] = 0.0;
-        sens[2] = le[2][0] - le[1][0];
-    } else {
-        for (int qq = 0; qq < 3; ++qq) sens[qq] = le[qq][0];
-    }
-    for (int qq = 0; qq < 3; ++qq) {
-        if (w.balance && qq == 1) continue;
-        const double arg = om * t + th[3 + qq];
-        grad[6 * s + qq] += sin(arg) * sens[qq];
-        grad[6 * s + 3 + qq] += th[qq] * cos(arg) * sens[qq];
-    }
-    // springs: f_0 = h(R_0 - R_1), f_2 = h(R_2 - R_1), f_1 = -f_0 - f_2 with
-    // h(d) = -k (|d| - L) d/|d|, dh/dd = -k [(1 - L/|d|) I + (L/|d|) dhat dhat^T]
-    double lR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int side = 0; side < 2; ++side) {
-        const int qq = side ? 2 : 0;
-        double dd[3], n2 = 0.0, lv[3];
-        for (int a = 0; a < 3; ++a) {
-            dd[a] = R[3 * w.bead[qq] + a] - R[3 * w.bead[1] + a];
-            n2 += dd[a] * dd[a];
-            lv[a] = le[qq][a] - le[1][a];
+    cl.sync();
+    if (q == 0 && threadIdx.x == 0) {
+        double le[3][3];
+        for (int qq = 0; qq < 3; ++qq) {
+            const double *p = cl.map_shared_rank(lq, qq);
+            for (int a = 0; a < 3; ++a) le[qq][a] = p[a];
         }
-        const double n = sqrt(n2), c1 = 1.0 - w.L / n, c2 = w.L / (n * n2);
-        const double dl = dd[0] * lv[0] + dd[1] * lv[1] + dd[2] * lv[2];
-        for (int a = 0; a < 3; ++a) {
-            const double ld = -w.k * (c1 * lv[a] + c2 * dd[a] * dl);
-            lR[qq][a] += ld;
-            lR[1][a] -= ld;
+        for (int qq = 0; qq < 3; ++qq)
+            for (int a = 0; a < 3; ++a) le[qq][a] /= m.bead_count[w.bead[qq]];
+        // drive: f_q = A_q sin(om t + phi_q) along x (balance: f_1 = -f_0 - f_2)
+        const double om = 2.0 * 3.14159265358979323846 / w.period;
+        const double *th = theta + 6 * s;
+        double sens[3];
+        if (w.balance) {
+            sens[0] = le[0][0] - le[1][0];
+            sens[1] = 0.0;
+            sens[2] = le[2][0] - le[1][0];
+        } else {
+            for (int qq = 0; qq < 3; ++qq) sens[qq] = le[qq][0];
         }
+        for (int qq = 0; qq < 3; ++qq) {
+            if (w.balance && qq == 1) continue;
+            const double arg = om * t + th[3 + qq];
+            grad[6 * s + qq] += sin(arg) * sens[qq];
+            grad[6 * s + 3 + qq] += th[qq] * cos(arg) * sens[qq];
+        }
+        // springs: f_0 = h(R_0 - R_1), f_2 = h(R_2 - R_1), f_1 = -f_0 - f_2 with
+        // h(d) = -k (|d| - L) d/|d|, dh/dd = -k [(1 - L/|d|) I + (L/|d|) dhat dhat^T]
+        double lR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int side = 0; side < 2; ++side) {
+            const int qq = side ? 2 : 0;
+            double dd[3], n2 = 0.0, lv[3];
+            for (int a = 0; a < 3; ++a) {
+                dd[a] = R[3 * w.bead[qq] + a] - R[3 * w.bead[1] + a];
+                n2 += dd[a] * dd[a];
+                lv[a] = le[qq][a] - le[1][a];
+            }
+            const double n = sqrt(n2), c1 = 1.0 - w.L / n, c2 = w.L / (n * n2);
+            const double dl = dd[0] * lv[0] + dd[1] * lv[1] + dd[2] * lv[2];
+            for (int a = 0; a < 3; ++a) {
+                const double ld = -w.k * (c1 * lv[a] + c2 * dd[a] * dl);
+                lR[qq][a] += ld;
+                lR[1][a] -= ld;
+            }
+        }
+        for (int qq = 0; qq < 3; ++qq)
+            for (int a = 0; a < 3; ++a) lam_R[3 * w.bead[qq] + a] = lR[qq][a];
     }
-    for (int qq = 0; qq < 3; ++qq)
-        for (int a = 0; a < 3; ++a) lam_R[3 * w.bead[qq] + a] = lR[qq][a];
+    cl.sync();  // the blocks' shared memory outlives block 0's reads
 }
 
 // one thread per node: lam_r_j += sum of its corners' membrane terms + lam_R_b / N_b
@@ -907,7 +948,8 @@ struct lbib_adjoint {
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
     // CUDA graphs of one full K-step segment: the forward steps, and the
     // reverse steps for either parity of the adjoint population buffers
-    cudaStream_t cap = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams: main branch and side branch
+    cudaEvent_t e_fork = nullptr, e_join = nullptr;
     cudaGraphExec_t g_fwd = nullptr, g_rev[2] = {nullptr, nullptr};
     bool graphs = true;  // replay segment graphs (LBIB_GRAPHS=0: launch directly)
     long long n_fwd = 0, n_rev[2] = {0, 0};
@@ -917,6 +959,9 @@ struct lbib_adjoint {
         for (cudaGraphExec_t g : g_rev)
             if (g) cudaGraphExecDestroy(g);
         if (cap) cudaStreamDestroy(cap);
+        if (cap2) cudaStreamDestroy(cap2);
+        if (e_fork) cudaEventDestroy(e_fork);
+        if (e_join) cudaEventDestroy(e_join);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -928,8 +973,24 @@ struct lbib_adjoint {
 
 namespace {
 
+// Fork st2 off st (st2 then runs beside st) and join it back.  Without a
+// second stream (direct launches) both are no-ops and everything runs on st.
+cudaError_t fork2(lbib_adjoint *a, cudaStream_t st, cudaStream_t st2) {
+    if (!st2) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(a->e_fork, st);
+    return e == cudaSuccess ? cudaStreamWaitEvent(st2, a->e_fork, 0) : e;
+}
+cudaError_t join2(lbib_adjoint *a, cudaStream_t st, cudaStream_t st2) {
+    if (!st2) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(a->e_join, st2);
+    return e == cudaSuccess ? cudaStreamWaitEvent(st, a->e_join, 0) : e;
+}
+
+// One recorded forward step.  The swimmer kernel (bead centres, drive,
+// springs) and the membrane kernel are independent: with st2 they run on two
+// branches.
 template <typename T>
-cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
+cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t st2 = nullptr) {
     const Plan &P = a->P;
     char *sl = a->slot(k), *sn = a->slot(k + 1);
     const double *r = (const double *)(sl + P.s_r);
@@ -937,9 +998,13 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
     T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
     const int M = P.M;
     if (M > 0) {
-        k_fwd_swimmer<<<P.S, SWIM_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), r,
-                                           a->at<long long>(P.o_tb), k, R, ext);
+        cudaError_t e;
+        if ((e = fork2(a, st, st2)) != cudaSuccess) return e;
+        k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st2 ? st2 : st>>>(a->m, a->at<Swim>(P.o_swim),
+                                                                   a->at<double>(P.o_theta), r,
+                                                                   a->at<long long>(P.o_tb), k, R, ext);
         k_fwd_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
+        if ((e = join2(a, st, st2)) != cudaSuccess) return e;
         k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F);
         a->launches += 3;
     }
@@ -961,8 +1026,10 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One reverse step; the membrane and swimmer transposes are independent
+// (two branches with st2).
 template <typename T>
-cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st) {
+cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st, cudaStream_t st2 = nullptr) {
     const Plan &P = a->P;
     char *sl = a->slot(k);
     const double *r = (const double *)(sl + P.s_r), *fn = (const double *)(sl + P.s_fn),
@@ -988,10 +1055,14 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     a->launches += 1;
     if (M > 0) {
         k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
+        cudaError_t e;
+        if ((e = fork2(a, st, st2)) != cudaSuccess) return e;
+        k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st2 ? st2 : st>>>(a->m, a->at<Swim>(P.o_swim),
+                                                                   a->at<double>(P.o_theta), R, lam_fn,
+                                                                   a->at<long long>(P.o_tb), k,
+                                                                   a->at<double>(P.o_lR), a->at<double>(P.o_grad));
         k_adj_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, lam_fn, a->at<double>(P.o_tria));
-        k_adj_swimmer<<<P.S, SWIM_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta), R, lam_fn,
-                                           a->at<long long>(P.o_tb), k, a->at<double>(P.o_lR),
-                                           a->at<double>(P.o_grad));
+        if ((e = join2(a, st, st2)) != cudaSuccess) return e;
         k_adj_node<<<(M + 127) / 128, 128, 0, st>>>(a->m, a->at<double>(P.o_tria), a->at<double>(P.o_lR), lam_r);
         a->launches += 4;
     }
@@ -1011,10 +1082,10 @@ cudaError_t capture(lbib_adjoint *a, bool reverse, int par) {
     for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
         if (reverse) {
             const int kk = P.K - 1 - k;
-            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap);
+            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, a->cap2);
             nxt = 1 - nxt;
         } else {
-            e = fwd_step<T>(a, k, a->cap);
+            e = fwd_step<T>(a, k, a->cap, a->cap2);
         }
     }
     cudaGraph_t g = nullptr;
@@ -1304,6 +1375,9 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     } while (0)
     for (int k = 0; k < 4; ++k) CUA(cudaEventCreate(&a->ev[k]));
     CUA(cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking));
+    CUA(cudaStreamCreateWithFlags(&a->cap2, cudaStreamNonBlocking));
+    CUA(cudaEventCreateWithFlags(&a->e_fork, cudaEventDisableTiming));
+    CUA(cudaEventCreateWithFlags(&a->e_join, cudaEventDisableTiming));
     std::vector<long long> tb(P.n_seg);
     for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
     auto put = [&](size_t off, const void *src, size_t n) {
