@@ -237,18 +237,32 @@ __device__ __forceinline__ void tri_force_jvp(const double *G, const TriState &S
 
 // ---------------------------------------------------------------- forward kernels
 
+// sin and cos of the drive phases omega t + phi_q (Sec. 2.2, driving-force
+// equation) for every step t of the run, swimmer and bead: one thread each,
+// once per forward sweep, so the per-step swimmer kernels only look them up
+__global__ void k_drive_table(const Swim *sw, const double *theta, long long n_steps, int S, double *tbl) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n_steps * S * 3) return;
+    const int q = (int)(i % 3), s = (int)((i / 3) % S);
+    const long long n = i / (3 * S);
+    const double om = 2.0 * 3.14159265358979323846 / sw[s].period;
+    const double arg = om * (double)n + theta[6 * s + 3 + q];
+    double *o = tbl + (n * S + s) * 6;
+    o[q] = sin(arg);
+    o[3 + q] = cos(arg);
+}
+
 // one cluster of three blocks per swimmer, block q summing the positions of
 // bead q (FP64, fixed order); block 0 reads the three centres from the
 // blocks' shared memory (distributed shared memory) and evaluates the drive
 // and spring forces (thread 0)
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
-    k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta, const double *r, const long long *t_base, int k,
-                  double *R, double *ext) {
+    k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta, const double *drv, const double *r,
+                  const long long *t_base, int k, double *R, double *ext) {
     namespace cg = cooperative_groups;
     __shared__ double sh[BEAD_THREADS / 32][3];
     __shared__ double Rq[3];
     cg::cluster_group cl = cg::this_cluster();
-    const double t = (double)(*t_base + k);
     const int s = blockIdx.x / 3, q = (int)cl.block_rank();
     const Swim w = sw[s];
     {
@@ -263,32 +277,38 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
         }
     }
     cl.sync();
-    if (q == 0 && threadIdx.x == 0) {
+    if (q == 0 && threadIdx.x < 32) {
+        // warp 0 of block 0: the two springs on lanes 0 and 1 (side q = 0, 2)
+        const int l = threadIdx.x;
         double Rs[3][3];
         for (int qq = 0; qq < 3; ++qq) {
             const double *p = cl.map_shared_rank(Rq, qq);
             for (int a = 0; a < 3; ++a) Rs[qq][a] = p[a];
         }
-        const double om = 2.0 * 3.14159265358979323846 / w.period;
         const double *th = theta + 6 * s;
+        const double *dv = drv + ((*t_base + k) * (long long)(gridDim.x / 3) + s) * 6;
         double fd[3];
-        fd[0] = th[0] * sin(om * t + th[3]);
-        fd[2] = th[2] * sin(om * t + th[5]);
-        fd[1] = w.balance ? -fd[0] - fd[2] : th[1] * sin(om * t + th[4]);
-        double fs[3][3];
-        for (int side = 0; side < 2; ++side) {
-            const int qq = side ? 2 : 0;
-            double dd[3], n2 = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                dd[a] = Rs[qq][a] - Rs[1][a];
-                n2 += dd[a] * dd[a];
-            }
-            const double n = sqrt(n2);
-            for (int a = 0; a < 3; ++a) fs[qq][a] = -w.k * (n - w.L) * dd[a] / n;
+        fd[0] = th[0] * dv[0];
+        fd[2] = th[2] * dv[2];
+        fd[1] = w.balance ? -fd[0] - fd[2] : th[1] * dv[1];
+        const int qs = l ? 2 : 0;
+        double dd[3], n2 = 0.0, fq[3];
+        for (int a = 0; a < 3; ++a) {
+            dd[a] = Rs[qs][a] - Rs[1][a];
+            n2 += dd[a] * dd[a];
         }
-        for (int a = 0; a < 3; ++a) fs[1][a] = -fs[0][a] - fs[2][a];
-        for (int qq = 0; qq < 3; ++qq)
-            for (int a = 0; a < 3; ++a) ext[3 * w.bead[qq] + a] = fs[qq][a] + (a == 0 ? fd[qq] : 0.0);
+        const double n = sqrt(n2);
+        for (int a = 0; a < 3; ++a) fq[a] = -w.k * (n - w.L) * dd[a] / n;
+        double fs[3][3];
+        for (int a = 0; a < 3; ++a) {
+            fs[0][a] = __shfl_sync(0xffffffffu, fq[a], 0);
+            fs[2][a] = __shfl_sync(0xffffffffu, fq[a], 1);
+            fs[1][a] = -fs[0][a] - fs[2][a];
+        }
+        if (l < 9) {
+            const int qq = l / 3, a = l % 3;
+            ext[3 * w.bead[qq] + a] = fs[qq][a] + (a == 0 ? fd[qq] : 0.0);
+        }
     }
     cl.sync();  // the blocks' shared memory outlives block 0's reads
 }
@@ -739,13 +759,12 @@ __global__ void k_adj_tri(Mesh m, const double *r, const double *lam_fn, double 
 // (thread 0) forms lam_e_b = the mean over bead b, the drive-parameter
 // gradient and the transpose of the spring forces -> lam_R
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
-    k_adj_swimmer(Mesh m, const Swim *sw, const double *theta, const double *R, const double *lam_fn,
-                  const long long *t_base, int k, double *lam_R, double *grad) {
+    k_adj_swimmer(Mesh m, const Swim *sw, const double *theta, const double *drv, const double *R,
+                  const double *lam_fn, const long long *t_base, int k, double *lam_R, double *grad) {
     namespace cg = cooperative_groups;
     __shared__ double sh[BEAD_THREADS / 32][3];
     __shared__ double lq[3];
     cg::cluster_group cl = cg::this_cluster();
-    const double t = (double)(*t_base + k);
     const int s = blockIdx.x / 3, q = (int)cl.block_rank();
     const Swim w = sw[s];
     {
@@ -756,7 +775,10 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
         bead_sum3(acc, sh, lq);
     }
     cl.sync();
-    if (q == 0 && threadIdx.x == 0) {
+    if (q == 0 && threadIdx.x < 32) {
+        // warp 0 of block 0: lane q < 3 the drive gradient of bead q, lanes 0
+        // and 1 the spring transposes of sides 0 and 2
+        const int l = threadIdx.x;
         double le[3][3];
         for (int qq = 0; qq < 3; ++qq) {
             const double *p = cl.map_shared_rank(lq, qq);
@@ -765,8 +787,8 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
         for (int qq = 0; qq < 3; ++qq)
             for (int a = 0; a < 3; ++a) le[qq][a] /= m.bead_count[w.bead[qq]];
         // drive: f_q = A_q sin(om t + phi_q) along x (balance: f_1 = -f_0 - f_2)
-        const double om = 2.0 * 3.14159265358979323846 / w.period;
         const double *th = theta + 6 * s;
+        const double *dv = drv + ((*t_base + k) * (long long)(gridDim.x / 3) + s) * 6;
         double sens[3];
         if (w.balance) {
             sens[0] = le[0][0] - le[1][0];
@@ -775,33 +797,30 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
         } else {
             for (int qq = 0; qq < 3; ++qq) sens[qq] = le[qq][0];
         }
-        for (int qq = 0; qq < 3; ++qq) {
-            if (w.balance && qq == 1) continue;
-            const double arg = om * t + th[3 + qq];
-            grad[6 * s + qq] += sin(arg) * sens[qq];
-            grad[6 * s + 3 + qq] += th[qq] * cos(arg) * sens[qq];
+        if (l < 3 && !(w.balance && l == 1)) {
+            grad[6 * s + l] += dv[l] * sens[l];
+            grad[6 * s + 3 + l] += th[l] * dv[3 + l] * sens[l];
         }
         // springs: f_0 = h(R_0 - R_1), f_2 = h(R_2 - R_1), f_1 = -f_0 - f_2 with
         // h(d) = -k (|d| - L) d/|d|, dh/dd = -k [(1 - L/|d|) I + (L/|d|) dhat dhat^T]
-        double lR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        for (int side = 0; side < 2; ++side) {
-            const int qq = side ? 2 : 0;
-            double dd[3], n2 = 0.0, lv[3];
-            for (int a = 0; a < 3; ++a) {
-                dd[a] = R[3 * w.bead[qq] + a] - R[3 * w.bead[1] + a];
-                n2 += dd[a] * dd[a];
-                lv[a] = le[qq][a] - le[1][a];
-            }
-            const double n = sqrt(n2), c1 = 1.0 - w.L / n, c2 = w.L / (n * n2);
-            const double dl = dd[0] * lv[0] + dd[1] * lv[1] + dd[2] * lv[2];
-            for (int a = 0; a < 3; ++a) {
-                const double ld = -w.k * (c1 * lv[a] + c2 * dd[a] * dl);
-                lR[qq][a] += ld;
-                lR[1][a] -= ld;
+        const int qs = l ? 2 : 0;
+        double dd[3], n2 = 0.0, lv[3], ld[3];
+        for (int a = 0; a < 3; ++a) {
+            dd[a] = R[3 * w.bead[qs] + a] - R[3 * w.bead[1] + a];
+            n2 += dd[a] * dd[a];
+            lv[a] = le[qs][a] - le[1][a];
+        }
+        const double n = sqrt(n2), c1 = 1.0 - w.L / n, c2 = w.L / (n * n2);
+        const double dl = dd[0] * lv[0] + dd[1] * lv[1] + dd[2] * lv[2];
+        for (int a = 0; a < 3; ++a) ld[a] = -w.k * (c1 * lv[a] + c2 * dd[a] * dl);
+        for (int a = 0; a < 3; ++a) {
+            const double l0 = __shfl_sync(0xffffffffu, ld[a], 0), l2 = __shfl_sync(0xffffffffu, ld[a], 1);
+            if (l == 0) {
+                lam_R[3 * w.bead[0] + a] = l0;
+                lam_R[3 * w.bead[1] + a] = -l0 - l2;
+                lam_R[3 * w.bead[2] + a] = l2;
             }
         }
-        for (int qq = 0; qq < 3; ++qq)
-            for (int a = 0; a < 3; ++a) lam_R[3 * w.bead[qq] + a] = lR[qq][a];
     }
     cl.sync();  // the blocks' shared memory outlives block 0's reads
 }
@@ -845,6 +864,7 @@ struct Plan {
     // per-checkpoint offsets
     size_t c_pops, c_r, ck_bytes;
     // workspace offsets
+    size_t o_drv = 0;  // drive table: per step and swimmer sin and cos of (omega t + phi_q), q = 0..2
     size_t o_tris, o_G, o_A0, o_cptr, o_cent, o_nb, o_bs, o_bc, o_bw, o_swim, o_theta, o_grad, o_disp, o_err,
         o_seed, o_lf0, o_lf1, o_lu, o_lF, o_lr, o_lfn, o_trif, o_tria, o_lR, o_tb, o_tbt, o_ck, o_slots, total;
 };
@@ -896,6 +916,7 @@ Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, i
     P.o_disp = o; o += up(3 * Sn * 8);
     P.o_err = o; o += up(4);
     P.o_seed = o; o += up(3 * Sn * 8);
+    P.o_drv = o; o += up((size_t)P.n_steps * Sn * 6 * 8);
     P.o_lf0 = o; o += up(Q * fp);
     P.o_lf1 = o; o += up(Q * fp);
     P.o_lu = o; o += up(3 * fp);
@@ -1001,7 +1022,8 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t st2 =
         cudaError_t e;
         if ((e = fork2(a, st, st2)) != cudaSuccess) return e;
         k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st2 ? st2 : st>>>(a->m, a->at<Swim>(P.o_swim),
-                                                                   a->at<double>(P.o_theta), r,
+                                                                   a->at<double>(P.o_theta),
+                                                                   a->at<double>(P.o_drv), r,
                                                                    a->at<long long>(P.o_tb), k, R, ext);
         k_fwd_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
         if ((e = join2(a, st, st2)) != cudaSuccess) return e;
@@ -1058,7 +1080,8 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
         cudaError_t e;
         if ((e = fork2(a, st, st2)) != cudaSuccess) return e;
         k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st2 ? st2 : st>>>(a->m, a->at<Swim>(P.o_swim),
-                                                                   a->at<double>(P.o_theta), R, lam_fn,
+                                                                   a->at<double>(P.o_theta),
+                                                                   a->at<double>(P.o_drv), R, lam_fn,
                                                                    a->at<long long>(P.o_tb), k,
                                                                    a->at<double>(P.o_lR), a->at<double>(P.o_grad));
         k_adj_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, lam_fn, a->at<double>(P.o_tria));
@@ -1147,6 +1170,13 @@ int forward_impl(lbib_adjoint *a, double *disp) {
     CU(cudaMemsetAsync(a->at<int>(P.o_err), 0, 4, a->s));
     CU(cudaEventRecord(a->ev[0], a->s));
     a->launches = 0;
+    if (P.S > 0) {  // the drive phases of every step, from the current theta
+        const long long n = P.n_steps * P.S * 3;
+        k_drive_table<<<(unsigned)((n + 255) / 256), 256, 0, a->s>>>(a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
+                                                                   P.n_steps, P.S, a->at<double>(P.o_drv));
+        a->launches += 1;
+        CU(cudaGetLastError());
+    }
     for (int g = 0; g < P.n_seg; ++g) {
         CU(run_segment<T>(a, g));
         CU(save_ck(a, a->seg_len(g), g + 1));  // the next checkpoint (the last one: the final state)
