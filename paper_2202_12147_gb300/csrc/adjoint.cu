@@ -146,6 +146,7 @@ __device__ __forceinline__ void group_sum3(double v[3], double (*sh)[3], double 
 
 constexpr int SWIM_THREADS = 768;  // three groups of 256: one per bead
 constexpr int BEAD_THREADS = 256;  // one block of a swimmer's three-block cluster: one bead
+constexpr int TRI_THREADS = 32;    // per-triangle FP64 kernels: one warp per block
 
 // The same fixed-order sum as one 256-thread group of group_sum3: warp sums,
 // then warp 0 adds the 8 warp sums in order.  Result in out[3].
@@ -969,8 +970,7 @@ struct lbib_adjoint {
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
     // CUDA graphs of one full K-step segment: the forward steps, and the
     // reverse steps for either parity of the adjoint population buffers
-    cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams: main branch and side branch
-    cudaEvent_t e_fork = nullptr, e_join = nullptr;
+    cudaStream_t cap = nullptr;
     cudaGraphExec_t g_fwd = nullptr, g_rev[2] = {nullptr, nullptr};
     bool graphs = true;  // replay segment graphs (LBIB_GRAPHS=0: launch directly)
     long long n_fwd = 0, n_rev[2] = {0, 0};
@@ -980,9 +980,6 @@ struct lbib_adjoint {
         for (cudaGraphExec_t g : g_rev)
             if (g) cudaGraphExecDestroy(g);
         if (cap) cudaStreamDestroy(cap);
-        if (cap2) cudaStreamDestroy(cap2);
-        if (e_fork) cudaEventDestroy(e_fork);
-        if (e_join) cudaEventDestroy(e_join);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -994,24 +991,11 @@ struct lbib_adjoint {
 
 namespace {
 
-// Fork st2 off st (st2 then runs beside st) and join it back.  Without a
-// second stream (direct launches) both are no-ops and everything runs on st.
-cudaError_t fork2(lbib_adjoint *a, cudaStream_t st, cudaStream_t st2) {
-    if (!st2) return cudaSuccess;
-    cudaError_t e = cudaEventRecord(a->e_fork, st);
-    return e == cudaSuccess ? cudaStreamWaitEvent(st2, a->e_fork, 0) : e;
-}
-cudaError_t join2(lbib_adjoint *a, cudaStream_t st, cudaStream_t st2) {
-    if (!st2) return cudaSuccess;
-    cudaError_t e = cudaEventRecord(a->e_join, st2);
-    return e == cudaSuccess ? cudaStreamWaitEvent(st, a->e_join, 0) : e;
-}
-
-// One recorded forward step.  The swimmer kernel (bead centres, drive,
-// springs) and the membrane kernel are independent: with st2 they run on two
-// branches.
+// One recorded forward step.  (The swimmer and membrane kernels are
+// independent, but running them on two graph branches measured slower than
+// one chain: 75 against 61 us per step on the 96^3 workload.)
 template <typename T>
-cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t st2 = nullptr) {
+cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
     const Plan &P = a->P;
     char *sl = a->slot(k), *sn = a->slot(k + 1);
     const double *r = (const double *)(sl + P.s_r);
@@ -1019,14 +1003,11 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t st2 =
     T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
     const int M = P.M;
     if (M > 0) {
-        cudaError_t e;
-        if ((e = fork2(a, st, st2)) != cudaSuccess) return e;
-        k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st2 ? st2 : st>>>(a->m, a->at<Swim>(P.o_swim),
-                                                                   a->at<double>(P.o_theta),
-                                                                   a->at<double>(P.o_drv), r,
-                                                                   a->at<long long>(P.o_tb), k, R, ext);
-        k_fwd_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
-        if ((e = join2(a, st, st2)) != cudaSuccess) return e;
+        k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
+                                                         a->at<double>(P.o_drv), r, a->at<long long>(P.o_tb), k, R,
+                                                         ext);
+        // FP64-latency-bound: small blocks spread the triangles over every SM
+        k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
         k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F);
         a->launches += 3;
     }
@@ -1048,10 +1029,8 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t st2 =
     return cudaGetLastError();
 }
 
-// One reverse step; the membrane and swimmer transposes are independent
-// (two branches with st2).
 template <typename T>
-cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st, cudaStream_t st2 = nullptr) {
+cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st) {
     const Plan &P = a->P;
     char *sl = a->slot(k);
     const double *r = (const double *)(sl + P.s_r), *fn = (const double *)(sl + P.s_fn),
@@ -1077,16 +1056,13 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     a->launches += 1;
     if (M > 0) {
         k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
-        cudaError_t e;
-        if ((e = fork2(a, st, st2)) != cudaSuccess) return e;
-        k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st2 ? st2 : st>>>(a->m, a->at<Swim>(P.o_swim),
-                                                                   a->at<double>(P.o_theta),
-                                                                   a->at<double>(P.o_drv), R, lam_fn,
-                                                                   a->at<long long>(P.o_tb), k,
-                                                                   a->at<double>(P.o_lR), a->at<double>(P.o_grad));
-        k_adj_tri<<<(P.T + 127) / 128, 128, 0, st>>>(a->m, r, lam_fn, a->at<double>(P.o_tria));
-        if ((e = join2(a, st, st2)) != cudaSuccess) return e;
-        k_adj_node<<<(M + 127) / 128, 128, 0, st>>>(a->m, a->at<double>(P.o_tria), a->at<double>(P.o_lR), lam_r);
+        k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
+                                                         a->at<double>(P.o_drv), R, lam_fn, a->at<long long>(P.o_tb), k,
+                                                         a->at<double>(P.o_lR), a->at<double>(P.o_grad));
+        k_adj_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, lam_fn,
+                                                                                a->at<double>(P.o_tria));
+        k_adj_node<<<(M + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, a->at<double>(P.o_tria),
+                                                                               a->at<double>(P.o_lR), lam_r);
         a->launches += 4;
     }
     return cudaGetLastError();
@@ -1105,10 +1081,10 @@ cudaError_t capture(lbib_adjoint *a, bool reverse, int par) {
     for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
         if (reverse) {
             const int kk = P.K - 1 - k;
-            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, a->cap2);
+            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap);
             nxt = 1 - nxt;
         } else {
-            e = fwd_step<T>(a, k, a->cap, a->cap2);
+            e = fwd_step<T>(a, k, a->cap);
         }
     }
     cudaGraph_t g = nullptr;
@@ -1405,9 +1381,6 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     } while (0)
     for (int k = 0; k < 4; ++k) CUA(cudaEventCreate(&a->ev[k]));
     CUA(cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking));
-    CUA(cudaStreamCreateWithFlags(&a->cap2, cudaStreamNonBlocking));
-    CUA(cudaEventCreateWithFlags(&a->e_fork, cudaEventDisableTiming));
-    CUA(cudaEventCreateWithFlags(&a->e_join, cudaEventDisableTiming));
     std::vector<long long> tb(P.n_seg);
     for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
     auto put = [&](size_t off, const void *src, size_t n) {
