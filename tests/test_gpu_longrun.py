@@ -1,0 +1,100 @@
+"""Long runs on the full-size two-swimmer boxes against the FP64 oracle's
+stored results (tests/golden/longrun_*.json, written by
+make_longrun_golden.py from oracle/ alone): the 256 x 128 x 128 side-by-side
+box of the benchmark over three drive periods (6000 steps) and the 256^3
+pair over one period (2000 steps), with FP32, FP16 and BF16 population
+storage, advanced as the benchmark advances them (16-step graph replays on
+two streams).
+
+Checked against the oracle:
+* x_cm of both swimmers every 100 steps;
+* the mean swimming velocity of every completed drive period (Sec. 3, Eq.
+  vel_swim), within 1 %, and the device's own record of the last one;
+* the velocity u after the last step at the stored cells (2048 random ones
+  and the 512 of largest |u|), as a relative L2 error over that sample.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu_sim
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+# relative L2 bound of the velocity sample: FP32 storage at the north-star
+# bound; 16-bit storage at the precision variant's 2e-3
+U_TOL = {"f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}
+
+
+def _gold(name):
+    with open(os.path.join(HERE, "golden", f"longrun_{name}.json")) as fh:
+        return json.load(fh)
+
+
+def _run(box, gold, storage):
+    from workloads import assemble
+    asm = assemble(box)
+    sim = gpu_sim(box, asm, storage=storage)
+    S = sim.n_swimmers
+    xs = [[sim.swimmer_state(s)["x_cm"] for s in range(S)]]
+    every = gold["every"]
+    for _ in range(gold["steps"] // every):
+        sim.lb_step(every)
+        xs.append([sim.swimmer_state(s)["x_cm"] for s in range(S)])
+    st = [sim.swimmer_state(s) for s in range(S)]
+    _, u = sim.lb_get_macros()
+    u = u[np_index(gold["cells"], u.device)].cpu().numpy().astype(np.float64)
+    sim.close()
+    return np.array(xs), st, u
+
+
+def np_index(cells, device):
+    import torch
+    return torch.tensor(cells, dtype=torch.long, device=device)
+
+
+def _check(gold, storage, xs, st, u):
+    xo = np.array([x for _, x in gold["x_cm"]])  # (samples, swimmers, 3)
+    assert xs.shape == xo.shape
+    # trajectories: the distance travelled is ~1e-3 lattice units per period
+    travel = np.abs(xo - xo[0]).max()
+    x_err = np.abs(xs - xo).max() / travel
+    # per-period mean swimming velocity along x (Sec. 3, Eq. vel_swim)
+    T, every = gold["period"], gold["every"]
+    idx = [k * T // every for k in range(gold["steps"] // T + 1)]
+    vg = (xs[idx[1:], :, 0] - xs[idx[:-1], :, 0]) / T
+    vo = (xo[idx[1:], :, 0] - xo[idx[:-1], :, 0]) / T
+    v_err = np.abs(vg - vo).max() / np.abs(vo).min()
+    # the device's record of the last completed period
+    v_dev = np.array([s["v_period"][0] for s in st])
+    dev_err = np.abs(v_dev - vo[-1]).max() / np.abs(vo[-1]).min()
+    uo = np.array(gold["u"])
+    u_err = np.linalg.norm(u - uo) / np.linalg.norm(uo)
+    print(f"{gold['case']} {storage}: x_cm {x_err:.2e} of the travel, period velocity {v_err:.2e} "
+          f"(device record {dev_err:.2e}), velocity sample rel. L2 {u_err:.2e}")
+    assert [s["periods"] for s in st] == [gold["steps"] // T] * len(st)
+    assert v_err < 1e-2
+    assert dev_err < 1e-2
+    assert x_err < (1e-3 if storage == "f32" else 1e-2)
+    assert u_err < U_TOL[storage]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_longrun_benchmark_box_three_periods(gpu_lib, storage):
+    from workloads import swimmer_pair
+    gold = _gold("side3_256x128x128")
+    box = swimmer_pair("side", 3)
+    assert list(box.dims) == gold["dims"]
+    _check(gold, storage, *_run(box, gold, storage))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_longrun_256cube_one_period(gpu_lib, storage):
+    from workloads import pair_side_256cube
+    gold = _gold("side3_256cube")
+    box = pair_side_256cube()
+    assert list(box.dims) == gold["dims"]
+    _check(gold, storage, *_run(box, gold, storage))
