@@ -424,24 +424,31 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
             __syncthreads();
             // a drive period ends with this step: record x_cm (mean of the
             // three bead centres) for the period-averaged velocity (Sec. 3)
+            // this step's trajectory points, slot (next - 1) mod LBIB_TRACK_STEPS:
+            // one thread per (swimmer, field) of the 22 fields of a point
+            {
+                lbib_track_point *tp = c.track + (size_t)((next - 1) % LBIB_TRACK_STEPS) * c.n_swimmers;
+                for (int i = threadIdx.x; i < 22 * c.n_swimmers; i += blockDim.x) {
+                    const int sw = i / 22, f = i % 22;
+                    const SwimDev d = c.swims[sw];
+                    if (f == 0) {
+                        tp[sw].step = next;
+                    } else if (f < 4) {
+                        const int a = f - 1;
+                        tp[sw].x_cm[a] = (c.bead_R[4 * d.bead[0] + a] + c.bead_R[4 * d.bead[1] + a] +
+                                          c.bead_R[4 * d.bead[2] + a]) / 3.0;
+                    } else if (f < 13) {
+                        const int q = (f - 4) / 3, a = (f - 4) % 3;
+                        tp[sw].R[q][a] = c.bead_R[4 * d.bead[q] + a];
+                    } else {
+                        const int q = (f - 13) / 3, a = (f - 13) % 3;
+                        const float4 V = c.bead_V[d.bead[q]];
+                        tp[sw].V[q][a] = a == 0 ? V.x : (a == 1 ? V.y : V.z);
+                    }
+                }
+            }
             for (int sw = threadIdx.x; sw < c.n_swimmers; sw += blockDim.x) {
                 const SwimDev d = c.swims[sw];
-                // this step's trajectory point, slot (next - 1) mod LBIB_TRACK_STEPS
-                lbib_track_point *tp = c.track + (size_t)((next - 1) % LBIB_TRACK_STEPS) * c.n_swimmers + sw;
-                tp->step = next;
-                for (int a = 0; a < 3; ++a) {
-                    const double *R = c.bead_R + 4 * d.bead[a];
-                    const float4 V = c.bead_V[d.bead[a]];
-                    tp->R[a][0] = R[0];
-                    tp->R[a][1] = R[1];
-                    tp->R[a][2] = R[2];
-                    tp->V[a][0] = V.x;
-                    tp->V[a][1] = V.y;
-                    tp->V[a][2] = V.z;
-                }
-                for (int a = 0; a < 3; ++a)
-                    tp->x_cm[a] = (c.bead_R[4 * d.bead[0] + a] + c.bead_R[4 * d.bead[1] + a] +
-                                   c.bead_R[4 * d.bead[2] + a]) / 3.0;
                 if (floor((double)next / d.period) > floor((double)(next - 1) / d.period)) {
                     double *rec = c.sw_period + 8 * sw;
                     for (int a = 0; a < 3; ++a) {
