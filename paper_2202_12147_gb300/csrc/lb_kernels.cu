@@ -599,8 +599,25 @@ __device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, uns
     if (c.n_nodes == 0 && tile == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
 }
 
+// Programmatic dependent launch between consecutive main-kernel launches of
+// one stream: every block first waits until the previous grid has completed
+// and its writes are visible (a no-op when the launch carries no programmatic
+// dependency), then allows the next launch to be scheduled, so that its
+// blocks take the SM slots the last wave of this grid frees instead of
+// waiting for a full launch after it.
+#ifndef LBIB_MAIN_PDL
+#define LBIB_MAIN_PDL 1
+#endif
+__device__ __forceinline__ void pdl_wait_and_release() {
+#if LBIB_MAIN_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 template <int ST, bool ODD, int FORCING, int CPT>
 __global__ void LBIB_LB_BOUNDS_ST(ST, CPT) k_lb_main(const DevCtx c) {
+    pdl_wait_and_release();
     const unsigned tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -1002,8 +1019,17 @@ static unsigned tile_threads(const DevCtx &c) {
 template <int ST, int FORCING, int CPT>
 static void main_dispatch_cpt(const DevCtx &c, bool odd, cudaStream_t s) {
     const dim3 blocks((unsigned)c.tiles_x, (unsigned)c.ny, (unsigned)c.nz);
-    if (odd) k_lb_main<ST, true, FORCING, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
-    else k_lb_main<ST, false, FORCING, CPT><<<blocks, tile_threads(c), 0, s>>>(c);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = blocks;
+    cfg.blockDim = dim3(tile_threads(c));
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = LBIB_MAIN_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (odd) cudaLaunchKernelEx(&cfg, k_lb_main<ST, true, FORCING, CPT>, c);
+    else cudaLaunchKernelEx(&cfg, k_lb_main<ST, false, FORCING, CPT>, c);
 }
 
 template <int ST, int FORCING>
