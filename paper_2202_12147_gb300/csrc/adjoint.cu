@@ -145,16 +145,6 @@ __device__ __forceinline__ void group_sum3(double v[3], double (*sh)[3], double 
 }
 
 constexpr int SWIM_THREADS = 768;  // three groups of 256: one per bead
-// Programmatic dependent launch along the per-step kernel chain: each kernel
-// first waits until its predecessor grid has completed and its writes are
-// visible (a no-op without a programmatic dependency), then lets its
-// successor be scheduled.  Every kernel of the chain waits before anything
-// else, so completion is ordered transitively along the chain.
-__device__ __forceinline__ void chain_wait_and_release() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 constexpr int BEAD_THREADS = 256;  // one block of a swimmer's three-block cluster: one bead
 constexpr int TRI_THREADS = 32;    // per-triangle FP64 kernels: one warp per block
 
@@ -270,7 +260,6 @@ __global__ void k_drive_table(const Swim *sw, const double *theta, long long n_s
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
     k_fwd_swimmer(Mesh m, const Swim *sw, const double *theta, const double *drv, const double *r,
                   const long long *t_base, int k, double *R, double *ext) {
-    chain_wait_and_release();
     namespace cg = cooperative_groups;
     __shared__ double sh[BEAD_THREADS / 32][3];
     __shared__ double Rq[3];
@@ -327,7 +316,6 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
 
 // one thread per triangle: corner forces -dW/dr
 __global__ void k_fwd_tri(Mesh m, const double *r, double *tri_f) {
-    chain_wait_and_release();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
     const int *v = m.tris + 3 * t;
@@ -347,7 +335,6 @@ __global__ void k_fwd_tri(Mesh m, const double *r, double *tri_f) {
 template <typename T>
 __global__ void k_fwd_spread(Dims d, Mesh m, const double *r, const double *tri_f, const double *ext, double *fn,
                              T *F) {
-    chain_wait_and_release();
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= m.M) return;
     const int e0 = m.csr_ptr[j], e1 = m.csr_ptr[j + 1];
@@ -450,7 +437,6 @@ template <typename T>
 __global__ void __launch_bounds__(256, 2) k_fwd_lb(Dims d, T omega, T rho0, double gx, double gy,
                                                                        double gz, const T *pops, const T *F, T *out,
                                                                        T *u_out, T *F_next) {
-    chain_wait_and_release();
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= d.N) return;
     int x, y, z;
@@ -474,7 +460,6 @@ __global__ void __launch_bounds__(256, 2) k_fwd_lb(Dims d, T omega, T rho0, doub
 __global__ void __launch_bounds__(128, 4) k_fwd_lb2(Dims d, float omega, float rho0, double gx, double gy, double gz,
                                                     const float *pops, const float *F, float *out, float *u_out,
                                                     float *F_next) {
-    chain_wait_and_release();
     const int cell = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (cell >= d.N) return;
     int x, y, z;
@@ -510,7 +495,6 @@ __global__ void __launch_bounds__(128, 4) k_fwd_lb2(Dims d, float omega, float r
 // one warp per node: r_j^{k+1} = r_j^k + sum_x u(x) Delta(x - r_j)
 template <typename T>
 __global__ void k_fwd_interp(Dims d, int M, const double *r, const T *u, double *r_next, int *err) {
-    chain_wait_and_release();
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= M) return;
     int cell[2];
@@ -569,7 +553,6 @@ __global__ void k_adj_seed(Mesh m, const double *seed_disp, double sign, int add
 // one warp per node: transpose of r^{k+1} = r^k + interp(u^k, r^k)
 template <typename T>
 __global__ void k_adj_interp(Dims d, int M, const double *r, const T *u, double *lam_r, T *lam_u) {
-    chain_wait_and_release();
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= M) return;
     int cell[2];
@@ -655,7 +638,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_adj_lb(Dims d, 
                                                                        double gz, const T *pops, const T *F,
                                                                        const T *lam_next, T *lam_u, T *lam_cur,
                                                                        T *lam_F) {
-    chain_wait_and_release();
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= d.N) return;
     int x, y, z;
@@ -684,7 +666,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_adj_lb(Dims d, 
 __global__ void __launch_bounds__(128, 4) k_adj_lb2(Dims d, float omega, float rho0, double gx, double gy, double gz,
                                                     const float *pops, const float *F, const float *lam_next,
                                                     float *lam_u, float *lam_cur, float *lam_F) {
-    chain_wait_and_release();
     const int cell = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (cell >= d.N) return;
     int x, y, z;
@@ -734,7 +715,6 @@ __global__ void __launch_bounds__(128, 4) k_adj_lb2(Dims d, float omega, float r
 template <typename T>
 __global__ void k_adj_spread(Dims d, int M, const double *r, const double *fn, const T *lam_F, double *lam_r,
                              double *lam_fn) {
-    chain_wait_and_release();
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= M) return;
     int cell[2];
@@ -764,7 +744,6 @@ __global__ void k_adj_spread(Dims d, int M, const double *r, const double *fn, c
 
 // one thread per triangle: membrane force Jacobian times lam_f at its corners
 __global__ void k_adj_tri(Mesh m, const double *r, const double *lam_fn, double *tri_adj) {
-    chain_wait_and_release();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
     const int *v = m.tris + 3 * t;
@@ -783,7 +762,6 @@ __global__ void k_adj_tri(Mesh m, const double *r, const double *lam_fn, double 
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
     k_adj_swimmer(Mesh m, const Swim *sw, const double *theta, const double *drv, const double *R,
                   const double *lam_fn, const long long *t_base, int k, double *lam_R, double *grad) {
-    chain_wait_and_release();
     namespace cg = cooperative_groups;
     __shared__ double sh[BEAD_THREADS / 32][3];
     __shared__ double lq[3];
@@ -850,7 +828,6 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
 
 // one thread per node: lam_r_j += sum of its corners' membrane terms + lam_R_b / N_b
 __global__ void k_adj_node(Mesh m, const double *tri_adj, const double *lam_R, double *lam_r) {
-    chain_wait_and_release();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m.M) return;
     double f[3] = {0.0, 0.0, 0.0};
@@ -1014,31 +991,9 @@ struct lbib_adjoint {
 
 namespace {
 
-// Launch one kernel of the per-step chain with a programmatic dependency on
-// the kernel before it in the stream (see chain_wait_and_release).
-template <typename... Exp, typename... Act>
-cudaError_t chain_launch(void (*k)(Exp...), dim3 grid, dim3 block, cudaStream_t s, Act &&...args) {
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr.val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.stream = s;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, static_cast<Act &&>(args)...);
-}
-
 // One recorded forward step.  (The swimmer and membrane kernels are
 // independent, but running them on two graph branches measured slower than
 // one chain: 75 against 61 us per step on the 96^3 workload.)
-#define CH(x)                                 \
-    do {                                      \
-        const cudaError_t e_ = (x);           \
-        if (e_ != cudaSuccess) return e_;     \
-    } while (0)
-
 template <typename T>
 cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
     const Plan &P = a->P;
@@ -1048,33 +1003,30 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
     T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
     const int M = P.M;
     if (M > 0) {
-        CH(chain_launch(k_fwd_swimmer, dim3(3 * P.S), dim3(BEAD_THREADS), st, a->m, a->at<Swim>(P.o_swim),
-                        a->at<double>(P.o_theta), a->at<double>(P.o_drv), r, a->at<long long>(P.o_tb), k, R, ext));
+        k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
+                                                         a->at<double>(P.o_drv), r, a->at<long long>(P.o_tb), k, R,
+                                                         ext);
         // FP64-latency-bound: small blocks spread the triangles over every SM
-        CH(chain_launch(k_fwd_tri, dim3((P.T + TRI_THREADS - 1) / TRI_THREADS), dim3(TRI_THREADS), st, a->m, r,
-                        a->at<double>(P.o_trif)));
-        CH(chain_launch(k_fwd_spread<T>, dim3((M + 3) / 4), dim3(128), st, P.d, a->m, r, a->at<double>(P.o_trif), ext,
-                        fn, F));
+        k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
+        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F);
         a->launches += 3;
     }
     if (sizeof(T) == 4 && P.d.nx % 2 == 0) {
         const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
-        CH(chain_launch(k_fwd_lb2, dim3(nb), dim3(128), st, P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0],
-                        a->p.g[1], a->p.g[2], (const float *)(sl + P.s_pops), (const float *)F,
-                        (float *)(sn + P.s_pops), (float *)u, (float *)(sn + P.s_F)));
+        k_fwd_lb2<<<nb, 128, 0, st>>>(P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                      (const float *)(sl + P.s_pops), (const float *)F, (float *)(sn + P.s_pops),
+                                      (float *)u, (float *)(sn + P.s_F));
     } else {
         const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-        CH(chain_launch(k_fwd_lb<T>, dim3(nb), dim3(256), st, P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0],
-                        a->p.g[1], a->p.g[2], (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u,
-                        (T *)(sn + P.s_F)));
+        k_fwd_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                         (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F));
     }
     a->launches += 1;
     if (M > 0) {
-        CH(chain_launch(k_fwd_interp<T>, dim3((M + 3) / 4), dim3(128), st, P.d, M, r, u, (double *)(sn + P.s_r),
-                        a->at<int>(P.o_err)));
+        k_fwd_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
         a->launches += 1;
     }
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -1088,35 +1040,33 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     double *lam_r = a->at<double>(P.o_lr), *lam_fn = a->at<double>(P.o_lfn);
     const int M = P.M;
     if (M > 0) {
-        CH(chain_launch(k_adj_interp<T>, dim3((M + 3) / 4), dim3(128), st, P.d, M, r, u, lam_r, lam_u));
+        k_adj_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, lam_r, lam_u);
         a->launches += 1;
     }
     if (sizeof(T) == 4 && P.d.nx % 2 == 0) {
         const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
-        CH(chain_launch(k_adj_lb2, dim3(nb), dim3(128), st, P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0],
-                        a->p.g[1], a->p.g[2], (const float *)(sl + P.s_pops), (const float *)F, (const float *)lam_next,
-                        (float *)lam_u, (float *)lam_cur, (float *)lam_F));
+        k_adj_lb2<<<nb, 128, 0, st>>>(P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                      (const float *)(sl + P.s_pops), (const float *)F, (const float *)lam_next,
+                                      (float *)lam_u, (float *)lam_cur, (float *)lam_F);
     } else {
         const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-        CH(chain_launch(k_adj_lb<T>, dim3(nb), dim3(256), st, P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0],
-                        a->p.g[1], a->p.g[2], (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F));
+        k_adj_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
+                                         (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F);
     }
     a->launches += 1;
     if (M > 0) {
-        CH(chain_launch(k_adj_spread<T>, dim3((M + 3) / 4), dim3(128), st, P.d, M, r, fn, lam_F, lam_r, lam_fn));
-        CH(chain_launch(k_adj_swimmer, dim3(3 * P.S), dim3(BEAD_THREADS), st, a->m, a->at<Swim>(P.o_swim),
-                        a->at<double>(P.o_theta), a->at<double>(P.o_drv), R, lam_fn, a->at<long long>(P.o_tb), k,
-                        a->at<double>(P.o_lR), a->at<double>(P.o_grad)));
-        CH(chain_launch(k_adj_tri, dim3((P.T + TRI_THREADS - 1) / TRI_THREADS), dim3(TRI_THREADS), st, a->m, r, lam_fn,
-                        a->at<double>(P.o_tria)));
-        CH(chain_launch(k_adj_node, dim3((M + TRI_THREADS - 1) / TRI_THREADS), dim3(TRI_THREADS), st, a->m,
-                        a->at<double>(P.o_tria), a->at<double>(P.o_lR), lam_r));
+        k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
+        k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
+                                                         a->at<double>(P.o_drv), R, lam_fn, a->at<long long>(P.o_tb), k,
+                                                         a->at<double>(P.o_lR), a->at<double>(P.o_grad));
+        k_adj_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, lam_fn,
+                                                                                a->at<double>(P.o_tria));
+        k_adj_node<<<(M + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, a->at<double>(P.o_tria),
+                                                                               a->at<double>(P.o_lR), lam_r);
         a->launches += 4;
     }
-    return cudaSuccess;
+    return cudaGetLastError();
 }
-
-#undef CH
 
 // capture the K forward steps of a full segment (slots 0 -> K), or its K
 // reverse steps starting on adjoint buffer `par`, into a graph
