@@ -268,7 +268,25 @@ __device__ void fold_bead_velocities(const DevCtx &c) {
     for (int b = w; b < c.n_beads; b += nw) {
         const BeadDev bd = c.beads[b];
         float sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int j = bd.node_start + l; j < bd.node_start + bd.node_count; j += 32) {
+        // four loads in flight per lane, added in the same order as one at a time
+        const int je = bd.node_start + bd.node_count;
+        int j = bd.node_start + l;
+        for (; j + 96 < je; j += 128) {
+            const float4 v0 = c.node_vel[j], v1 = c.node_vel[j + 32], v2 = c.node_vel[j + 64], v3 = c.node_vel[j + 96];
+            sx += v0.x;
+            sy += v0.y;
+            sz += v0.z;
+            sx += v1.x;
+            sy += v1.y;
+            sz += v1.z;
+            sx += v2.x;
+            sy += v2.y;
+            sz += v2.z;
+            sx += v3.x;
+            sy += v3.y;
+            sz += v3.z;
+        }
+        for (; j < je; j += 32) {
             const float4 v = c.node_vel[j];
             sx += v.x;
             sy += v.y;
