@@ -328,11 +328,19 @@ __device__ __forceinline__ void mark_stencil_plane(const DevCtx &c, int ox, int 
     }
 #pragma unroll
     for (int k = 0; k < 2 * KW; ++k) old[k] = marks[tile[k]];
+    // neighbouring nodes share most of their tiles: of the lanes of this warp
+    // that would stamp the same tile, only the lowest does the atomic
+    const unsigned act = __activemask();
 #pragma unroll
     for (int k = 0; k < 2 * KW; ++k) {
-        if ((k & 1) && tile[k] == tile[k - 1]) continue;  // both ends of the row in one tile
-        if (old[k] != stamp && atomicExch(&marks[tile[k]], stamp) != stamp)
-            c.tile_list[(size_t)p * c.n_tiles + atomicAdd(&c.tile_count[p], 1)] = tile[k];
+        const bool want = !((k & 1) && tile[k] == tile[k - 1])  // both ends of the row in one tile
+                          && old[k] != stamp;
+        const unsigned wm = __ballot_sync(act, want);
+        if (want) {
+            const unsigned peers = __match_any_sync(wm, tile[k]);
+            if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && atomicExch(&marks[tile[k]], stamp) != stamp)
+                c.tile_list[(size_t)p * c.n_tiles + atomicAdd(&c.tile_count[p], 1)] = tile[k];
+        }
     }
 }
 
