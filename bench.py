@@ -36,7 +36,7 @@ E2E_CHUNK = 16  # steps between trajectory copies in the end-to-end measurement
 # 256x128x128 two-swimmer box, from the ncu capture summarised in
 # profiles/k_lb_main_pair_side_3_256x128x128.md (mean of both AA parities).
 # Reported as roofline.traffic only for FP32 storage.
-K_LB_MAIN_F32_DRAM_BYTES = 558.8e6
+K_LB_MAIN_F32_DRAM_BYTES = 558.6e6
 WORKLOAD = "two_swimmer_boxes_256x128x128_x6"
 
 
