@@ -334,15 +334,17 @@ def _f_dev(f, w, rho0=1.0):
 def _run_configs(a, stream):
     """The other configurations of the problem statement on one GPU, each with
     its error against the FP64 oracle: one swimmer in 48^3 (radius 4,
-    subdivision 2, period 500) for its full 500 steps, and two side-by-side
-    swimmers in 256^3 (gap 3 radii) for 16 steps (the oracle's share of the
-    budget); throughput of both in FP32 / FP16 / BF16 storage (64 timed
-    steps for 256^3); and the oracle's throughput on one core and on all."""
+    subdivision 2, period 500) for its full 500 steps, two side-by-side
+    swimmers in 256^3 (gap 3 radii) for 16 steps, and the paper's own
+    1024 x 256 x 256 box with two in-line swimmers for 8 steps (the oracle's
+    share of the budget); throughput of each in FP32 / FP16 / BF16 storage
+    (64 / 32 timed steps for the large boxes); and the oracle's throughput on
+    one core and on all."""
     import numpy as np
     import torch
     import oracle
     from paper_2202_12147_gb300 import Simulation, lattice
-    from workloads import assemble, pair_side_256cube, single_swimmer_48
+    from workloads import assemble, pair_side_256cube, paper_box_1024x256x256, single_swimmer_48
     cg, wg = lattice()
     co, wo = oracle.lattice()
     perm = [next(k for k in range(19) if (co[k] == cg[i]).all()) for i in range(19)]
@@ -357,7 +359,8 @@ def _run_configs(a, stream):
 
     out = {}
     for name, box, n_err, n_time in (("single_swimmer_48", single_swimmer_48(), 500, 500),
-                                     ("pair_side_256cube", pair_side_256cube(), 16, 64)):
+                                     ("pair_side_256cube", pair_side_256cube(), 16, 64),
+                                     ("paper_box_1024x256x256", paper_box_1024x256x256(), 8, 32)):
         asm = assemble(box)
         osim = oracle.OracleSim(box, asm)
         x0 = osim.swimmer_centres()
@@ -368,7 +371,10 @@ def _run_configs(a, stream):
         for st in ("f32", "f16", "bf16"):
             sim = Simulation(box.dims, asm, tau=box.tau, rho0=box.rho0, storage=st)
             sim.lb_step(n_err)
-            u = u_of(sim.get_populations())
+            if box.n_cells > 50_000_000:  # the library's macroscopic fields (no 10 GB population copy)
+                u = sim.lb_get_macros()[1].cpu().numpy().astype(np.float64)
+            else:
+                u = u_of(sim.get_populations())
             disp = np.array([sim.swimmer_state(k)["disp"] for k in range(sim.n_swimmers)])
             if n_err % 2:
                 sim.lb_step(1)  # even parity: the timed steps replay whole graphs

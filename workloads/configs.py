@@ -156,6 +156,21 @@ def pair_side_256cube():
     return swimmer_pair("side", 3, dims=(256, 256, 256))
 
 
+def paper_box_1024x256x256(period=20000.0):
+    """The paper's simulation box (Sec. 3): 1024 x 256 x 256 cells, with two
+    swimmers of bead radius 5 and spring length 36 (subdivision 3 = 642
+    nodes per bead, k = 0.005, drive 1e-3, alpha = pi/2, period 2e4 steps)
+    in line along x, their centres two swimmer lengths apart (the paper's
+    closest in-line case), placed symmetrically about the box centre."""
+    a, L = 5.0, 36.0
+    l_swim = 2 * L + 2 * a
+    dims = (1024, 256, 256)
+    cx, cy, cz = (float(d // 2) for d in dims)
+    sw = tuple(SwimmerSpec(center=(cx + s * l_swim, cy, cz), radius=a, subdiv=3, spacing=L, k_spring=0.005, Gs=0.01,
+                           period=period).with_drive(1e-3, 1e-3, math.pi / 2) for s in (-1.0, 1.0))
+    return BoxSpec(dims=dims, swimmers=sw, name="paper_inline_2L_1024x256x256")
+
+
 def balanced_drive(A=1e-3, B=1e-3, alpha=math.pi / 2):
     """Per-bead drive (A1, A2, A3, phi1, phi2, phi3) whose middle bead carries
     minus the sum of the outer two: f1 + f3 = A sin(wt) + B sin(wt + alpha)
