@@ -394,7 +394,10 @@ def _run_configs(a, stream):
             esize = 4 if st == "f32" else 2
             bw = (box.n_cells - marked) * 19 * 2 * esize / (lb_ms / lb_n / 1e3) / 1e9
             res[st] = {"MLUPS": box.n_cells * n_time / (ms / 1e3) / 1e6, "velocity_rel_l2": rel(u, u_ref),
-                       "displacement_rel_err": float(np.abs(disp[:, 0] - d_ref[:, 0]).max() / np.abs(d_ref[:, 0]).max()),
+                       # a few steps into a long drive period the swimmers have not moved yet:
+                       # no relative displacement error then
+                       "displacement_rel_err": (float(np.abs(disp[:, 0] - d_ref[:, 0]).max() / np.abs(d_ref[:, 0]).max())
+                                                if n_err >= 0.01 * box.swimmers[0].period else None),
                        "k_lb_main_GBs": bw,
                        "timing": "MLUPS: lb_step (graph replays), CUDA events; k_lb_main_GBs: a second run of the "
                                  "same steps with events around every main-kernel launch"}
