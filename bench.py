@@ -33,8 +33,8 @@ METRIC = "MLUPS incl. IBM and % of HBM roofline (FP32 vs FP16-storage vs batched
 FALLBACK_HBM_GBS = 6800.0
 E2E_CHUNK = 16  # steps between trajectory copies in the end-to-end measurement
 # DRAM bytes (read + write) per launch of the FP32 main fluid kernel on one
-# 256x128x128 two-swimmer box, from the ncu capture summarised in
-# profiles/k_lb_main_pair_side_3_256x128x128.md (mean of both AA parities).
+# 256x128x128 two-swimmer box, from an ncu capture of that kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of both AA parities).
 # Reported as roofline.traffic only for FP32 storage.
 K_LB_MAIN_F32_DRAM_BYTES = 558.6e6
 WORKLOAD = "two_swimmer_boxes_256x128x128_x6"
@@ -59,8 +59,9 @@ def _args():
                     help="skip the adjoint (drive-gradient) line")
     ap.add_argument("--adjoint-precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--configs", action="store_true",
-                    help="also measure the single-swimmer 48^3 and the 256^3 precision configurations "
-                         "(throughput, error against the oracle) and the oracle on one core")
+                    help="also measure the single-swimmer 48^3, the 256^3 precision configuration and the "
+                         "paper's 1024x256x256 box (throughput, error against the oracle) and the oracle on "
+                         "one core")
     return ap.parse_args()
 
 
