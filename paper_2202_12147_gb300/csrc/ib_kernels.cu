@@ -246,9 +246,11 @@ __device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid) {
             const unsigned cell = rowbase + (unsigned)xx;
             const float w = sw[ln][0][k] * wyz;
             if (DET) {
-                atomicAdd(&c.Fdet[cell], (unsigned long long)llrint((double)(w * f.x) * FIX_SCALE));
-                atomicAdd(&c.Fdet[c.Npad + cell], (unsigned long long)llrint((double)(w * f.y) * FIX_SCALE));
-                atomicAdd(&c.Fdet[2 * c.Npad + cell], (unsigned long long)llrint((double)(w * f.z) * FIX_SCALE));
+                // the FP32 contribution scaled by 2^48 (exact) and rounded to the
+                // nearest integer: no FP64 arithmetic, which is slow on this GPU
+                atomicAdd(&c.Fdet[cell], (unsigned long long)__float2ll_rn((w * f.x) * FIX_SCALE_F));
+                atomicAdd(&c.Fdet[c.Npad + cell], (unsigned long long)__float2ll_rn((w * f.y) * FIX_SCALE_F));
+                atomicAdd(&c.Fdet[2 * c.Npad + cell], (unsigned long long)__float2ll_rn((w * f.z) * FIX_SCALE_F));
             } else {
                 atomicAdd(&c.F[cell], make_float4(w * f.x, w * f.y, w * f.z, 0.f));
             }

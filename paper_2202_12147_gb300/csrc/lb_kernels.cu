@@ -151,7 +151,8 @@ __device__ __forceinline__ float3 take_fdet(unsigned long long *Fd, long long Np
     Fd[cell] = 0ull;
     Fd[Npad + cell] = 0ull;
     Fd[2 * Npad + cell] = 0ull;
-    return make_float3((float)((double)a * FIX_INV), (float)((double)b * FIX_INV), (float)((double)c * FIX_INV));
+    // one rounding of the integer to FP32, then the exact scaling by 2^-48
+    return make_float3(__ll2float_rn(a) * FIX_INV_F, __ll2float_rn(b) * FIX_INV_F, __ll2float_rn(c) * FIX_INV_F);
 }
 
 // Full update of cell (x, y, z): load (streaming pull of the AA pattern),

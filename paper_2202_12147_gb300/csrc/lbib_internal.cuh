@@ -156,6 +156,12 @@ struct ClassArgs {
 // (resolution 3.6e-15, range +-32768 per cell)
 constexpr double FIX_SCALE = 281474976710656.0;
 constexpr double FIX_INV = 1.0 / 281474976710656.0;
+// the same powers of two in FP32 (exact), for conversions without FP64
+// arithmetic: the fixed-point values are the same integers as with the FP64
+// scaling, and the read-back equals it for |F| < 32 per cell (integers below
+// 2^53, exact in FP64)
+constexpr float FIX_SCALE_F = 281474976710656.0f;
+constexpr float FIX_INV_F = 3.5527136788005009e-15f;
 
 // ---------------------------------------------------------------- delta-kernel stencil
 // 1-D kernel weights on the KW stencil cells floor(p) - KW/2 + 1 ... floor(p) + KW/2.
