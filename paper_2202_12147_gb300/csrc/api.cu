@@ -78,7 +78,7 @@ struct Layout {
     size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0;
     // aux
     size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
-           obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0, oswp = 0, obv = 0, otrk = 0;
+           obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0, oswp = 0, obv = 0, otrk = 0, obacc = 0;
 };
 
 bool valid_params(const lb_params *p, std::string &why) {
@@ -190,6 +190,7 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     L.oxcm = o; o += up((size_t)S * 24 + 24);
     L.oswp = o; o += up((size_t)S * 64 + 64);
     L.obv = o; o += up((size_t)B * 16 + 16);
+    L.obacc = o; o += up((size_t)B * 24 + 24);
     L.otrk = o; o += up((size_t)LBIB_TRACK_STEPS * S * sizeof(lbib_track_point) + 16);
     L.bytes[2] = o;
     return L;
@@ -620,6 +621,7 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.xcm0 = (double *)(A + L.oxcm);
     d.sw_period = (double *)(A + L.oswp);
     d.bead_V = (float4 *)(A + L.obv);
+    d.bead_acc = (unsigned long long *)(A + L.obacc);
     d.track = (lbib_track_point *)(A + L.otrk);
 
     auto bail = [&](int code) {

@@ -264,50 +264,20 @@ __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) { g
 
 // Fold an advection into the bead centres: R_b += mean_j v_j (the mean is
 // linear, so this keeps R_b the centre of mass of its nodes, Fig. 1 caption).
-// One warp per bead, fixed-order sums.  Run by one block.
+// The blocks of the interpolation have summed their nodes' velocities into
+// bead_acc in fixed point (2^-48 units, exact integer sums); one thread per
+// bead takes and clears its sums.  Run by one block.
 __device__ void fold_bead_velocities(const DevCtx &c) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int b = w; b < c.n_beads; b += nw) {
-        const BeadDev bd = c.beads[b];
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        // four loads in flight per lane, added in the same order as one at a time
-        const int je = bd.node_start + bd.node_count;
-        int j = bd.node_start + l;
-        for (; j + 96 < je; j += 128) {
-            const float4 v0 = c.node_vel[j], v1 = c.node_vel[j + 32], v2 = c.node_vel[j + 64], v3 = c.node_vel[j + 96];
-            sx += v0.x;
-            sy += v0.y;
-            sz += v0.z;
-            sx += v1.x;
-            sy += v1.y;
-            sz += v1.z;
-            sx += v2.x;
-            sy += v2.y;
-            sz += v2.z;
-            sx += v3.x;
-            sy += v3.y;
-            sz += v3.z;
+    for (int b = threadIdx.x; b < c.n_beads; b += blockDim.x) {
+        const double inv = 1.0 / c.beads[b].node_count;
+        double *R = c.bead_R + 4 * b;
+        double v[3];
+        for (int a = 0; a < 3; ++a) {
+            const long long q = (long long)atomicExch(&c.bead_acc[3 * b + a], 0ull);
+            v[a] = (double)q * FIX_INV * inv;
+            R[a] += v[a];
         }
-        for (; j < je; j += 32) {
-            const float4 v = c.node_vel[j];
-            sx += v.x;
-            sy += v.y;
-            sz += v.z;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            sz += __shfl_xor_sync(0xffffffffu, sz, o);
-        }
-        if (l == 0) {
-            double *R = c.bead_R + 4 * b;
-            const float vx = sx * bd.inv_count, vy = sy * bd.inv_count, vz = sz * bd.inv_count;
-            R[0] += (double)vx;
-            R[1] += (double)vy;
-            R[2] += (double)vz;
-            c.bead_V[b] = make_float4(vx, vy, vz, 0.f);
-        }
+        c.bead_V[b] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
     }
 }
 
@@ -371,6 +341,18 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
     const int nx = c.nx, ny = c.ny, nz = c.nz;
     double px = 0.0, py = 0.0, pz = 0.0;
     float vx = 0.f, vy = 0.f, vz = 0.f;
+    // fixed-point sums of this block's node velocities per bead (bead index
+    // minus that of the block's first node), flushed once per block: the
+    // bead-velocity means need no serial pass over the nodes afterwards
+    constexpr int SLOTS = INT_TPB / KW;
+    __shared__ unsigned long long s_acc[SLOTS][3];
+    __shared__ int s_b0;
+    const bool fold = ADVECT && mark_parity >= 0;
+    if (fold) {
+        for (int i = threadIdx.x; i < 3 * SLOTS; i += blockDim.x) s_acc[i / 3][i % 3] = 0ull;
+        if (threadIdx.x == 0) s_b0 = bid * SLOTS < c.n_nodes ? c.node_bead[bid * SLOTS] : 0;
+        __syncthreads();
+    }
     if (active) {
         px = c.rx[j];
         py = c.ry[j];
@@ -425,6 +407,16 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
             const float sp2 = vx * vx + vy * vy + vz * vz;
             if (!isfinite(sp2) || !isfinite(px + py + pz)) atomicOr(&c.ctl->err, ERR_NONFINITE);
             else if (sp2 > 0.01f) atomicOr(&c.ctl->err, ERR_UNSTABLE);
+            if (fold) {
+                const int b = c.node_bead[j], sl = b - s_b0;
+                const unsigned long long q[3] = {(unsigned long long)__float2ll_rn(vx * FIX_SCALE_F),
+                                                 (unsigned long long)__float2ll_rn(vy * FIX_SCALE_F),
+                                                 (unsigned long long)__float2ll_rn(vz * FIX_SCALE_F)};
+                for (int a = 0; a < 3; ++a) {
+                    if (sl >= 0 && sl < SLOTS) atomicAdd(&s_acc[sl][a], q[a]);
+                    else atomicAdd(&c.bead_acc[3 * b + a], q[a]);
+                }
+            }
         }
     }
     if (ADVECT && mark_parity >= 0) {
@@ -438,6 +430,13 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
             float fr;
             const int ox = stencil_axis(px, nx, KW, fr), oy = stencil_axis(py, ny, KW, fr), oz = stencil_axis(pz, nz, KW, fr);
             mark_stencil_plane<KW>(c, ox, oy, oz, l, next);
+        }
+        // the block's bead sums into the global accumulators (integer sums:
+        // the same result in any order)
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * SLOTS; i += blockDim.x) {
+            const unsigned long long v = s_acc[i / 3][i % 3];
+            if (v != 0ull) atomicAdd(&c.bead_acc[3 * (s_b0 + i / 3) + i % 3], v);
         }
         // the last block to finish folds the step's velocities into the bead
         // centres and closes the step (a completion count, no waiting)

@@ -122,6 +122,7 @@ struct DevCtx {
     double *bead_R;            // bead centres, 4 doubles per bead
     float4 *bead_ext;          // (f^d + f^s) / N_v per bead
     float4 *bead_V;            // mean node velocity of each bead in the last step
+    unsigned long long *bead_acc;  // [n_beads][3] fixed-point sums of the step's node velocities (zero between steps)
     lbib_track_point *track;   // [LBIB_TRACK_STEPS][n_swimmers] ring of trajectory points
 
     Control *ctl;
