@@ -152,10 +152,10 @@ __device__ __forceinline__ void prepare_body(const DevCtx &c, int bid) {
     if (bid == 0 && threadIdx.x == 0) c.tile_count[(c.ctl->step + 1) & 1] = 0;
     if (bid < c.n_swimmers) {
         swimmer_forces(c, bid);
-        return;
+    } else {
+        const int t = (bid - c.n_swimmers) * PREP_TPB + threadIdx.x;
+        if (t < c.n_tris) triangle_forces(c, t);
     }
-    const int t = (bid - c.n_swimmers) * PREP_TPB + threadIdx.x;
-    if (t < c.n_tris) triangle_forces(c, t);
 }
 
 __global__ void __launch_bounds__(PREP_TPB) k_ib_prepare(const DevCtx c) { prepare_body(c, blockIdx.x); }
@@ -606,41 +606,69 @@ __device__ __forceinline__ int batch_box(const int *off, int n, int b) {
     return lo;
 }
 
+// The batched immersed-boundary kernels walk their virtual blocks (the
+// blocks each box would launch alone) with a grid of at most a few blocks per
+// SM, so that the chain of many boxes, which runs at high priority beside the
+// main fluid launches, holds a bounded share of every SM.
 __global__ void __launch_bounds__(PREP_TPB) k_ib_prepare_batch(const BatchDev bt) {
-    const int b = batch_box(bt.off_prep, bt.n_boxes, blockIdx.x);
-    prepare_body(bt.boxes[b], blockIdx.x - bt.off_prep[b]);
+    for (int vb = blockIdx.x; vb < bt.blocks_prep; vb += gridDim.x) {
+        const int b = batch_box(bt.off_prep, bt.n_boxes, vb);
+        prepare_body(bt.boxes[b], vb - bt.off_prep[b]);
+    }
 }
 
 template <int KW, bool DET>
 __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread_batch(const BatchDev bt) {
-    const int b = batch_box(bt.off_gs, bt.n_boxes, blockIdx.x);
-    gather_spread_body<KW, DET>(bt.boxes[b], blockIdx.x - bt.off_gs[b]);
+    for (int vb = blockIdx.x; vb < bt.blocks_gs; vb += gridDim.x) {
+        const int b = batch_box(bt.off_gs, bt.n_boxes, vb);
+        gather_spread_body<KW, DET>(bt.boxes[b], vb - bt.off_gs[b]);
+        __syncthreads();  // the shared node tables are refilled by the next virtual block
+    }
 }
 
 template <int KW>
 __global__ void __launch_bounds__(INT_TPB) k_ib_interp_batch(const BatchDev bt) {
-    const int b = batch_box(bt.off_int, bt.n_boxes, blockIdx.x);
-    const DevCtx &c = bt.boxes[b];
-    interp_body<KW, true>(c, blockIdx.x - bt.off_int[b], bt.off_int[b + 1] - bt.off_int[b], nullptr,
-                          (int)((c.ctl->step + 1) & 1));
+    for (int vb = blockIdx.x; vb < bt.blocks_int; vb += gridDim.x) {
+        const int b = batch_box(bt.off_int, bt.n_boxes, vb);
+        const DevCtx &c = bt.boxes[b];
+        interp_body<KW, true>(c, vb - bt.off_int[b], bt.off_int[b + 1] - bt.off_int[b], nullptr,
+                              (int)((c.ctl->step + 1) & 1));
+        __syncthreads();  // shared accumulators and the last-block flag are reused
+    }
+}
+
+#ifndef LBIB_BATCH_IB_BLOCKS_PER_SM
+#define LBIB_BATCH_IB_BLOCKS_PER_SM 2
+#endif
+static int batch_ib_grid(int blocks) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    const int cap = LBIB_BATCH_IB_BLOCKS_PER_SM * sms;
+    return cap > 0 && blocks > cap ? cap : blocks;
 }
 
 cudaError_t launch_ib_batch(const BatchDev &bt, int kernel, int deterministic, int phase, cudaStream_t s) {
     if (phase == 0) {
-        if (bt.blocks_prep) launch_prio(k_ib_prepare_batch, bt.blocks_prep, PREP_TPB, 0, s, bt);
+        if (bt.blocks_prep) launch_prio(k_ib_prepare_batch, batch_ib_grid(bt.blocks_prep), PREP_TPB, 0, s, bt);
     } else if (phase == 1) {
         if (!bt.blocks_gs) return cudaSuccess;
+        const int g = batch_ib_grid(bt.blocks_gs);
         if (kernel == LBIB_LINEAR2) {
-            if (deterministic) launch_prio(k_ib_gather_spread_batch<2, true>, bt.blocks_gs, GS_TPB, 0, s, bt);
-            else launch_prio(k_ib_gather_spread_batch<2, false>, bt.blocks_gs, GS_TPB, 0, s, bt);
+            if (deterministic) launch_prio(k_ib_gather_spread_batch<2, true>, g, GS_TPB, 0, s, bt);
+            else launch_prio(k_ib_gather_spread_batch<2, false>, g, GS_TPB, 0, s, bt);
         } else {
-            if (deterministic) launch_prio(k_ib_gather_spread_batch<4, true>, bt.blocks_gs, GS_TPB, 0, s, bt);
-            else launch_prio(k_ib_gather_spread_batch<4, false>, bt.blocks_gs, GS_TPB, 0, s, bt);
+            if (deterministic) launch_prio(k_ib_gather_spread_batch<4, true>, g, GS_TPB, 0, s, bt);
+            else launch_prio(k_ib_gather_spread_batch<4, false>, g, GS_TPB, 0, s, bt);
         }
     } else {
         if (!bt.blocks_int) return cudaSuccess;
-        if (kernel == LBIB_LINEAR2) launch_prio(k_ib_interp_batch<2>, bt.blocks_int, INT_TPB, 0, s, bt);
-        else launch_prio(k_ib_interp_batch<4>, bt.blocks_int, INT_TPB, 0, s, bt);
+        const int g = batch_ib_grid(bt.blocks_int);
+        if (kernel == LBIB_LINEAR2) launch_prio(k_ib_interp_batch<2>, g, INT_TPB, 0, s, bt);
+        else launch_prio(k_ib_interp_batch<4>, g, INT_TPB, 0, s, bt);
     }
     return cudaGetLastError();
 }
