@@ -44,6 +44,11 @@ namespace lbib {
 constexpr int PREP_TPB = 128;
 constexpr int GS_TPB = 128;
 constexpr int GS_NODES = 32;  // nodes per gather/spread block
+// deterministic spreading: per-block hash table of stencil cells
+constexpr int GS_HT_BITS = 10;
+constexpr int GS_HT = 1 << GS_HT_BITS;
+constexpr int GS_HT_PROBES = 16;
+constexpr unsigned GS_HT_EMPTY = 0xffffffffu;
 constexpr int INT_TPB = 128;
 
 // deterministic block reductions (fixed shuffle tree, then warps in order)
@@ -223,6 +228,22 @@ __device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid) {
         so[threadIdx.x][2] = stencil_axis(c.rz[j], c.nz, KW, fr);
         weights1d<KW>(fr, sw[threadIdx.x][2]);
     }
+    // deterministic mode: the block's fixed-point contributions are summed
+    // per cell in a shared hash table first (integer sums: the same result in
+    // any order), then added to the field once per distinct cell; neighbouring
+    // nodes share most of their stencil cells
+    unsigned *hk = nullptr;
+    unsigned long long (*hv)[3] = nullptr;
+    if constexpr (DET) {
+        __shared__ unsigned s_hk[GS_HT];
+        __shared__ unsigned long long s_hv[GS_HT][3];
+        hk = s_hk;
+        hv = s_hv;
+        for (int i = threadIdx.x; i < GS_HT; i += blockDim.x) {
+            s_hk[i] = GS_HT_EMPTY;
+            s_hv[i][0] = s_hv[i][1] = s_hv[i][2] = 0ull;
+        }
+    }
     __syncthreads();
     constexpr int ROWS = KW * KW;
     const int nx = c.nx, ny = c.ny, nz = c.nz;
@@ -248,12 +269,36 @@ __device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid) {
             if (DET) {
                 // the FP32 contribution scaled by 2^48 (exact) and rounded to the
                 // nearest integer: no FP64 arithmetic, which is slow on this GPU
-                atomicAdd(&c.Fdet[cell], (unsigned long long)__float2ll_rn((w * f.x) * FIX_SCALE_F));
-                atomicAdd(&c.Fdet[c.Npad + cell], (unsigned long long)__float2ll_rn((w * f.y) * FIX_SCALE_F));
-                atomicAdd(&c.Fdet[2 * c.Npad + cell], (unsigned long long)__float2ll_rn((w * f.z) * FIX_SCALE_F));
+                const unsigned long long q[3] = {(unsigned long long)__float2ll_rn((w * f.x) * FIX_SCALE_F),
+                                                 (unsigned long long)__float2ll_rn((w * f.y) * FIX_SCALE_F),
+                                                 (unsigned long long)__float2ll_rn((w * f.z) * FIX_SCALE_F)};
+                // linear probing, bounded: a full neighbourhood goes straight to the field
+                unsigned h = (cell * 2654435761u) >> (32 - GS_HT_BITS);
+                bool held = false;
+                for (int pr = 0; pr < GS_HT_PROBES; ++pr) {
+                    const unsigned old = atomicCAS(&hk[h], GS_HT_EMPTY, cell);
+                    if (old == GS_HT_EMPTY || old == cell) {
+                        held = true;
+                        break;
+                    }
+                    h = (h + 1) & (GS_HT - 1);
+                }
+                for (int a = 0; a < 3; ++a) {
+                    if (held) atomicAdd(&hv[h][a], q[a]);
+                    else atomicAdd(&c.Fdet[(size_t)a * c.Npad + cell], q[a]);
+                }
             } else {
                 atomicAdd(&c.F[cell], make_float4(w * f.x, w * f.y, w * f.z, 0.f));
             }
+        }
+    }
+    if constexpr (DET) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < GS_HT; i += blockDim.x) {
+            const unsigned cell = hk[i];
+            if (cell == GS_HT_EMPTY) continue;
+            for (int a = 0; a < 3; ++a)
+                if (hv[i][a] != 0ull) atomicAdd(&c.Fdet[(size_t)a * c.Npad + cell], hv[i][a]);
         }
     }
     if (__any_sync(0xffffffffu, unmarked) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_MARK);
