@@ -1293,6 +1293,12 @@ int lb_batch_create(lbib_ctx *const *ctxs, int n, lbib_batch **out) {
     bt.blocks_marked = std::max(1, std::min(marked, 65535));
     bt.max_tile_threads = max_threads;
     bt.cells_per_thread = cpt;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return bail(fail(LBIB_ECUDA, "querying the device failed"));
+        bt.ib_grid_cap = BATCH_IB_BLOCKS_PER_SM * sms;
+    }
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&b->ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||

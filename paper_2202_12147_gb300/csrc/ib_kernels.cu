@@ -682,26 +682,16 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp_batch(const BatchDev bt) 
     }
 }
 
-#ifndef LBIB_BATCH_IB_BLOCKS_PER_SM
-#define LBIB_BATCH_IB_BLOCKS_PER_SM 2
-#endif
-static int batch_ib_grid(int blocks) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 1;
-    }
-    const int cap = LBIB_BATCH_IB_BLOCKS_PER_SM * sms;
-    return cap > 0 && blocks > cap ? cap : blocks;
+static int batch_ib_grid(const BatchDev &bt, int blocks) {
+    return bt.ib_grid_cap > 0 && blocks > bt.ib_grid_cap ? bt.ib_grid_cap : blocks;
 }
 
 cudaError_t launch_ib_batch(const BatchDev &bt, int kernel, int deterministic, int phase, cudaStream_t s) {
     if (phase == 0) {
-        if (bt.blocks_prep) launch_prio(k_ib_prepare_batch, batch_ib_grid(bt.blocks_prep), PREP_TPB, 0, s, bt);
+        if (bt.blocks_prep) launch_prio(k_ib_prepare_batch, batch_ib_grid(bt, bt.blocks_prep), PREP_TPB, 0, s, bt);
     } else if (phase == 1) {
         if (!bt.blocks_gs) return cudaSuccess;
-        const int g = batch_ib_grid(bt.blocks_gs);
+        const int g = batch_ib_grid(bt, bt.blocks_gs);
         if (kernel == LBIB_LINEAR2) {
             if (deterministic) launch_prio(k_ib_gather_spread_batch<2, true>, g, GS_TPB, 0, s, bt);
             else launch_prio(k_ib_gather_spread_batch<2, false>, g, GS_TPB, 0, s, bt);
@@ -711,7 +701,7 @@ cudaError_t launch_ib_batch(const BatchDev &bt, int kernel, int deterministic, i
         }
     } else {
         if (!bt.blocks_int) return cudaSuccess;
-        const int g = batch_ib_grid(bt.blocks_int);
+        const int g = batch_ib_grid(bt, bt.blocks_int);
         if (kernel == LBIB_LINEAR2) launch_prio(k_ib_interp_batch<2>, g, INT_TPB, 0, s, bt);
         else launch_prio(k_ib_interp_batch<4>, g, INT_TPB, 0, s, bt);
     }

@@ -143,7 +143,13 @@ struct BatchDev {
     int blocks_main, blocks_prep, blocks_gs, blocks_int, blocks_marked;
     int max_tile_threads;  // widest tile of any box, in threads
     int cells_per_thread;  // common to every box of the batch
+    int ib_grid_cap;       // most blocks of a batched immersed-boundary launch (BATCH_IB_BLOCKS_PER_SM per SM)
 };
+
+// blocks per SM of the batched immersed-boundary launches, which walk their
+// virtual blocks in a grid-stride loop (measured: 1 too few, 2 best, 4 and
+// uncapped slower on the 64-box ensemble)
+constexpr int BATCH_IB_BLOCKS_PER_SM = 2;
 
 // Boxes of one size passed by value to one launch of the main fluid kernel
 // (grid (tiles_x, ny, nz * n)); the descriptors sit in the parameter bank.
