@@ -269,7 +269,7 @@ int lb_profile_read(lbib_ctx *ctx, double *total_ms, long long *launches);
  * start-up.  It needs no context and no caller scratch.
  *
  * Computes F(x) = sum_j f_j Delta(x - r_j) on a periodic nx x ny x nz box
- * (Sec. 2.3, Eq. spreading) with the same fixed-point accumulation as a
+ * with the same fixed-point accumulation as a
  * deterministic context, so the result is bitwise reproducible and equals
  * the force field ib_spread produces for the same positions and forces.
  *   nodes        DEVICE, n_nodes x 3 FP64 unwrapped positions (row-major)

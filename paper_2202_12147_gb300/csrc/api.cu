@@ -54,20 +54,6 @@ int env_int(const char *name, int dflt) {
 // two-swimmer box took 131 us, with it 105 us (direct launches: 108 us).
 bool use_graphs(long long) { return env_int("LBIB_GRAPHS", 1) != 0; }
 
-// Priority of the immersed-boundary stream: the highest by default;
-// LBIB_IB_PRIORITY=0 gives it the default priority (for comparisons).
-int ib_priority(int lo, int hi) { return env_int("LBIB_IB_PRIORITY", 1) ? hi : lo; }
-
-// Extra cells between population planes (a multiple of 64), so that the 19
-// planes do not start a power of two apart; LBIB_PLANE_PAD overrides it.
-long long plane_pad() {
-    const char *v = getenv("LBIB_PLANE_PAD");
-    if (v && v[0]) {
-        long long k = atoll(v);
-        return k < 0 ? 0 : (k + 63) / 64 * 64;
-    }
-    return 0;
-}
 
 struct Layout {
     long long N = 0, Npad = 0;
@@ -146,7 +132,7 @@ bool valid_structure(const lb_params *p, const lbib_structure *s, std::string &w
 Layout make_layout(const lb_params *p, const lbib_structure *s) {
     Layout L;
     L.N = (long long)p->nx * p->ny * p->nz;
-    L.Npad = (L.N + 63) / 64 * 64 + plane_pad();
+    L.Npad = (L.N + 63) / 64 * 64;
     L.esize = p->storage == LBIB_F32 ? 4 : 2;
     L.tile_x = p->nx <= LB_TPB ? p->nx : LB_TPB;
     L.tiles_x = (p->nx + L.tile_x - 1) / L.tile_x;
@@ -227,7 +213,6 @@ struct lbib_ctx {
     Control *h_ctl = nullptr;      // pinned
     lbib_swimmer_state *h_sws = nullptr;  // pinned
     int n_nodes = 0, n_swimmers = 0;
-    int slab_grid = 0;  // > 0: main fluid update by the TMA-staged slab kernel with this grid
     lbib_batch *batch = nullptr;   // set while the context belongs to a batch
     void *buf[LBIB_NBUF] = {nullptr, nullptr, nullptr};  // the caller buffers
 };
@@ -256,9 +241,8 @@ struct lbib_batch {
 
 namespace {
 
-// the update of every unmarked tile: TMA-staged rows or the tile kernel
+// the update of every unmarked tile
 cudaError_t main_fluid(lbib_ctx *c, bool odd, cudaStream_t s) {
-    if (c->slab_grid > 0) return launch_lb_slab(c->d, c->p.storage, c->p.forcing, odd, c->slab_grid, s);
     return launch_lb_main(c->d, c->p.storage, c->p.forcing, odd, s);
 }
 
@@ -674,20 +658,13 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         d.marked_grid = env_int("LBIB_MARKED_GRID", std::min(L.n_tiles, std::max(32, cnt + cnt / 4 + 16)));
     }
 
-    // main fluid kernel: TMA-staged slabs (LBIB_MAIN_KERNEL=slabs) or tiles
-    {
-        const char *mk = getenv("LBIB_MAIN_KERNEL");
-        const bool want = mk && std::string(mk) == "slabs";
-        c->slab_grid = want && lb_slab_supported(d, p->storage) ? lb_slab_grid(d, p->storage) : 0;
-    }
-
     // streams and events of the two-stream step; the IB stream gets the
     // highest priority so its small kernels are scheduled between fluid blocks
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&c->ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->ib, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&c->cap_ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->cap_ib, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->e_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->e_main, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->e_ib, cudaEventDisableTiming) != cudaSuccess)
@@ -1301,9 +1278,9 @@ int lb_batch_create(lbib_ctx *const *ctxs, int n, lbib_batch **out) {
     }
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&b->ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&b->ib, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&b->cap_ib, cudaStreamNonBlocking, ib_priority(prio_lo, prio_hi)) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&b->cap_ib, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->e_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->e_main, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->e_ib, cudaEventDisableTiming) != cudaSuccess)

@@ -547,9 +547,13 @@ __global__ void __launch_bounds__(INT_TPB) k_ib_interp(const DevCtx c, float *ve
 }
 
 // Observables, part 1: one block per (swimmer, bead), sums in a fixed order.
-// The centre is the FP64 mean of the node positions; velocities, forces and
-// torques are summed in FP32 like the FP32 node data they come from (the
-// lever arms r_j - R_b are taken in FP64 first).
+// The centre is the FP64 mean of the node positions.  The bead force
+// F_b = sum_j f_j and torque T_b = sum_j (r_j - R_b) x f_j are summed in FP64:
+// the membrane forces cancel over a bead (translation and rotation invariance
+// of the strain energy, Sec. 2.2), so F_b (the drive plus the springs) is a
+// small remainder of much larger node forces and T_b a remainder near zero;
+// an FP32 sum would lose the digits that are left.  The mean bead velocity
+// stays an FP32 sum like the FP32 node velocities it comes from.
 __global__ void __launch_bounds__(PREP_TPB) k_swimmer_beads(const DevCtx c) {
     __shared__ double smd[96];
     __shared__ float smf[96];
@@ -567,24 +571,26 @@ __global__ void __launch_bounds__(PREP_TPB) k_swimmer_beads(const DevCtx c) {
     }
     block_sum3(a, b, cc, smd);
     const double R0 = a * inv, R1 = b * inv, R2 = cc * inv;
-    float va = 0.f, vb = 0.f, vc = 0.f, fa = 0.f, fb = 0.f, fc = 0.f, ta = 0.f, tb = 0.f, tc = 0.f;
+    float va = 0.f, vb = 0.f, vc = 0.f;
+    double fa = 0.0, fb = 0.0, fc = 0.0, ta = 0.0, tb = 0.0, tc = 0.0;
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const float4 v = c.node_vel[j];
         const float4 f = c.node_force[j];
-        const float dx = (float)(c.rx[j] - R0), dy = (float)(c.ry[j] - R1), dz = (float)(c.rz[j] - R2);
+        const double dx = c.rx[j] - R0, dy = c.ry[j] - R1, dz = c.rz[j] - R2;
+        const double gx = f.x, gy = f.y, gz = f.z;
         va += v.x;
         vb += v.y;
         vc += v.z;
-        fa += f.x;
-        fb += f.y;
-        fc += f.z;
-        ta += dy * f.z - dz * f.y;
-        tb += dz * f.x - dx * f.z;
-        tc += dx * f.y - dy * f.x;
+        fa += gx;
+        fb += gy;
+        fc += gz;
+        ta += dy * gz - dz * gy;
+        tb += dz * gx - dx * gz;
+        tc += dx * gy - dy * gx;
     }
     block_sum3(va, vb, vc, smf);
-    block_sum3(fa, fb, fc, smf);
-    block_sum3(ta, tb, tc, smf);
+    block_sum3(fa, fb, fc, smd);
+    block_sum3(ta, tb, tc, smd);
     if (threadIdx.x == 0) {
         st->R[q][0] = R0;
         st->R[q][1] = R1;

@@ -623,269 +623,6 @@ __global__ void LBIB_LB_BOUNDS_ST(ST, CPT) k_lb_main(const DevCtx c) {
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// ---------------------------------------------------------------- TMA-staged slabs
-// Main fluid update of the unmarked rows with the populations staged through
-// shared memory by the bulk-copy (TMA) engine, for boxes whose rows are 64,
-// 128 or 256 cells long.  A slab is R consecutive rows (in y, at one z) with
-// R x nx x (bytes per value) = SLAB_PLANE_BYTES per plane, so every bulk copy
-// moves that much (less at a periodic y seam).  Each persistent block has one
-// producer thread and 256 consumer threads and a double buffer of two slab
-// stages (2 x 19 x SLAB_PLANE_BYTES):
-//   producer: loads the 19 plane slabs a slab reads (even step: plane i of
-//     its rows; odd step: plane opp(i) of rows y - c_iy at z - c_iz, so the x
-//     shift becomes a shared-memory index) on the stage's `full` mbarrier;
-//     when the consumers have marked the stage `done`, it sends each plane
-//     slab to its destination rows with bulk stores (skipping stamped rows,
-//     which the marked-tile kernel updates) and, once the stores have read
-//     the stage, refills it with the block's next slab;
-//   consumers: collide two adjacent cells per thread from shared memory,
-//     group by group of whole rows, and write the results back into the
-//     stage at their destination positions (the odd step's x shift wraps
-//     inside the row).
-// While the consumers work on one stage the other one is in flight.  The AA
-// pattern makes this race-free: the row-planes a row reads are exactly the
-// ones it writes, and no other row touches them.
-#ifndef LBIB_SLAB_PLANE_BYTES
-#define LBIB_SLAB_PLANE_BYTES 4096
-#endif
-#ifndef LBIB_SLAB_MINB
-#define LBIB_SLAB_MINB 1
-#endif
-constexpr int SLAB_PLANE_BYTES = LBIB_SLAB_PLANE_BYTES;
-constexpr int SLAB_CONSUMERS = 256;
-constexpr int SLAB_THREADS = SLAB_CONSUMERS + 32;
-constexpr long long SLAB_WAIT_LIMIT = 1ll << 26;  // bounded mbarrier polls
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(smem_addr(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar)) : "memory");
-}
-// bounded wait for the phase of the given parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
-    for (long long it = 0; it < limit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__host__ __device__ inline size_t slab_smem_bytes() {
-    return 2 * (size_t)Q * SLAB_PLANE_BYTES + 4 * sizeof(unsigned long long) + 4 * sizeof(int);
-}
-
-// rows per slab (0: the slab kernel does not handle this box)
-__host__ __device__ inline int slab_rows(int nx, int ny, int esize) {
-    const int rowbytes = nx * esize;
-    if (nx < 2 || 512 % nx || SLAB_PLANE_BYTES % rowbytes) return 0;
-    const int R = SLAB_PLANE_BYTES / rowbytes;
-    return (R <= 32 && ny % R == 0) ? R : 0;
-}
-
-template <int ST, bool ODD, int FORCING>
-__global__ void __launch_bounds__(SLAB_THREADS, LBIB_SLAB_MINB) k_lb_slab(const DevCtx c, int R) {
-    using S = Store<ST>;
-    using T = typename S::T;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int nx = c.nx, ny = c.ny, nz = c.nz;
-    const int slabs_y = ny / R, n_slabs = slabs_y * nz;
-    const unsigned rowbytes = (unsigned)(nx * sizeof(T));
-    T *const sbuf = reinterpret_cast<T *>(smem);
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem + 2 * (size_t)Q * SLAB_PLANE_BYTES);
-    unsigned long long *done = full + 2;
-    int *slab_id = reinterpret_cast<int *>(done + 2);
-    unsigned *slab_mask = reinterpret_cast<unsigned *>(slab_id + 2);
-    T *P = reinterpret_cast<T *>(c.pops);
-    const size_t Np = (size_t)c.Npad, nxy = (size_t)nx * ny;
-    auto buf = [&](int st, int i) { return sbuf + ((size_t)st * Q + i) * R * nx; };
-    auto wrapy = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
-    auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < 2; ++st) {
-            mbar_init(&full[st], 1);
-            mbar_init(&done[st], SLAB_CONSUMERS);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    if (threadIdx.x >= SLAB_CONSUMERS) {
-        // ------------------------------------------------ producer
-        if (threadIdx.x != SLAB_CONSUMERS) return;
-        const int *marks = c.marks + (ODD ? c.n_tiles : 0);
-        const int gen = c.ctl->gen[ODD ? 1 : 0];
-        const unsigned all = R == 32 ? 0xffffffffu : ((1u << R) - 1u);
-        auto marked_rows = [&](int s) {  // bit rr: row y0 + rr of slab s is stamped
-            const int y0 = (s % slabs_y) * R, z = s / slabs_y;
-            unsigned m = 0;
-            for (int rr = 0; rr < R; ++rr) m |= (marks[y0 + rr + ny * z] == gen ? 1u : 0u) << rr;
-            return m;
-        };
-        auto next_slab = [&](int s) {
-            while (s < n_slabs && marked_rows(s) == all) s += gridDim.x;
-            return s;
-        };
-        auto load = [&](int st, int s) {  // publish slab s (or the end) in stage st
-            if (s >= n_slabs) {
-                slab_id[st] = -1;
-                mbar_arrive(&full[st]);
-                return;
-            }
-            slab_id[st] = s;
-            slab_mask[st] = marked_rows(s);
-            mbar_expect_tx(&full[st], Q * R * rowbytes);
-            const int y0 = (s % slabs_y) * R, z = s / slabs_y;
-#pragma unroll 1
-            for (int i = 0; i < Q; ++i) {
-                const int pl = ODD ? opp(i) : i, dy = ODD ? -cy(i) : 0;
-                const size_t zo = (size_t)wrapz(z + (ODD ? -cz(i) : 0)) * nxy;
-                for (int rr = 0; rr < R;) {
-                    const int yy = wrapy(y0 + rr + dy);
-                    const int len = min(R - rr, ny - yy);
-                    bulk_load(buf(st, i) + (size_t)rr * nx, P + pl * Np + zo + (size_t)yy * nx, len * rowbytes, &full[st]);
-                    rr += len;
-                }
-            }
-        };
-        int s = next_slab(blockIdx.x);
-        for (int st = 0; st < 2; ++st) {
-            load(st, s);
-            if (s < n_slabs) s = next_slab(s + gridDim.x);
-        }
-        for (int j = 0;; ++j) {
-            const int st = j & 1;
-            const int cur = slab_id[st];
-            if (cur < 0) break;
-            if (!mbar_wait(&done[st], (unsigned)(j >> 1) & 1u, SLAB_WAIT_LIMIT)) {
-                atomicOr(&c.ctl->err, ERR_TIMEOUT);
-                break;
-            }
-            const unsigned mask = slab_mask[st];
-            const int y0 = (cur % slabs_y) * R, z = cur / slabs_y;
-#pragma unroll 1
-            for (int k = 0; k < Q; ++k) {  // plane k of the stage -> plane k of the destination rows
-                const int dy = ODD ? cy(k) : 0;
-                const size_t zo = (size_t)wrapz(z + (ODD ? cz(k) : 0)) * nxy;
-                for (int rr = 0; rr < R;) {
-                    if ((mask >> rr) & 1u) {
-                        ++rr;
-                        continue;
-                    }
-                    const int yy = wrapy(y0 + rr + dy);
-                    int len = 1;
-                    while (rr + len < R && !((mask >> (rr + len)) & 1u) && yy + len < ny) ++len;
-                    bulk_store(P + k * Np + zo + (size_t)yy * nx, buf(st, k) + (size_t)rr * nx, len * rowbytes);
-                    rr += len;
-                }
-            }
-            bulk_commit();
-            bulk_wait_read0();  // the stage may be overwritten
-            load(st, s);
-            if (s < n_slabs) s = next_slab(s + gridDim.x);
-        }
-        bulk_wait_all();  // every store has reached global memory
-        if (c.n_nodes == 0 && blockIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
-        return;
-    }
-
-    // ---------------------------------------------------- consumers
-    const int half = nx / 2, G = SLAB_CONSUMERS / half;  // rows per group
-    const int gr = threadIdx.x / half, x0 = 2 * (threadIdx.x % half);
-    const int xm = x0 ? x0 - 1 : nx - 1, x1 = x0 + 1, xp = x0 + 2 == nx ? 0 : x0 + 2;
-    const bool forced = c.has_g != 0;
-    bool ok = true;
-    for (int j = 0;; ++j) {
-        const int st = j & 1;
-        const bool late = !mbar_wait(&full[st], (unsigned)(j >> 1) & 1u, SLAB_WAIT_LIMIT);
-        unsigned any_late;
-        asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-                     : "=r"(any_late)
-                     : "r"((unsigned)late), "n"(SLAB_CONSUMERS)
-                     : "memory");
-        if (any_late) {
-            if (threadIdx.x == 0) atomicOr(&c.ctl->err, ERR_TIMEOUT);
-            break;
-        }
-        if (slab_id[st] < 0) break;
-        const unsigned mask = slab_mask[st];
-        for (int g0 = 0; g0 < R; g0 += G) {
-            const int rr = g0 + gr;
-            const bool act = rr < R && !((mask >> rr) & 1u);
-            float2 d[Q];
-            if (act) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const float m = S::scaled ? wgt(i) * c.st_inv_scale : 1.0f;
-                    const T *b = buf(st, i) + (size_t)rr * nx;
-                    if (!ODD || cx(i) == 0) d[i] = S::ld2(b + x0, m);
-                    else if (cx(i) > 0) d[i] = make_float2(S::ld(b + xm, m), S::ld(b + x0, m));
-                    else d[i] = make_float2(S::ld(b + x1, m), S::ld(b + xp, m));
-                }
-            }
-            asm volatile("bar.sync 1, %0;" ::"n"(SLAB_CONSUMERS) : "memory");  // the group's rows are read
-            if (act) {
-                float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
-                if (forced) {
-                    Fx = sp2(c.g[0]);
-                    Fy = sp2(c.g[1]);
-                    Fz = sp2(c.g[2]);
-                }
-                float2 ux, uy, uz, rho;
-                collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
-                ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const float m = S::scaled ? c.st_scale / wgt(i) : 1.0f;
-                    if (!ODD) {
-                        S::st2(buf(st, opp(i)) + (size_t)rr * nx + x0, d[i], m);  // slot opp(i) of the same cell
-                    } else {
-                        T *b = buf(st, i) + (size_t)rr * nx;                     // slot i of cell x + c_i
-                        if (cx(i) == 0) {
-                            S::st2(b + x0, d[i], m);
-                        } else if (cx(i) > 0) {
-                            S::st(b + x1, d[i].x, m);
-                            S::st(b + xp, d[i].y, m);
-                        } else {
-                            S::st(b + xm, d[i].x, m);
-                            S::st(b + x0, d[i].y, m);
-                        }
-                    }
-                }
-            }
-        }
-        fence_async_smem();
-        mbar_arrive(&done[st]);
-    }
-    report_bad(c, !ok);
-}
-
 // The marked tiles of this parity's list: a persistent grid walks the list.
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nblk) {
@@ -1120,55 +857,6 @@ static void class_dispatch(const ClassArgs &ca, int cpt, bool odd, cudaStream_t 
 cudaError_t launch_lb_class(const ClassArgs &ca, int storage, int forcing, int cpt, bool odd, cudaStream_t s) {
     LBIB_DISPATCH(class_dispatch, storage, forcing, ca, cpt, odd, s);
     return cudaGetLastError();
-}
-
-template <int ST, int FORCING>
-static void slab_dispatch(const DevCtx &c, bool odd, int grid, cudaStream_t s, cudaError_t *e) {
-    using T = typename Store<ST>::T;
-    const int R = slab_rows(c.nx, c.ny, (int)sizeof(T));
-    if (odd) k_lb_slab<ST, true, FORCING><<<grid, SLAB_THREADS, slab_smem_bytes(), s>>>(c, R);
-    else k_lb_slab<ST, false, FORCING><<<grid, SLAB_THREADS, slab_smem_bytes(), s>>>(c, R);
-    *e = cudaGetLastError();
-}
-
-// allow the slab kernels of one storage format their dynamic shared memory
-template <int ST>
-static cudaError_t slab_set_attr() {
-    const int B = (int)slab_smem_bytes();
-    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_lb_slab<ST, false, LBIB_GUO>, A, B)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_lb_slab<ST, true, LBIB_GUO>, A, B)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_lb_slab<ST, false, LBIB_SHAN_CHEN>, A, B)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_lb_slab<ST, true, LBIB_SHAN_CHEN>, A, B);
-}
-
-bool lb_slab_supported(const DevCtx &c, int storage) {
-    const int es = storage == LBIB_F32 ? 4 : 2;
-    return c.tile_x == c.nx && c.tiles_x == 1 && slab_rows(c.nx, c.ny, es) > 0;
-}
-
-cudaError_t launch_lb_slab(const DevCtx &c, int storage, int forcing, bool odd, int grid, cudaStream_t s) {
-    cudaError_t e = cudaSuccess;
-    LBIB_DISPATCH(slab_dispatch, storage, forcing, c, odd, grid, s, &e);
-    return e;
-}
-
-int lb_slab_grid(const DevCtx &c, int storage) {
-    int dev = 0, sms = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 0;
-    cudaError_t e = storage == LBIB_F16 ? slab_set_attr<LBIB_F16>()
-                    : storage == LBIB_BF16 ? slab_set_attr<LBIB_BF16>() : slab_set_attr<LBIB_F32>();
-    if (e != cudaSuccess) return 0;
-    if (storage == LBIB_F16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_slab<LBIB_F16, false, LBIB_GUO>, SLAB_THREADS, slab_smem_bytes());
-    else if (storage == LBIB_BF16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_slab<LBIB_BF16, false, LBIB_GUO>, SLAB_THREADS, slab_smem_bytes());
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_slab<LBIB_F32, false, LBIB_GUO>, SLAB_THREADS, slab_smem_bytes());
-    if (e != cudaSuccess || per < 1) return 0;
-    const int es = storage == LBIB_F32 ? 4 : 2;
-    const int R = slab_rows(c.nx, c.ny, es);
-    const int slabs = R ? (c.ny / R) * c.nz : 0;
-    return std::min(slabs, sms * per);
 }
 
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s) {

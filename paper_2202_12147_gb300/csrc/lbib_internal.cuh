@@ -229,10 +229,6 @@ bool check_structure(const lb_params *p, const lbib_structure *s, std::string &w
 // ---------------------------------------------------------------- launchers
 // LB (lb_kernels.cu)
 cudaError_t launch_lb_main(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
-// main fluid update with TMA-staged slabs of rows (rows of 64, 128 or 256 cells)
-bool lb_slab_supported(const DevCtx &c, int storage);
-int lb_slab_grid(const DevCtx &c, int storage);  // persistent grid size (0: cannot run)
-cudaError_t launch_lb_slab(const DevCtx &c, int storage, int forcing, bool odd, int grid, cudaStream_t s);
 cudaError_t launch_lb_marked(const DevCtx &c, int storage, int forcing, bool odd, cudaStream_t s);
 cudaError_t launch_lb_macros(const DevCtx &c, int storage, bool odd, float *rho, float *u, cudaStream_t s);
 cudaError_t launch_lb_batch(const BatchDev &bt, int storage, int forcing, int det, bool marked, bool odd, cudaStream_t s);

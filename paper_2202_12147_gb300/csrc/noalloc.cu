@@ -78,15 +78,18 @@ __global__ void k_spread_fixed(const double *r, const float *f, int n_nodes, int
     for (int k = 0; k < KW; ++k) {
         const unsigned cell = rowbase + (unsigned)((ox + k) % nx);
         const float w = wx[k] * wyz;
-        atomicAdd(&acc[cell], (unsigned long long)llrint((double)(w * fx) * FIX_SCALE));
-        atomicAdd(&acc[N + cell], (unsigned long long)llrint((double)(w * fy) * FIX_SCALE));
-        atomicAdd(&acc[2 * N + cell], (unsigned long long)llrint((double)(w * fz) * FIX_SCALE));
+        // scaling by 2^48 is exact in FP32, so this is the nearest integer to
+        // the FP32 contribution in 2^-48 units, with no FP64 arithmetic
+        atomicAdd(&acc[cell], (unsigned long long)__float2ll_rn((w * fx) * FIX_SCALE_F));
+        atomicAdd(&acc[N + cell], (unsigned long long)__float2ll_rn((w * fy) * FIX_SCALE_F));
+        atomicAdd(&acc[2 * N + cell], (unsigned long long)__float2ll_rn((w * fz) * FIX_SCALE_F));
     }
 }
 
 __global__ void k_acc_to_float(const unsigned long long *acc, long long N, float *out) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x)
-        for (int a = 0; a < 3; ++a) out[3 * k + a] = (float)((double)(long long)acc[a * N + k] * FIX_INV);
+        // one rounding (integer to FP32), then an exact scaling by 2^-48
+        for (int a = 0; a < 3; ++a) out[3 * k + a] = __ll2float_rn((long long)acc[a * N + k]) * FIX_INV_F;
 }
 
 }  // namespace

@@ -1,18 +1,32 @@
 """Long runs on the full-size two-swimmer boxes against the FP64 oracle's
 stored results (tests/golden/longrun_*.json, written by
-make_longrun_golden.py from oracle/ alone): the 256 x 128 x 128 side-by-side
-box of the benchmark over three drive periods (6000 steps) and the 256^3
-pair over one period (2000 steps), with FP32, FP16 and BF16 population
-storage, advanced as the benchmark advances them (16-step graph replays on
-two streams).
+make_longrun_golden.py from oracle/ alone), with FP32, FP16 and BF16
+population storage, advanced as the benchmark advances them (16-step graph
+replays on two streams):
 
-Checked against the oracle:
+* the six pairs of the 256 x 128 x 128 box (in line and side by side, surface
+  gaps of 3, 5 and 8 bead radii), each over the drive periods its stored run
+  holds (at least one period of 2000 steps);
+* the 256^3 side-by-side pair over the periods its stored run holds (five
+  periods = 10,000 steps when complete).
+
+Checked against the oracle, with the bounds the workloads state:
 * x_cm of both swimmers every 100 steps;
 * the mean swimming velocity of every completed drive period (Sec. 3, Eq.
-  vel_swim), within 1 % (BF16 storage: 2 %), and the device's own record of
-  the last one;
-* the velocity u after the last step at the stored cells (2048 random ones
-  and the 512 of largest |u|), as a relative L2 error over that sample.
+  vel_swim) within 1 %, and the device's own record of the last one;
+* the velocity u at the stored cells (2048 random ones and the 512 of
+  largest |u|) after drive period 1 and after the last stored period, as a
+  relative L2 error over that sample: <= 1e-5 for FP32 storage, <= 2e-3 for
+  FP16 and BF16.
+
+BF16 keeps 8 significant bits, so every stored deviation is rounded at up to
+3.9e-3 relative whatever the storage scale, while the net swimming velocity
+is a small second-order drift (about 5e-8 lattice units per step against
+bead oscillation velocities of 1e-4).  Where its period velocity misses the
+1 % bound the case is marked as an expected failure (strict, so that a pass
+shows up too).  The BF16 runs use deterministic spreading so that the
+outcome is the same on every run (float atomics reorder the sums; two
+non-deterministic runs of the three-period case gave 1.5 % and 2.0 %).
 """
 import json
 import os
@@ -25,44 +39,64 @@ from gpu_helpers import gpu_sim
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-# relative L2 bound of the velocity sample: 1e-5 for FP32 storage, 2e-3 for
-# the 16-bit storage formats (the same bounds as the short parity runs)
 U_TOL = {"f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}
-# relative bound of the per-period mean swimming velocity: 1 %; BF16 storage
-# (8-bit significand, 3.9e-3 relative rounding of every stored deviation) misses
-# it on the three-period run (1.5 % and 2.0 % in two runs: the float atomics of
-# spreading make runs differ; FP16 0.13 %), so its bound is 3 %
-V_TOL = {"f32": 1e-2, "f16": 1e-2, "bf16": 3e-2}
+V_TOL = 1e-2
+PAIR_CASES = [f"{arr}{gap}_256x128x128" for arr in ("inline", "side") for gap in (3, 5, 8)]
+# BF16 cases whose period velocity misses 1 % (measured, deterministic spreading)
+BF16_V_MISS = {}
 
 
 def _gold(name):
-    with open(os.path.join(HERE, "golden", f"longrun_{name}.json")) as fh:
+    path = os.path.join(HERE, "golden", f"longrun_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"no stored oracle run {os.path.basename(path)}")
+    with open(path) as fh:
         return json.load(fh)
 
 
+def _samples(gold):
+    """{step: (cells, u)} of the stored velocity samples."""
+    if "u_samples" in gold:
+        return {int(k): (v["cells"], np.array(v["u"])) for k, v in gold["u_samples"].items()}
+    return {gold["steps"]: (gold["cells"], np.array(gold["u"]))}
+
+
+def _box(name):
+    from workloads import pair_side_256cube, swimmer_pair
+    if name == "side3_256cube":
+        return pair_side_256cube()
+    head = name.split("_")[0]
+    return swimmer_pair(head[:-1], int(head[-1]))
+
+
 def _run(box, gold, storage):
+    import torch
     from workloads import assemble
     asm = assemble(box)
-    sim = gpu_sim(box, asm, storage=storage)
+    sim = gpu_sim(box, asm, storage=storage, deterministic=(storage == "bf16"))
     S = sim.n_swimmers
+    want = _samples(gold)
     xs = [[sim.swimmer_state(s)["x_cm"] for s in range(S)]]
+    us = {}
     every = gold["every"]
-    for _ in range(gold["steps"] // every):
+    for k in range(gold["steps"] // every):
         sim.lb_step(every)
         xs.append([sim.swimmer_state(s)["x_cm"] for s in range(S)])
+        t = (k + 1) * every
+        if t in want:
+            _, u = sim.lb_get_macros()
+            idx = torch.tensor(want[t][0], dtype=torch.long, device=u.device)
+            us[t] = u[idx].cpu().numpy().astype(np.float64)
     st = [sim.swimmer_state(s) for s in range(S)]
-    _, u = sim.lb_get_macros()
-    u = u[np_index(gold["cells"], u.device)].cpu().numpy().astype(np.float64)
     sim.close()
-    return np.array(xs), st, u
+    return np.array(xs), st, us
 
 
-def np_index(cells, device):
-    import torch
-    return torch.tensor(cells, dtype=torch.long, device=device)
-
-
-def _check(gold, storage, xs, st, u):
+def _check(name, storage):
+    gold = _gold(name)
+    box = _box(name)
+    assert list(box.dims) == gold["dims"]
+    xs, st, us = _run(box, gold, storage)
     xo = np.array([x for _, x in gold["x_cm"]])  # (samples, swimmers, 3)
     assert xs.shape == xo.shape
     # trajectories: the distance travelled is ~1e-3 lattice units per period
@@ -70,37 +104,44 @@ def _check(gold, storage, xs, st, u):
     x_err = np.abs(xs - xo).max() / travel
     # per-period mean swimming velocity along x (Sec. 3, Eq. vel_swim)
     T, every = gold["period"], gold["every"]
-    idx = [k * T // every for k in range(gold["steps"] // T + 1)]
+    P = gold["steps"] // T
+    idx = [k * T // every for k in range(P + 1)]
     vg = (xs[idx[1:], :, 0] - xs[idx[:-1], :, 0]) / T
     vo = (xo[idx[1:], :, 0] - xo[idx[:-1], :, 0]) / T
     v_err = np.abs(vg - vo).max() / np.abs(vo).min()
     # the device's record of the last completed period
     v_dev = np.array([s["v_period"][0] for s in st])
     dev_err = np.abs(v_dev - vo[-1]).max() / np.abs(vo[-1]).min()
-    uo = np.array(gold["u"])
-    u_err = np.linalg.norm(u - uo) / np.linalg.norm(uo)
-    print(f"{gold['case']} {storage}: x_cm {x_err:.2e} of the travel, period velocity {v_err:.2e} "
-          f"(device record {dev_err:.2e}), velocity sample rel. L2 {u_err:.2e}")
-    assert [s["periods"] for s in st] == [gold["steps"] // T] * len(st)
-    assert v_err < V_TOL[storage]
-    assert dev_err < V_TOL[storage]
+    u_err = {}
+    for t, (cells, uo) in _samples(gold).items():
+        u_err[t] = np.linalg.norm(us[t] - uo) / np.linalg.norm(uo)
+    print(f"{name} {storage}, {P} periods: x_cm {x_err:.2e} of the travel, period velocity {v_err:.2e} "
+          f"(device record {dev_err:.2e}; oracle v of the last period {vo[-1]}), velocity sample rel. L2 "
+          + ", ".join(f"step {t}: {e:.2e}" for t, e in sorted(u_err.items())))
+    assert [s["periods"] for s in st] == [P] * len(st)
     assert x_err < (1e-3 if storage == "f32" else 1e-2)
-    assert u_err < U_TOL[storage]
+    for t, e in u_err.items():
+        assert e < U_TOL[storage], (t, e)
+    assert v_err < V_TOL
+    assert dev_err < V_TOL
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
-def test_longrun_benchmark_box_three_periods(gpu_lib, storage):
-    from workloads import swimmer_pair
-    gold = _gold("side3_256x128x128")
-    box = swimmer_pair("side", 3)
-    assert list(box.dims) == gold["dims"]
-    _check(gold, storage, *_run(box, gold, storage))
+def _params(cases):
+    out = []
+    for c in cases:
+        for storage in ("f32", "f16", "bf16"):
+            marks = []
+            if storage == "bf16" and c in BF16_V_MISS:
+                marks = [pytest.mark.xfail(strict=True, reason=BF16_V_MISS[c])]
+            out.append(pytest.param(c, storage, marks=marks, id=f"{c}-{storage}"))
+    return out
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
-def test_longrun_256cube_one_period(gpu_lib, storage):
-    from workloads import pair_side_256cube
-    gold = _gold("side3_256cube")
-    box = pair_side_256cube()
-    assert list(box.dims) == gold["dims"]
-    _check(gold, storage, *_run(box, gold, storage))
+@pytest.mark.parametrize("name,storage", _params(PAIR_CASES))
+def test_longrun_pair_256x128x128(gpu_lib, name, storage):
+    _check(name, storage)
+
+
+@pytest.mark.parametrize("name,storage", _params(["side3_256cube"]))
+def test_longrun_pair_256cube(gpu_lib, name, storage):
+    _check(name, storage)

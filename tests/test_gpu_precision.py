@@ -1,11 +1,10 @@
 """Reduced-precision population storage (FP16 / BF16 of the scaled shifted
 deviations d_i / w_i * S, collided in FP32) against the FP64 oracle.
 
-Tolerance: velocity field relative L2 <= 2e-3 for FP16 storage after the
-stated step counts, swimmer displacement within 1 %.  A 16-bit float keeps
-11 (FP16) or 8 (BF16) significant bits, so each stored deviation carries a
-relative rounding error of 2^-12 or 2^-9 per step; BF16 is reported against
-a looser bound that follows from its 8-bit mantissa (2^-9 ~ 2e-3 per value).
+Tolerance: velocity field relative L2 <= 2e-3 after the stated step counts
+and swimmer displacement within 1 %, for both 16-bit formats.  A 16-bit
+float keeps 11 (FP16) or 8 (BF16) significant bits, so each stored deviation
+carries a relative rounding error of up to 2^-12 or 2^-9 per step.
 """
 import numpy as np
 import pytest
@@ -16,7 +15,7 @@ from workloads import assemble, fluid_box, random_populations, single_swimmer_48
 
 pytestmark = pytest.mark.gpu
 
-BOUND = {"f16": 2e-3, "bf16": 1.6e-2}
+BOUND = {"f16": 2e-3, "bf16": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +46,7 @@ def test_fluid_step_reduced_storage(perm, storage):
     _, ug = oracle.macros(fg)
     _, uo = oracle.macros(fo)
     err = rel_l2(ug, uo)
+    print(f"{storage}: velocity rel L2 after 20 steps {err:.3e}")
     assert err < BOUND[storage], err
     sim.close()
 
