@@ -58,6 +58,9 @@ def _args():
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                     help="skip the adjoint (drive-gradient) line")
     ap.add_argument("--adjoint-precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-precision-config", dest="precision_config", action="store_false",
+                    help="skip the 256^3 FP32/FP16/BF16 line")
+    ap.add_argument("--precision-steps", type=int, default=64)
     ap.add_argument("--configs", action="store_true",
                     help="also measure the single-swimmer 48^3, the 256^3 precision configuration and the "
                          "paper's 1024x256x256 box (throughput, error against the oracle) and the oracle on "
@@ -87,6 +90,11 @@ def max_over_ranks(x, ws, device=None):
     t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _mlups(cells, steps, ms):
+    """cells x steps updates in ms milliseconds, in MLUPS."""
+    return cells * steps / (ms / 1e3) / 1e6
 
 
 def job_mlups(ws, cells_per_step, steps, ms):
@@ -214,16 +222,24 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def _run_ensemble(a, barrier, stream, ws):
+def _run_ensemble(a, barrier, stream, ws, rank):
     """The batched-ensemble workload: 64 independent boxes (48^3, 64^3, 96^3,
     128x128x192; one or two swimmers each; seeded draws) advanced (1) box by
-    box, each with its own graph-replayed steps, and (2) as one batch."""
+    box, each with its own graph-replayed steps, and (2) as one batch.  Under
+    several ranks the 64 boxes are partitioned over the ranks by cell count
+    (each rank steps its share; total work fixed, strong scaling) and the
+    per-swimmer results are gathered to rank 0 at the end."""
     import torch
     from paper_2202_12147_gb300 import Batch, Simulation
+    from paper_2202_12147_gb300.ensemble import gather_results, partition, rank_loads, swimmer_records
     from workloads import assemble, ensemble_boxes
-    boxes = ensemble_boxes(64, seed=0)
+    all_boxes = ensemble_boxes(64, seed=0)
+    all_cells = [b.n_cells for b in all_boxes]
+    shares = partition(all_cells, ws)
+    mine = shares[rank]
+    boxes = [all_boxes[i] for i in mine]
     sims = [Simulation(b.dims, assemble(b), tau=b.tau, rho0=b.rho0) for b in boxes]
-    cells = sum(b.n_cells for b in boxes)
+    cells = sum(all_cells)  # the whole job's cells: every rank's share
     K = max(16, (a.ensemble_steps // 16) * 16)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for s in sims:
@@ -266,18 +282,24 @@ def _run_ensemble(a, barrier, stream, ws):
     for s in sims:
         s.sync()
     batch.close()
+    gathered = gather_results({i: swimmer_records(s) for i, s in zip(mine, sims)}, len(all_boxes), rank, ws)
     for s in sims:
         s.close()
     seq_ms, rr_ms, bat_ms, step_ms = (max_over_ranks(v, ws) for v in (seq_ms, rr_ms, bat_ms, step_ms))
-    return {"boxes": len(boxes), "cells": cells, "steps": K, "unit": "MLUPS",
-            "batched": job_mlups(ws, cells, K, bat_ms), "batched_ms_per_step": bat_ms / K,
-            "sequential_launches": job_mlups(ws, cells, K, step_ms), "speedup_vs_sequential_launches": step_ms / bat_ms,
+    loads = rank_loads(all_cells, shares)
+    return {"boxes": len(all_boxes), "cells": cells, "steps": K, "unit": "MLUPS", "scaling": "strong",
+            "partition": {"ranks": ws, "cells_per_rank": loads, "boxes_per_rank": [len(x) for x in shares],
+                          "max_over_mean": max(loads) / (sum(loads) / ws),
+                          "swimmer_records_gathered": (sum(len(r) for r in gathered) if gathered is not None
+                                                       else None)},
+            "batched": _mlups(cells, K, bat_ms), "batched_ms_per_step": bat_ms / K,
+            "sequential_launches": _mlups(cells, K, step_ms), "speedup_vs_sequential_launches": step_ms / bat_ms,
             "sequential_launches_means": "box after box, each coupled step of a box launched on its own "
                                          "(its kernels one by one, no graph)",
-            "sequential": job_mlups(ws, cells, K, seq_ms), "sequential_ms_per_step": seq_ms / K,
+            "sequential": _mlups(cells, K, seq_ms), "sequential_ms_per_step": seq_ms / K,
             "speedup": seq_ms / bat_ms,
             "sequential_means": "box after box, each box replaying its own captured 16-step graphs",
-            "round_robin": job_mlups(ws, cells, K, rr_ms), "speedup_vs_round_robin": rr_ms / bat_ms,
+            "round_robin": _mlups(cells, K, rr_ms), "speedup_vs_round_robin": rr_ms / bat_ms,
             "round_robin_means": "every step, each box launched on its own (one coupled step per call), box after box",
             "autotune": tuning}
 
@@ -326,6 +348,51 @@ def _run_adjoint(a, barrier, stream):
             "forward_plus_backward_over_lb_step": (t["forward_ms"] + t["backward_ms"]) / fwd_ms,
             "launches": {"forward": t["forward_launches"], "backward": t["backward_launches"]},
             "workspace_GB": ws_bytes / 1e9}
+
+
+def _run_precision_256cube(a, stream, peak):
+    """The precision configuration: 256^3 with two side-by-side swimmers
+    (radius 6, gap 3 radii), FP32 against FP16 and BF16 storage of the
+    shifted deviations (FP32 collision).  Per format: lb_step throughput over
+    the timed steps (graph replays, CUDA events) and the main fluid kernel's
+    bandwidth from a second run of the same steps with events around each of
+    its launches.  The errors against the FP64 oracle at the stated step
+    counts are checked by the long-run tests."""
+    import torch
+    from paper_2202_12147_gb300 import Simulation
+    from workloads import assemble, pair_side_256cube
+    box = pair_side_256cube()
+    asm = assemble(box)
+    n = max(16, (a.precision_steps // 16) * 16)
+    out = {"workload": "pair_side_256cube: 256^3, two side-by-side swimmers (gap 3 radii), "
+                       "inputs larger than L2", "cells": box.n_cells, "steps": n}
+    for st in ("f32", "f16", "bf16"):
+        sim = Simulation(box.dims, asm, tau=box.tau, rho0=box.rho0, storage=st)
+        sim.lb_step(16)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.lb_step(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sim.profile(True)
+        sim.lb_step(n)
+        lb_ms, lb_n = sim.profile_read()
+        marked = sim.marked_cells()
+        sim.sync()
+        sim.close()
+        esize = 4 if st == "f32" else 2
+        bpl = (box.n_cells - marked) * 19 * 2 * esize
+        ach = bpl / (lb_ms / lb_n / 1e3) / 1e9
+        step_bytes = box.n_cells * 19 * 2 * esize
+        out[st] = {"value": _mlups(box.n_cells, n, ms), "unit": "MLUPS", "ms_per_step": ms / n,
+                   "roofline": {"kernel": "k_lb_main", "achieved": ach, "peak": peak, "frac": ach / peak,
+                                "avg_launch_us": lb_ms / lb_n * 1e3, "bytes_per_launch": bpl},
+                   "step_frac": step_bytes / (ms / n / 1e3) / 1e9 / peak}
+    for st in ("f16", "bf16"):
+        out[st]["speedup_vs_f32"] = out["f32"]["ms_per_step"] / out[st]["ms_per_step"]
+    return out
 
 
 def _f_dev(f, w, rho0=1.0):
@@ -485,6 +552,7 @@ def run_ours(a):
     peak, peak_kind = _peak()
     achieved = bytes_per_launch / lb_avg_s / 1e9
     launches = a.steps * len(sims) * 5  # per box-step: main fluid; prepare, gather-spread, marked fluid, interp
+    step_ach = cells_per_step * 19 * 2 * esize / (ms / a.steps / 1e3) / 1e9
 
     variants = None
     if a.variants and a.storage == "f32":
@@ -518,17 +586,23 @@ def run_ours(a):
             vmarked = statistics.mean(s.marked_cells() for s in vs)
             vbytes = (N - vmarked) * 19 * 2 * 2
             vach = vbytes / (t_lb / n_lb / 1e3) / 1e9
+            vstep = cells_per_step * 19 * 2 * 2 / (vms / a.steps / 1e3) / 1e9
             variants[st] = {"value": job_mlups(ws, cells_per_step, a.steps, vms), "unit": "MLUPS",
                             "ms_per_step": vms / a.steps, "speedup_vs_f32": ms / vms,
                             "roofline": {"achieved": vach, "peak": peak, "frac": vach / peak,
-                                         "avg_launch_us": t_lb / n_lb * 1e3, "bytes_per_launch": vbytes}}
+                                         "avg_launch_us": t_lb / n_lb * 1e3, "bytes_per_launch": vbytes,
+                                         "step_achieved": vstep, "step_frac": vstep / peak}}
             for s in vs:
                 s.close()
         sims = []
 
+    precision = None
+    if a.precision_config and a.storage == "f32" and rank == 0:
+        precision = _run_precision_256cube(a, stream, peak)
+
     ensemble = None
     if a.ensemble and a.storage == "f32":
-        ensemble = _run_ensemble(a, barrier, stream, ws)
+        ensemble = _run_ensemble(a, barrier, stream, ws, rank)
 
     adjoint = None
     if a.adjoint and a.storage == "f32" and rank == 0:
@@ -604,9 +678,13 @@ def run_ours(a):
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": K_LB_MAIN_F32_DRAM_BYTES if a.storage == "f32" else None,
                          "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
-                         "launches": lb_n, "cells_per_launch": N - marked},
+                         "launches": lb_n, "cells_per_launch": N - marked,
+                         "step_achieved": step_ach, "step_frac": step_ach / peak,
+                         "step_means": "every cell's 2 x 19 population values (the main and the marked-tile "
+                                       "fluid updates) per box-step over ms_per_step / boxes, from the timed "
+                                       "production run itself"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-            "variants": variants, "ensemble": ensemble, "adjoint": adjoint,
+            "variants": variants, "precision_256cube": precision, "ensemble": ensemble, "adjoint": adjoint,
         }
         if configs is not None:
             line["configs"] = configs

@@ -43,7 +43,10 @@ U_TOL = {"f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}
 V_TOL = 1e-2
 PAIR_CASES = [f"{arr}{gap}_256x128x128" for arr in ("inline", "side") for gap in (3, 5, 8)]
 # BF16 cases whose period velocity misses 1 % (measured, deterministic spreading)
-BF16_V_MISS = {}
+BF16_V_MISS = {
+    "side3_256x128x128": "BF16 storage: per-period swimming velocity 1.48e-2 off over three periods (8-bit "
+                         "significand; FP16 1.7e-3, FP32 3.5e-4 on the same run)",
+}
 
 
 def _gold(name):
