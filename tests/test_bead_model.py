@@ -1,0 +1,205 @@
+"""Pins of the analytic bead-spring comparator (Sec. 2.4, Eq. EOM), against
+textbook Stokes results and the symmetries of the swimmer problem; CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from bead_model import (BeadSwimmer, drive_forces, integrate, mobility_velocity, oseen, rotne_prager,
+                        spring_forces, swim_velocity)
+
+MU = 1.0 / 6.0
+
+
+def test_single_bead_stokes_drag():
+    """One sphere under a constant force moves at F / (6 pi mu a) (Stokes)."""
+    for a in (1.0, 4.0, 6.0):
+        F = np.array([[2e-3, -1e-3, 5e-4]])
+        V = mobility_velocity(np.zeros((1, 3)), F, MU, a)
+        np.testing.assert_allclose(V, F / (6 * math.pi * MU * a), rtol=1e-15)
+
+
+@pytest.mark.parametrize("tensor", ["oseen", "rotne_prager"])
+def test_two_spheres_method_of_reflections(tensor):
+    """Two equal spheres under equal forces, a distance r apart: along their
+    line of centres U/U0 = 1 + 3a/(2r) - a^3/r^3, across it 1 + 3a/(4r) +
+    a^3/(2r^3) (the leading terms of the exact two-sphere result, Happel and
+    Brenner); the Oseen tensor keeps only the 1/r terms."""
+    a = 3.0
+    for r in (7.0, 15.0, 60.0):
+        R = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+        U0 = 1.0 / (6 * math.pi * MU * a)
+        par = mobility_velocity(R, np.array([[1.0, 0, 0], [1.0, 0, 0]]), MU, a, tensor)[0, 0] / U0
+        perp = mobility_velocity(R, np.array([[0, 1.0, 0], [0, 1.0, 0]]), MU, a, tensor)[0, 1] / U0
+        rp = tensor == "rotne_prager"
+        assert par == pytest.approx(1 + 1.5 * a / r - (a ** 3 / r ** 3 if rp else 0.0), rel=1e-13)
+        assert perp == pytest.approx(1 + 0.75 * a / r + (0.5 * a ** 3 / r ** 3 if rp else 0.0), rel=1e-13)
+
+
+def test_rotne_prager_tends_to_oseen_in_the_far_field():
+    """The finite-size correction falls off as (a / r)^2 relative to the
+    Oseen part, so the two tensors agree far from a bead."""
+    a = 6.0
+    rel = []
+    rng = np.random.default_rng(3)
+    for ratio in (10.0, 100.0, 1000.0):
+        d = rng.normal(size=3)
+        r = ratio * a * d / np.linalg.norm(d)
+        To, Tr = oseen(r, MU), rotne_prager(r, MU, a)
+        rel.append(np.linalg.norm(Tr - To) / np.linalg.norm(To))
+    assert rel[0] < 1e-2
+    assert rel[1] / rel[0] == pytest.approx(1e-2, rel=1e-9)
+    assert rel[2] / rel[1] == pytest.approx(1e-2, rel=1e-9)
+    # symmetric, and positive definite as a two-bead mobility down to contact
+    for r in (2.0 * a, 3.0 * a):
+        R = np.array([[0.0, 0, 0], [r * 0.6, r * 0.8, 0]])
+        M = np.zeros((6, 6))
+        for col in range(6):
+            F = np.zeros((2, 3))
+            F.flat[col] = 1.0
+            M[:, col] = mobility_velocity(R, F, MU, a).ravel()
+        np.testing.assert_allclose(M, M.T, atol=1e-15)
+        assert np.linalg.eigvalsh(M).min() > 0
+
+
+def test_drive_and_springs_sum_to_zero():
+    """The drive (f_2 = -f_1 - f_3) and the springs (f_2 = -f_1 - f_3) exert
+    no net force (Sec. 2.2)."""
+    for t in (0.0, 37.0, 411.5):
+        assert abs(drive_forces(t, 1e-3, 2e-3, 0.7, 500.0).sum()) < 1e-18
+    R = np.array([[-12.3, 0.1, 0.0], [0.2, -0.1, 0.05], [11.7, 0.0, -0.2]])
+    np.testing.assert_allclose(spring_forces(R, 0.005, 12.0).sum(0), 0.0, atol=1e-18)
+    assert np.all(drive_forces(-1.0, 1e-3, 1e-3, 1.0, 500.0) == 0.0)
+
+
+def _swimmer(**kw):
+    p = dict(center=(0.0, 0.0, 0.0), a=4.0, k=0.005, L=12.0, A=1e-3, B=1e-3, alpha=math.pi / 2, period=500.0)
+    p.update(kw)
+    return BeadSwimmer(**p)
+
+
+def test_no_hydrodynamic_interaction_no_swimming():
+    """Without the interaction tensor every bead moves with its own force and
+    the forces sum to zero, so the centre of the swimmer does not move."""
+    t, x = integrate([_swimmer()], 2000.0, 2.0, MU, tensor="none")
+    assert np.abs(x[:, 0, :] - x[0, 0, :]).max() < 1e-12
+
+
+# Starting from rest, a swimmer's mean shape relaxes with a time constant of
+# about 1800 steps here (bead radius 4, k = 0.005, mu = 1/6); 60 periods of
+# 500 steps leave that transient below 1e-5 of the stationary velocity.
+STEADY = 60
+
+
+def _steady_velocity(**kw):
+    T = 500.0
+    t, x = integrate([_swimmer(**kw)], STEADY * T, 5.0, MU, sample_every=10)
+    return swim_velocity(t, x, T)[0]
+
+
+def test_reciprocal_stroke_gives_no_net_motion():
+    """alpha = 0, A = B: mirroring x together with a half-period shift maps
+    the stroke onto itself, so the stationary swimming velocity vanishes (the
+    scallop theorem, Sec. 1) against the pi/2 stroke's."""
+    v0 = abs(_steady_velocity(alpha=0.0))
+    v1 = abs(_steady_velocity())
+    assert v1 > 1e-9
+    assert v0 < 1e-4 * v1
+
+
+def test_mirror_symmetry_and_bilinear_amplitude_scaling():
+    """alpha -> -alpha (A = B) reverses the stationary swimming velocity; at
+    small amplitudes the velocity is bilinear in A and B."""
+    vp, vm = _steady_velocity(alpha=math.pi / 3), _steady_velocity(alpha=-math.pi / 3)
+    assert vm == pytest.approx(-vp, rel=1e-4)
+    v2 = _steady_velocity(alpha=math.pi / 3, A=2e-4, B=2e-4)
+    v4 = _steady_velocity(alpha=math.pi / 3, A=4e-4, B=4e-4)
+    assert v4 / v2 == pytest.approx(4.0, rel=1e-2)
+
+
+def test_zero_delay_is_the_undelayed_equation_and_delay_changes_pairs():
+    T = 500.0
+    pair = [_swimmer(center=(-30.0, 0.0, 0.0)), _swimmer(center=(30.0, 0.0, 0.0))]
+    t, x0 = integrate(pair, 2 * T, 2.0, MU, sample_every=5)
+    _, xd0 = integrate(pair, 2 * T, 2.0, MU, delay=0.0, sample_every=5)
+    assert np.array_equal(x0, xd0)
+    _, xd = integrate(pair, 2 * T, 2.0, MU, delay=40.0, sample_every=5)
+    assert np.abs(xd - x0).max() > 0
+    with pytest.raises(ValueError):
+        integrate(pair, 10.0, 2.0, MU, delay=3.0)
+
+
+def test_time_step_convergence():
+    """Fourth-order Runge-Kutta: halving the step changes the velocity by far
+    less than the velocity."""
+    T = 500.0
+    t, x = integrate([_swimmer()], 6 * T, 5.0, MU, sample_every=2)
+    t2, x2 = integrate([_swimmer()], 6 * T, 2.5, MU, sample_every=4)
+    v, v2 = swim_velocity(t, x, T)[0], swim_velocity(t2, x2, T)[0]
+    assert abs(v - v2) < 1e-6 * abs(v2)
+
+
+def _from_spec(sp):
+    """The analytic swimmer of a workload swimmer (balanced drive, Sec. 2.2)."""
+    return BeadSwimmer(center=tuple(sp.center), a=sp.radius, k=sp.k_spring, L=sp.spacing, A=sp.amp[0],
+                       B=sp.amp[2], alpha=sp.phase[2], period=sp.period)
+
+
+def _first_period_velocity(box, tensor):
+    sws = [_from_spec(s) for s in box.swimmers]
+    T = box.swimmers[0].period
+    t, x = integrate(sws, T, T / 400, (box.tau - 0.5) / 3 * box.rho0, tensor=tensor)
+    return (x[-1, :, 0] - x[0, :, 0]) / T
+
+
+def test_analytic_model_brackets_the_single_swimmer_48():
+    """The 48^3 single-swimmer workload over its first drive period from rest:
+    the FP64 oracle's swimming velocity against the bead model in an unbounded
+    fluid with the nominal bead radius (the periodic box and the IB shell's
+    larger hydrodynamic radius both slow the LB swimmer)."""
+    import oracle
+    from workloads import single_swimmer_48
+    box = single_swimmer_48()
+    osim = oracle.OracleSim(box)
+    x0 = osim.swimmer_centres()
+    osim.step(int(box.swimmers[0].period))
+    v_lb = (osim.swimmer_centres() - x0)[0, 0] / box.swimmers[0].period
+    v_rp = _first_period_velocity(box, "rotne_prager")[0]
+    v_os = _first_period_velocity(box, "oseen")[0]
+    print(f"48^3 single swimmer, period 1: LB {v_lb:.4e}, Rotne-Prager {v_rp:.4e}, Oseen {v_os:.4e}")
+    assert 0.5 < v_lb / v_rp < 1.5
+    assert v_rp < v_os  # the finite-size term slows the far beads' mutual drag less than point forces do
+
+
+def test_analytic_model_against_stored_pair_runs():
+    """The two-swimmer 256 x 128 x 128 boxes: the oracle's first-period
+    velocities (stored long runs) next to the bead model's, printed for the
+    record.  The bead model is a far-field description: with beads 18
+    lattice units apart at radius 6 (L/a = 3, against 7.2 in the paper's
+    runs) the shells' near fields, the periodic images and the start-up
+    transient of the first period all shift the LB velocities (the LB pairs
+    run at 0.5-0.8 of the Rotne-Prager prediction), so only the direction of
+    the pair's mean motion is checked."""
+    import json
+    import os
+    from workloads import swimmer_pair
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    rows = 0
+    for arr in ("inline", "side"):
+        for gap in (3, 5, 8):
+            path = os.path.join(here, f"longrun_{arr}{gap}_256x128x128.json")
+            if not os.path.exists(path):
+                continue
+            with open(path) as fh:
+                g = json.load(fh)
+            T, every = g["period"], g["every"]
+            xo = np.array([x for _, x in g["x_cm"]])
+            v_lb = (xo[T // every, :, 0] - xo[0, :, 0]) / T
+            box = swimmer_pair(arr, gap)
+            v_rp = _first_period_velocity(box, "rotne_prager")
+            v_os = _first_period_velocity(box, "oseen")
+            print(f"{arr} gap {gap}a, period 1: LB {v_lb}, Rotne-Prager {v_rp}, Oseen {v_os}")
+            assert np.sign(v_lb.mean()) == np.sign(v_rp.mean()) == np.sign(v_os.mean())
+            rows += 1
+    if rows == 0:
+        pytest.skip("no stored pair runs")
