@@ -66,6 +66,11 @@ def lib():
             L.orc_membrane_energy.argtypes = [i, d, d, i, P, P, P]
             L.orc_membrane_energy.restype = d
             L.orc_membrane_forces.argtypes = [i, d, d, i, P, P, P, P]
+            L.orc_bending_rest.argtypes = [i, P, P, P]
+            L.orc_bending_energy_v.argtypes = [d, i, P, P, P, P]
+            L.orc_bending_forces.argtypes = [d, i, P, P, P, P]
+            L.orc_volume.argtypes = [i, P, P, P]
+            L.orc_volume_forces.argtypes = [d, d, i, P, P, P]
             L.orc_set_threads.argtypes = [i]
             L.orc_set_threads.restype = i
             # complex-step twins (double complex arguments as complex128 arrays)
@@ -230,6 +235,81 @@ def membrane_forces(X, x, tris, p1, p2=0.0, law=NEOHOOKE, out=None):
     return out
 
 
+# Kantor-Nelson bending (Sec. 2.2): the discrete energy kb_disc (1 - cos(theta
+# - theta0)) per edge stands for the Helfrich energy kb/2 (2H)^2 dA; on a
+# regular triangulation of a sphere of radius R the normals of neighbouring
+# triangles (edge l, centroids l / sqrt(3) apart) differ by theta = l / (sqrt(3) R),
+# so sum_e (1 - cos theta) -> 4 pi / sqrt(3) against the Helfrich 8 pi:
+# kb_disc = 2 sqrt(3) kb.
+KB_DISC_PER_KB = 2.0 * 3.0 ** 0.5
+
+
+def bending_edges(tris):
+    """Every edge shared by two triangles as (a, b, c, d): the edge a-b, c the
+    third node of the triangle that runs a -> b, d that of the one running
+    b -> a (both outward).  Raises unless every edge has exactly those two."""
+    tris = np.asarray(tris)
+    third = {}
+    for t in tris:
+        for k in range(3):
+            a, b, c = int(t[k]), int(t[(k + 1) % 3]), int(t[(k + 2) % 3])
+            if (a, b) in third:
+                raise ValueError(f"directed edge {a}->{b} in two triangles")
+            third[(a, b)] = c
+    out = []
+    for (a, b), c in third.items():
+        if a < b:
+            if (b, a) not in third:
+                raise ValueError(f"edge {a}-{b} on one triangle only (open surface)")
+            out.append((a, b, c, third[(b, a)]))
+    return np.array(out, dtype=np.int32).reshape(-1, 4)
+
+
+def bending_rest(edges, X):
+    """(ne, 2): cos and sin of every edge's angle at the rest positions X."""
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    out = np.zeros((edges.shape[0], 2))
+    lib().orc_bending_rest(edges.shape[0], _p(edges), _p(_f64(X)), _p(out))
+    return out
+
+
+def bending_energy(kb, edges, cs0, x):
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    W = np.zeros(1)
+    lib().orc_bending_energy_v(KB_DISC_PER_KB * float(kb), edges.shape[0], _p(edges), _p(_f64(cs0)), _p(_f64(x)),
+                               _p(W))
+    return float(W[0])
+
+
+def bending_forces(kb, edges, cs0, x, out=None):
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    x = _f64(x)
+    if out is None:
+        out = np.zeros_like(x)
+    elif out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise TypeError("out must be a C-contiguous float64 array")
+    lib().orc_bending_forces(KB_DISC_PER_KB * float(kb), edges.shape[0], _p(edges), _p(_f64(cs0)), _p(x), _p(out))
+    return out
+
+
+def volume(tris, x):
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    V = np.zeros(1)
+    lib().orc_volume(tris.shape[0], _p(tris), _p(_f64(x)), _p(V))
+    return float(V[0])
+
+
+def volume_forces(kv, V0, tris, x, out=None):
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    x = _f64(x)
+    if out is None:
+        out = np.zeros_like(x)
+    elif out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise TypeError("out must be a C-contiguous float64 array")
+    lib().orc_volume_forces(float(kv), float(V0), tris.shape[0], _p(tris), _p(x), _p(out))
+    return out
+
+
 class OracleSim:
     """The coupled LB/IB time step in FP64 (order as in the module docstring).
 
@@ -264,6 +344,22 @@ class OracleSim:
         self.v = np.zeros_like(self.r)
         self.node_force = np.zeros_like(self.r)
         self.F = None
+        # per bead: membrane law, bending edges with their rest angles, rest volume
+        nb = self.asm["beads"].shape[0]
+        self.law = np.asarray(self.asm.get("bead_law", np.zeros(nb, np.int32)))
+        self.skC = np.asarray(self.asm.get("bead_C", np.zeros(nb)))
+        self.kb = np.asarray(self.asm.get("bead_kb", np.zeros(nb)))
+        self.kv = np.asarray(self.asm.get("bead_kv", np.zeros(nb)))
+        self.bend = {}
+        self.V0 = {}
+        for b in range(nb):
+            n0, nn, t0, nt = self.asm["beads"][b]
+            tris = self.asm["tris"][t0:t0 + nt]
+            if self.kb[b] != 0.0:
+                ed = bending_edges(tris)
+                self.bend[b] = (ed, bending_rest(ed, self.asm["nodes"]))
+            if self.kv[b] != 0.0:
+                self.V0[b] = volume(tris, self.asm["nodes"])
 
     def node_forces(self):
         """Steps 1-3: f^tot for every node at the current positions and time."""
@@ -273,8 +369,16 @@ class OracleSim:
         fn = np.zeros(self.r.shape, dtype=np.result_type(self.r.dtype, self.drive.dtype))
         for b in range(beads.shape[0]):
             n0, nn, t0, nt = beads[b]
+            law = SKALAK if self.law[b] == 1 else NEOHOOKE
             membrane_forces(self.rest.astype(fn.dtype), self.r.astype(fn.dtype), a["tris"][t0:t0 + nt],
-                            a["bead_Gs"][b], out=fn)
+                            a["bead_Gs"][b], self.skC[b], law=law, out=fn)
+            if b in self.bend or b in self.V0:
+                if fn.dtype != np.float64:
+                    raise NotImplementedError("bending and volume forces are real-valued only")
+                if b in self.bend:
+                    bending_forces(self.kb[b], *self.bend[b], self.r, out=fn)
+                if b in self.V0:
+                    volume_forces(self.kv[b], self.V0[b], a["tris"][t0:t0 + nt], self.r, out=fn)
         for k, s in enumerate(a["swimmers"]):
             ids = s["beads"]
             fd = drive(self.drive[k, 0:3], self.drive[k, 3:6], s["balance"], s["period"], self.t)

@@ -254,3 +254,143 @@ def test_icosphere_volume_converges():
     assert all(e > 0 for e in errs)
     assert errs[4] < 0.01 * 4 * math.pi / 3
     assert all(errs[i + 1] < errs[i] / 3 for i in range(4))
+
+
+# ---------------------------------------------------------------- bending and volume (Sec. 2.2)
+
+def _bead(subdiv=3, radius=6.0):
+    from workloads.mesh import icosphere
+    X, T = icosphere(subdiv)
+    return X * radius, T
+
+
+def _rotation(seed):
+    q = np.random.default_rng(seed).normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def test_bending_edges_cover_every_edge_twice_oriented():
+    X, T = _bead(2)
+    ed = oracle.bending_edges(T)
+    assert ed.shape == (30 * 4 ** 2, 4)  # E = 30 * 4^s
+    # every triangle appears once on each side of its three edges
+    tri_set = {tuple(sorted(t)) for t in T.tolist()}
+    for a, b, c, d in ed:
+        assert tuple(sorted((a, b, c))) in tri_set and tuple(sorted((a, b, d))) in tri_set
+        assert c != d
+    with pytest.raises(ValueError):
+        oracle.bending_edges(T[:-1])  # an open surface
+
+
+@pytest.mark.parametrize("subdiv", [2, 3])
+def test_bending_forces_are_minus_energy_gradient(subdiv):
+    X, T = _bead(subdiv)
+    ed = oracle.bending_edges(T)
+    cs0 = oracle.bending_rest(ed, X)
+    rng = np.random.default_rng(subdiv)
+    x = X + rng.normal(scale=0.1, size=X.shape)
+    f = oracle.bending_forces(1.25e-3, ed, cs0, x)
+    h = 1e-6
+    for j in rng.choice(len(X), 8, replace=False):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[j, a] += h
+            xm[j, a] -= h
+            fd = -(oracle.bending_energy(1.25e-3, ed, cs0, xp) - oracle.bending_energy(1.25e-3, ed, cs0, xm)) / (2 * h)
+            assert abs(fd - f[j, a]) < 1e-7 * np.abs(f).max()
+    # no net force or torque (translation and rotation invariance)
+    assert np.abs(f.sum(0)).max() < 1e-12 * np.abs(f).sum()
+    assert np.abs(np.cross(x, f).sum(0)).max() < 1e-12 * (np.linalg.norm(x, axis=1)[:, None] * np.abs(f)).sum()
+
+
+def test_bending_rest_shape_rigid_motion_and_scaling_are_free():
+    """The rest angles make the stress-free bead a rest state; rotating,
+    translating or uniformly scaling it leaves every angle unchanged."""
+    X, T = _bead(3)
+    ed = oracle.bending_edges(T)
+    cs0 = oracle.bending_rest(ed, X)
+    for x in (X, X @ _rotation(1).T + np.array([3.0, -7.0, 11.0]), 1.3 * X):
+        assert abs(oracle.bending_energy(1.25e-3, ed, cs0, x)) < 1e-15
+        assert np.abs(oracle.bending_forces(1.25e-3, ed, cs0, x)).max() < 1e-15
+    # a local bump costs energy
+    x = X.copy()
+    x[7] *= 1.05
+    assert oracle.bending_energy(1.25e-3, ed, cs0, x) > 0
+
+
+@pytest.mark.parametrize("subdiv", [2, 3, 4])
+def test_bending_modulus_matches_helfrich_energy_of_a_sphere(subdiv):
+    """Without rest angles (theta0 = 0) the discrete energy of a triangulated
+    sphere approaches the Helfrich energy kb/2 (2H)^2 dA = 8 pi kb of a
+    sphere of any radius; icosphere meshes are not quite regular, which
+    leaves the discrete sum 3-4 % above it."""
+    for radius in (1.0, 6.0):
+        X, T = _bead(subdiv, radius)
+        ed = oracle.bending_edges(T)
+        flat = np.tile([1.0, 0.0], (ed.shape[0], 1))
+        kb = 1.25e-3
+        W = oracle.bending_energy(kb, ed, flat, X)
+        assert W / (8 * np.pi * kb) == pytest.approx(1.0, abs=0.05)
+
+
+def test_volume_of_icospheres():
+    for s in (2, 3, 4):
+        X, T = _bead(s, 5.0)
+        V = oracle.volume(T, X)
+        assert V < 4 / 3 * np.pi * 125
+        assert V == pytest.approx(4 / 3 * np.pi * 125, rel=2.0 / 4 ** s)
+        # independent of the origin (closed surface)
+        assert oracle.volume(T, X + 17.0) == pytest.approx(V, rel=1e-12)
+
+
+def test_volume_penalty_closed_form_for_a_scaled_sphere():
+    """x = s X: W_v = kv/2 V0 (s^3 - 1)^2 (Eq. vol_cons), and since
+    dW/ds = -sum_j f_j . X_j, sum_j f_j . X_j = -3 kv V0 s^2 (s^3 - 1); the
+    forces point along the surface normals, inward for s > 1."""
+    X, T = _bead(3)
+    V0 = oracle.volume(T, X)
+    kv = 1.0
+    for s in (0.97, 1.02, 1.1):
+        x = s * X
+        assert 0.5 * kv * (oracle.volume(T, x) - V0) ** 2 / V0 == pytest.approx(0.5 * kv * V0 * (s ** 3 - 1) ** 2,
+                                                                               rel=1e-10)
+        f = oracle.volume_forces(kv, V0, T, x)
+        assert (f * X).sum() == pytest.approx(-3 * kv * V0 * s ** 2 * (s ** 3 - 1), rel=1e-10)
+        radial = (f * X).sum(1) / np.linalg.norm(X, axis=1)
+        assert np.all(np.sign(radial) == -np.sign(s - 1.0))
+        assert np.abs(f.sum(0)).max() < 1e-12 * np.abs(f).sum()
+
+
+def test_volume_forces_are_minus_energy_gradient():
+    X, T = _bead(3)
+    V0 = oracle.volume(T, X)
+    rng = np.random.default_rng(5)
+    x = X + rng.normal(scale=0.1, size=X.shape)
+    f = oracle.volume_forces(1.0, V0, T, x)
+    W = lambda y: 0.5 * (oracle.volume(T, y) - V0) ** 2 / V0  # noqa: E731
+    h = 1e-3  # W is a polynomial of degree 6 in x: central differences are exact up to h^2 terms
+    for j in rng.choice(len(X), 8, replace=False):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[j, a] += h
+            xm[j, a] -= h
+            assert abs(-(W(xp) - W(xm)) / (2 * h) - f[j, a]) < 1e-8 * np.abs(f).max()
+    assert np.abs(np.cross(x, f).sum(0)).max() < 1e-12 * (np.linalg.norm(x, axis=1)[:, None] * np.abs(f)).sum()
+
+
+def test_paper_membrane_bead_at_rest_is_a_fixed_point():
+    """A swimmer with the paper's membrane (Skalak, bending, volume) and no
+    drive, at its rest shape: every membrane force vanishes, so nothing moves."""
+    import math
+    from workloads import BoxSpec, SwimmerSpec, assemble
+    sw = SwimmerSpec(center=(16.0, 12.0, 12.0), radius=3.0, subdiv=1, spacing=9.0).with_drive(
+        0.0, 0.0, math.pi / 2).with_paper_membrane()
+    box = BoxSpec(dims=(32, 24, 24), swimmers=(sw,))
+    sim = oracle.OracleSim(box, assemble(box))
+    assert np.abs(sim.node_forces()).max() < 1e-15
+    sim.step(3)
+    assert np.abs(sim.r - sim.rest).max() < 1e-15

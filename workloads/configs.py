@@ -39,10 +39,24 @@ class SwimmerSpec:
     phase: tuple = (0.0, 0.0, math.pi / 2)
     balance: bool = True
     period: float = 500.0
+    # membrane law of the beads (Sec. 2.2): "neohooke" (shear modulus Gs) or
+    # "skalak" (Gs is then kappa_s, and C the area-dilatation parameter,
+    # kappa_a / kappa_s = 1 + 2 C); bending modulus kb of the Helfrich energy
+    # and volume-penalty modulus kv (Eq. vol_cons); zero switches a term off
+    law: str = "neohooke"
+    C: float = 0.0
+    kb: float = 0.0
+    kv: float = 0.0
 
     def with_drive(self, A, B, alpha):
         """The paper's protocol: f1 = A sin(wt), f3 = B sin(wt+alpha), f2 = -f1-f3."""
         return replace(self, amp=(A, 0.0, B), phase=(0.0, 0.0, alpha), balance=True)
+
+    def with_paper_membrane(self):
+        """The paper's bead membrane (Sec. 3): Skalak law with kappa_s = 5e-2
+        and kappa_a = 1 (C = (kappa_a / kappa_s - 1) / 2 = 9.5), bending
+        modulus 1.25e-3, volume penalty kappa_v = 1."""
+        return replace(self, law="skalak", Gs=5e-2, C=9.5, kb=1.25e-3, kv=1.0)
 
 
 @dataclass(frozen=True)
@@ -69,10 +83,13 @@ def assemble(box: BoxSpec):
       nodes   (M,3) float64  initial node positions (= membrane rest shape)
       tris    (T,3) int32    global node ids, outward orientation
       beads   (B,4) int32    node_start, node_count, tri_start, tri_count
-      bead_Gs (B,)  float64  neo-Hookean shear modulus per bead
+      bead_Gs (B,)  float64  neo-Hookean shear modulus (Skalak: kappa_s) per bead
+      bead_law (B,) int32    0 neo-Hookean, 1 Skalak
+      bead_C, bead_kb, bead_kv (B,) float64  Skalak C, bending and volume moduli
       swimmers list of dicts: beads (3 ids), k, L, amp, phase, balance, period
     """
     nodes, tris, beads, gs, sw = [], [], [], [], []
+    law, cc, kb, kv = [], [], [], []
     m0 = 0
     t0 = 0
     cache = {}
@@ -87,6 +104,12 @@ def assemble(box: BoxSpec):
             tris.append(utris + m0)
             beads.append((m0, len(unit), t0, len(utris)))
             gs.append(s.Gs)
+            if s.law not in ("neohooke", "skalak"):
+                raise ValueError(f"unknown membrane law {s.law}")
+            law.append(1 if s.law == "skalak" else 0)
+            cc.append(s.C)
+            kb.append(s.kb)
+            kv.append(s.kv)
             ids.append(len(beads) - 1)
             m0 += len(unit)
             t0 += len(utris)
@@ -100,7 +123,9 @@ def assemble(box: BoxSpec):
         nodes = np.zeros((0, 3))
         tris = np.zeros((0, 3), dtype=np.int32)
     return dict(nodes=nodes, tris=tris, beads=np.array(beads, dtype=np.int32).reshape(-1, 4),
-                bead_Gs=np.array(gs, dtype=np.float64), swimmers=sw)
+                bead_Gs=np.array(gs, dtype=np.float64), bead_law=np.array(law, dtype=np.int32),
+                bead_C=np.array(cc, dtype=np.float64), bead_kb=np.array(kb, dtype=np.float64),
+                bead_kv=np.array(kv, dtype=np.float64), swimmers=sw)
 
 
 # ----------------------------------------------------------------------------
