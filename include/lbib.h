@@ -83,12 +83,30 @@ typedef struct {
 } lb_params;
 
 /* One bead: its mesh nodes [node_start, node_start + node_count) and
- * triangles [tri_start, tri_start + tri_count) of the structure arrays;
- * Gs the neo-Hookean shear modulus of its membrane. */
+ * triangles [tri_start, tri_start + tri_count) of the structure arrays, and
+ * its membrane (Sec. 2.2):
+ *   law = LBIB_NEOHOOKE: strain energy Gs/2 (I1 - 1 + 1/(I2 + 1)) per
+ *         reference area (Gs the small-strain shear modulus);
+ *   law = LBIB_SKALAK:   Gs/4 (I1^2 + 2 I1 - 2 I2 + C I2^2) (Gs = kappa_s,
+ *         kappa_a / kappa_s = 1 + 2 C);
+ *   kb >= 0: bending modulus of the Helfrich energy, discretised per edge
+ *         after Kantor and Nelson as 2 sqrt(3) kb (1 - cos(theta - theta0)),
+ *         theta the angle between the normals of the edge's two triangles
+ *         and theta0 its value in the rest shape (needs a closed surface:
+ *         every edge on exactly two triangles of the bead);
+ *   kv >= 0: volume penalty kv/2 (V - V0)^2 / V0 (Eq. vol_cons), V0 the
+ *         enclosed volume of the rest shape (closed, outward surface).
+ * Zero kb or kv switches the term off. */
+#define LBIB_NEOHOOKE 0
+#define LBIB_SKALAK 1
 typedef struct {
     int node_start, node_count;
     int tri_start, tri_count;
     double Gs;
+    int law;
+    double C;
+    double kb;
+    double kv;
 } lbib_bead;
 
 /* One three-bead swimmer (Sec. 2.2).  bead[0..2] index the bead table in

@@ -14,6 +14,7 @@ _lib = None
 
 LBIB_OK, LBIB_EINVAL, LBIB_ECUDA, LBIB_ENONFINITE, LBIB_EUNSTABLE, LBIB_ETIMEOUT, LBIB_ESIZE = 0, -1, -2, -3, -4, -5, -6
 F32, F16, BF16, F64 = 0, 1, 2, 3
+NEOHOOKE, SKALAK = 0, 1
 GUO, SHAN_CHEN = 0, 1
 PESKIN4, LINEAR2 = 0, 1
 NBUF = 3
@@ -40,7 +41,8 @@ class LbParams(ctypes.Structure):
 
 class Bead(ctypes.Structure):
     _fields_ = [("node_start", ctypes.c_int), ("node_count", ctypes.c_int), ("tri_start", ctypes.c_int),
-                ("tri_count", ctypes.c_int), ("Gs", ctypes.c_double)]
+                ("tri_count", ctypes.c_int), ("Gs", ctypes.c_double), ("law", ctypes.c_int), ("C", ctypes.c_double),
+                ("kb", ctypes.c_double), ("kv", ctypes.c_double)]
 
 
 class Swimmer(ctypes.Structure):

@@ -867,7 +867,7 @@ struct Plan {
     // workspace offsets
     size_t o_drv = 0;  // drive table: per step and swimmer sin and cos of (omega t + phi_q), q = 0..2
     size_t o_tris, o_G, o_A0, o_cptr, o_cent, o_nb, o_bs, o_bc, o_bw, o_swim, o_theta, o_grad, o_disp, o_err,
-        o_seed, o_lf0, o_lf1, o_lu, o_lF, o_lr, o_lfn, o_trif, o_tria, o_lR, o_tb, o_tbt, o_ck, o_slots, total;
+        o_seed, o_lf0, o_lf1, o_lu, o_lF, o_lr, o_lfn, o_trif, o_tria, o_lR, o_tb, o_tbt, o_ck, o_slots[2], total;
 };
 
 Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, int K) {
@@ -927,10 +927,13 @@ Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, i
     P.o_trif = o; o += up(9 * Tn * 8);
     P.o_tria = o; o += up(9 * Tn * 8);
     P.o_lR = o; o += up(bd);
-    P.o_tb = o; o += up(8);                          // first step of the running segment
+    P.o_tb = o; o += up(16);                         // first step of the segment in each slot set
     P.o_tbt = o; o += up((size_t)P.n_seg * 8);       // g K for every segment g
     P.o_ck = o; o += (size_t)(P.n_seg + 1) * P.ck_bytes;  // + the final state
-    P.o_slots = o; o += (size_t)(K + 1) * P.slot_bytes;
+    // two sets of K + 1 step records: the reverse sweep of one segment runs
+    // beside the recompute of the segment before it
+    P.o_slots[0] = o; o += (size_t)(K + 1) * P.slot_bytes;
+    P.o_slots[1] = o; o += (size_t)(K + 1) * P.slot_bytes;
     P.total = o;
     return P;
 }
@@ -951,6 +954,11 @@ bool check(const lb_params *p, const lbib_structure *s, long long n_steps, int K
     }
     if (n_steps < 1 || K < 1) { why = "n_steps and K must be >= 1"; return false; }
     if (n_steps > (1ll << 40)) { why = "n_steps too large"; return false; }
+    for (int b = 0; s && b < s->n_beads; ++b)
+        if (s->beads[b].law != LBIB_NEOHOOKE || s->beads[b].kb != 0.0 || s->beads[b].kv != 0.0) {
+            why = "the adjoint engine supports the neo-Hookean membrane without bending or volume terms";
+            return false;
+        }
     return true;
 }
 
@@ -963,28 +971,41 @@ struct lbib_adjoint {
     char *ws;
     Mesh m;
     std::vector<double> rest;  // rest node positions (host)
-    int slots_seg = -1;        // segment whose steps the slots currently hold
+    int slots_seg[2] = {-1, -1};  // segment whose steps each slot set currently holds
     bool have_fwd = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // the reverse sweep recomputes segment g - 1 on stream s2 while the caller
+    // stream runs the reverse steps of segment g: e_ready[set] marks a
+    // recompute done, e_free[set] the reverse steps that read the set done
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t e_ready[2] = {nullptr, nullptr}, e_free[2] = {nullptr, nullptr};
     float fwd_ms = 0.f, bwd_ms = 0.f;
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
     // CUDA graphs of one full K-step segment: the forward steps, and the
     // reverse steps for either parity of the adjoint population buffers
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t g_fwd = nullptr, g_rev[2] = {nullptr, nullptr};
+    cudaGraphExec_t g_fwd[2] = {nullptr, nullptr}, g_rev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     bool graphs = true;  // replay segment graphs (LBIB_GRAPHS=0: launch directly)
     long long n_fwd = 0, n_rev[2] = {0, 0};
 
     ~lbib_adjoint() {
-        if (g_fwd) cudaGraphExecDestroy(g_fwd);
-        for (cudaGraphExec_t g : g_rev)
+        for (cudaGraphExec_t g : g_fwd)
             if (g) cudaGraphExecDestroy(g);
+        for (auto &gp : g_rev)
+            for (cudaGraphExec_t g : gp)
+                if (g) cudaGraphExecDestroy(g);
         if (cap) cudaStreamDestroy(cap);
+        if (s2) cudaStreamDestroy(s2);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
+        for (int k = 0; k < 2; ++k) {
+            if (e_ready[k]) cudaEventDestroy(e_ready[k]);
+            if (e_free[k]) cudaEventDestroy(e_free[k]);
+        }
     }
     template <typename X> X *at(size_t off) const { return (X *)(ws + off); }
-    char *slot(int k) const { return ws + P.o_slots + (size_t)k * P.slot_bytes; }
+    char *slot(int k, int set) const { return ws + P.o_slots[set] + (size_t)k * P.slot_bytes; }
+    long long *tbase(int set) const { return (long long *)(ws + P.o_tb) + set; }
     char *ck(int c) const { return ws + P.o_ck + (size_t)c * P.ck_bytes; }
     int seg_len(int g) const { return (int)std::min<long long>(P.K, P.n_steps - (long long)g * P.K); }
 };
@@ -995,17 +1016,16 @@ namespace {
 // independent, but running them on two graph branches measured slower than
 // one chain: 75 against 61 us per step on the 96^3 workload.)
 template <typename T>
-cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
+cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, int set) {
     const Plan &P = a->P;
-    char *sl = a->slot(k), *sn = a->slot(k + 1);
+    char *sl = a->slot(k, set), *sn = a->slot(k + 1, set);
     const double *r = (const double *)(sl + P.s_r);
     double *fn = (double *)(sl + P.s_fn), *R = (double *)(sl + P.s_R), *ext = (double *)(sl + P.s_ext);
     T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
     const int M = P.M;
     if (M > 0) {
         k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
-                                                         a->at<double>(P.o_drv), r, a->at<long long>(P.o_tb), k, R,
-                                                         ext);
+                                                         a->at<double>(P.o_drv), r, a->tbase(set), k, R, ext);
         // FP64-latency-bound: small blocks spread the triangles over every SM
         k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
         k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F);
@@ -1030,9 +1050,9 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st) {
+cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st, int set) {
     const Plan &P = a->P;
-    char *sl = a->slot(k);
+    char *sl = a->slot(k, set);
     const double *r = (const double *)(sl + P.s_r), *fn = (const double *)(sl + P.s_fn),
                  *R = (const double *)(sl + P.s_R);
     const T *F = (const T *)(sl + P.s_F), *u = (const T *)(sl + P.s_u);
@@ -1057,7 +1077,7 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     if (M > 0) {
         k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
         k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
-                                                         a->at<double>(P.o_drv), R, lam_fn, a->at<long long>(P.o_tb), k,
+                                                         a->at<double>(P.o_drv), R, lam_fn, a->tbase(set), k,
                                                          a->at<double>(P.o_lR), a->at<double>(P.o_grad));
         k_adj_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, lam_fn,
                                                                                 a->at<double>(P.o_tria));
@@ -1068,10 +1088,10 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     return cudaGetLastError();
 }
 
-// capture the K forward steps of a full segment (slots 0 -> K), or its K
-// reverse steps starting on adjoint buffer `par`, into a graph
+// capture the K forward steps of a full segment (slots 0 -> K of a slot set),
+// or its K reverse steps starting on adjoint buffer `par`, into a graph
 template <typename T>
-cudaError_t capture(lbib_adjoint *a, bool reverse, int par) {
+cudaError_t capture(lbib_adjoint *a, bool reverse, int par, int set) {
     const Plan &P = a->P;
     const long long n0 = a->launches;
     cudaError_t e = cudaStreamBeginCapture(a->cap, cudaStreamCaptureModeThreadLocal);
@@ -1081,62 +1101,62 @@ cudaError_t capture(lbib_adjoint *a, bool reverse, int par) {
     for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
         if (reverse) {
             const int kk = P.K - 1 - k;
-            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap);
+            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, set);
             nxt = 1 - nxt;
         } else {
-            e = fwd_step<T>(a, k, a->cap);
+            e = fwd_step<T>(a, k, a->cap, set);
         }
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(a->cap, &g);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(reverse ? &a->g_rev[par] : &a->g_fwd, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(reverse ? &a->g_rev[par][set] : &a->g_fwd[set], g, 0);
     if (g) cudaGraphDestroy(g);
     (reverse ? a->n_rev[par] : a->n_fwd) = a->launches - n0;
     a->launches = n0;
     return e;
 }
 
-// set the device step counter to the first step of segment g
-cudaError_t set_tbase(lbib_adjoint *a, int g) {
-    return cudaMemcpyAsync(a->at<long long>(a->P.o_tb), a->at<long long>(a->P.o_tbt) + g, 8, cudaMemcpyDeviceToDevice,
-                           a->s);
+// set the step counter of a slot set to the first step of segment g
+cudaError_t set_tbase(lbib_adjoint *a, int g, int set, cudaStream_t st) {
+    return cudaMemcpyAsync(a->tbase(set), a->at<long long>(a->P.o_tbt) + g, 8, cudaMemcpyDeviceToDevice, st);
 }
 
-// run segment g forward from its checkpoint, filling slots 0..len
+// run segment g forward from its checkpoint, filling slots 0..len of a set
 template <typename T>
-cudaError_t run_segment(lbib_adjoint *a, int g) {
+cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st) {
     const Plan &P = a->P;
-    char *s0 = a->slot(0), *c = a->ck(g);
+    char *s0 = a->slot(0, set), *c = a->ck(g);
     cudaError_t e;
     if ((e = cudaMemcpyAsync(s0 + P.s_pops, c + P.c_pops, Q * (size_t)P.d.Npad * P.esize, cudaMemcpyDeviceToDevice,
-                             a->s)) != cudaSuccess)
+                             st)) != cudaSuccess)
         return e;
     if (P.M > 0 &&
-        (e = cudaMemcpyAsync(s0 + P.s_r, c + P.c_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToDevice, a->s)) != cudaSuccess)
+        (e = cudaMemcpyAsync(s0 + P.s_r, c + P.c_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return e;
-    if ((e = cudaMemsetAsync(s0 + P.s_F, 0, 3 * (size_t)P.d.Npad * P.esize, a->s)) != cudaSuccess) return e;
-    if ((e = set_tbase(a, g)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(s0 + P.s_F, 0, 3 * (size_t)P.d.Npad * P.esize, st)) != cudaSuccess) return e;
+    if ((e = set_tbase(a, g, set, st)) != cudaSuccess) return e;
     const int len = a->seg_len(g);
     if (len == P.K && a->graphs) {
-        if (!a->g_fwd && (e = capture<T>(a, false, 0)) != cudaSuccess) return e;
-        if ((e = cudaGraphLaunch(a->g_fwd, a->s)) != cudaSuccess) return e;
+        if (!a->g_fwd[set] && (e = capture<T>(a, false, 0, set)) != cudaSuccess) return e;
+        if ((e = cudaGraphLaunch(a->g_fwd[set], st)) != cudaSuccess) return e;
         a->launches += a->n_fwd;
     } else {
         for (int k = 0; k < len; ++k)
-            if ((e = fwd_step<T>(a, k, a->s)) != cudaSuccess) return e;
+            if ((e = fwd_step<T>(a, k, st, set)) != cudaSuccess) return e;
     }
-    a->slots_seg = g;
+    a->slots_seg[set] = g;
     return cudaSuccess;
 }
 
 // copy the populations and positions of slot k into checkpoint c
 cudaError_t save_ck(lbib_adjoint *a, int k, int c) {
     const Plan &P = a->P;
-    cudaError_t e = cudaMemcpyAsync(a->ck(c) + P.c_pops, a->slot(k) + P.s_pops, Q * (size_t)P.d.Npad * P.esize,
+    cudaError_t e = cudaMemcpyAsync(a->ck(c) + P.c_pops, a->slot(k, 0) + P.s_pops, Q * (size_t)P.d.Npad * P.esize,
                                     cudaMemcpyDeviceToDevice, a->s);
     if (e == cudaSuccess && P.M > 0)
-        e = cudaMemcpyAsync(a->ck(c) + P.c_r, a->slot(k) + P.s_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToDevice, a->s);
+        e = cudaMemcpyAsync(a->ck(c) + P.c_r, a->slot(k, 0) + P.s_r, 3 * (size_t)P.M * 8, cudaMemcpyDeviceToDevice,
+                            a->s);
     return e;
 }
 
@@ -1153,8 +1173,9 @@ int forward_impl(lbib_adjoint *a, double *disp) {
         a->launches += 1;
         CU(cudaGetLastError());
     }
+    a->slots_seg[1] = -1;
     for (int g = 0; g < P.n_seg; ++g) {
-        CU(run_segment<T>(a, g));
+        CU(run_segment<T>(a, g, 0, a->s));
         CU(save_ck(a, a->seg_len(g), g + 1));  // the next checkpoint (the last one: the final state)
     }
     if (P.S > 0) {
@@ -1240,21 +1261,43 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
         a->launches += 1;
         CU(cudaGetLastError());
     }
+    // segment g's records in slot set `cur`; the recompute of segment g - 1
+    // into the other set runs on s2 beside the reverse steps of segment g
+    int cur = a->slots_seg[0] == P.n_seg - 1 ? 0 : (a->slots_seg[1] == P.n_seg - 1 ? 1 : -1);
+    if (cur < 0) {
+        cur = 0;
+        CU(run_segment<T>(a, P.n_seg - 1, 0, a->s));
+    }
+    CU(cudaEventRecord(a->e_free[0], a->s));
+    CU(cudaEventRecord(a->e_free[1], a->s));
+    bool ready_on_s2[2] = {false, false};
     for (int g = P.n_seg - 1; g >= 0; --g) {
-        if (a->slots_seg != g) CU(run_segment<T>(a, g));
-        CU(set_tbase(a, g));
+        const int oth = 1 - cur;
+        if (g > 0) {
+            CU(cudaStreamWaitEvent(a->s2, a->e_free[oth], 0));
+            CU(run_segment<T>(a, g - 1, oth, a->s2));
+            CU(cudaEventRecord(a->e_ready[oth], a->s2));
+            ready_on_s2[oth] = true;
+        }
+        if (ready_on_s2[cur]) {
+            CU(cudaStreamWaitEvent(a->s, a->e_ready[cur], 0));
+            ready_on_s2[cur] = false;
+        }
+        CU(set_tbase(a, g, cur, a->s));
         const int len = a->seg_len(g);
         if (len == P.K && a->graphs) {
-            if (!a->g_rev[nxt]) CU(capture<T>(a, true, nxt));
-            CU(cudaGraphLaunch(a->g_rev[nxt], a->s));
+            if (!a->g_rev[nxt][cur]) CU(capture<T>(a, true, nxt, cur));
+            CU(cudaGraphLaunch(a->g_rev[nxt][cur], a->s));
             a->launches += a->n_rev[nxt];
             if (P.K & 1) nxt = 1 - nxt;
         } else {
             for (int k = len - 1; k >= 0; --k) {
-                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], a->s));
+                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], a->s, cur));
                 nxt = 1 - nxt;
             }
         }
+        CU(cudaEventRecord(a->e_free[cur], a->s));
+        cur = oth;
     }
     if (P.M > 0) {  // x_cm(0) enters the displacement with a minus sign
         k_adj_seed<<<(P.M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_seed), -1.0, 1, lam_r);
@@ -1380,7 +1423,12 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
             return cleanup(fail(LBIB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
     } while (0)
     for (int k = 0; k < 4; ++k) CUA(cudaEventCreate(&a->ev[k]));
+    for (int k = 0; k < 2; ++k) {
+        CUA(cudaEventCreateWithFlags(&a->e_ready[k], cudaEventDisableTiming));
+        CUA(cudaEventCreateWithFlags(&a->e_free[k], cudaEventDisableTiming));
+    }
     CUA(cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking));
+    CUA(cudaStreamCreateWithFlags(&a->s2, cudaStreamNonBlocking));
     std::vector<long long> tb(P.n_seg);
     for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
     auto put = [&](size_t off, const void *src, size_t n) {
@@ -1416,7 +1464,7 @@ int lb_adjoint_set_drive(lbib_adjoint *a, const double *theta) {
         CU(cudaStreamSynchronize(a->s));
     }
     a->have_fwd = false;
-    a->slots_seg = -1;
+    a->slots_seg[0] = a->slots_seg[1] = -1;
     return LBIB_OK;
 }
 
@@ -1437,7 +1485,7 @@ int lb_adjoint_set_initial(lbib_adjoint *a, const double *f, const double *r) {
         CU(cudaStreamSynchronize(a->s));
     }
     a->have_fwd = false;
-    a->slots_seg = -1;
+    a->slots_seg[0] = a->slots_seg[1] = -1;
     return LBIB_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "lbib_internal.cuh"
@@ -63,6 +64,8 @@ struct Layout {
     // fields
     size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0;
     // aux
+    int n_edges = 0;
+    size_t oedge = 0, ovg = 0, ovfix = 0;
     size_t orx = 0, ory = 0, orz = 0, onf = 0, onv = 0, otf = 0, otri = 0, ocp = 0, oce = 0, onb = 0,
            obead = 0, oswim = 0, obd = 0, obe = 0, octl = 0, osws = 0, oxcm = 0, oswp = 0, obv = 0, otrk = 0, obacc = 0;
 };
@@ -81,6 +84,51 @@ bool valid_params(const lb_params *p, std::string &why) {
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(p->g[a])) { why = "g must be finite"; return false; }
     return true;
+}
+
+// directed edge a -> b of a triangle as one key
+inline long long edge_key(int a, int b) { return ((long long)a << 32) | (unsigned)b; }
+
+// third node of the triangle of bead d that runs a -> b along its boundary,
+// for every directed edge of the bead's triangles (-1 if two triangles share one)
+std::unordered_map<long long, int> directed_edges(const lbib_structure *s, const lbib_bead &d) {
+    std::unordered_map<long long, int> m;
+    m.reserve(3 * (size_t)d.tri_count);
+    for (int t = d.tri_start; t < d.tri_start + d.tri_count; ++t) {
+        const int *v = s->tris + 3 * t;
+        for (int q = 0; q < 3; ++q) {
+            auto r = m.emplace(edge_key(v[q], v[(q + 1) % 3]), v[(q + 2) % 3]);
+            if (!r.second) r.first->second = -1;
+        }
+    }
+    return m;
+}
+
+bool closed_surface(const lbib_structure *s, const lbib_bead &d) {
+    const auto m = directed_edges(s, d);
+    for (const auto &kv : m) {
+        if (kv.second < 0) return false;
+        const int a = (int)(kv.first >> 32), b = (int)(kv.first & 0xffffffffll);
+        auto it = m.find(edge_key(b, a));
+        if (it == m.end() || it->second < 0) return false;
+    }
+    return true;
+}
+
+// bending edges of one bead in a fixed order (by triangle, then corner): the
+// edge a -> b of a triangle (third node c) with a < b, and d the third node of
+// the triangle running b -> a
+std::vector<std::array<int, 4>> bending_edges(const lbib_structure *s, const lbib_bead &d) {
+    const auto m = directed_edges(s, d);
+    std::vector<std::array<int, 4>> out;
+    for (int t = d.tri_start; t < d.tri_start + d.tri_count; ++t) {
+        const int *v = s->tris + 3 * t;
+        for (int q = 0; q < 3; ++q) {
+            const int a = v[q], b = v[(q + 1) % 3], c = v[(q + 2) % 3];
+            if (a < b) out.push_back({a, b, c, m.at(edge_key(b, a))});
+        }
+    }
+    return out;
 }
 
 bool valid_structure(const lb_params *p, const lbib_structure *s, std::string &why) {
@@ -122,6 +170,17 @@ bool valid_structure(const lb_params *p, const lbib_structure *s, std::string &w
                     return false;
                 }
             }
+        if (d.law != LBIB_NEOHOOKE && d.law != LBIB_SKALAK) { why = "unknown membrane law"; return false; }
+        if (!std::isfinite(d.Gs) || !std::isfinite(d.C) || !(d.kb >= 0.0) || !(d.kv >= 0.0) || !std::isfinite(d.kb) ||
+            !std::isfinite(d.kv)) {
+            why = "membrane moduli must be finite, kb and kv >= 0";
+            return false;
+        }
+        if ((d.kb > 0.0 || d.kv > 0.0) && !closed_surface(s, d)) {
+            why = "bending and volume terms need a closed surface (every edge on exactly two triangles, "
+                  "consistently oriented)";
+            return false;
+        }
     }
     for (long long j = 0; j < 3ll * s->n_nodes; ++j)
         if (!std::isfinite(s->rest_nodes[j])) { why = "non-finite node coordinate"; return false; }
@@ -162,10 +221,20 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     L.orz = o; o += up((size_t)M * 8 + 8);
     L.onf = o; o += up((size_t)M * 16 + 16);
     L.onv = o; o += up((size_t)M * 16 + 16);
-    L.otf = o; o += up((size_t)T * 48 + 16);
+    long long E = 0;  // bending edges: 3/2 per triangle of a closed bead with a bending modulus
+    bool vol = false;
+    for (int b = 0; b < B; ++b) {
+        if (s->beads[b].kb > 0.0) E += 3ll * s->beads[b].tri_count / 2;
+        vol |= s->beads[b].kv > 0.0;
+    }
+    L.n_edges = (int)E;
+    L.otf = o; o += up(((size_t)3 * T + 4 * (size_t)E) * 16 + 16);
     L.otri = o; o += up((size_t)T * sizeof(TriDev) + 16);
     L.ocp = o; o += up((size_t)(M + 1) * 4);
-    L.oce = o; o += up((size_t)3 * T * 4 + 4);
+    L.oce = o; o += up(((size_t)3 * T + 4 * (size_t)E) * 4 + 4);
+    L.oedge = o; o += up((size_t)E * sizeof(EdgeDev) + 16);
+    L.ovg = o; o += up((vol ? (size_t)3 * T : 0) * 16 + 16);
+    L.ovfix = o; o += up((size_t)B * 8 + 16);
     L.onb = o; o += up((size_t)M * 4 + 4);
     L.obead = o; o += up((size_t)B * sizeof(BeadDev) + 16);
     L.oswim = o; o += up((size_t)S * sizeof(SwimDev) + 16);
@@ -461,7 +530,11 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
 
     // mesh preprocessing on the host (reference shapes, node -> triangle lists)
     std::vector<TriDev> tri(T);
-    std::vector<int> cptr(M + 1, 0), cent(3 * (size_t)T), nbead(M, 0);
+    const int E = L.n_edges;
+    std::vector<int> cptr(M + 1, 0), cent(3 * (size_t)T + 4 * (size_t)E), nbead(M, 0);
+    std::vector<EdgeDev> edges;
+    edges.reserve(E);
+    bool has_volume = false;
     std::vector<BeadDev> beads(B);
     std::vector<SwimDev> swims(S);
     for (int bi = 0; bi < B; ++bi) {
@@ -469,7 +542,66 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         beads[bi].node_start = bd.node_start;
         beads[bi].node_count = bd.node_count;
         beads[bi].inv_count = (float)(1.0 / bd.node_count);
-        beads[bi].pad[0] = beads[bi].pad[1] = 0;
+        beads[bi].pad = 0;
+        beads[bi].pad2 = 0.0;
+        beads[bi].kv = (float)bd.kv;
+        beads[bi].V0 = 0.0;
+        if (bd.kv > 0.0) {
+            // enclosed volume of the rest shape (divergence theorem, outward triangles),
+            // about the first node of the bead
+            const double *X = s->rest_nodes, *o = X + 3 * bd.node_start;
+            double V = 0.0;
+            for (int t = bd.tri_start; t < bd.tri_start + bd.tri_count; ++t) {
+                const int *v = s->tris + 3 * t;
+                double p[3][3];
+                for (int q = 0; q < 3; ++q)
+                    for (int a = 0; a < 3; ++a) p[q][a] = X[3 * v[q] + a] - o[a];
+                V += (p[0][0] * (p[1][1] * p[2][2] - p[1][2] * p[2][1]) + p[0][1] * (p[1][2] * p[2][0] - p[1][0] * p[2][2]) +
+                      p[0][2] * (p[1][0] * p[2][1] - p[1][1] * p[2][0])) / 6.0;
+            }
+            if (!(V > 0.0)) return fail(LBIB_EINVAL, "a bead with a volume penalty encloses no positive volume");
+            beads[bi].V0 = V;
+            has_volume = true;
+        }
+        if (bd.kb > 0.0) {
+            // bending edges with the rest angle between their triangles' normals
+            const double *X = s->rest_nodes;
+            for (const auto &q : bending_edges(s, bd)) {
+                double P[4][3];
+                for (int k = 0; k < 4; ++k)
+                    for (int a = 0; a < 3; ++a) P[k][a] = X[3 * q[k] + a];
+                double e[3], u[3], w[3], n1[3], n2[3];
+                for (int a = 0; a < 3; ++a) {
+                    e[a] = P[1][a] - P[0][a];  // b - a
+                    u[a] = P[2][a] - P[0][a];  // c - a
+                    w[a] = P[3][a] - P[1][a];  // d - b
+                }
+                // N1 = e x (c - a), N2 = (d - b) x e
+                n1[0] = e[1] * u[2] - e[2] * u[1];
+                n1[1] = e[2] * u[0] - e[0] * u[2];
+                n1[2] = e[0] * u[1] - e[1] * u[0];
+                n2[0] = w[1] * e[2] - w[2] * e[1];
+                n2[1] = w[2] * e[0] - w[0] * e[2];
+                n2[2] = w[0] * e[1] - w[1] * e[0];
+                const double l1 = std::sqrt(n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2]);
+                const double l2 = std::sqrt(n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2]);
+                const double le = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+                if (!(l1 > 0.0 && l2 > 0.0 && le > 0.0)) return fail(LBIB_EINVAL, "degenerate rest triangle");
+                double cth = 0.0, sth = 0.0;
+                for (int a = 0; a < 3; ++a) cth += n1[a] * n2[a] / (l1 * l2);
+                // sin: (n1 x n2) . e / |e|
+                const double cx = n1[1] * n2[2] - n1[2] * n2[1], cy = n1[2] * n2[0] - n1[0] * n2[2],
+                             cz = n1[0] * n2[1] - n1[1] * n2[0];
+                sth = (cx * e[0] + cy * e[1] + cz * e[2]) / (l1 * l2 * le);
+                EdgeDev ed;
+                for (int k = 0; k < 4; ++k) ed.v[k] = q[k];
+                ed.c0 = (float)cth;
+                ed.s0 = (float)sth;
+                ed.kb = (float)(2.0 * std::sqrt(3.0) * bd.kb);
+                ed.pad = 0;
+                edges.push_back(ed);
+            }
+        }
         {
             // reach: largest rest distance of a node from the bead centre, plus a
             // margin of 1 lattice unit for membrane deformation
@@ -508,16 +640,23 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
             td.v[0] = v[0];
             td.v[1] = v[1];
             td.v[2] = v[2];
-            td.pad[0] = td.pad[1] = 0;
+            td.skC = (float)bd.C;
+            td.law = bd.law;
         }
     }
+    if ((int)edges.size() != E) return fail(LBIB_EINVAL, "bending edge count does not match the closed surfaces");
+    // node -> corner entries: its triangle corners, then its bending-edge slots
     for (int t = 0; t < T; ++t)
         for (int q = 0; q < 3; ++q) cptr[s->tris[3 * t + q] + 1]++;
+    for (int e = 0; e < E; ++e)
+        for (int q = 0; q < 4; ++q) cptr[edges[e].v[q] + 1]++;
     for (int j = 0; j < M; ++j) cptr[j + 1] += cptr[j];
     {
         std::vector<int> fill(cptr.begin(), cptr.end() - 1);
         for (int t = 0; t < T; ++t)
             for (int q = 0; q < 3; ++q) cent[fill[s->tris[3 * t + q]]++] = 3 * t + q;
+        for (int e = 0; e < E; ++e)
+            for (int q = 0; q < 4; ++q) cent[fill[edges[e].v[q]]++] = 3 * T + 4 * e + q;
     }
     for (int k = 0; k < S; ++k) {
         const lbib_swimmer &w = s->swimmers[k];
@@ -595,6 +734,11 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.tris = (const TriDev *)(A + L.otri);
     d.csr_ptr = (const int *)(A + L.ocp);
     d.csr_ent = (const int *)(A + L.oce);
+    d.n_edges = E;
+    d.edges = (const EdgeDev *)(A + L.oedge);
+    d.has_volume = has_volume ? 1 : 0;
+    d.tri_vgrad = has_volume ? (float4 *)(A + L.ovg) : nullptr;
+    d.bead_Vfix = (long long *)(A + L.ovfix);
     d.node_bead = (const int *)(A + L.onb);
     d.beads = (const BeadDev *)(A + L.obead);
     d.swims = (const SwimDev *)(A + L.oswim);
@@ -642,7 +786,8 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     };
     bool ok = h2d(d.rx, sx.data(), M * 8) && h2d(d.ry, sy.data(), M * 8) && h2d(d.rz, sz.data(), M * 8) &&
               h2d((void *)d.tris, tri.data(), T * sizeof(TriDev)) && h2d((void *)d.csr_ptr, cptr.data(), (M + 1) * 4) &&
-              h2d((void *)d.csr_ent, cent.data(), 3 * (size_t)T * 4) && h2d((void *)d.node_bead, nbead.data(), M * 4) &&
+              h2d((void *)d.csr_ent, cent.data(), cent.size() * 4) && h2d((void *)d.node_bead, nbead.data(), M * 4) &&
+              h2d((void *)d.edges, edges.data(), edges.size() * sizeof(EdgeDev)) &&
               h2d((void *)d.beads, beads.data(), B * sizeof(BeadDev)) && h2d((void *)d.swims, swims.data(), S * sizeof(SwimDev));
     if (!ok) return bail(fail(LBIB_ECUDA, "uploading mesh tables failed"));
     if (launch_bead_init(d, u) != cudaSuccess || launch_swimmer_state(d, true, u) != cudaSuccess ||

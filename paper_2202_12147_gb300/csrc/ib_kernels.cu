@@ -122,6 +122,57 @@ __device__ void swimmer_forces(const DevCtx &c, int s) {
     }
 }
 
+// Enclosed volume of a bead by the divergence theorem, V = sum over its
+// triangles of (1/6) p0 . (p1 x p2) with p = r - R_b: each triangle adds its
+// term in FP64, rounded to VOL_FIX units, to the bead's sum (integer adds:
+// the same result in any order); the corners keep dV/dr = (1/6) p_next x
+// p_prev for the nodal forces.  Called by every lane of a warp (active: this
+// lane has a triangle).
+__device__ __forceinline__ void triangle_volume(const DevCtx &c, int t, bool active) {
+    long long q = 0;
+    int b = -1;
+    if (active) {
+        const TriDev T = c.tris[t];
+        b = c.node_bead[T.v[0]];
+        if (c.beads[b].kv > 0.f) {
+            const double *R = c.bead_R + 4 * b;
+            double p[3][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                p[k][0] = c.rx[T.v[k]] - R[0];
+                p[k][1] = c.ry[T.v[k]] - R[1];
+                p[k][2] = c.rz[T.v[k]] - R[2];
+            }
+            const double v = p[0][0] * (p[1][1] * p[2][2] - p[1][2] * p[2][1]) +
+                             p[0][1] * (p[1][2] * p[2][0] - p[1][0] * p[2][2]) +
+                             p[0][2] * (p[1][0] * p[2][1] - p[1][1] * p[2][0]);
+            q = __double2ll_rn(v * (VOL_FIX / 6.0));
+            float4 *g = c.tri_vgrad + 3 * (size_t)t;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                const float ux = (float)p[k1][0], uy = (float)p[k1][1], uz = (float)p[k1][2];
+                const float wx = (float)p[k2][0], wy = (float)p[k2][1], wz = (float)p[k2][2];
+                g[k] = make_float4((uy * wz - uz * wy) * (1.0f / 6.0f), (uz * wx - ux * wz) * (1.0f / 6.0f),
+                                   (ux * wy - uy * wx) * (1.0f / 6.0f), 0.f);
+            }
+        } else {
+            b = -1;
+        }
+    }
+    // one atomic per warp when its lanes hold triangles of one bead (the usual case)
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    long long *acc = c.bead_Vfix;
+    if (__all_sync(0xffffffffu, b == b0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if ((threadIdx.x & 31) == 0 && b0 >= 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(acc + b0), (unsigned long long)q);
+    } else if (b >= 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(acc + b), (unsigned long long)q);
+    }
+}
+
 __device__ void triangle_forces(const DevCtx &c, int t) {
     const TriDev T = c.tris[t];
     const int n0 = T.v[0], n1 = T.v[1], n2 = T.v[2];
@@ -134,12 +185,23 @@ __device__ void triangle_forces(const DevCtx &c, int t) {
     const float trM = T.Gi[0] * E00 + 2.0f * T.Gi[1] * E01 + T.Gi[2] * E11;
     const float detM = (E00 * E11 - E01 * E01) * T.inv_detG;
     const float I2 = 2.0f * trM + 4.0f * detM;
-    const float J2 = 1.0f + I2;
-    const float coef = T.K / (J2 * J2);
-    const float a = I2 * (I2 + 2.0f);
-    const float S00 = coef * (a * (float)T.G[2] - 2.0f * E11);
-    const float S01 = coef * (-a * (float)T.G[1] + 2.0f * E01);
-    const float S11 = coef * (a * (float)T.G[0] - 2.0f * E00);
+    // dW/dd = d S with S = K [cG adj(G) + cE adj(E)], K = A0 modulus / det G:
+    //   neo-Hookean: cG = I2 (I2 + 2) / J^4, cE = -2 / J^4 (J^2 = 1 + I2);
+    //   Skalak:      cG = I1 + C I2,       cE = 2 (C I2 - 1)  (I1 = 2 tr M)
+    float cG, cE;
+    if (T.law == LBIB_SKALAK) {
+        const float I1 = 2.0f * trM;
+        cG = I1 + T.skC * I2;
+        cE = 2.0f * (T.skC * I2 - 1.0f);
+    } else {
+        const float J2 = 1.0f + I2;
+        const float iJ4 = 1.0f / (J2 * J2);
+        cG = I2 * (I2 + 2.0f) * iJ4;
+        cE = -2.0f * iJ4;
+    }
+    const float S00 = T.K * (cG * (float)T.G[2] + cE * E11);
+    const float S01 = T.K * (-cG * (float)T.G[1] - cE * E01);
+    const float S11 = T.K * (cG * (float)T.G[0] + cE * E00);
     const float d1x = (float)ax, d1y = (float)ay, d1z = (float)az;
     const float d2x = (float)bx, d2y = (float)by, d2z = (float)bz;
     // dW/dd1 = d1 S00 + d2 S01, dW/dd2 = d1 S01 + d2 S11
@@ -151,15 +213,73 @@ __device__ void triangle_forces(const DevCtx &c, int t) {
     o[2] = make_float4(-w2x, -w2y, -w2z, 0.f);
 }
 
+// Bending of one edge (Sec. 2.2, Kantor-Nelson discretisation of the
+// Helfrich energy): W = kb (1 - cos(theta - theta0)), theta the angle from the
+// normal n1 of triangle (a, b, c) to the normal n2 of triangle (b, a, d) about
+// the edge direction, so f_k = -kb sin(theta - theta0) dtheta/dr_k with the
+// angle's gradient for the two wings and the edge nodes
+//   dtheta/dc = -|e| n1 / |N1|,  dtheta/dd = -|e| n2 / |N2|,
+//   dtheta/da = -(1 - s) dtheta/dc - (1 - s') dtheta/dd,
+//   dtheta/db = -s dtheta/dc - s' dtheta/dd,
+// e = b - a and s, s' the positions of c and d projected onto the edge in
+// units of |e|.  Positions are taken relative to a in FP64, the rest in FP32.
+__device__ void edge_forces(const DevCtx &c, int k) {
+    const EdgeDev Ed = c.edges[k];
+    const int a = Ed.v[0];
+    const double ox = c.rx[a], oy = c.ry[a], oz = c.rz[a];
+    float P[3][3];  // b, c, d relative to a
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int n = Ed.v[q + 1];
+        P[q][0] = (float)(c.rx[n] - ox);
+        P[q][1] = (float)(c.ry[n] - oy);
+        P[q][2] = (float)(c.rz[n] - oz);
+    }
+    const float ex = P[0][0], ey = P[0][1], ez = P[0][2];
+    const float ux = P[1][0], uy = P[1][1], uz = P[1][2];                          // c - a
+    const float wx = P[2][0] - ex, wy = P[2][1] - ey, wz = P[2][2] - ez;          // d - b
+    // N1 = e x (c - a), N2 = (d - b) x e
+    const float N1x = ey * uz - ez * uy, N1y = ez * ux - ex * uz, N1z = ex * uy - ey * ux;
+    const float N2x = wy * ez - wz * ey, N2y = wz * ex - wx * ez, N2z = wx * ey - wy * ex;
+    const float le2 = ex * ex + ey * ey + ez * ez;
+    const float il1 = rsqrtf(N1x * N1x + N1y * N1y + N1z * N1z);
+    const float il2 = rsqrtf(N2x * N2x + N2y * N2y + N2z * N2z);
+    const float ile = rsqrtf(le2);
+    const float m1x = N1x * il1, m1y = N1y * il1, m1z = N1z * il1;
+    const float m2x = N2x * il2, m2y = N2y * il2, m2z = N2z * il2;
+    const float cth = m1x * m2x + m1y * m2y + m1z * m2z;
+    const float sth = ((m1y * m2z - m1z * m2y) * ex + (m1z * m2x - m1x * m2z) * ey + (m1x * m2y - m1y * m2x) * ez) * ile;
+    // -dW/dtheta
+    const float g = -Ed.kb * (sth * Ed.c0 - cth * Ed.s0);
+    const float le = le2 * ile;
+    const float hc = -le * il1, hd = -le * il2;  // dtheta/dc = hc n1, dtheta/dd = hd n2
+    const float s1 = (ux * ex + uy * ey + uz * ez) / le2;
+    const float s2 = (P[2][0] * ex + P[2][1] * ey + P[2][2] * ez) / le2;
+    const float gcx = hc * m1x, gcy = hc * m1y, gcz = hc * m1z;
+    const float gdx = hd * m2x, gdy = hd * m2y, gdz = hd * m2z;
+    float4 *o = c.tri_force + 3 * (size_t)c.n_tris + 4 * (size_t)k;
+    o[0] = make_float4(g * (-(1.f - s1) * gcx - (1.f - s2) * gdx), g * (-(1.f - s1) * gcy - (1.f - s2) * gdy),
+                       g * (-(1.f - s1) * gcz - (1.f - s2) * gdz), 0.f);
+    o[1] = make_float4(g * (-s1 * gcx - s2 * gdx), g * (-s1 * gcy - s2 * gdy), g * (-s1 * gcz - s2 * gdz), 0.f);
+    o[2] = make_float4(g * gcx, g * gcy, g * gcz, 0.f);
+    o[3] = make_float4(g * gdx, g * gdy, g * gdz, 0.f);
+}
+
+// blocks of k_ib_prepare: swimmers, then triangles, then bending edges
 __device__ __forceinline__ void prepare_body(const DevCtx &c, int bid) {
     // the other parity's tile list (the previous step's) is consumed: empty it
     // for the marks of the next step
     if (bid == 0 && threadIdx.x == 0) c.tile_count[(c.ctl->step + 1) & 1] = 0;
+    const int tri_blocks = (c.n_tris + PREP_TPB - 1) / PREP_TPB;
     if (bid < c.n_swimmers) {
         swimmer_forces(c, bid);
-    } else {
+    } else if (bid < c.n_swimmers + tri_blocks) {
         const int t = (bid - c.n_swimmers) * PREP_TPB + threadIdx.x;
         if (t < c.n_tris) triangle_forces(c, t);
+        if (c.has_volume) triangle_volume(c, t, t < c.n_tris);
+    } else {
+        const int k = (bid - c.n_swimmers - tri_blocks) * PREP_TPB + threadIdx.x;
+        if (k < c.n_edges) edge_forces(c, k);
     }
 }
 
@@ -216,7 +336,27 @@ __device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid) {
             fy += w.y;
             fz += w.z;
         }
-        const float4 ext = c.bead_ext[c.node_bead[j]];
+        const int bj = c.node_bead[j];
+        if (c.has_volume && c.beads[bj].kv > 0.f) {
+            // volume penalty (Sec. 2.2, Eq. vol_cons): f_j = -kv (V - V0) / V0 dV/dr_j,
+            // dV/dr_j summed over the node's triangle corners in list order
+            const BeadDev bd = c.beads[bj];
+            const double V = (double)c.bead_Vfix[bj] * (1.0 / VOL_FIX);
+            const float fac = (float)(-(double)bd.kv * (V - bd.V0) / bd.V0);
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+            for (int e = e0; e < e1; ++e) {
+                const int en = c.csr_ent[e];
+                if (en >= 3 * c.n_tris) break;  // the node's bending-edge entries follow its triangle corners
+                const float4 w = c.tri_vgrad[en];
+                gx += w.x;
+                gy += w.y;
+                gz += w.z;
+            }
+            fx += fac * gx;
+            fy += fac * gy;
+            fz += fac * gz;
+        }
+        const float4 ext = c.bead_ext[bj];
         const float4 f = make_float4(fx + ext.x, fy + ext.y, fz + ext.z, 0.f);
         sf[threadIdx.x] = f;
         c.node_force[j] = f;
@@ -302,6 +442,20 @@ __device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid) {
         }
     }
     if (__any_sync(0xffffffffu, unmarked) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_MARK);
+    if (c.has_volume) {
+        // the last block to finish clears the bead volumes for the next
+        // k_ib_prepare (a completion count, no waiting)
+        __shared__ int s_vlast;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_vlast = atomicAdd(&c.ctl->vol_done, 1) == (c.n_nodes + GS_NODES - 1) / GS_NODES - 1;
+        __syncthreads();
+        if (s_vlast) {
+            for (int i = threadIdx.x; i < c.n_beads; i += blockDim.x) c.bead_Vfix[i] = 0;
+            if (threadIdx.x == 0) c.ctl->vol_done = 0;
+        }
+    }
 }
 
 template <int KW, bool DET>
@@ -714,7 +868,9 @@ cudaError_t launch_ib_batch(const BatchDev &bt, int kernel, int deterministic, i
     return cudaGetLastError();
 }
 
-int ib_blocks_prepare(const DevCtx &c) { return c.n_swimmers + (c.n_tris + PREP_TPB - 1) / PREP_TPB; }
+int ib_blocks_prepare(const DevCtx &c) {
+    return c.n_swimmers + (c.n_tris + PREP_TPB - 1) / PREP_TPB + (c.n_edges + PREP_TPB - 1) / PREP_TPB;
+}
 int ib_blocks_spread(const DevCtx &c) { return (c.n_nodes + GS_NODES - 1) / GS_NODES; }
 int ib_blocks_interp(const DevCtx &c, int kernel) {
     const int lanes = kernel == LBIB_LINEAR2 ? 2 : 4;
@@ -722,7 +878,7 @@ int ib_blocks_interp(const DevCtx &c, int kernel) {
 }
 
 cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s) {
-    const int blocks = c.n_swimmers + (c.n_tris + PREP_TPB - 1) / PREP_TPB;
+    const int blocks = ib_blocks_prepare(c);
     if (blocks == 0) return cudaSuccess;
     launch_prio(k_ib_prepare, blocks, PREP_TPB, 0, s, c);
     return cudaGetLastError();

@@ -352,12 +352,27 @@ __device__ __forceinline__ void collide_pair_scaled(float2 (&e)[Q], const DevCtx
     }
 }
 
-// Update of the two cells (x0, y, z), (x0 + 1, y, z), x0 even.  Populations
-// whose source or destination keeps the pair adjacent (even steps, and
-// directions with c_x = 0 on odd steps) move as one pair-aligned vector; the
-// x-shifted ones of odd steps move one value at a time (with periodic wrap).
+// x-shifted values of the odd step move between neighbouring lanes of a warp
+// (the cells of one tile row are spread over consecutive lanes, CPT cells
+// each, the valid lanes first); a lane whose neighbour holds no cells of the
+// row reads or writes the value across the edge itself.
+constexpr unsigned FULL_MASK = 0xffffffffu;
+__device__ __forceinline__ bool next_lane_valid(bool valid) {
+    const bool nv = __shfl_down_sync(FULL_MASK, valid ? 1 : 0, 1) != 0;
+    return (threadIdx.x & 31) != 31 && nv;
+}
+
+// Update of the two cells (x0, y, z), (x0 + 1, y, z), x0 even, by every lane
+// of the warp (valid: this lane has cells).  Populations whose source or
+// destination keeps the pair adjacent (even steps, and directions with
+// c_x = 0 on odd steps) move as one pair-aligned vector; the x-shifted ones of
+// odd steps move as the aligned pair of this lane's slots, the value across
+// the pair's edge coming from (or going to) the neighbouring lane.
 template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
-__device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
+__device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y, unsigned z, bool valid_lane) {
+    // only the odd step exchanges values between lanes; an even step's idle lanes leave at once
+    if (!ODD && !valid_lane) return true;
+    const bool valid = ODD ? valid_lane : true;
     using S = Store<ST>;
     using T = typename S::T;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
@@ -369,6 +384,8 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
     const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
     const unsigned cell = x0 + r0 + s0;
     const size_t Np = (size_t)c.Npad;
+    const bool first = (threadIdx.x & 31) == 0;
+    const bool nextv = ODD ? next_lane_valid(valid) : false;
     // 16-bit storage: the values stay in the storage scale (collide_pair_scaled)
     float2 d[Q];
 #pragma unroll
@@ -379,16 +396,25 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
             const int dy = -cy(i), dz = -cz(i);
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
             const T *pl = P + opp(i) * Np + row;
-            if (cx(i) == 0) d[i] = S::ld2(pl + x0, m);
-            else if (cx(i) > 0) d[i] = make_float2(S::ld(pl + xm, m), S::ld(pl + x0, m));
-            else d[i] = make_float2(S::ld(pl + x1, m), S::ld(pl + xp, m));
+            const float2 w = valid ? S::ld2(pl + x0, m) : make_float2(0.f, 0.f);
+            if (cx(i) == 0) {
+                d[i] = w;
+            } else if (cx(i) > 0) {  // cells x0 - 1, x0
+                float e = __shfl_up_sync(FULL_MASK, w.y, 1);
+                if (first && valid) e = S::ld(pl + xm, m);
+                d[i] = make_float2(e, w.x);
+            } else {                 // cells x0 + 1, x0 + 2
+                float e = __shfl_down_sync(FULL_MASK, w.x, 1);
+                if (!nextv && valid) e = S::ld(pl + xp, m);
+                d[i] = make_float2(w.y, e);
+            }
         } else {
-            d[i] = S::ld2(P + i * Np + cell, m);
+            d[i] = valid ? S::ld2(P + i * Np + cell, m) : make_float2(0.f, 0.f);
         }
     }
     const bool forced = MARKED || c.has_g;
     float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
-    if (MARKED) {
+    if (MARKED && valid) {
         if (DET) {
             const float3 f0 = take_fdet(c.Fdet, c.Npad, cell), f1 = take_fdet(c.Fdet, c.Npad, cell + 1);
             Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
@@ -407,7 +433,7 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
     float2 ux, uy, uz, rho;
     if (S::scaled) collide_pair_scaled<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
     else collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
-    if (MARKED) {
+    if (MARKED && valid) {
         c.U[cell] = make_float4(ux.x, uy.x, uz.x, rho.x);
         c.U[cell + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
     }
@@ -420,19 +446,27 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
             T *pl = P + i * Np + row;
             if (cx(i) == 0) {
-                S::st2(pl + x0, d[i], m);
-            } else if (cx(i) > 0) {
-                S::st(pl + x1, d[i].x, m);
-                S::st(pl + xp, d[i].y, m);
-            } else {
-                S::st(pl + xm, d[i].x, m);
-                S::st(pl + x0, d[i].y, m);
+                if (valid) S::st2(pl + x0, d[i], m);
+            } else if (cx(i) > 0) {  // to cells x0 + 1, x0 + 2: slots x0, x0 + 1 hold x0 - 1, x0
+                const float e = __shfl_up_sync(FULL_MASK, d[i].y, 1);
+                if (valid) {
+                    if (!first) S::st2(pl + x0, make_float2(e, d[i].x), m);
+                    else S::st(pl + x1, d[i].x, m);
+                    if (!nextv) S::st(pl + xp, d[i].y, m);
+                }
+            } else {                 // to cells x0 - 1, x0: slots x0, x0 + 1 hold x0 + 1, x0 + 2
+                const float e = __shfl_down_sync(FULL_MASK, d[i].x, 1);
+                if (valid) {
+                    if (nextv) S::st2(pl + x0, make_float2(d[i].y, e), m);
+                    else S::st(pl + x0, d[i].y, m);
+                    if (first) S::st(pl + xm, d[i].x, m);
+                }
             }
-        } else {
+        } else if (valid) {
             S::st2(P + opp(i) * Np + cell, d[i], m);
         }
     }
-    return isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
+    return !valid || (isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y));
 }
 
 // 16-bit formats: a packed pair of stored values to FP32 and back (no rescaling).
@@ -454,13 +488,20 @@ __device__ __forceinline__ unsigned pack2_raw(float2 v) {
     return r;
 }
 
-// Update of four cells x0 .. x0 + 3 (x0 a multiple of 4) with 16-bit storage.
-// Each direction moves as one 8-byte word when its cells stay aligned; the
-// x-shifted directions of odd steps read the aligned word plus the one value
-// across its edge and reassemble with byte permutes, and write one value, an
-// aligned pair and one value.  The collision runs as two packed pairs.
+// Update of four cells x0 .. x0 + 3 (x0 a multiple of 4) with 16-bit storage,
+// by every lane of the warp (valid: this lane has cells).  Each direction
+// moves as one aligned 8-byte word of this lane's four slots; for the
+// x-shifted directions of odd steps the value across the word's edge comes
+// from (or goes to) the neighbouring lane, reassembled with byte permutes.
+// The collision runs as two packed pairs.
+#ifndef LBIB_Q_STORE8
+#define LBIB_Q_STORE8 1
+#endif
 template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
-__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
+__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z, bool valid_lane) {
+    // only the odd step exchanges values between lanes; an even step's idle lanes leave at once
+    if (!ODD && !valid_lane) return true;
+    const bool valid = ODD ? valid_lane : true;
     using T = unsigned short;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
     const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
@@ -470,6 +511,8 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
     const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
     const unsigned cell = x0 + r0 + s0;
     const size_t Np = (size_t)c.Npad;
+    const bool first = (threadIdx.x & 31) == 0;
+    const bool nextv = ODD ? next_lane_valid(valid) : false;
     uint2 raw[Q];  // cells x0..x0+3 of each direction, 2 values per word
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -478,23 +521,27 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
             const int dy = -cy(i), dz = -cz(i);
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
             const T *pl = P + opp(i) * Np + row;
-            const uint2 w = *reinterpret_cast<const uint2 *>(pl + x0);
+            const uint2 w = valid ? *reinterpret_cast<const uint2 *>(pl + x0) : make_uint2(0u, 0u);
             if (cx(i) == 0) {
                 raw[i] = w;
             } else if (cx(i) > 0) {  // cells x0-1 .. x0+2
-                const unsigned e = pl[xm];
+                unsigned e = __shfl_up_sync(FULL_MASK, w.y, 1) >> 16;
+                if (first && valid) e = pl[xm];
                 raw[i] = make_uint2(__byte_perm(e, w.x, 0x5410), __byte_perm(w.x, w.y, 0x5432));
             } else {                 // cells x0+1 .. x0+4
-                const unsigned e = pl[x4];
+                unsigned e = __shfl_down_sync(FULL_MASK, w.x, 1);
+                if (!nextv && valid) e = pl[x4];
                 raw[i] = make_uint2(__byte_perm(w.x, w.y, 0x5432), __byte_perm(w.y, e, 0x5432));
             }
         } else {
-            raw[i] = *reinterpret_cast<const uint2 *>(P + i * Np + cell);
+            raw[i] = valid ? *reinterpret_cast<const uint2 *>(P + i * Np + cell) : make_uint2(0u, 0u);
         }
     }
     const bool forced = MARKED || c.has_g;
     bool ok = true;
-    unsigned keep[Q];  // first pair's x-shifted outputs, written together with the second pair's
+    // first pair's outputs (x-shifted ones of odd steps, and with 8-byte
+    // stores all of them), written together with the second pair's
+    unsigned keep[Q];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float2 d[Q];
@@ -502,7 +549,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
         for (int i = 0; i < Q; ++i) d[i] = unpack2_raw<ST>(h ? raw[i].y : raw[i].x);  // storage scale
         const unsigned cl = cell + 2 * h;
         float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
-        if (MARKED) {
+        if (MARKED && valid) {
             if (DET) {
                 const float3 f0 = take_fdet(c.Fdet, c.Npad, cl), f1 = take_fdet(c.Fdet, c.Npad, cl + 1);
                 Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
@@ -520,11 +567,11 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
         }
         float2 ux, uy, uz, rho;
         collide_pair_scaled<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
-        if (MARKED) {
+        if (MARKED && valid) {
             c.U[cl] = make_float4(ux.x, uy.x, uz.x, rho.x);
             c.U[cl + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
         }
-        ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
+        ok &= !valid || (isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y));
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned e = pack2_raw<ST>(d[i]);  // this pair's cells (x0 + 2h, x0 + 2h + 1)
@@ -534,22 +581,46 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
                 const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
                 T *pl = P + i * Np + row;
                 if (cx(i) == 0) {
-                    *reinterpret_cast<unsigned *>(pl + x0 + 2 * h) = e;
+                    if (LBIB_Q_STORE8) {
+                        if (h == 0) keep[i] = e;
+                        else if (valid) *reinterpret_cast<uint2 *>(pl + x0) = make_uint2(keep[i], e);
+                    } else if (valid) {
+                        *reinterpret_cast<unsigned *>(pl + x0 + 2 * h) = e;
+                    }
                 } else if (h == 0) {
                     keep[i] = e;
                 } else {
                     const unsigned a = keep[i], b = e;
-                    if (cx(i) > 0) {  // to cells x0+1 .. x0+4
-                        pl[x0 + 1] = (T)(a & 0xffffu);
-                        *reinterpret_cast<unsigned *>(pl + x0 + 2) = __byte_perm(a, b, 0x5432);
-                        pl[x4] = (T)(b >> 16);
-                    } else {          // to cells x0-1 .. x0+2
-                        pl[xm] = (T)(a & 0xffffu);
-                        *reinterpret_cast<unsigned *>(pl + x0) = __byte_perm(a, b, 0x5432);
-                        pl[x0 + 2] = (T)(b >> 16);
+                    if (cx(i) > 0) {  // to cells x0+1 .. x0+4: slots x0 .. x0+3 hold cells x0-1 .. x0+2
+                        const unsigned pb = __shfl_up_sync(FULL_MASK, b, 1);
+                        if (valid) {
+                            if (!first) {
+                                *reinterpret_cast<uint2 *>(pl + x0) =
+                                    make_uint2(__byte_perm(pb, a, 0x5432), __byte_perm(a, b, 0x5432));
+                            } else {
+                                pl[x0 + 1] = (T)(a & 0xffffu);
+                                *reinterpret_cast<unsigned *>(pl + x0 + 2) = __byte_perm(a, b, 0x5432);
+                            }
+                            if (!nextv) pl[x4] = (T)(b >> 16);
+                        }
+                    } else {          // to cells x0-1 .. x0+2: slots x0 .. x0+3 hold cells x0+1 .. x0+4
+                        const unsigned na = __shfl_down_sync(FULL_MASK, a, 1);
+                        if (valid) {
+                            if (nextv) {
+                                *reinterpret_cast<uint2 *>(pl + x0) =
+                                    make_uint2(__byte_perm(a, b, 0x5432), __byte_perm(b, na, 0x5432));
+                            } else {
+                                *reinterpret_cast<unsigned *>(pl + x0) = __byte_perm(a, b, 0x5432);
+                                pl[x0 + 2] = (T)(b >> 16);
+                            }
+                            if (first) pl[xm] = (T)(a & 0xffffu);
+                        }
                     }
                 }
-            } else {
+            } else if (LBIB_Q_STORE8) {
+                if (h == 0) keep[i] = e;
+                else if (valid) *reinterpret_cast<uint2 *>(P + opp(i) * Np + cell) = make_uint2(keep[i], e);
+            } else if (valid) {
                 *reinterpret_cast<unsigned *>(P + opp(i) * Np + cl) = e;
             }
         }
@@ -590,12 +661,12 @@ __device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, uns
     // is written before this launch and not again until it has finished
     if (c.marks[(ODD ? c.n_tiles : 0) + tile] == c.ctl->gen[ODD ? 1 : 0]) return;
     const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
+    const bool valid = CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx;
     bool ok = true;
-    if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
-        if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, y, z);
-        else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, y, z);
-        else ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, y, z);
-    }
+    // the multi-cell updates run on every lane (they exchange values between lanes)
+    if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, y, z, valid);
+    else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, y, z, valid);
+    else if (valid) ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, y, z);
     report_bad(c, !ok);
     if (c.n_nodes == 0 && tile == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
 }
@@ -635,11 +706,10 @@ __device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nbl
         const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
         const unsigned y = yz % c.ny, z = yz / c.ny;
         const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
-        if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
-            if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z);
-            else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z);
-            else ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
-        }
+        const bool valid = CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx;
+        if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
+        else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
+        else if (valid) ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
     }
     report_bad(c, !ok);
 }
@@ -703,11 +773,10 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked_batch(const BatchDev bt) {
         const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
         const unsigned y = yz % c.ny, z = yz / c.ny;
         const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
-        if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
-            if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z);
-            else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z);
-            else ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
-        }
+        const bool valid = CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx;
+        if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
+        else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
+        else if (valid) ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
         if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_NONFINITE);
         ok = true;
     }

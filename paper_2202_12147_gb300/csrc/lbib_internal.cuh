@@ -53,6 +53,7 @@ struct Control {
     int err;
     int done;        // blocks of the current interpolation launch that have finished
     int gen[2];      // per step parity: the step whose stamps mark the tiles (see k_lb_main)
+    int vol_done;    // blocks of the current gather/spread launch that have read the bead volumes
 };
 
 // Per-triangle reference data of the linear FEM membrane.
@@ -62,17 +63,36 @@ struct TriDev {
     float K;         // A0 * Gs / det G
     float inv_detG;  // 1 / det G
     int v[3];        // node ids
-    int pad[2];
+    float skC;       // Skalak: C (kappa_a / kappa_s = 1 + 2 C)
+    int law;         // LBIB_NEOHOOKE (K = A0 Gs / det G) or LBIB_SKALAK (K = A0 kappa_s / det G)
 };
 static_assert(sizeof(TriDev) == 64, "TriDev layout");
+
+// One bending edge: node ids a, b (the edge), c, d (the opposite corners of
+// the triangles a, b, c and b, a, d, both outward); cos and sin of the rest
+// angle between the two triangles' normals; the discrete modulus.
+struct EdgeDev {
+    int v[4];
+    float c0, s0;
+    float kb;        // 2 sqrt(3) times the bending modulus
+    int pad;
+};
+static_assert(sizeof(EdgeDev) == 32, "EdgeDev layout");
 
 struct BeadDev {
     int node_start, node_count;
     int swimmer, slot;  // owning swimmer and position 0..2 along its axis
     float inv_count;    // 1 / node_count
     float reach;        // bound on |r_j - R| over the bead's nodes (rest radius + margin)
-    int pad[2];
+    float kv;           // volume-penalty modulus (0: off)
+    int pad;
+    double V0;          // enclosed volume of the rest shape
+    double pad2;
 };
+static_assert(sizeof(BeadDev) == 48, "BeadDev layout");
+
+// fixed-point scale of the bead volume sums: 2^40 units per cubic lattice unit
+constexpr double VOL_FIX = 1099511627776.0;
 
 struct SwimDev {
     int bead[3];
@@ -112,10 +132,16 @@ struct DevCtx {
     double *rx, *ry, *rz;      // node positions (SoA)
     float4 *node_force;        // f^tot per node
     float4 *node_vel;          // interpolated velocity per node
-    float4 *tri_force;         // 3 corner forces per triangle
+    float4 *tri_force;         // 3 corner forces per triangle, then 4 per bending edge
     const TriDev *tris;
-    const int *csr_ptr;        // node -> incident (triangle*3 + corner)
-    const int *csr_ent;
+    int n_edges;               // bending edges (beads with a bending modulus)
+    int has_volume;            // some bead has a volume penalty
+    const EdgeDev *edges;
+    float4 *tri_vgrad;         // per triangle corner: (1/6) (r_next - R) x (r_prev - R), R the bead centre
+    long long *bead_Vfix;      // [n_beads] enclosed volume of each bead at this step's positions, fixed point
+                               // (VOL_FIX); summed by k_ib_prepare, read and cleared by k_ib_gather_spread
+    const int *csr_ptr;        // node -> incident corner entries: triangle*3 + corner, then
+    const int *csr_ent;        //         3*n_tris + edge*4 + slot for bending edges
     const int *node_bead;
     const BeadDev *beads;
     const SwimDev *swims;

@@ -7,7 +7,9 @@ Structure format (host arrays):
   nodes    (M,3) float64  rest shape = initial node positions
   tris     (T,3) int32    global node ids, outward orientation
   beads    (B,4) int32    node_start, node_count, tri_start, tri_count
-  bead_Gs  (B,)  float64  neo-Hookean shear modulus of each bead
+  bead_Gs  (B,)  float64  neo-Hookean shear modulus of each bead (Skalak: kappa_s)
+  bead_law, bead_C, bead_kb, bead_kv (B,), optional: membrane law (0
+           neo-Hookean, 1 Skalak), Skalak C, bending and volume moduli
   swimmers list of dicts with keys beads (3 ids), k, L, amp (3), phase (3),
            balance (bool), period
 """
@@ -59,10 +61,19 @@ class _HostStructure:
         self.tris = np.ascontiguousarray(st["tris"], dtype=np.int32)
         beads = np.asarray(st["beads"], dtype=np.int32).reshape(-1, 4)
         gs = np.asarray(st["bead_Gs"], dtype=np.float64)
-        self.B = (_lib.Bead * max(1, len(beads)))()
+        nb = len(beads)
+        law = np.asarray(st.get("bead_law", np.zeros(nb, np.int32)))
+        cc = np.asarray(st.get("bead_C", np.zeros(nb)), dtype=np.float64)
+        kb = np.asarray(st.get("bead_kb", np.zeros(nb)), dtype=np.float64)
+        kv = np.asarray(st.get("bead_kv", np.zeros(nb)), dtype=np.float64)
+        self.B = (_lib.Bead * max(1, nb))()
         for b, row in enumerate(beads):
             self.B[b].node_start, self.B[b].node_count, self.B[b].tri_start, self.B[b].tri_count = (int(v) for v in row)
             self.B[b].Gs = float(gs[b])
+            self.B[b].law = int(law[b])
+            self.B[b].C = float(cc[b])
+            self.B[b].kb = float(kb[b])
+            self.B[b].kv = float(kv[b])
         sws = st["swimmers"]
         self.S = (_lib.Swimmer * max(1, len(sws)))()
         for k, s in enumerate(sws):

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -88,8 +89,10 @@ def _adjoint_bytes(dims, structure, n_steps, K, storage=3, forcing=0, kernel=0):
 
 
 def test_adjoint_workspace_sizes_without_gpu():
-    """Checkpoint-and-recompute memory: K + 1 step records plus one checkpoint
-    per segment (and the final state), not one record per step."""
+    """Checkpoint-and-recompute memory: two sets of K + 1 step records (the
+    reverse sweep of one segment runs beside the recompute of the one before
+    it) plus one checkpoint per segment (and the final state), not one record
+    per step."""
     from workloads import adjoint_single_96, assemble
     box = adjoint_single_96()
     asm = assemble(box)
@@ -98,7 +101,7 @@ def test_adjoint_workspace_sizes_without_gpu():
     b32 = _adjoint_bytes(box.dims, asm, 1000, 100, storage=0)
     rec64 = 25 * n * 8       # populations, F and u of one step, FP64
     ck64 = 19 * n * 8
-    assert 101 * rec64 + 11 * ck64 < b64 < 101 * rec64 + 11 * ck64 + 2 * 19 * n * 8 + 8 * n * 8 + (64 << 20)
+    assert 202 * rec64 + 11 * ck64 < b64 < 202 * rec64 + 11 * ck64 + 2 * 19 * n * 8 + 8 * n * 8 + (64 << 20)
     assert b32 < 0.55 * b64
     # ten periods cost ten more checkpoints, not ten times the records
     b10 = _adjoint_bytes(box.dims, asm, 10000, 100)
@@ -115,3 +118,33 @@ def test_adjoint_invalid_arguments_rejected(bad):
     kw.update(bad)
     with pytest.raises(_lib.LbibError):
         _adjoint_bytes(box.dims, assemble(box), **kw)
+
+
+def test_membrane_model_sizes_and_validation():
+    """The paper's membrane (Skalak, bending, volume penalty) adds bending
+    edges (3/2 per triangle of a closed bead) and volume data to the
+    auxiliary buffer; bending on an open surface, an unknown law and
+    negative moduli are rejected before anything is allocated."""
+    import math
+    from paper_2202_12147_gb300 import _lib, required_sizes
+    from workloads import BoxSpec, SwimmerSpec, assemble
+    sw = SwimmerSpec(center=(16.0, 12.0, 12.0), radius=3.0, subdiv=1, spacing=9.0).with_drive(1e-3, 1e-3, math.pi / 2)
+    plain = assemble(BoxSpec(dims=(32, 24, 24), swimmers=(sw,)))
+    paper = assemble(BoxSpec(dims=(32, 24, 24), swimmers=(sw.with_paper_membrane(),)))
+    assert list(paper["bead_law"]) == [1, 1, 1] and paper["bead_kb"][0] == 1.25e-3 and paper["bead_kv"][0] == 1.0
+    s0 = required_sizes((32, 24, 24), plain)
+    s1 = required_sizes((32, 24, 24), paper)
+    assert s1[2] > s0[2] and s1[:2] == s0[:2]
+    bad = dict(paper)
+    bad["tris"] = paper["tris"][1:]  # one triangle missing: open surface
+    bad["beads"] = paper["beads"].copy()
+    bad["beads"][0, 3] -= 1
+    bad["beads"][1:, 2] -= 1
+    with pytest.raises(_lib.LbibError):
+        required_sizes((32, 24, 24), bad)
+    for key, val in (("bead_law", np.array([2, 1, 1], np.int32)), ("bead_kb", np.array([-1.0, 0.0, 0.0])),
+                     ("bead_kv", np.array([np.nan, 0.0, 0.0]))):
+        st = dict(paper)
+        st[key] = val
+        with pytest.raises(_lib.LbibError):
+            required_sizes((32, 24, 24), st)

@@ -56,8 +56,41 @@ def test_reduced_storage_odd_rows(perm, storage):
         fo, _, _ = oracle.lb_step(fo, box.dims, box.tau, g=box.g)
     _, ug = oracle.macros(gpu_f_to_oracle(sim.get_populations(), perm))
     _, uo = oracle.macros(fo)
-    assert rel_l2(ug, uo) < (2e-3 if storage == "f16" else 1.6e-2)
+    err = rel_l2(ug, uo)
+    print(f"{storage}, nx = 27, 9 steps: velocity rel L2 {err:.2e}")
+    # random deviations as large as the velocity they carry: each stored value
+    # is rounded at up to 2^-p relative (p = 12 FP16, 9 BF16), and the error
+    # of the velocity, a signed sum of them, stays within twice that
+    assert err < 2.0 * 2.0 ** -(12 if storage == "f16" else 9)
     sim.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("dims", [(264, 6, 5), (200, 7, 5), (36, 9, 7)])
+def test_multi_cell_lanes_partial_warps(perm, storage, dims):
+    """Two (FP32) or four (16-bit) cells per lane, with the x-shifted values of
+    odd steps passed between lanes: rows of two tiles (264 = 256 + 8 cells),
+    a row whose last warp is partly idle (200 cells), a row shorter than a
+    warp's cells (36); 1, 2 and 5 steps (both parities).  A value moved to
+    the wrong cell shows as an O(1) error of the deviations."""
+    box = fluid_box(dims, tau=0.9, g=(1e-6, 0.0, -5e-7))
+    _, w = oracle.lattice()
+    f0 = random_populations(box.n_cells, w, seed=sum(dims), rho_amp=1e-3, u_amp=1e-3)
+    dev_o = []
+    fo = f0
+    for n in range(1, 6):
+        fo, _, _ = oracle.lb_step(fo, box.dims, box.tau, g=box.g)
+        dev_o.append(fo - w[None, :] * box.rho0)
+    for steps in (1, 2, 5):
+        sim = gpu_sim(box, storage=storage)
+        sim.set_populations(oracle_f_to_gpu(f0, perm))
+        sim.lb_step(steps)
+        dg = gpu_f_to_oracle(sim.get_populations(), perm) - w[None, :] * box.rho0
+        sim.close()
+        do = dev_o[steps - 1]
+        err = np.abs(dg - do).max() / np.abs(do).max()
+        bound = {"f32": 1e-5, "f16": 5e-3, "bf16": 3e-2}[storage]
+        assert err < bound, (steps, err)
 
 
 @pytest.mark.parametrize("tau", [0.51, 3.0])

@@ -1,0 +1,153 @@
+"""The paper's bead membrane on the GPU (Sec. 2.2): Skalak strain energy,
+Kantor-Nelson bending and the volume penalty (Eq. vol_cons), against the
+FP64 oracle; and the forcing cross-check of the paper's scheme (Shan-Chen
+velocity shift) against Guo forcing on the swimmer's velocity."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import gpu_f_to_oracle, gpu_sim, lattice_perm, rel_l2
+from workloads import BoxSpec, SwimmerSpec, assemble, perturbed_nodes
+from dataclasses import replace
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def perm(gpu_lib):
+    return lattice_perm()
+
+
+def _box(membrane, kernel="peskin4", forcing="guo", dims=(40, 36, 34), center=(20.3, 18.6, 17.2), period=500.0):
+    s = SwimmerSpec(center=center, radius=4.0, subdiv=2, spacing=12.0, period=period).with_drive(
+        1e-3, 1e-3, math.pi / 2)
+    if membrane == "skalak":
+        s = replace(s, law="skalak", Gs=5e-2, C=9.5)
+    elif membrane == "skalak_bending":
+        s = replace(s, law="skalak", Gs=5e-2, C=9.5, kb=1.25e-3)
+    elif membrane == "paper":
+        s = s.with_paper_membrane()
+    elif membrane == "bending_volume_neohooke":
+        s = replace(s, kb=1.25e-3, kv=1.0)
+    return BoxSpec(dims=dims, swimmers=(s,), kernel=kernel, forcing=forcing)
+
+
+@pytest.mark.parametrize("membrane", ["skalak", "skalak_bending", "paper", "bending_volume_neohooke"])
+def test_node_forces_element_wise(perm, membrane):
+    """Nodes displaced by 0.05 lattice units (stretch, bend and compress
+    every bead): the GPU's nodal forces f^tot against the oracle's."""
+    box = _box(membrane)
+    asm = assemble(box)
+    sim = gpu_sim(box, asm)
+    r = perturbed_nodes(asm["nodes"], seed=7, amp=0.05) * 0.98 + 0.02 * asm["nodes"].mean(0)  # also shrink
+    sim.set_nodes(r)
+    for _ in range(2):  # twice at the same step: the volume sums start from zero each time
+        sim.ib_spread()
+        fg = sim.get_node_forces().astype(np.float64)
+        osim = oracle.OracleSim(box, asm)
+        osim.r = r.copy()
+        fo = osim.node_forces()
+        err = np.abs(fg - fo).max() / np.abs(fo).max()
+        print(f"{membrane}: node forces max error {err:.2e} of max |f| {np.abs(fo).max():.2e}")
+        assert err < 1e-5
+    Fg = sim.get_force_field().astype(np.float64)
+    Fo = oracle.spread(r, fg, box.dims)
+    assert np.abs(Fg - Fo).max() < 1e-6 * np.abs(Fo).max()
+    sim.close()
+
+
+def test_volume_penalty_alone_against_closed_form(perm):
+    """A bead shrunk uniformly about its centre by s: the volume forces sum,
+    weighted by the rest positions about the centre, to
+    -3 kv V0 s^2 (s^3 - 1) (the oracle's closed-form pin); only the volume
+    penalty acts (neo-Hookean modulus and bending zero, no drive)."""
+    s = SwimmerSpec(center=(20.0, 18.0, 17.0), radius=4.0, subdiv=2, spacing=12.0, Gs=0.0, kv=1.0).with_drive(
+        0.0, 0.0, 0.0)
+    box = BoxSpec(dims=(40, 36, 34), swimmers=(s,))
+    asm = assemble(box)
+    sim = gpu_sim(box, asm)
+    X = asm["nodes"]
+    b0, n = asm["beads"][1][0], asm["beads"][1][1]
+    ctr = X[b0:b0 + n].mean(0)
+    sc = 0.97
+    r = X.copy()
+    for b in range(3):
+        m0, mn = asm["beads"][b][0], asm["beads"][b][1]
+        cb = X[m0:m0 + mn].mean(0)
+        r[m0:m0 + mn] = cb + sc * (X[m0:m0 + mn] - cb)
+    sim.set_nodes(r)
+    sim.ib_spread()
+    f = sim.get_node_forces().astype(np.float64)[b0:b0 + n]
+    V0 = oracle.volume(asm["tris"][asm["beads"][1][2]:asm["beads"][1][2] + asm["beads"][1][3]], X)
+    lhs = (f * (X[b0:b0 + n] - ctr)).sum()
+    rhs = -3 * 1.0 * V0 * sc ** 2 * (sc ** 3 - 1)
+    print(f"volume penalty: sum f.X {lhs:.6e}, closed form {rhs:.6e}")
+    assert lhs == pytest.approx(rhs, rel=1e-5)
+    sim.close()
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_coupled_paper_membrane_against_oracle(perm, deterministic):
+    """The 48^3 single swimmer with the paper's membrane, 150 coupled steps:
+    velocity field within 1e-5 relative L2, node positions within 1e-6."""
+    s = SwimmerSpec(center=(24.0, 24.0, 24.0), radius=4.0, subdiv=2, spacing=12.0, period=500.0).with_drive(
+        1e-3, 1e-3, math.pi / 2).with_paper_membrane()
+    box = BoxSpec(dims=(48, 48, 48), swimmers=(s,))
+    asm = assemble(box)
+    sim = gpu_sim(box, asm, deterministic=deterministic)
+    sim.lb_step(150)
+    osim = oracle.OracleSim(box, asm).step(150)
+    _, ug = oracle.macros(gpu_f_to_oracle(sim.get_populations(), perm))
+    _, uo = oracle.macros(osim.f)
+    err = rel_l2(ug, uo)
+    dr = np.abs(sim.get_nodes() - osim.r).max()
+    print(f"paper membrane, 150 steps: velocity rel L2 {err:.2e}, node positions {dr:.2e}")
+    assert err < 1e-5
+    assert dr < 1e-6
+    sim.close()
+
+
+def test_paper_membrane_deterministic_and_batched_bitwise(gpu_lib):
+    """Deterministic spreading with the paper's membrane: two runs, and the
+    box stepped inside a batch, end bitwise equal."""
+    from paper_2202_12147_gb300 import Batch
+    box = _box("paper", dims=(48, 40, 36), center=(24.0, 20.0, 18.0))
+    asm = assemble(box)
+    outs = []
+    for mode in ("alone", "alone", "batch"):
+        sim = gpu_sim(box, asm, deterministic=True)
+        other = gpu_sim(_box("skalak", dims=(32, 32, 32), center=(16.0, 16.0, 16.0)), deterministic=True)
+        if mode == "batch":
+            b = Batch([sim, other])
+            b.lb_step(37)
+            b.close()
+        else:
+            sim.lb_step(37)
+        outs.append((sim.get_nodes(), sim.get_populations()))
+        sim.close()
+        other.close()
+    for r, f in outs[1:]:
+        assert np.array_equal(r, outs[0][0]) and np.array_equal(f, outs[0][1])
+
+
+@pytest.mark.parametrize("kernel", ["peskin4", "linear2"])
+def test_guo_and_shan_chen_give_the_same_swimming_velocity(gpu_lib, kernel):
+    """The paper's forcing (Shan-Chen velocity shift, Sec. 2.1 Eq. sc) and
+    Guo's forcing differ at second order in the force, which is tiny here:
+    the swimmer's displacement over a drive period (paper membrane, 48^3,
+    period 500) agrees within 1 %."""
+    d = {}
+    for forcing in ("guo", "shan_chen"):
+        s = SwimmerSpec(center=(24.0, 24.0, 24.0), radius=4.0, subdiv=2, spacing=12.0, period=500.0).with_drive(
+            1e-3, 1e-3, math.pi / 2).with_paper_membrane()
+        box = BoxSpec(dims=(48, 48, 48), swimmers=(s,), kernel=kernel, forcing=forcing)
+        sim = gpu_sim(box, assemble(box))
+        sim.lb_step(500)
+        d[forcing] = sim.swimmer_state(0)["disp"][0]
+        sim.close()
+    rel = abs(d["shan_chen"] - d["guo"]) / abs(d["guo"])
+    print(f"{kernel}: displacement over one period, Guo {d['guo']:.6e}, Shan-Chen {d['shan_chen']:.6e}, "
+          f"relative difference {rel:.2e}")
+    assert rel < 1e-2
