@@ -43,18 +43,21 @@ def test_node_forces_element_wise(perm, membrane):
     sim = gpu_sim(box, asm)
     r = perturbed_nodes(asm["nodes"], seed=7, amp=0.05) * 0.98 + 0.02 * asm["nodes"].mean(0)  # also shrink
     sim.set_nodes(r)
-    for _ in range(2):  # twice at the same step: the volume sums start from zero each time
-        sim.ib_spread()
-        fg = sim.get_node_forces().astype(np.float64)
-        osim = oracle.OracleSim(box, asm)
-        osim.r = r.copy()
-        fo = osim.node_forces()
-        err = np.abs(fg - fo).max() / np.abs(fo).max()
-        print(f"{membrane}: node forces max error {err:.2e} of max |f| {np.abs(fo).max():.2e}")
-        assert err < 1e-5
+    osim = oracle.OracleSim(box, asm)
+    osim.r = r.copy()
+    fo = osim.node_forces()
+    sim.ib_spread()
+    fg = sim.get_node_forces().astype(np.float64)
+    err = np.abs(fg - fo).max() / np.abs(fo).max()
+    print(f"{membrane}: node forces max error {err:.2e} of max |f| {np.abs(fo).max():.2e}")
+    assert err < 1e-5
     Fg = sim.get_force_field().astype(np.float64)
     Fo = oracle.spread(r, fg, box.dims)
     assert np.abs(Fg - Fo).max() < 1e-6 * np.abs(Fo).max()
+    # a second evaluation at the same step (spreading adds into the field
+    # again): the bead volume sums start from zero every time
+    sim.ib_spread()
+    assert np.array_equal(sim.get_node_forces(), fg.astype(np.float32))
     sim.close()
 
 
@@ -132,16 +135,21 @@ def test_paper_membrane_deterministic_and_batched_bitwise(gpu_lib):
         assert np.array_equal(r, outs[0][0]) and np.array_equal(f, outs[0][1])
 
 
-@pytest.mark.parametrize("kernel", ["peskin4", "linear2"])
-def test_guo_and_shan_chen_give_the_same_swimming_velocity(gpu_lib, kernel):
+@pytest.mark.parametrize("kernel,membrane", [("peskin4", "paper"), ("linear2", "neohooke")])
+def test_guo_and_shan_chen_give_the_same_swimming_velocity(gpu_lib, kernel, membrane):
     """The paper's forcing (Shan-Chen velocity shift, Sec. 2.1 Eq. sc) and
     Guo's forcing differ at second order in the force, which is tiny here:
-    the swimmer's displacement over a drive period (paper membrane, 48^3,
-    period 500) agrees within 1 %."""
+    the swimmer's displacement over a drive period (48^3, period 500)
+    agrees within 1 %.  With the 2-point kernel the paper's stiff membrane
+    (kappa_a = 1) makes the explicit coupling unstable (the oracle and the
+    GPU alike reach non-finite values within 50-75 steps), so that kernel is
+    checked with the neo-Hookean membrane (Gs = 0.01)."""
     d = {}
     for forcing in ("guo", "shan_chen"):
         s = SwimmerSpec(center=(24.0, 24.0, 24.0), radius=4.0, subdiv=2, spacing=12.0, period=500.0).with_drive(
-            1e-3, 1e-3, math.pi / 2).with_paper_membrane()
+            1e-3, 1e-3, math.pi / 2)
+        if membrane == "paper":
+            s = s.with_paper_membrane()
         box = BoxSpec(dims=(48, 48, 48), swimmers=(s,), kernel=kernel, forcing=forcing)
         sim = gpu_sim(box, assemble(box))
         sim.lb_step(500)
