@@ -979,6 +979,10 @@ struct lbib_adjoint {
     // recompute done, e_free[set] the reverse steps that read the set done
     cudaStream_t s2 = nullptr;
     cudaEvent_t e_ready[2] = {nullptr, nullptr}, e_free[2] = {nullptr, nullptr};
+    // the reverse steps run on a high-priority stream forked from the caller's,
+    // so the recompute beside them takes the SM slots they leave
+    cudaStream_t s_rev = nullptr;
+    cudaEvent_t e_fork = nullptr, e_join = nullptr;
     float fwd_ms = 0.f, bwd_ms = 0.f;
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
     // CUDA graphs of one full K-step segment: the forward steps, and the
@@ -996,6 +1000,9 @@ struct lbib_adjoint {
                 if (g) cudaGraphExecDestroy(g);
         if (cap) cudaStreamDestroy(cap);
         if (s2) cudaStreamDestroy(s2);
+        if (s_rev) cudaStreamDestroy(s_rev);
+        if (e_fork) cudaEventDestroy(e_fork);
+        if (e_join) cudaEventDestroy(e_join);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
         for (int k = 0; k < 2; ++k) {
@@ -1268,8 +1275,11 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
         cur = 0;
         CU(run_segment<T>(a, P.n_seg - 1, 0, a->s));
     }
-    CU(cudaEventRecord(a->e_free[0], a->s));
-    CU(cudaEventRecord(a->e_free[1], a->s));
+    cudaStream_t rs = a->s_rev;
+    CU(cudaEventRecord(a->e_fork, a->s));
+    CU(cudaStreamWaitEvent(rs, a->e_fork, 0));
+    CU(cudaEventRecord(a->e_free[0], rs));
+    CU(cudaEventRecord(a->e_free[1], rs));
     bool ready_on_s2[2] = {false, false};
     for (int g = P.n_seg - 1; g >= 0; --g) {
         const int oth = 1 - cur;
@@ -1280,25 +1290,27 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
             ready_on_s2[oth] = true;
         }
         if (ready_on_s2[cur]) {
-            CU(cudaStreamWaitEvent(a->s, a->e_ready[cur], 0));
+            CU(cudaStreamWaitEvent(rs, a->e_ready[cur], 0));
             ready_on_s2[cur] = false;
         }
-        CU(set_tbase(a, g, cur, a->s));
+        CU(set_tbase(a, g, cur, rs));
         const int len = a->seg_len(g);
         if (len == P.K && a->graphs) {
             if (!a->g_rev[nxt][cur]) CU(capture<T>(a, true, nxt, cur));
-            CU(cudaGraphLaunch(a->g_rev[nxt][cur], a->s));
+            CU(cudaGraphLaunch(a->g_rev[nxt][cur], rs));
             a->launches += a->n_rev[nxt];
             if (P.K & 1) nxt = 1 - nxt;
         } else {
             for (int k = len - 1; k >= 0; --k) {
-                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], a->s, cur));
+                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], rs, cur));
                 nxt = 1 - nxt;
             }
         }
-        CU(cudaEventRecord(a->e_free[cur], a->s));
+        CU(cudaEventRecord(a->e_free[cur], rs));
         cur = oth;
     }
+    CU(cudaEventRecord(a->e_join, rs));
+    CU(cudaStreamWaitEvent(a->s, a->e_join, 0));
     if (P.M > 0) {  // x_cm(0) enters the displacement with a minus sign
         k_adj_seed<<<(P.M + 127) / 128, 128, 0, a->s>>>(a->m, a->at<double>(P.o_seed), -1.0, 1, lam_r);
         a->launches += 1;
@@ -1429,6 +1441,13 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     }
     CUA(cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking));
     CUA(cudaStreamCreateWithFlags(&a->s2, cudaStreamNonBlocking));
+    {
+        int lo = 0, hi = 0;
+        CUA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CUA(cudaStreamCreateWithPriority(&a->s_rev, cudaStreamNonBlocking, hi));
+    }
+    CUA(cudaEventCreateWithFlags(&a->e_fork, cudaEventDisableTiming));
+    CUA(cudaEventCreateWithFlags(&a->e_join, cudaEventDisableTiming));
     std::vector<long long> tb(P.n_seg);
     for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
     auto put = [&](size_t off, const void *src, size_t n) {

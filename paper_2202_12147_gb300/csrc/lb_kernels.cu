@@ -352,27 +352,12 @@ __device__ __forceinline__ void collide_pair_scaled(float2 (&e)[Q], const DevCtx
     }
 }
 
-// x-shifted values of the odd step move between neighbouring lanes of a warp
-// (the cells of one tile row are spread over consecutive lanes, CPT cells
-// each, the valid lanes first); a lane whose neighbour holds no cells of the
-// row reads or writes the value across the edge itself.
-constexpr unsigned FULL_MASK = 0xffffffffu;
-__device__ __forceinline__ bool next_lane_valid(bool valid) {
-    const bool nv = __shfl_down_sync(FULL_MASK, valid ? 1 : 0, 1) != 0;
-    return (threadIdx.x & 31) != 31 && nv;
-}
-
-// Update of the two cells (x0, y, z), (x0 + 1, y, z), x0 even, by every lane
-// of the warp (valid: this lane has cells).  Populations whose source or
-// destination keeps the pair adjacent (even steps, and directions with
-// c_x = 0 on odd steps) move as one pair-aligned vector; the x-shifted ones of
-// odd steps move as the aligned pair of this lane's slots, the value across
-// the pair's edge coming from (or going to) the neighbouring lane.
+// Update of the two cells (x0, y, z), (x0 + 1, y, z), x0 even.  Populations
+// whose source or destination keeps the pair adjacent (even steps, and
+// directions with c_x = 0 on odd steps) move as one pair-aligned vector; the
+// x-shifted ones of odd steps move one value at a time (with periodic wrap).
 template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
-__device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y, unsigned z, bool valid_lane) {
-    // only the odd step exchanges values between lanes; an even step's idle lanes leave at once
-    if (!ODD && !valid_lane) return true;
-    const bool valid = ODD ? valid_lane : true;
+__device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
     using S = Store<ST>;
     using T = typename S::T;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
@@ -384,8 +369,6 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
     const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
     const unsigned cell = x0 + r0 + s0;
     const size_t Np = (size_t)c.Npad;
-    const bool first = (threadIdx.x & 31) == 0;
-    const bool nextv = ODD ? next_lane_valid(valid) : false;
     // 16-bit storage: the values stay in the storage scale (collide_pair_scaled)
     float2 d[Q];
 #pragma unroll
@@ -396,25 +379,16 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
             const int dy = -cy(i), dz = -cz(i);
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
             const T *pl = P + opp(i) * Np + row;
-            const float2 w = valid ? S::ld2(pl + x0, m) : make_float2(0.f, 0.f);
-            if (cx(i) == 0) {
-                d[i] = w;
-            } else if (cx(i) > 0) {  // cells x0 - 1, x0
-                float e = __shfl_up_sync(FULL_MASK, w.y, 1);
-                if (first && valid) e = S::ld(pl + xm, m);
-                d[i] = make_float2(e, w.x);
-            } else {                 // cells x0 + 1, x0 + 2
-                float e = __shfl_down_sync(FULL_MASK, w.x, 1);
-                if (!nextv && valid) e = S::ld(pl + xp, m);
-                d[i] = make_float2(w.y, e);
-            }
+            if (cx(i) == 0) d[i] = S::ld2(pl + x0, m);
+            else if (cx(i) > 0) d[i] = make_float2(S::ld(pl + xm, m), S::ld(pl + x0, m));
+            else d[i] = make_float2(S::ld(pl + x1, m), S::ld(pl + xp, m));
         } else {
-            d[i] = valid ? S::ld2(P + i * Np + cell, m) : make_float2(0.f, 0.f);
+            d[i] = S::ld2(P + i * Np + cell, m);
         }
     }
     const bool forced = MARKED || c.has_g;
     float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
-    if (MARKED && valid) {
+    if (MARKED) {
         if (DET) {
             const float3 f0 = take_fdet(c.Fdet, c.Npad, cell), f1 = take_fdet(c.Fdet, c.Npad, cell + 1);
             Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
@@ -433,7 +407,7 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
     float2 ux, uy, uz, rho;
     if (S::scaled) collide_pair_scaled<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
     else collide_pair<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
-    if (MARKED && valid) {
+    if (MARKED) {
         c.U[cell] = make_float4(ux.x, uy.x, uz.x, rho.x);
         c.U[cell + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
     }
@@ -446,27 +420,19 @@ __device__ __forceinline__ bool lb_pair(const DevCtx &c, unsigned x0, unsigned y
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
             T *pl = P + i * Np + row;
             if (cx(i) == 0) {
-                if (valid) S::st2(pl + x0, d[i], m);
-            } else if (cx(i) > 0) {  // to cells x0 + 1, x0 + 2: slots x0, x0 + 1 hold x0 - 1, x0
-                const float e = __shfl_up_sync(FULL_MASK, d[i].y, 1);
-                if (valid) {
-                    if (!first) S::st2(pl + x0, make_float2(e, d[i].x), m);
-                    else S::st(pl + x1, d[i].x, m);
-                    if (!nextv) S::st(pl + xp, d[i].y, m);
-                }
-            } else {                 // to cells x0 - 1, x0: slots x0, x0 + 1 hold x0 + 1, x0 + 2
-                const float e = __shfl_down_sync(FULL_MASK, d[i].x, 1);
-                if (valid) {
-                    if (nextv) S::st2(pl + x0, make_float2(d[i].y, e), m);
-                    else S::st(pl + x0, d[i].y, m);
-                    if (first) S::st(pl + xm, d[i].x, m);
-                }
+                S::st2(pl + x0, d[i], m);
+            } else if (cx(i) > 0) {
+                S::st(pl + x1, d[i].x, m);
+                S::st(pl + xp, d[i].y, m);
+            } else {
+                S::st(pl + xm, d[i].x, m);
+                S::st(pl + x0, d[i].y, m);
             }
-        } else if (valid) {
+        } else {
             S::st2(P + opp(i) * Np + cell, d[i], m);
         }
     }
-    return !valid || (isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y));
+    return isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
 }
 
 // 16-bit formats: a packed pair of stored values to FP32 and back (no rescaling).
@@ -488,20 +454,19 @@ __device__ __forceinline__ unsigned pack2_raw(float2 v) {
     return r;
 }
 
-// Update of four cells x0 .. x0 + 3 (x0 a multiple of 4) with 16-bit storage,
-// by every lane of the warp (valid: this lane has cells).  Each direction
-// moves as one aligned 8-byte word of this lane's four slots; for the
-// x-shifted directions of odd steps the value across the word's edge comes
-// from (or goes to) the neighbouring lane, reassembled with byte permutes.
-// The collision runs as two packed pairs.
-#ifndef LBIB_Q_STORE8
-#define LBIB_Q_STORE8 1
+// Update of four cells x0 .. x0 + 3 (x0 a multiple of 4) with 16-bit storage.
+// Each direction moves as one 8-byte word when its cells stay aligned (read,
+// and written once both pairs are collided); the x-shifted directions of odd
+// steps read the aligned word plus the one value across its edge and
+// reassemble with byte permutes, and write one value, an aligned pair and one
+// value.  (Passing the edge values between neighbouring lanes with shuffles
+// instead measured slower: odd steps 76 against 67 us FP16, 109 against 96 us
+// FP32, on a 256 x 128 x 128 box.)  The collision runs as two packed pairs.
+#ifndef LBIB_Q_ODD_STORE8
+#define LBIB_Q_ODD_STORE8 0
 #endif
 template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
-__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z, bool valid_lane) {
-    // only the odd step exchanges values between lanes; an even step's idle lanes leave at once
-    if (!ODD && !valid_lane) return true;
-    const bool valid = ODD ? valid_lane : true;
+__device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
     using T = unsigned short;
     T *__restrict__ P = reinterpret_cast<T *>(c.pops);
     const unsigned nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
@@ -511,8 +476,6 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
     const unsigned sm = (z ? z - 1 : nz - 1) * nxy, s0 = z * nxy, sp = ((z + 1 == nz) ? 0 : z + 1) * nxy;
     const unsigned cell = x0 + r0 + s0;
     const size_t Np = (size_t)c.Npad;
-    const bool first = (threadIdx.x & 31) == 0;
-    const bool nextv = ODD ? next_lane_valid(valid) : false;
     uint2 raw[Q];  // cells x0..x0+3 of each direction, 2 values per word
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -521,27 +484,23 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
             const int dy = -cy(i), dz = -cz(i);
             const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
             const T *pl = P + opp(i) * Np + row;
-            const uint2 w = valid ? *reinterpret_cast<const uint2 *>(pl + x0) : make_uint2(0u, 0u);
+            const uint2 w = *reinterpret_cast<const uint2 *>(pl + x0);
             if (cx(i) == 0) {
                 raw[i] = w;
             } else if (cx(i) > 0) {  // cells x0-1 .. x0+2
-                unsigned e = __shfl_up_sync(FULL_MASK, w.y, 1) >> 16;
-                if (first && valid) e = pl[xm];
+                const unsigned e = pl[xm];
                 raw[i] = make_uint2(__byte_perm(e, w.x, 0x5410), __byte_perm(w.x, w.y, 0x5432));
             } else {                 // cells x0+1 .. x0+4
-                unsigned e = __shfl_down_sync(FULL_MASK, w.x, 1);
-                if (!nextv && valid) e = pl[x4];
+                const unsigned e = pl[x4];
                 raw[i] = make_uint2(__byte_perm(w.x, w.y, 0x5432), __byte_perm(w.y, e, 0x5432));
             }
         } else {
-            raw[i] = valid ? *reinterpret_cast<const uint2 *>(P + i * Np + cell) : make_uint2(0u, 0u);
+            raw[i] = *reinterpret_cast<const uint2 *>(P + i * Np + cell);
         }
     }
     const bool forced = MARKED || c.has_g;
     bool ok = true;
-    // first pair's outputs (x-shifted ones of odd steps, and with 8-byte
-    // stores all of them), written together with the second pair's
-    unsigned keep[Q];
+    unsigned keep[Q];  // first pair's outputs, written together with the second pair's
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float2 d[Q];
@@ -549,7 +508,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
         for (int i = 0; i < Q; ++i) d[i] = unpack2_raw<ST>(h ? raw[i].y : raw[i].x);  // storage scale
         const unsigned cl = cell + 2 * h;
         float2 Fx = sp2(0.f), Fy = sp2(0.f), Fz = sp2(0.f);
-        if (MARKED && valid) {
+        if (MARKED) {
             if (DET) {
                 const float3 f0 = take_fdet(c.Fdet, c.Npad, cl), f1 = take_fdet(c.Fdet, c.Npad, cl + 1);
                 Fx = make_float2(f0.x, f1.x); Fy = make_float2(f0.y, f1.y); Fz = make_float2(f0.z, f1.z);
@@ -567,11 +526,11 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
         }
         float2 ux, uy, uz, rho;
         collide_pair_scaled<FORCING>(d, c, forced, Fx, Fy, Fz, ux, uy, uz, rho);
-        if (MARKED && valid) {
+        if (MARKED) {
             c.U[cl] = make_float4(ux.x, uy.x, uz.x, rho.x);
             c.U[cl + 1] = make_float4(ux.y, uy.y, uz.y, rho.y);
         }
-        ok &= !valid || (isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y));
+        ok &= isfinite(rho.x + rho.y) && isfinite(ux.x + uy.x + uz.x + ux.y + uy.y + uz.y);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned e = pack2_raw<ST>(d[i]);  // this pair's cells (x0 + 2h, x0 + 2h + 1)
@@ -581,47 +540,30 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
                 const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
                 T *pl = P + i * Np + row;
                 if (cx(i) == 0) {
-                    if (LBIB_Q_STORE8) {
-                        if (h == 0) keep[i] = e;
-                        else if (valid) *reinterpret_cast<uint2 *>(pl + x0) = make_uint2(keep[i], e);
-                    } else if (valid) {
-                        *reinterpret_cast<unsigned *>(pl + x0 + 2 * h) = e;
-                    }
+#if LBIB_Q_ODD_STORE8
+                    if (h == 0) keep[i] = e;
+                    else *reinterpret_cast<uint2 *>(pl + x0) = make_uint2(keep[i], e);
+#else
+                    *reinterpret_cast<unsigned *>(pl + x0 + 2 * h) = e;
+#endif
                 } else if (h == 0) {
                     keep[i] = e;
                 } else {
                     const unsigned a = keep[i], b = e;
-                    if (cx(i) > 0) {  // to cells x0+1 .. x0+4: slots x0 .. x0+3 hold cells x0-1 .. x0+2
-                        const unsigned pb = __shfl_up_sync(FULL_MASK, b, 1);
-                        if (valid) {
-                            if (!first) {
-                                *reinterpret_cast<uint2 *>(pl + x0) =
-                                    make_uint2(__byte_perm(pb, a, 0x5432), __byte_perm(a, b, 0x5432));
-                            } else {
-                                pl[x0 + 1] = (T)(a & 0xffffu);
-                                *reinterpret_cast<unsigned *>(pl + x0 + 2) = __byte_perm(a, b, 0x5432);
-                            }
-                            if (!nextv) pl[x4] = (T)(b >> 16);
-                        }
-                    } else {          // to cells x0-1 .. x0+2: slots x0 .. x0+3 hold cells x0+1 .. x0+4
-                        const unsigned na = __shfl_down_sync(FULL_MASK, a, 1);
-                        if (valid) {
-                            if (nextv) {
-                                *reinterpret_cast<uint2 *>(pl + x0) =
-                                    make_uint2(__byte_perm(a, b, 0x5432), __byte_perm(b, na, 0x5432));
-                            } else {
-                                *reinterpret_cast<unsigned *>(pl + x0) = __byte_perm(a, b, 0x5432);
-                                pl[x0 + 2] = (T)(b >> 16);
-                            }
-                            if (first) pl[xm] = (T)(a & 0xffffu);
-                        }
+                    if (cx(i) > 0) {  // to cells x0+1 .. x0+4
+                        pl[x0 + 1] = (T)(a & 0xffffu);
+                        *reinterpret_cast<unsigned *>(pl + x0 + 2) = __byte_perm(a, b, 0x5432);
+                        pl[x4] = (T)(b >> 16);
+                    } else {          // to cells x0-1 .. x0+2
+                        pl[xm] = (T)(a & 0xffffu);
+                        *reinterpret_cast<unsigned *>(pl + x0) = __byte_perm(a, b, 0x5432);
+                        pl[x0 + 2] = (T)(b >> 16);
                     }
                 }
-            } else if (LBIB_Q_STORE8) {
+            } else {
+                // the four cells' values as one aligned 8-byte word
                 if (h == 0) keep[i] = e;
-                else if (valid) *reinterpret_cast<uint2 *>(P + opp(i) * Np + cell) = make_uint2(keep[i], e);
-            } else if (valid) {
-                *reinterpret_cast<unsigned *>(P + opp(i) * Np + cl) = e;
+                else *reinterpret_cast<uint2 *>(P + opp(i) * Np + cell) = make_uint2(keep[i], e);
             }
         }
     }
@@ -661,12 +603,12 @@ __device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, uns
     // is written before this launch and not again until it has finished
     if (c.marks[(ODD ? c.n_tiles : 0) + tile] == c.ctl->gen[ODD ? 1 : 0]) return;
     const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
-    const bool valid = CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx;
     bool ok = true;
-    // the multi-cell updates run on every lane (they exchange values between lanes)
-    if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, y, z, valid);
-    else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, y, z, valid);
-    else if (valid) ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, y, z);
+    if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+        if (CPT == 4) ok = lb_quad<ST, ODD, FORCING, false, false>(c, x, y, z);
+        else if (CPT == 2) ok = lb_pair<ST, ODD, FORCING, false, false>(c, x, y, z);
+        else ok = lb_cell<ST, ODD, FORCING, false, false>(c, x, y, z);
+    }
     report_bad(c, !ok);
     if (c.n_nodes == 0 && tile == 0 && threadIdx.x == 0) c.ctl->step += 1;  // no IB chain to advance it
 }
@@ -694,22 +636,36 @@ __global__ void LBIB_LB_BOUNDS_ST(ST, CPT) k_lb_main(const DevCtx c) {
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// Stamp the tiles listed for the next step (parity q) with its number: the
+// main update of the step before the previous one, the last reader of that
+// parity's stamps, has finished before this kernel starts, and the next main
+// update starts after it.
+__device__ __forceinline__ void commit_next_stamps(const DevCtx &c, int q, int next, int bid, int nblk) {
+    const int m = c.tile_count[q];
+    const int *list = c.tile_list + (size_t)q * c.n_tiles;
+    int *marks = c.marks + (size_t)q * c.n_tiles;
+    for (int k = bid * blockDim.x + threadIdx.x; k < m; k += nblk * blockDim.x) marks[list[k]] = next;
+    if (bid == 0 && threadIdx.x == 0) c.ctl->gen[q] = next;
+}
+
 // The marked tiles of this parity's list: a persistent grid walks the list.
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nblk) {
     const int p = ODD ? 1 : 0;
     const int n = c.tile_count[p];
     const int *list = c.tile_list + (size_t)p * c.n_tiles;
+    commit_next_stamps(c, 1 - p, (int)c.ctl->step + 1, bid, nblk);
     bool ok = true;
     for (int k = bid; k < n; k += nblk) {
         const int tile = list[k];
         const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
         const unsigned y = yz % c.ny, z = yz / c.ny;
         const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
-        const bool valid = CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx;
-        if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
-        else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
-        else if (valid) ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
+        if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+            if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
+        }
     }
     report_bad(c, !ok);
 }
@@ -751,6 +707,9 @@ template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked_batch(const BatchDev bt) {
     __shared__ int s_pref[LBIB_MAX_BATCH + 1];
     const int p = ODD ? 1 : 0;
+    // every box's next-step stamps (the boxes' step counters agree)
+    for (int b = 0; b < bt.n_boxes; ++b)
+        commit_next_stamps(bt.boxes[b], 1 - p, (int)bt.boxes[b].ctl->step + 1, blockIdx.x, gridDim.x);
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int b = 0; b < bt.n_boxes; ++b) {
@@ -773,10 +732,11 @@ __global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked_batch(const BatchDev bt) {
         const unsigned tx = tile % c.tiles_x, yz = tile / c.tiles_x;
         const unsigned y = yz % c.ny, z = yz / c.ny;
         const unsigned x = tx * c.tile_x + CPT * threadIdx.x;
-        const bool valid = CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx;
-        if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
-        else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z, valid);
-        else if (valid) ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
+        if (CPT * threadIdx.x < (unsigned)c.tile_x && x < (unsigned)c.nx) {
+            if (CPT == 4) ok &= lb_quad<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else if (CPT == 2) ok &= lb_pair<ST, ODD, FORCING, DET, true>(c, x, y, z);
+            else ok &= lb_cell<ST, ODD, FORCING, DET, true>(c, x, y, z);
+        }
         if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_NONFINITE);
         ok = true;
     }
