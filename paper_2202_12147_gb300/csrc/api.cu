@@ -62,7 +62,7 @@ struct Layout {
     size_t esize = 4;
     size_t bytes[LBIB_NBUF] = {0, 0, 0};
     // fields
-    size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0, oPend = 0;
+    size_t oF = 0, oFdet = 0, oU = 0, oMarks = 0, oList = 0, oCount = 0;
     // aux
     int n_edges = 0;
     size_t oedge = 0, ovg = 0, ovfix = 0;
@@ -213,8 +213,6 @@ Layout make_layout(const lb_params *p, const lbib_structure *s) {
     o += up(2 * (size_t)L.n_tiles * 4);
     L.oCount = o;
     o += up(4 * 4);
-    L.oPend = o;
-    o += up((size_t)L.n_tiles * 4);
     L.bytes[1] = o;
     const int M = s ? s->n_nodes : 0, T = s ? s->n_tris : 0, B = s ? s->n_beads : 0, S = s ? s->n_swimmers : 0;
     o = 0;
@@ -268,10 +266,7 @@ struct lbib_ctx {
     cudaStream_t ib = nullptr;     // immersed-boundary chain of a step, concurrent with the fluid update
     cudaStream_t cap = nullptr;    // private streams used only to capture graphs
     cudaStream_t cap_ib = nullptr;
-    // step-to-step dependencies: e_main after a step's main update, e_ib after its
-    // marked-tile update (the next main update waits for it), e_done after its
-    // interpolation (the end of the step's IB chain)
-    cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr, e_done = nullptr;
+    cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr;  // step-to-step dependencies
     cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS steps from an even step
     long long step = 0;            // host mirror of the device step counter
     bool profiling = false;
@@ -299,7 +294,7 @@ struct lbib_batch {
     int storage = 0, forcing = 0, kernel = 0, det = 0;
     bool any_nodes = false;
     cudaStream_t user = nullptr, ib = nullptr, cap = nullptr, cap_ib = nullptr;
-    cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr, e_done = nullptr;
+    cudaEvent_t e_fork = nullptr, e_main = nullptr, e_ib = nullptr;
     cudaGraphExec_t graph = nullptr;
     long long step = 0;
     bool profiling = false;
@@ -341,22 +336,19 @@ cudaError_t fork(lbib_ctx *c, cudaStream_t sm, cudaStream_t sib) {
     if ((e = cudaEventRecord(c->e_fork, sm)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(sib, c->e_fork, 0)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(c->e_main, sm)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(c->e_done, sm)) != cudaSuccess) return e;
     return cudaEventRecord(c->e_ib, sm);
 }
 
 // Order the main stream after the immersed-boundary stream.
-cudaError_t join(lbib_ctx *c, cudaStream_t sm) { return cudaStreamWaitEvent(sm, c->e_done, 0); }
+cudaError_t join(lbib_ctx *c, cudaStream_t sm) { return cudaStreamWaitEvent(sm, c->e_ib, 0); }
 
 // One coupled step on two streams (between fork and join).  Main stream: the
 // fluid update of every unmarked tile (the bulk of the bytes).  IB stream,
-// concurrently: forces and spreading (which also lists the tiles of the next
-// step: the node stencils widened by one cell, which the nodes cannot leave
-// in one step), the fluid update of the marked tiles (which commits the next
-// step's stamps), interpolation and advection.  The main stream's next step
-// waits for this step's marked-tile update only (its populations and the next
-// stamps), not for the interpolation; the IB stream's fluid update waits for
-// the previous step's main-stream update.
+// concurrently: forces and spreading, the fluid update of the marked tiles,
+// interpolation and advection, then the marks for the next step (other
+// parity).  The main stream's next step waits for this step's IB chain
+// (populations of marked tiles and the next marks); the IB stream's fluid
+// update waits for the previous step's main-stream update.
 cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t sm, cudaStream_t sib, bool timed = false) {
     cudaError_t e;
     const int p = odd ? 1 : 0;
@@ -371,13 +363,12 @@ cudaError_t enqueue_step(lbib_ctx *c, bool odd, cudaStream_t sm, cudaStream_t si
     if ((e = main_fluid(c, odd, sm)) != cudaSuccess) return e;
     if (timed && (e = timed_event(c, sm)) != cudaSuccess) return e;
     if ((e = launch_ib_prepare(c->d, sib)) != cudaSuccess) return e;
-    if ((e = launch_ib_gather_spread(c->d, c->p.kernel, true, sib)) != cudaSuccess) return e;
+    if ((e = launch_ib_gather_spread(c->d, c->p.kernel, sib)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(sib, c->e_main, 0)) != cudaSuccess) return e;  // previous step's main update
     if ((e = cudaEventRecord(c->e_main, sm)) != cudaSuccess) return e;
     if ((e = launch_lb_marked(c->d, c->p.storage, c->p.forcing, odd, sib)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(c->e_ib, sib)) != cudaSuccess) return e;
     if ((e = launch_ib_interp(c->d, c->p.kernel, true, nullptr, 1 - p, sib)) != cudaSuccess) return e;
-    return cudaEventRecord(c->e_done, sib);
+    return cudaEventRecord(c->e_ib, sib);
 }
 
 // Capture n coupled steps, the first of parity p0, into an executable graph
@@ -734,7 +725,6 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.marks = (int *)(F + L.oMarks);
     d.tile_list = (int *)(F + L.oList);
     d.tile_count = (int *)(F + L.oCount);
-    d.pend = (int *)(F + L.oPend);
     d.rx = (double *)(A + L.orx);
     d.ry = (double *)(A + L.ory);
     d.rz = (double *)(A + L.orz);
@@ -783,7 +773,6 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         // stamps -1 (never marked); generations a different negative value, so no
         // tile counts as marked until a step stamps it
         cudaMemsetAsync(d.marks, 0xff, 2 * (size_t)L.n_tiles * 4, u) != cudaSuccess ||
-        cudaMemsetAsync(d.pend, 0xff, (size_t)L.n_tiles * 4, u) != cudaSuccess ||
         cudaMemsetAsync((char *)d.ctl + offsetof(Control, gen), 0xfe, sizeof(int) * 2, u) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "cudaMemsetAsync failed"));
     std::vector<double> sx(M), sy(M), sz(M);
@@ -823,8 +812,7 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         cudaStreamCreateWithPriority(&c->cap_ib, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->e_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->e_main, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->e_ib, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->e_done, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&c->e_ib, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "creating streams or events failed"));
 
     // capture GRAPH_STEPS coupled steps (alternating AA parity) into one graph
@@ -875,7 +863,7 @@ int ib_spread(lbib_ctx *c) {
     if (!c) return fail(LBIB_EINVAL, "ctx is NULL");
     if (c->n_nodes == 0) return LBIB_OK;
     CU(launch_ib_prepare(c->d, c->user));
-    CU(launch_ib_gather_spread(c->d, c->p.kernel, false, c->user));
+    CU(launch_ib_gather_spread(c->d, c->p.kernel, c->user));
     return LBIB_OK;
 }
 
@@ -1234,7 +1222,6 @@ int lb_destroy(lbib_ctx *c) {
     if (c->e_fork) cudaEventDestroy(c->e_fork);
     if (c->e_main) cudaEventDestroy(c->e_main);
     if (c->e_ib) cudaEventDestroy(c->e_ib);
-    if (c->e_done) cudaEventDestroy(c->e_done);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->h_sws) cudaFreeHost(c->h_sws);
     delete c;
@@ -1277,7 +1264,6 @@ cudaError_t batch_fork(lbib_batch *b, cudaStream_t sm, cudaStream_t sib) {
     if ((e = cudaEventRecord(b->e_fork, sm)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(sib, b->e_fork, 0)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(b->e_main, sm)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(b->e_done, sm)) != cudaSuccess) return e;
     return cudaEventRecord(b->e_ib, sm);
 }
 
@@ -1305,9 +1291,8 @@ cudaError_t batch_enqueue_step(lbib_batch *b, bool odd, cudaStream_t sm, cudaStr
     if ((e = cudaStreamWaitEvent(sib, b->e_main, 0)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(b->e_main, sm)) != cudaSuccess) return e;
     if ((e = launch_lb_batch(bt, b->storage, b->forcing, b->det, true, odd, sib)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(b->e_ib, sib)) != cudaSuccess) return e;
     if ((e = launch_ib_batch(bt, b->kernel, b->det, 2, sib)) != cudaSuccess) return e;
-    return cudaEventRecord(b->e_done, sib);
+    return cudaEventRecord(b->e_ib, sib);
 }
 
 // capture GRAPH_STEPS batch steps, starting at the parity of the current step
@@ -1323,7 +1308,7 @@ cudaError_t capture_batch_graph(lbib_batch *b) {
     ce = batch_fork(b, b->cap, b->cap_ib);
     for (int k = 0; k < GRAPH_STEPS && ce == cudaSuccess; ++k)
         ce = batch_enqueue_step(b, ((b->step + k) & 1) != 0, b->cap, b->cap_ib, false);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->e_done, 0);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->e_ib, 0);
     const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
     if (ce == cudaSuccess) ce = ee;
     if (ce == cudaSuccess) ce = cudaGraphInstantiateWithFlags(&b->graph, g, cudaGraphInstantiateFlagUseNodePriority);
@@ -1443,8 +1428,7 @@ int lb_batch_create(lbib_ctx *const *ctxs, int n, lbib_batch **out) {
         cudaStreamCreateWithPriority(&b->cap_ib, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->e_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->e_main, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->e_ib, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->e_done, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&b->e_ib, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(LBIB_ECUDA, "creating batch streams or events failed"));
     b->class_cpt.assign(b->classes.size(), cpt);
     const cudaError_t ce = capture_batch_graph(b);
@@ -1467,7 +1451,7 @@ int lb_batch_step(lbib_batch *b, long long n) {
         const long long s = b->ctx[0]->step;
         if (graphs && !b->profiling && ((s - b->step) & 1) == 0 && n >= GRAPH_STEPS) {
             if (forked) {
-                CU(cudaStreamWaitEvent(b->user, b->e_done, 0));
+                CU(cudaStreamWaitEvent(b->user, b->e_ib, 0));
                 forked = false;
             }
             CU(cudaGraphLaunch(b->graph, b->user));
@@ -1483,7 +1467,7 @@ int lb_batch_step(lbib_batch *b, long long n) {
             n -= 1;
         }
     }
-    if (forked) CU(cudaStreamWaitEvent(b->user, b->e_done, 0));
+    if (forked) CU(cudaStreamWaitEvent(b->user, b->e_ib, 0));
     return LBIB_OK;
 }
 
@@ -1637,7 +1621,6 @@ int lb_batch_destroy(lbib_batch *b) {
     if (b->e_fork) cudaEventDestroy(b->e_fork);
     if (b->e_main) cudaEventDestroy(b->e_main);
     if (b->e_ib) cudaEventDestroy(b->e_ib);
-    if (b->e_done) cudaEventDestroy(b->e_done);
     if (b->dev) cudaFree(b->dev);
     delete b;
     return LBIB_OK;

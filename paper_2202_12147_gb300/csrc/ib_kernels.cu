@@ -306,21 +306,8 @@ __global__ void __launch_bounds__(PREP_TPB) k_bead_init(const DevCtx c) {
     }
 }
 
-// List tile `tile` for step `next` (parity p): the first lane of the warp to
-// see it unlisted takes it (neighbouring nodes share most of their tiles).
-__device__ __forceinline__ void list_next_tile(const DevCtx &c, int tile, int next, int p) {
-    const bool want = c.pend[tile] != next;
-    const unsigned act = __activemask();
-    const unsigned wm = __ballot_sync(act, want);
-    if (want) {
-        const unsigned peers = __match_any_sync(wm, tile);
-        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && atomicExch(&c.pend[tile], next) != next)
-            c.tile_list[(size_t)p * c.n_tiles + atomicAdd(&c.tile_count[p], 1)] = tile;
-    }
-}
-
 template <int KW, bool DET>
-__device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid, bool stamp_next) {
+__device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid) {
     __shared__ float4 sf[GS_NODES];
     __shared__ int so[GS_NODES][3];
     __shared__ float sw[GS_NODES][3][KW];
@@ -455,24 +442,6 @@ __device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid, boo
         }
     }
     if (__any_sync(0xffffffffu, unmarked) && (threadIdx.x & 31) == 0) atomicOr(&c.ctl->err, ERR_MARK);
-    if (stamp_next) {
-        // the tiles of the next step: this step's stencils widened by one cell
-        // on every side (a node moves less than 0.1 lattice units per step,
-        // checked by the interpolation), listed now and stamped by this step's
-        // marked-tile update, so that the next main update need not wait for
-        // the interpolation
-        constexpr int W = KW + 2;
-        const int next = stamp + 1, p = next & 1;
-        for (int task = threadIdx.x; task < nloc * W * W; task += GS_TPB) {
-            const int ln = task / (W * W), row = task % (W * W);
-            const int yy = (so[ln][1] + ny - 1 + row % W) % ny, zz = (so[ln][2] + nz - 1 + row / W) % nz;
-            const int trow = c.tiles_x * (yy + ny * zz);
-            const int t0 = ((so[ln][0] + nx - 1) % nx) / c.tile_x + trow;
-            const int t1 = ((so[ln][0] + KW) % nx) / c.tile_x + trow;
-            list_next_tile(c, t0, next, p);
-            if (t1 != t0) list_next_tile(c, t1, next, p);
-        }
-    }
     if (c.has_volume) {
         // the last block to finish clears the bead volumes for the next
         // k_ib_prepare (a completion count, no waiting)
@@ -490,9 +459,7 @@ __device__ __forceinline__ void gather_spread_body(const DevCtx &c, int bid, boo
 }
 
 template <int KW, bool DET>
-__global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c, int stamp_next) {
-    gather_spread_body<KW, DET>(c, blockIdx.x, stamp_next != 0);
-}
+__global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread(const DevCtx c) { gather_spread_body<KW, DET>(c, blockIdx.x); }
 
 // Fold an advection into the bead centres: R_b += mean_j v_j (the mean is
 // linear, so this keeps R_b the centre of mass of its nodes, Fig. 1 caption).
@@ -652,7 +619,17 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
         }
     }
     if (ADVECT && mark_parity >= 0) {
+        // stamp the tiles of the moved node's stencil for the next step
         const int next = (int)c.ctl->step + 1;
+        const int gbase = (threadIdx.x & 31) & ~(KW - 1);
+        px = __shfl_sync(0xffffffffu, px, gbase);
+        py = __shfl_sync(0xffffffffu, py, gbase);
+        pz = __shfl_sync(0xffffffffu, pz, gbase);
+        if (active) {
+            float fr;
+            const int ox = stencil_axis(px, nx, KW, fr), oy = stencil_axis(py, ny, KW, fr), oz = stencil_axis(pz, nz, KW, fr);
+            mark_stencil_plane<KW>(c, ox, oy, oz, l, next);
+        }
         // the block's bead sums into the global accumulators (integer sums:
         // the same result in any order)
         __syncthreads();
@@ -711,6 +688,7 @@ __device__ __forceinline__ void interp_body(const DevCtx &c, int bid, int nblk, 
             }
             if (threadIdx.x == 0) {
                 c.ctl->done = 0;
+                c.ctl->gen[next & 1] = next;
                 c.ctl->step = next;
             }
         }
@@ -848,7 +826,7 @@ template <int KW, bool DET>
 __global__ void __launch_bounds__(GS_TPB) k_ib_gather_spread_batch(const BatchDev bt) {
     for (int vb = blockIdx.x; vb < bt.blocks_gs; vb += gridDim.x) {
         const int b = batch_box(bt.off_gs, bt.n_boxes, vb);
-        gather_spread_body<KW, DET>(bt.boxes[b], vb - bt.off_gs[b], true);
+        gather_spread_body<KW, DET>(bt.boxes[b], vb - bt.off_gs[b]);
         __syncthreads();  // the shared node tables are refilled by the next virtual block
     }
 }
@@ -912,16 +890,15 @@ cudaError_t launch_bead_init(const DevCtx &c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, bool stamp_next, cudaStream_t s) {
+cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s) {
     if (c.n_nodes == 0) return cudaSuccess;
     const int blocks = (c.n_nodes + GS_NODES - 1) / GS_NODES;
-    const int sn = stamp_next ? 1 : 0;
     if (kernel == LBIB_LINEAR2) {
-        if (c.deterministic) launch_prio(k_ib_gather_spread<2, true>, blocks, GS_TPB, 0, s, c, sn);
-        else launch_prio(k_ib_gather_spread<2, false>, blocks, GS_TPB, 0, s, c, sn);
+        if (c.deterministic) launch_prio(k_ib_gather_spread<2, true>, blocks, GS_TPB, 0, s, c);
+        else launch_prio(k_ib_gather_spread<2, false>, blocks, GS_TPB, 0, s, c);
     } else {
-        if (c.deterministic) launch_prio(k_ib_gather_spread<4, true>, blocks, GS_TPB, 0, s, c, sn);
-        else launch_prio(k_ib_gather_spread<4, false>, blocks, GS_TPB, 0, s, c, sn);
+        if (c.deterministic) launch_prio(k_ib_gather_spread<4, true>, blocks, GS_TPB, 0, s, c);
+        else launch_prio(k_ib_gather_spread<4, false>, blocks, GS_TPB, 0, s, c);
     }
     return cudaGetLastError();
 }

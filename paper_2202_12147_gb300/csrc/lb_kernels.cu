@@ -636,25 +636,12 @@ __global__ void LBIB_LB_BOUNDS_ST(ST, CPT) k_lb_main(const DevCtx c) {
     lb_main_body<ST, ODD, FORCING, CPT>(c, tile, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// Stamp the tiles listed for the next step (parity q) with its number: the
-// main update of the step before the previous one, the last reader of that
-// parity's stamps, has finished before this kernel starts, and the next main
-// update starts after it.
-__device__ __forceinline__ void commit_next_stamps(const DevCtx &c, int q, int next, int bid, int nblk) {
-    const int m = c.tile_count[q];
-    const int *list = c.tile_list + (size_t)q * c.n_tiles;
-    int *marks = c.marks + (size_t)q * c.n_tiles;
-    for (int k = bid * blockDim.x + threadIdx.x; k < m; k += nblk * blockDim.x) marks[list[k]] = next;
-    if (bid == 0 && threadIdx.x == 0) c.ctl->gen[q] = next;
-}
-
 // The marked tiles of this parity's list: a persistent grid walks the list.
 template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __device__ __forceinline__ void lb_marked_body(const DevCtx &c, int bid, int nblk) {
     const int p = ODD ? 1 : 0;
     const int n = c.tile_count[p];
     const int *list = c.tile_list + (size_t)p * c.n_tiles;
-    commit_next_stamps(c, 1 - p, (int)c.ctl->step + 1, bid, nblk);
     bool ok = true;
     for (int k = bid; k < n; k += nblk) {
         const int tile = list[k];
@@ -707,9 +694,6 @@ template <int ST, bool ODD, int FORCING, bool DET, int CPT>
 __global__ void LBIB_LB_BOUNDS(CPT) k_lb_marked_batch(const BatchDev bt) {
     __shared__ int s_pref[LBIB_MAX_BATCH + 1];
     const int p = ODD ? 1 : 0;
-    // every box's next-step stamps (the boxes' step counters agree)
-    for (int b = 0; b < bt.n_boxes; ++b)
-        commit_next_stamps(bt.boxes[b], 1 - p, (int)bt.boxes[b].ctl->step + 1, blockIdx.x, gridDim.x);
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int b = 0; b < bt.n_boxes; ++b) {

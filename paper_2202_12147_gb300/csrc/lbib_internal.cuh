@@ -128,8 +128,6 @@ struct DevCtx {
     int *marks;                // [2][n_tiles]: step number whose node stencils touch the tile, per step parity
                                // (tile = x / tile_x + tiles_x * (y + ny * z))
     int *tile_list;            // [2][n_tiles]: the marked tiles of each parity, in marking order
-    int *pend;                 // [n_tiles]: the step whose list last took the tile (set while listing, before
-                               // the marked-tile update of the step before commits the stamps)
     int *tile_count;           // [2]: entries in each list
     double *rx, *ry, *rz;      // node positions (SoA)
     float4 *node_force;        // f^tot per node
@@ -263,7 +261,7 @@ cudaError_t launch_lb_batch(const BatchDev &bt, int storage, int forcing, int de
 cudaError_t launch_lb_class(const ClassArgs &ca, int storage, int forcing, int cpt, bool odd, cudaStream_t s);
 // IB (ib_kernels.cu)
 cudaError_t launch_ib_prepare(const DevCtx &c, cudaStream_t s);
-cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, bool stamp_next, cudaStream_t s);
+cudaError_t launch_ib_gather_spread(const DevCtx &c, int kernel, cudaStream_t s);
 cudaError_t launch_ib_interp(const DevCtx &c, int kernel, bool advect, float *vel_out, int mark_parity, cudaStream_t s);
 cudaError_t launch_swimmer_state(const DevCtx &c, bool init, cudaStream_t s);
 cudaError_t launch_bead_init(const DevCtx &c, cudaStream_t s);
