@@ -170,25 +170,35 @@ class Clocks:
 
 def _oracle_sample(seconds):
     """The FP64 oracle, as it stands, on one 256x128x128 two-swimmer box:
-    coupled steps until `seconds` have elapsed (at least two)."""
+    coupled steps until `seconds` have elapsed (at least two), on every core
+    of the process's affinity mask and then on one core."""
     import oracle
-    box = _boxes()[3]  # side by side, gap 3 radii
-    sim = oracle.OracleSim(box)
-    sim.step(1)  # first-touch of the arrays outside the timing
-    n = 0
-    t0 = time.perf_counter()
-    while True:
-        sim.step(1)
-        n += 1
-        dt = time.perf_counter() - t0
-        if n >= 2 and dt >= seconds:
-            break
+
+    def run(threads, secs):
+        oracle.set_threads(threads)
+        box = _boxes()[3]  # side by side, gap 3 radii
+        sim = oracle.OracleSim(box)
+        sim.step(1)  # first-touch of the arrays outside the timing
+        n = 0
+        t0 = time.perf_counter()
+        while True:
+            sim.step(1)
+            n += 1
+            dt = time.perf_counter() - t0
+            if n >= 2 and dt >= secs:
+                break
+        return box.n_cells * n / dt / 1e6, n, dt
+
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    mlups = box.n_cells * n / dt / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
-            "kind": "oracle",
+    cores = int(os.environ.get("OMP_NUM_THREADS", cores))
+    mlups, n, dt = run(cores, seconds)
+    one, n1, dt1 = run(1, seconds / 2)
+    oracle.set_threads(cores)
+    return {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{n} coupled steps of one 256x128x128 two-swimmer box (side by side, gap 3 radii), "
-                      f"FP64, {dt:.1f} s"}
+                      f"FP64, {dt:.1f} s",
+            "single_core": {"value": one, "unit": "MLUPS", "cores": 1,
+                            "sample": f"{n1} coupled steps of the same box on one core, {dt1:.1f} s"}}
 
 
 def run_reference(a):

@@ -334,7 +334,7 @@ __global__ void k_fwd_tri(Mesh m, const double *r, double *tri_f) {
 // the corners, fixed order), recorded, then F(x) += f_j Delta(x - r_j)
 template <typename T>
 __global__ void k_fwd_spread(Dims d, Mesh m, const double *r, const double *tri_f, const double *ext, double *fn,
-                             T *F) {
+                             T *F, int *rowtag, const long long *tb, int k) {
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= m.M) return;
     const int e0 = m.csr_ptr[j], e1 = m.csr_ptr[j + 1];
@@ -351,10 +351,14 @@ __global__ void k_fwd_spread(Dims d, Mesh m, const double *r, const double *tri_
     int cell[2];
     T w[2], g[2][3];
     lane_cells<T>(d, r + 3 * j, lane, cell, w, g);
+    // tag the rows (y, z) of the stencil cells with the step (absolute index
+    // + 1): the reverse sweep updates them apart from the rest of the box
+    const int tag = (int)(*tb + k + 1);
     for (int h = 0; h < 2; ++h) {
         atomicAdd(F + cell[h], (T)f[0] * w[h]);
         atomicAdd(F + d.Npad + cell[h], (T)f[1] * w[h]);
         atomicAdd(F + 2 * d.Npad + cell[h], (T)f[2] * w[h]);
+        rowtag[cell[h] / d.nx] = tag;
     }
 }
 
@@ -711,6 +715,76 @@ __global__ void __launch_bounds__(128, 4) k_adj_lb2(Dims d, float omega, float r
     }
 }
 
+// The reverse fluid update by rows (y, z): NEAR launches update the rows under
+// the step's node stencils (tagged by the forward spreading), the others the
+// rest of the box.  Away from the stencils F = 0 (apart from a uniform body
+// force), lam_u = 0 and lam_F is never read, so those rows skip them.  One
+// block per row, two adjacent cells per thread (FP32, even rows) or one.
+template <typename T, bool NEAR, bool PAIR>
+__global__ void __launch_bounds__(128) k_adj_lb_rows(Dims d, T omega, T rho0, double gx, double gy, double gz,
+                                                     const T *pops, const T *F, const T *lam_next, T *lam_u, T *lam_cur,
+                                                     T *lam_F, const int *rowtag, const long long *tb, int k) {
+    const int row = blockIdx.x;
+    const bool near = rowtag[row] == (int)(*tb + k + 1);
+    if (near != NEAR) return;
+    const int y = row % d.ny, z = row / d.ny;
+    constexpr int CPT = PAIR ? 2 : 1;
+    for (int x = CPT * threadIdx.x; x < d.nx; x += CPT * blockDim.x) {
+        const int cell = x + d.nx * row;
+        T ls[CPT][Q], dv[CPT][Q];
+        const Nbr n0(d, x, y, z);
+        if constexpr (PAIR) {
+            // 8-byte vector accesses wherever both cells' values stay adjacent
+            const Nbr n1(d, x + 1, y, z);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float *pl = lam_next + i * d.Npad;
+                if (cx(i) == 0) {
+                    const float2 v = *reinterpret_cast<const float2 *>(pl + cell + n0.off(i));
+                    ls[0][i] = v.x;
+                    ls[1][i] = v.y;
+                } else {
+                    ls[0][i] = pl[cell + n0.off(i)];
+                    ls[1][i] = pl[cell + 1 + n1.off(i)];
+                }
+                const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
+                dv[0][i] = v.x;
+                dv[1][i] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                ls[0][i] = lam_next[i * d.Npad + cell + n0.off(i)];
+                dv[0][i] = pops[i * d.Npad + cell];
+            }
+        }
+        T lam[CPT][Q], lF[CPT][3];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            T Fv[3] = {(T)gx, (T)gy, (T)gz}, lu[3] = {0, 0, 0};
+            if constexpr (NEAR) {
+                for (int a = 0; a < 3; ++a) {
+                    Fv[a] += F[a * d.Npad + cell + c];
+                    lu[a] = lam_u[a * d.Npad + cell + c];
+                }
+            }
+            adj_cell(ls[c], dv[c], Fv, lu, omega, rho0, lam[c], lF[c]);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if constexpr (PAIR) *reinterpret_cast<float2 *>(lam_cur + i * d.Npad + cell) = make_float2(lam[0][i], lam[1][i]);
+            else lam_cur[i * d.Npad + cell] = lam[0][i];
+        }
+        if constexpr (NEAR) {
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < CPT; ++c) {
+                    lam_F[a * d.Npad + cell + c] = lF[c][a];
+                    lam_u[a * d.Npad + cell + c] = 0;
+                }
+        }
+    }
+}
+
 // one warp per node: transpose of spreading
 template <typename T>
 __global__ void k_adj_spread(Dims d, int M, const double *r, const double *fn, const T *lam_F, double *lam_r,
@@ -861,7 +935,7 @@ struct Plan {
     long long n_steps;
     int K, n_seg;
     // per-slot offsets
-    size_t s_pops, s_F, s_u, s_r, s_fn, s_R, s_ext, slot_bytes;
+    size_t s_pops, s_F, s_u, s_r, s_fn, s_R, s_ext, s_rows, slot_bytes;
     // per-checkpoint offsets
     size_t c_pops, c_r, ck_bytes;
     // workspace offsets
@@ -895,6 +969,7 @@ Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, i
     P.s_fn = o; o += up(nd);
     P.s_R = o; o += up(bd);
     P.s_ext = o; o += up(bd);
+    P.s_rows = o; o += up((size_t)p->ny * p->nz * 4);  // rows (y, z) under the step's node stencils
     P.slot_bytes = o;
     o = 0;
     P.c_pops = o; o += up(Q * fp);
@@ -983,6 +1058,10 @@ struct lbib_adjoint {
     // so the recompute beside them takes the SM slots they leave
     cudaStream_t s_rev = nullptr;
     cudaEvent_t e_fork = nullptr, e_join = nullptr;
+    // the reverse fluid update of the rows away from the stencils, beside the
+    // node chain: its stream, its capture stream and the step-to-step events
+    cudaStream_t s_bulk = nullptr, cap_b = nullptr;
+    cudaEvent_t e_near = nullptr, e_bulk = nullptr;
     float fwd_ms = 0.f, bwd_ms = 0.f;
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
     // CUDA graphs of one full K-step segment: the forward steps, and the
@@ -1001,6 +1080,10 @@ struct lbib_adjoint {
         if (cap) cudaStreamDestroy(cap);
         if (s2) cudaStreamDestroy(s2);
         if (s_rev) cudaStreamDestroy(s_rev);
+        if (s_bulk) cudaStreamDestroy(s_bulk);
+        if (cap_b) cudaStreamDestroy(cap_b);
+        if (e_near) cudaEventDestroy(e_near);
+        if (e_bulk) cudaEventDestroy(e_bulk);
         if (e_fork) cudaEventDestroy(e_fork);
         if (e_join) cudaEventDestroy(e_join);
         for (cudaEvent_t e : ev)
@@ -1035,7 +1118,8 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, int set) {
                                                          a->at<double>(P.o_drv), r, a->tbase(set), k, R, ext);
         // FP64-latency-bound: small blocks spread the triangles over every SM
         k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
-        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F);
+        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F,
+                                                      (int *)(sl + P.s_rows), a->tbase(set), k);
         a->launches += 3;
     }
     if (sizeof(T) == 4 && P.d.nx % 2 == 0) {
@@ -1056,8 +1140,25 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, int set) {
     return cudaGetLastError();
 }
 
+// the two-cell row kernel exists for FP32 only
+template <typename T, bool NEAR>
+void rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1, double g2,
+               const T *pops, const T *F, const T *lam_next, T *lam_u, T *lam_cur, T *lam_F, const int *rows,
+               const long long *tb, int k) {
+    if constexpr (sizeof(T) == 4)
+        k_adj_lb_rows<T, NEAR, true><<<nrow, tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, lam_next, lam_u, lam_cur,
+                                                          lam_F, rows, tb, k);
+}
+
+// One reverse step on two streams: st carries the node-level chain and the
+// fluid update of the rows under the step's stencils, sb the fluid update of
+// every other row, which needs no immersed-boundary quantity and runs beside
+// the chain.  The rows' update of step k waits for the other rows of step
+// k + 1 (e_bulk), and the other rows of step k for the stencil rows of step k
+// (e_near: then every value they pull of step k + 1 is final, and the buffer
+// they write was last read by step k + 1).
 template <typename T>
-cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st, int set) {
+cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st, cudaStream_t sb, int set) {
     const Plan &P = a->P;
     char *sl = a->slot(k, set);
     const double *r = (const double *)(sl + P.s_r), *fn = (const double *)(sl + P.s_fn),
@@ -1066,22 +1167,34 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     T *lam_u = a->at<T>(P.o_lu), *lam_F = a->at<T>(P.o_lF);
     double *lam_r = a->at<double>(P.o_lr), *lam_fn = a->at<double>(P.o_lfn);
     const int M = P.M;
+    const int *rows = (const int *)(sl + P.s_rows);
+    const unsigned nrow = (unsigned)(P.d.ny * P.d.nz);
+    const bool pair = sizeof(T) == 4 && P.d.nx % 2 == 0;
+    const unsigned tpb = (unsigned)std::min(128, std::max(32, (P.d.nx / (pair ? 2 : 1) + 31) / 32 * 32));
+    const T om = (T)(1.0 / a->p.tau), r0 = (T)a->p.rho0;
+    const double g0 = a->p.g[0], g1 = a->p.g[1], g2 = a->p.g[2];
+    cudaError_t e;
     if (M > 0) {
         k_adj_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, lam_r, lam_u);
         a->launches += 1;
-    }
-    if (sizeof(T) == 4 && P.d.nx % 2 == 0) {
-        const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
-        k_adj_lb2<<<nb, 128, 0, st>>>(P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                      (const float *)(sl + P.s_pops), (const float *)F, (const float *)lam_next,
-                                      (float *)lam_u, (float *)lam_cur, (float *)lam_F);
-    } else {
-        const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-        k_adj_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                         (const T *)(sl + P.s_pops), F, lam_next, lam_u, lam_cur, lam_F);
-    }
-    a->launches += 1;
-    if (M > 0) {
+        if ((e = cudaStreamWaitEvent(st, a->e_bulk, 0)) != cudaSuccess) return e;
+        if (pair)
+            rows_pair<T, true>(P, nrow, tpb, st, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F, lam_next, lam_u,
+                               lam_cur, lam_F, rows, a->tbase(set), k);
+        else
+            k_adj_lb_rows<T, true, false><<<nrow, tpb, 0, st>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
+                                                                 lam_next, lam_u, lam_cur, lam_F, rows, a->tbase(set), k);
+        a->launches += 1;
+        if ((e = cudaEventRecord(a->e_near, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sb, a->e_near, 0)) != cudaSuccess) return e;
+        if (pair)
+            rows_pair<T, false>(P, nrow, tpb, sb, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F, lam_next, lam_u,
+                                lam_cur, lam_F, rows, a->tbase(set), k);
+        else
+            k_adj_lb_rows<T, false, false><<<nrow, tpb, 0, sb>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
+                                                                  lam_next, lam_u, lam_cur, lam_F, rows, a->tbase(set), k);
+        a->launches += 1;
+        if ((e = cudaEventRecord(a->e_bulk, sb)) != cudaSuccess) return e;
         k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
         k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
                                                          a->at<double>(P.o_drv), R, lam_fn, a->tbase(set), k,
@@ -1091,8 +1204,30 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
         k_adj_node<<<(M + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, a->at<double>(P.o_tria),
                                                                                a->at<double>(P.o_lR), lam_r);
         a->launches += 4;
+        return cudaGetLastError();
     }
+    // no nodes: the whole box in one launch
+    if (pair) {
+        const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
+        k_adj_lb2<<<nb, 128, 0, st>>>(P.d, (float)om, (float)r0, g0, g1, g2, (const float *)(sl + P.s_pops),
+                                      (const float *)F, (const float *)lam_next, (float *)lam_u, (float *)lam_cur,
+                                      (float *)lam_F);
+    } else {
+        const unsigned nb = (unsigned)((P.d.N + 255) / 256);
+        k_adj_lb<T><<<nb, 256, 0, st>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F, lam_next, lam_u,
+                                         lam_cur, lam_F);
+    }
+    a->launches += 1;
     return cudaGetLastError();
+}
+
+// Start a run of reverse steps on stream st with the second stream sb: sb
+// follows st, and the first step's stencil rows need not wait for sb.
+cudaError_t rev_fork(lbib_adjoint *a, cudaStream_t st, cudaStream_t sb) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(a->e_near, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(sb, a->e_near, 0)) != cudaSuccess) return e;
+    return cudaEventRecord(a->e_bulk, st);
 }
 
 // capture the K forward steps of a full segment (slots 0 -> K of a slot set),
@@ -1105,15 +1240,17 @@ cudaError_t capture(lbib_adjoint *a, bool reverse, int par, int set) {
     if (e != cudaSuccess) return e;
     T *lam[2] = {a->at<T>(P.o_lf0), a->at<T>(P.o_lf1)};
     int nxt = par;
+    if (reverse) e = rev_fork(a, a->cap, a->cap_b);
     for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
         if (reverse) {
             const int kk = P.K - 1 - k;
-            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, set);
+            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, a->cap_b, set);
             nxt = 1 - nxt;
         } else {
             e = fwd_step<T>(a, k, a->cap, set);
         }
     }
+    if (reverse && e == cudaSuccess) e = cudaStreamWaitEvent(a->cap, a->e_bulk, 0);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(a->cap, &g);
     if (e == cudaSuccess) e = e2;
@@ -1301,10 +1438,12 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
             a->launches += a->n_rev[nxt];
             if (P.K & 1) nxt = 1 - nxt;
         } else {
+            CU(rev_fork(a, rs, a->s_bulk));
             for (int k = len - 1; k >= 0; --k) {
-                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], rs, cur));
+                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], rs, a->s_bulk, cur));
                 nxt = 1 - nxt;
             }
+            CU(cudaStreamWaitEvent(rs, a->e_bulk, 0));
         }
         CU(cudaEventRecord(a->e_free[cur], rs));
         cur = oth;
@@ -1447,6 +1586,10 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
         CUA(cudaStreamCreateWithPriority(&a->s_rev, cudaStreamNonBlocking, hi));
     }
     CUA(cudaEventCreateWithFlags(&a->e_fork, cudaEventDisableTiming));
+    CUA(cudaStreamCreateWithFlags(&a->s_bulk, cudaStreamNonBlocking));
+    CUA(cudaStreamCreateWithFlags(&a->cap_b, cudaStreamNonBlocking));
+    CUA(cudaEventCreateWithFlags(&a->e_near, cudaEventDisableTiming));
+    CUA(cudaEventCreateWithFlags(&a->e_bulk, cudaEventDisableTiming));
     CUA(cudaEventCreateWithFlags(&a->e_join, cudaEventDisableTiming));
     std::vector<long long> tb(P.n_seg);
     for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
