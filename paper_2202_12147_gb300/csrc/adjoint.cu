@@ -497,6 +497,66 @@ __global__ void __launch_bounds__(128, 4) k_fwd_lb2(Dims d, float omega, float r
 }
 
 // one warp per node: r_j^{k+1} = r_j^k + sum_x u(x) Delta(x - r_j)
+// The forward record update by rows (y, z), as the reverse one: NEAR launches
+// update the rows under the step's node stencils (tagged by the spreading of
+// this step), reading F and writing the velocity the interpolation needs; the
+// others update the rest of the box, where F is the uniform body force and
+// the velocity is not needed.  Both push into the next slot and clear its
+// force field.
+template <typename T, bool NEAR, bool PAIR>
+__global__ void __launch_bounds__(128) k_fwd_lb_rows(Dims d, T omega, T rho0, double gx, double gy, double gz,
+                                                     const T *pops, const T *F, T *out, T *u_out, T *F_next,
+                                                     const int *rowtag, const long long *tb, int k) {
+    const int row = blockIdx.x;
+    const bool near = rowtag[row] == (int)(*tb + k + 1);
+    if (near != NEAR) return;
+    const int y = row % d.ny, z = row / d.ny;
+    constexpr int CPT = PAIR ? 2 : 1;
+    for (int x = CPT * threadIdx.x; x < d.nx; x += CPT * blockDim.x) {
+        const int cell = x + d.nx * row;
+        T dv[CPT][Q], p[CPT][Q], u[CPT][3];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if constexpr (PAIR) {
+                const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
+                dv[0][i] = v.x;
+                dv[1][i] = v.y;
+            } else {
+                dv[0][i] = pops[i * d.Npad + cell];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            T Fv[3] = {(T)gx, (T)gy, (T)gz};
+            if constexpr (NEAR)
+                for (int a = 0; a < 3; ++a) Fv[a] += F[a * d.Npad + cell + c];
+            fwd_cell(dv[c], Fv[0], Fv[1], Fv[2], omega, rho0, p[c], u[c]);
+        }
+        const Nbr n0(d, x, y, z);
+        if constexpr (PAIR) {
+            const Nbr n1(d, x + 1, y, z);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                float *pl = out + i * d.Npad;
+                if (cx(i) == 0) {
+                    *reinterpret_cast<float2 *>(pl + cell + n0.off(i)) = make_float2(p[0][i], p[1][i]);
+                } else {
+                    pl[cell + n0.off(i)] = p[0][i];
+                    pl[cell + 1 + n1.off(i)] = p[1][i];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[i * d.Npad + cell + n0.off(i)] = p[0][i];
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < CPT; ++c) {
+                if constexpr (NEAR) u_out[a * d.Npad + cell + c] = u[c][a];
+                F_next[a * d.Npad + cell + c] = (T)0;
+            }
+    }
+}
+
 template <typename T>
 __global__ void k_fwd_interp(Dims d, int M, const double *r, const T *u, double *r_next, int *err) {
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
@@ -1062,6 +1122,10 @@ struct lbib_adjoint {
     // node chain: its stream, its capture stream and the step-to-step events
     cudaStream_t s_bulk = nullptr, cap_b = nullptr;
     cudaEvent_t e_near = nullptr, e_bulk = nullptr;
+    // the same split of the recorded forward steps: the rows away from the
+    // stencils of the forward sweep (beside a->s) and of the recompute (beside s2)
+    cudaStream_t s_fb = nullptr, s2b = nullptr;
+    cudaEvent_t e_nearf = nullptr, e_bulkf = nullptr;
     float fwd_ms = 0.f, bwd_ms = 0.f;
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
     // CUDA graphs of one full K-step segment: the forward steps, and the
@@ -1084,6 +1148,10 @@ struct lbib_adjoint {
         if (cap_b) cudaStreamDestroy(cap_b);
         if (e_near) cudaEventDestroy(e_near);
         if (e_bulk) cudaEventDestroy(e_bulk);
+        if (s_fb) cudaStreamDestroy(s_fb);
+        if (s2b) cudaStreamDestroy(s2b);
+        if (e_nearf) cudaEventDestroy(e_nearf);
+        if (e_bulkf) cudaEventDestroy(e_bulkf);
         if (e_fork) cudaEventDestroy(e_fork);
         if (e_join) cudaEventDestroy(e_join);
         for (cudaEvent_t e : ev)
@@ -1105,42 +1173,16 @@ namespace {
 // One recorded forward step.  (The swimmer and membrane kernels are
 // independent, but running them on two graph branches measured slower than
 // one chain: 75 against 61 us per step on the 96^3 workload.)
-template <typename T>
-cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, int set) {
-    const Plan &P = a->P;
-    char *sl = a->slot(k, set), *sn = a->slot(k + 1, set);
-    const double *r = (const double *)(sl + P.s_r);
-    double *fn = (double *)(sl + P.s_fn), *R = (double *)(sl + P.s_R), *ext = (double *)(sl + P.s_ext);
-    T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
-    const int M = P.M;
-    if (M > 0) {
-        k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
-                                                         a->at<double>(P.o_drv), r, a->tbase(set), k, R, ext);
-        // FP64-latency-bound: small blocks spread the triangles over every SM
-        k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
-        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F,
-                                                      (int *)(sl + P.s_rows), a->tbase(set), k);
-        a->launches += 3;
-    }
-    if (sizeof(T) == 4 && P.d.nx % 2 == 0) {
-        const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
-        k_fwd_lb2<<<nb, 128, 0, st>>>(P.d, (float)(1.0 / a->p.tau), (float)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                      (const float *)(sl + P.s_pops), (const float *)F, (float *)(sn + P.s_pops),
-                                      (float *)u, (float *)(sn + P.s_F));
-    } else {
-        const unsigned nb = (unsigned)((P.d.N + 255) / 256);
-        k_fwd_lb<T><<<nb, 256, 0, st>>>(P.d, (T)(1.0 / a->p.tau), (T)a->p.rho0, a->p.g[0], a->p.g[1], a->p.g[2],
-                                         (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F));
-    }
-    a->launches += 1;
-    if (M > 0) {
-        k_fwd_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
-        a->launches += 1;
-    }
-    return cudaGetLastError();
+// the two-cell row kernels exist for FP32 only
+template <typename T, bool NEAR>
+void fwd_rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1,
+                   double g2, const T *pops, const T *F, T *out, T *u, T *F_next, const int *rows, const long long *tb,
+                   int k) {
+    if constexpr (sizeof(T) == 4)
+        k_fwd_lb_rows<T, NEAR, true><<<nrow, tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, out, u, F_next, rows, tb,
+                                                          k);
 }
 
-// the two-cell row kernel exists for FP32 only
 template <typename T, bool NEAR>
 void rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1, double g2,
                const T *pops, const T *F, const T *lam_next, T *lam_u, T *lam_cur, T *lam_F, const int *rows,
@@ -1148,6 +1190,71 @@ void rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om,
     if constexpr (sizeof(T) == 4)
         k_adj_lb_rows<T, NEAR, true><<<nrow, tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, lam_next, lam_u, lam_cur,
                                                           lam_F, rows, tb, k);
+}
+
+// One recorded forward step on two streams: st carries the node-level chain
+// and the fluid update of the rows under the stencils (which the
+// interpolation reads), sb the fluid update of every other row, beside the
+// chain.  The spreading of step k waits for the other rows of step k - 1
+// (they clear the force field it adds into, and push populations step k
+// reads), and the other rows of step k wait for the spreading of step k
+// (their row tags; the stencil rows of step k - 1 come before it on st).
+template <typename T>
+cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t sb, int set) {
+    const Plan &P = a->P;
+    char *sl = a->slot(k, set), *sn = a->slot(k + 1, set);
+    const double *r = (const double *)(sl + P.s_r);
+    double *fn = (double *)(sl + P.s_fn), *R = (double *)(sl + P.s_R), *ext = (double *)(sl + P.s_ext);
+    T *F = (T *)(sl + P.s_F), *u = (T *)(sl + P.s_u);
+    const int M = P.M;
+    const T om = (T)(1.0 / a->p.tau), r0 = (T)a->p.rho0;
+    const double g0 = a->p.g[0], g1 = a->p.g[1], g2 = a->p.g[2];
+    const bool pair = sizeof(T) == 4 && P.d.nx % 2 == 0;
+    cudaError_t e;
+    if (M > 0) {
+        const int *rows = (const int *)(sl + P.s_rows);
+        const unsigned nrow = (unsigned)(P.d.ny * P.d.nz);
+        const unsigned tpb = (unsigned)std::min(128, std::max(32, (P.d.nx / (pair ? 2 : 1) + 31) / 32 * 32));
+        k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
+                                                         a->at<double>(P.o_drv), r, a->tbase(set), k, R, ext);
+        // FP64-latency-bound: small blocks spread the triangles over every SM
+        k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
+        if ((e = cudaStreamWaitEvent(st, a->e_bulkf, 0)) != cudaSuccess) return e;
+        k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F,
+                                                      (int *)(sl + P.s_rows), a->tbase(set), k);
+        a->launches += 3;
+        if ((e = cudaEventRecord(a->e_nearf, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sb, a->e_nearf, 0)) != cudaSuccess) return e;
+        if (pair)
+            fwd_rows_pair<T, false>(P, nrow, tpb, sb, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
+                                    (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows, a->tbase(set), k);
+        else
+            k_fwd_lb_rows<T, false, false><<<nrow, tpb, 0, sb>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
+                                                                  (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows,
+                                                                  a->tbase(set), k);
+        if ((e = cudaEventRecord(a->e_bulkf, sb)) != cudaSuccess) return e;
+        if (pair)
+            fwd_rows_pair<T, true>(P, nrow, tpb, st, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
+                                   (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows, a->tbase(set), k);
+        else
+            k_fwd_lb_rows<T, true, false><<<nrow, tpb, 0, st>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
+                                                                 (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows,
+                                                                 a->tbase(set), k);
+        k_fwd_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
+        a->launches += 3;
+        return cudaGetLastError();
+    }
+    if (pair) {
+        const unsigned nb = (unsigned)((P.d.N / 2 + 127) / 128);
+        k_fwd_lb2<<<nb, 128, 0, st>>>(P.d, (float)om, (float)r0, g0, g1, g2, (const float *)(sl + P.s_pops),
+                                      (const float *)F, (float *)(sn + P.s_pops), (float *)u, (float *)(sn + P.s_F));
+    } else {
+        const unsigned nb = (unsigned)((P.d.N + 255) / 256);
+        k_fwd_lb<T><<<nb, 256, 0, st>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F, (T *)(sn + P.s_pops),
+                                         u, (T *)(sn + P.s_F));
+    }
+    a->launches += 1;
+    return cudaGetLastError();
 }
 
 // One reverse step on two streams: st carries the node-level chain and the
@@ -1221,6 +1328,16 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     return cudaGetLastError();
 }
 
+// Start a run of recorded forward steps on stream st with the second stream
+// sb: sb follows st through each step's spreading, and the first step's
+// spreading need not wait for sb.
+cudaError_t fwd_fork(lbib_adjoint *a, cudaStream_t st, cudaStream_t sb) {
+    cudaError_t e;
+    if ((e = cudaEventRecord(a->e_nearf, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(sb, a->e_nearf, 0)) != cudaSuccess) return e;
+    return cudaEventRecord(a->e_bulkf, st);
+}
+
 // Start a run of reverse steps on stream st with the second stream sb: sb
 // follows st, and the first step's stencil rows need not wait for sb.
 cudaError_t rev_fork(lbib_adjoint *a, cudaStream_t st, cudaStream_t sb) {
@@ -1240,17 +1357,17 @@ cudaError_t capture(lbib_adjoint *a, bool reverse, int par, int set) {
     if (e != cudaSuccess) return e;
     T *lam[2] = {a->at<T>(P.o_lf0), a->at<T>(P.o_lf1)};
     int nxt = par;
-    if (reverse) e = rev_fork(a, a->cap, a->cap_b);
+    e = reverse ? rev_fork(a, a->cap, a->cap_b) : fwd_fork(a, a->cap, a->cap_b);
     for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
         if (reverse) {
             const int kk = P.K - 1 - k;
             e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, a->cap_b, set);
             nxt = 1 - nxt;
         } else {
-            e = fwd_step<T>(a, k, a->cap, set);
+            e = fwd_step<T>(a, k, a->cap, a->cap_b, set);
         }
     }
-    if (reverse && e == cudaSuccess) e = cudaStreamWaitEvent(a->cap, a->e_bulk, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(a->cap, reverse ? a->e_bulk : a->e_bulkf, 0);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(a->cap, &g);
     if (e == cudaSuccess) e = e2;
@@ -1268,7 +1385,7 @@ cudaError_t set_tbase(lbib_adjoint *a, int g, int set, cudaStream_t st) {
 
 // run segment g forward from its checkpoint, filling slots 0..len of a set
 template <typename T>
-cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st) {
+cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st, cudaStream_t sb) {
     const Plan &P = a->P;
     char *s0 = a->slot(0, set), *c = a->ck(g);
     cudaError_t e;
@@ -1286,8 +1403,10 @@ cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st) {
         if ((e = cudaGraphLaunch(a->g_fwd[set], st)) != cudaSuccess) return e;
         a->launches += a->n_fwd;
     } else {
+        if ((e = fwd_fork(a, st, sb)) != cudaSuccess) return e;
         for (int k = 0; k < len; ++k)
-            if ((e = fwd_step<T>(a, k, st, set)) != cudaSuccess) return e;
+            if ((e = fwd_step<T>(a, k, st, sb, set)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, a->e_bulkf, 0)) != cudaSuccess) return e;
     }
     a->slots_seg[set] = g;
     return cudaSuccess;
@@ -1319,7 +1438,7 @@ int forward_impl(lbib_adjoint *a, double *disp) {
     }
     a->slots_seg[1] = -1;
     for (int g = 0; g < P.n_seg; ++g) {
-        CU(run_segment<T>(a, g, 0, a->s));
+        CU(run_segment<T>(a, g, 0, a->s, a->s_fb));
         CU(save_ck(a, a->seg_len(g), g + 1));  // the next checkpoint (the last one: the final state)
     }
     if (P.S > 0) {
@@ -1410,7 +1529,7 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
     int cur = a->slots_seg[0] == P.n_seg - 1 ? 0 : (a->slots_seg[1] == P.n_seg - 1 ? 1 : -1);
     if (cur < 0) {
         cur = 0;
-        CU(run_segment<T>(a, P.n_seg - 1, 0, a->s));
+        CU(run_segment<T>(a, P.n_seg - 1, 0, a->s, a->s_fb));
     }
     cudaStream_t rs = a->s_rev;
     CU(cudaEventRecord(a->e_fork, a->s));
@@ -1422,7 +1541,7 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
         const int oth = 1 - cur;
         if (g > 0) {
             CU(cudaStreamWaitEvent(a->s2, a->e_free[oth], 0));
-            CU(run_segment<T>(a, g - 1, oth, a->s2));
+            CU(run_segment<T>(a, g - 1, oth, a->s2, a->s2b));
             CU(cudaEventRecord(a->e_ready[oth], a->s2));
             ready_on_s2[oth] = true;
         }
@@ -1590,6 +1709,10 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     CUA(cudaStreamCreateWithFlags(&a->cap_b, cudaStreamNonBlocking));
     CUA(cudaEventCreateWithFlags(&a->e_near, cudaEventDisableTiming));
     CUA(cudaEventCreateWithFlags(&a->e_bulk, cudaEventDisableTiming));
+    CUA(cudaStreamCreateWithFlags(&a->s_fb, cudaStreamNonBlocking));
+    CUA(cudaStreamCreateWithFlags(&a->s2b, cudaStreamNonBlocking));
+    CUA(cudaEventCreateWithFlags(&a->e_nearf, cudaEventDisableTiming));
+    CUA(cudaEventCreateWithFlags(&a->e_bulkf, cudaEventDisableTiming));
     CUA(cudaEventCreateWithFlags(&a->e_join, cudaEventDisableTiming));
     std::vector<long long> tb(P.n_seg);
     for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
