@@ -209,6 +209,32 @@ def test_deterministic_spread_is_bitwise_reproducible(perm):
     sim.close()
 
 
+def test_deterministic_spread_with_scattered_nodes(perm):
+    """Nodes scattered at random over a 48^3 box: the 32 nodes a spreading
+    block holds touch up to 2048 distinct cells, more than its shared table
+    of 1024, so contributions also take the direct path to the global
+    fixed-point field.  The field is still bitwise reproducible, and equal to
+    the float-atomic field and to the oracle's spreading of the same node
+    forces to FP32 rounding."""
+    from workloads import single_swimmer_48
+    box = single_swimmer_48()
+    asm = assemble(box)
+    rng = np.random.default_rng(8)
+    r = rng.uniform(0.0, 48.0, size=asm["nodes"].shape)
+    outs = []
+    for det in (True, True, False):
+        sim = gpu_sim(box, asm, deterministic=det)
+        sim.set_nodes(r)
+        sim.ib_spread()
+        outs.append((sim.get_force_field().astype(np.float64), sim.get_node_forces().astype(np.float64)))
+        sim.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    scale = np.abs(outs[0][0]).max()
+    assert np.abs(outs[0][0] - outs[2][0]).max() < 1e-6 * scale
+    Fo = oracle.spread(r, outs[0][1], box.dims)
+    assert np.abs(outs[0][0] - Fo).max() < 1e-6 * np.abs(Fo).max()
+
+
 @pytest.mark.parametrize("deterministic", [False, True])
 def test_coupled_single_swimmer_48(perm, deterministic):
     """The 48^3 single-swimmer workload (beads of radius 4 at subdivision 2,
