@@ -694,10 +694,9 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
     d.tile_x = L.tile_x;
     d.tiles_x = L.tiles_x;
     // adjacent cells per fluid thread: four for 16-bit storage, two for FP32,
-    // when the rows split into tiles of that many cells (LBIB_CELLS_PER_THREAD caps it)
+    // when the rows split into tiles of that many cells
     {
         int cpt = p->storage == LBIB_F32 ? 2 : 4;
-        cpt = std::min(cpt, env_int("LBIB_CELLS_PER_THREAD", 4));
         while (cpt > 1 && (L.tile_x % cpt || p->nx % cpt)) cpt /= 2;
         d.cells_per_thread = cpt < 1 ? 1 : (cpt == 3 ? 2 : cpt);
     }
@@ -800,7 +799,7 @@ int lb_init(const lb_params *p, const lbib_structure *s, const lbib_buffers *b, 
         int cnt = 0;
         if (cudaMemcpy(&cnt, d.tile_count, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return bail(fail(LBIB_ECUDA, "reading the marked-tile count failed"));
-        d.marked_grid = env_int("LBIB_MARKED_GRID", std::min(L.n_tiles, std::max(32, cnt + cnt / 4 + 16)));
+        d.marked_grid = std::min(L.n_tiles, std::max(32, cnt + cnt / 4 + 16));
     }
 
     // streams and events of the two-stream step; the IB stream gets the

@@ -462,9 +462,6 @@ __device__ __forceinline__ unsigned pack2_raw(float2 v) {
 // value.  (Passing the edge values between neighbouring lanes with shuffles
 // instead measured slower: odd steps 76 against 67 us FP16, 109 against 96 us
 // FP32, on a 256 x 128 x 128 box.)  The collision runs as two packed pairs.
-#ifndef LBIB_Q_ODD_STORE8
-#define LBIB_Q_ODD_STORE8 0
-#endif
 template <int ST, bool ODD, int FORCING, bool DET, bool MARKED>
 __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y, unsigned z) {
     using T = unsigned short;
@@ -540,12 +537,7 @@ __device__ __forceinline__ bool lb_quad(const DevCtx &c, unsigned x0, unsigned y
                 const unsigned row = (dy < 0 ? rm : dy > 0 ? rp : r0) + (dz < 0 ? sm : dz > 0 ? sp : s0);
                 T *pl = P + i * Np + row;
                 if (cx(i) == 0) {
-#if LBIB_Q_ODD_STORE8
-                    if (h == 0) keep[i] = e;
-                    else *reinterpret_cast<uint2 *>(pl + x0) = make_uint2(keep[i], e);
-#else
                     *reinterpret_cast<unsigned *>(pl + x0 + 2 * h) = e;
-#endif
                 } else if (h == 0) {
                     keep[i] = e;
                 } else {
@@ -575,22 +567,14 @@ __device__ __forceinline__ void report_bad(const DevCtx &c, bool bad) {
 }
 
 // Every unmarked tile: one block per tile, grid (tiles_x, ny, nz).
-#ifndef LBIB_LB_GENERIC_MINB
 #define LBIB_LB_GENERIC_MINB 3
-#endif
 // CPT = cells per thread: 1, or 2 (adjacent pairs, packed arithmetic; even tile_x).
 // Register budget: one cell per thread, 3 blocks of 256 threads per SM; two
 // cells per thread, 4 blocks of 128 threads (1024 cells in flight per SM);
 // four cells per thread (16-bit storage), 8 blocks of 64 threads.
-#ifndef LBIB_LB_QUAD_MINB
 #define LBIB_LB_QUAD_MINB 8
-#endif
-#ifndef LBIB_LB_PAIR16_MINB
 #define LBIB_LB_PAIR16_MINB 4
-#endif
-#ifndef LBIB_LB_PAIR32_MINB
 #define LBIB_LB_PAIR32_MINB 4
-#endif
 #define LBIB_LB_BOUNDS(CPT) \
     __launch_bounds__((CPT) == 4 ? LB_TPB / 4 : ((CPT) == 2 ? LB_TPB / 2 : LB_TPB), (CPT) == 1 ? LBIB_LB_GENERIC_MINB : ((CPT) == 2 ? 4 : LBIB_LB_QUAD_MINB))
 // the same with the storage format: 16-bit two-cell threads need fewer registers
@@ -619,14 +603,9 @@ __device__ __forceinline__ void lb_main_body(const DevCtx &c, unsigned tile, uns
 // dependency), then allows the next launch to be scheduled, so that its
 // blocks take the SM slots the last wave of this grid frees instead of
 // waiting for a full launch after it.
-#ifndef LBIB_MAIN_PDL
-#define LBIB_MAIN_PDL 1
-#endif
 __device__ __forceinline__ void pdl_wait_and_release() {
-#if LBIB_MAIN_PDL
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-#endif
 }
 
 template <int ST, bool ODD, int FORCING, int CPT>
@@ -778,7 +757,7 @@ static void main_dispatch_cpt(const DevCtx &c, bool odd, cudaStream_t s) {
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     // 16-bit storage only: measured on six 256x128x128 two-swimmer boxes,
     // FP16 59.7k -> 61.2k MLUPS with it, FP32 39.8k -> 39.6k
-    at[0].val.programmaticStreamSerializationAllowed = ST != LBIB_F32 ? LBIB_MAIN_PDL : 0;
+    at[0].val.programmaticStreamSerializationAllowed = ST != LBIB_F32 ? 1 : 0;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if (odd) cudaLaunchKernelEx(&cfg, k_lb_main<ST, true, FORCING, CPT>, c);
