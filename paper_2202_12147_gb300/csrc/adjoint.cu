@@ -57,11 +57,13 @@ struct Mesh {
     const int *tris;        // T x 3 node ids
     const double *G;        // T x 3 rest metric G00, G01, G11
     const double *A0Gs;     // T: rest area x shear modulus
+    const double *iG;       // T: 1 / det G
     const int *csr_ptr;     // M + 1
     const int *csr_ent;     // 3T entries 3 t + q
     const int *node_bead;   // M
     const int *bead_start;  // B
     const int *bead_count;  // B
+    const double *bead_inv; // B: 1 / node count
     const int *bead_swim;   // B
 };
 
@@ -173,12 +175,15 @@ __device__ __forceinline__ void bead_sum3(double v[3], double (*sh)[3], double *
 //   dW/dd = s d M,  s = A0 Gs / (det G J^4),
 //   M = (J^4 - 1) adj G - 2 adj E,  adj [[a, b], [b, c]] = [[c, -b], [-b, a]],
 // and the corner forces are f1 = -P[:,0], f2 = -P[:,1], f0 = P[:,0] + P[:,1].
+// FP64 runs at 1/64 of the FP32 rate here and one warp per SM carries these
+// kernels, so every FP64 divide is a long serial sequence: 1 / det G comes
+// precomputed per triangle and 1 / J^4 is formed once.
 struct TriState {
     double d1[3], d2[3];
-    double E00, E01, E11, detG, I2, J2, J4, s, M00, M01, M11;
+    double E00, E01, E11, iG, I2, J2, iJ4, s, M00, M01, M11;
 };
 
-__device__ __forceinline__ void tri_state(const double *G, double A0Gs, const double *x0, const double *x1,
+__device__ __forceinline__ void tri_state(const double *G, double iG, double A0Gs, const double *x0, const double *x1,
                                           const double *x2, TriState &S) {
     for (int a = 0; a < 3; ++a) {
         S.d1[a] = x1[a] - x0[a];
@@ -190,13 +195,13 @@ __device__ __forceinline__ void tri_state(const double *G, double A0Gs, const do
     S.E00 = 0.5 * (g00 - G[0]);
     S.E01 = 0.5 * (g01 - G[1]);
     S.E11 = 0.5 * (g11 - G[2]);
-    S.detG = G[0] * G[2] - G[1] * G[1];
-    const double trGiE = (G[2] * S.E00 - 2.0 * G[1] * S.E01 + G[0] * S.E11) / S.detG;
+    S.iG = iG;
+    const double trGiE = (G[2] * S.E00 - 2.0 * G[1] * S.E01 + G[0] * S.E11) * iG;
     const double detE = S.E00 * S.E11 - S.E01 * S.E01;
-    S.I2 = 2.0 * trGiE + 4.0 * detE / S.detG;
+    S.I2 = 2.0 * trGiE + 4.0 * detE * iG;
     S.J2 = 1.0 + S.I2;
-    S.J4 = S.J2 * S.J2;
-    S.s = A0Gs / (S.detG * S.J4);
+    S.iJ4 = 1.0 / (S.J2 * S.J2);
+    S.s = A0Gs * iG * S.iJ4;
     const double c = S.I2 * (S.I2 + 2.0);  // J^4 - 1
     S.M00 = c * G[2] - 2.0 * S.E11;
     S.M01 = -c * G[1] + 2.0 * S.E01;
@@ -217,11 +222,11 @@ __device__ __forceinline__ void tri_force_jvp(const double *G, const TriState &S
     const double dE11 = S.d2[0] * e2[0] + S.d2[1] * e2[1] + S.d2[2] * e2[2];
     const double dE01 = 0.5 * (S.d1[0] * e2[0] + S.d1[1] * e2[1] + S.d1[2] * e2[2] + e1[0] * S.d2[0] +
                                e1[1] * S.d2[1] + e1[2] * S.d2[2]);
-    const double dtr = (G[2] * dE00 - 2.0 * G[1] * dE01 + G[0] * dE11) / S.detG;
+    const double dtr = (G[2] * dE00 - 2.0 * G[1] * dE01 + G[0] * dE11) * S.iG;
     const double ddetE = dE00 * S.E11 + S.E00 * dE11 - 2.0 * S.E01 * dE01;
-    const double dI2 = 2.0 * dtr + 4.0 * ddetE / S.detG;
+    const double dI2 = 2.0 * dtr + 4.0 * ddetE * S.iG;
     const double dJ4 = 2.0 * S.J2 * dI2;
-    const double ds = -S.s * dJ4 / S.J4;
+    const double ds = -S.s * dJ4 * S.iJ4;
     const double dM00 = dJ4 * G[2] - 2.0 * dE11;
     const double dM01 = -dJ4 * G[1] + 2.0 * dE01;
     const double dM11 = dJ4 * G[0] - 2.0 * dE00;
@@ -273,7 +278,7 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
             for (int a = 0; a < 3; ++a) acc[a] += r[3 * j + a];
         bead_sum3(acc, sh, Rq);
         if (threadIdx.x < 3) {
-            Rq[threadIdx.x] /= nn;
+            Rq[threadIdx.x] *= m.bead_inv[b];
             R[3 * b + threadIdx.x] = Rq[threadIdx.x];
         }
     }
@@ -298,8 +303,8 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
             dd[a] = Rs[qs][a] - Rs[1][a];
             n2 += dd[a] * dd[a];
         }
-        const double n = sqrt(n2);
-        for (int a = 0; a < 3; ++a) fq[a] = -w.k * (n - w.L) * dd[a] / n;
+        const double n = sqrt(n2), h = -w.k * (n - w.L) / n;
+        for (int a = 0; a < 3; ++a) fq[a] = h * dd[a];
         double fs[3][3];
         for (int a = 0; a < 3; ++a) {
             fs[0][a] = __shfl_sync(0xffffffffu, fq[a], 0);
@@ -320,7 +325,7 @@ __global__ void k_fwd_tri(Mesh m, const double *r, double *tri_f) {
     if (t >= m.T) return;
     const int *v = m.tris + 3 * t;
     TriState S;
-    tri_state(m.G + 3 * t, m.A0Gs[t], r + 3 * v[0], r + 3 * v[1], r + 3 * v[2], S);
+    tri_state(m.G + 3 * t, m.iG[t], m.A0Gs[t], r + 3 * v[0], r + 3 * v[1], r + 3 * v[2], S);
     for (int a = 0; a < 3; ++a) {
         const double P0 = S.s * (S.d1[a] * S.M00 + S.d2[a] * S.M01);
         const double P1 = S.s * (S.d1[a] * S.M01 + S.d2[a] * S.M11);
@@ -344,7 +349,7 @@ __global__ void k_fwd_spread(Dims d, Mesh m, const double *r, const double *tri_
         for (int a = 0; a < 3; ++a) f[a] += tri_f[3 * k + a];
     }
     const int b = m.node_bead[j];
-    const double inv = 1.0 / m.bead_count[b];
+    const double inv = m.bead_inv[b];
     for (int a = 0; a < 3; ++a) f[a] = warp_sum(f[a]) + ext[3 * b + a] * inv;
     if (lane == 0)
         for (int a = 0; a < 3; ++a) fn[3 * j + a] = f[a];
@@ -882,7 +887,7 @@ __global__ void k_adj_tri(Mesh m, const double *r, const double *lam_fn, double 
     if (t >= m.T) return;
     const int *v = m.tris + 3 * t;
     TriState S;
-    tri_state(m.G + 3 * t, m.A0Gs[t], r + 3 * v[0], r + 3 * v[1], r + 3 * v[2], S);
+    tri_state(m.G + 3 * t, m.iG[t], m.A0Gs[t], r + 3 * v[0], r + 3 * v[1], r + 3 * v[2], S);
     double df[3][3];
     tri_force_jvp(m.G + 3 * t, S, lam_fn + 3 * v[0], lam_fn + 3 * v[1], lam_fn + 3 * v[2], df);
     for (int q = 0; q < 3; ++q)
@@ -920,7 +925,7 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
             for (int a = 0; a < 3; ++a) le[qq][a] = p[a];
         }
         for (int qq = 0; qq < 3; ++qq)
-            for (int a = 0; a < 3; ++a) le[qq][a] /= m.bead_count[w.bead[qq]];
+            for (int a = 0; a < 3; ++a) le[qq][a] *= m.bead_inv[w.bead[qq]];
         // drive: f_q = A_q sin(om t + phi_q) along x (balance: f_1 = -f_0 - f_2)
         const double *th = theta + 6 * s;
         const double *dv = drv + ((*t_base + k) * (long long)(gridDim.x / 3) + s) * 6;
@@ -945,7 +950,7 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(BEAD_THREADS)
             n2 += dd[a] * dd[a];
             lv[a] = le[qs][a] - le[1][a];
         }
-        const double n = sqrt(n2), c1 = 1.0 - w.L / n, c2 = w.L / (n * n2);
+        const double n = sqrt(n2), in = 1.0 / n, c1 = 1.0 - w.L * in, c2 = w.L * in * in * in;
         const double dl = dd[0] * lv[0] + dd[1] * lv[1] + dd[2] * lv[2];
         for (int a = 0; a < 3; ++a) ld[a] = -w.k * (c1 * lv[a] + c2 * dd[a] * dl);
         for (int a = 0; a < 3; ++a) {
@@ -970,7 +975,7 @@ __global__ void k_adj_node(Mesh m, const double *tri_adj, const double *lam_R, d
         for (int a = 0; a < 3; ++a) f[a] += tri_adj[3 * k + a];
     }
     const int b = m.node_bead[j];
-    const double inv = 1.0 / m.bead_count[b];
+    const double inv = m.bead_inv[b];
     for (int a = 0; a < 3; ++a) lam_r[3 * j + a] += f[a] + lam_R[3 * b + a] * inv;
 }
 
@@ -1000,7 +1005,7 @@ struct Plan {
     size_t c_pops, c_r, ck_bytes;
     // workspace offsets
     size_t o_drv = 0;  // drive table: per step and swimmer sin and cos of (omega t + phi_q), q = 0..2
-    size_t o_tris, o_G, o_A0, o_cptr, o_cent, o_nb, o_bs, o_bc, o_bw, o_swim, o_theta, o_grad, o_disp, o_err,
+    size_t o_tris, o_G, o_A0, o_iG, o_bi, o_cptr, o_cent, o_nb, o_bs, o_bc, o_bw, o_swim, o_theta, o_grad, o_disp, o_err,
         o_seed, o_lf0, o_lf1, o_lu, o_lF, o_lr, o_lfn, o_trif, o_tria, o_lR, o_tb, o_tbt, o_ck, o_slots[2], total;
 };
 
@@ -1040,6 +1045,8 @@ Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, i
     P.o_tris = o; o += up(3 * Tn * 4);
     P.o_G = o; o += up(3 * Tn * 8);
     P.o_A0 = o; o += up(Tn * 8);
+    P.o_iG = o; o += up(Tn * 8);
+    P.o_bi = o; o += up(Bn * 8);
     P.o_cptr = o; o += up((Mn + 1) * 4);
     P.o_cent = o; o += up(3 * Tn * 4);
     P.o_nb = o; o += up(Mn * 4);
@@ -1126,6 +1133,11 @@ struct lbib_adjoint {
     // stencils of the forward sweep (beside a->s) and of the recompute (beside s2)
     cudaStream_t s_fb = nullptr, s2b = nullptr;
     cudaEvent_t e_nearf = nullptr, e_bulkf = nullptr;
+    // a third stream beside each chain stream (the forward sweep's, the
+    // recompute's, the reverse's, the capture's): the triangle kernel of a
+    // step runs on it beside the swimmer kernel, which it does not depend on
+    cudaStream_t s_t = nullptr, s2t = nullptr, s_revt = nullptr, cap_t = nullptr;
+    cudaEvent_t e_tf_fork = nullptr, e_tf_join = nullptr, e_tr_fork = nullptr, e_tr_join = nullptr;
     float fwd_ms = 0.f, bwd_ms = 0.f;
     long long fwd_launches = 0, bwd_launches = 0, launches = 0;
     // CUDA graphs of one full K-step segment: the forward steps, and the
@@ -1152,6 +1164,10 @@ struct lbib_adjoint {
         if (s2b) cudaStreamDestroy(s2b);
         if (e_nearf) cudaEventDestroy(e_nearf);
         if (e_bulkf) cudaEventDestroy(e_bulkf);
+        for (cudaStream_t x : {s_t, s2t, s_revt, cap_t})
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t x : {e_tf_fork, e_tf_join, e_tr_fork, e_tr_join})
+            if (x) cudaEventDestroy(x);
         if (e_fork) cudaEventDestroy(e_fork);
         if (e_join) cudaEventDestroy(e_join);
         for (cudaEvent_t e : ev)
@@ -1200,7 +1216,7 @@ void rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om,
 // reads), and the other rows of step k wait for the spreading of step k
 // (their row tags; the stencil rows of step k - 1 come before it on st).
 template <typename T>
-cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t sb, int set) {
+cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t sb, cudaStream_t sx, int set) {
     const Plan &P = a->P;
     char *sl = a->slot(k, set), *sn = a->slot(k + 1, set);
     const double *r = (const double *)(sl + P.s_r);
@@ -1215,10 +1231,16 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t sb, i
         const int *rows = (const int *)(sl + P.s_rows);
         const unsigned nrow = (unsigned)(P.d.ny * P.d.nz);
         const unsigned tpb = (unsigned)std::min(128, std::max(32, (P.d.nx / (pair ? 2 : 1) + 31) / 32 * 32));
+        // the triangles' corner forces (sx) beside the bead centres and
+        // swimmer forces (st): both read only this step's positions
+        if ((e = cudaEventRecord(a->e_tf_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sx, a->e_tf_fork, 0)) != cudaSuccess) return e;
+        // FP64-latency-bound: small blocks spread the triangles over every SM
+        k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, sx>>>(a->m, r, a->at<double>(P.o_trif));
+        if ((e = cudaEventRecord(a->e_tf_join, sx)) != cudaSuccess) return e;
         k_fwd_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
                                                          a->at<double>(P.o_drv), r, a->tbase(set), k, R, ext);
-        // FP64-latency-bound: small blocks spread the triangles over every SM
-        k_fwd_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, a->at<double>(P.o_trif));
+        if ((e = cudaStreamWaitEvent(st, a->e_tf_join, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(st, a->e_bulkf, 0)) != cudaSuccess) return e;
         k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F,
                                                       (int *)(sl + P.s_rows), a->tbase(set), k);
@@ -1265,7 +1287,8 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t sb, i
 // (e_near: then every value they pull of step k + 1 is final, and the buffer
 // they write was last read by step k + 1).
 template <typename T>
-cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st, cudaStream_t sb, int set) {
+cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream_t st, cudaStream_t sb,
+                     cudaStream_t sx, int set) {
     const Plan &P = a->P;
     char *sl = a->slot(k, set);
     const double *r = (const double *)(sl + P.s_r), *fn = (const double *)(sl + P.s_fn),
@@ -1303,11 +1326,17 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
         a->launches += 1;
         if ((e = cudaEventRecord(a->e_bulk, sb)) != cudaSuccess) return e;
         k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
+        // the triangles' transposes (sx) beside the swimmer's (st): both read
+        // lam_fn only, and the node kernel sums what both wrote
+        if ((e = cudaEventRecord(a->e_tr_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sx, a->e_tr_fork, 0)) != cudaSuccess) return e;
+        k_adj_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, sx>>>(a->m, r, lam_fn,
+                                                                                a->at<double>(P.o_tria));
+        if ((e = cudaEventRecord(a->e_tr_join, sx)) != cudaSuccess) return e;
         k_adj_swimmer<<<3 * P.S, BEAD_THREADS, 0, st>>>(a->m, a->at<Swim>(P.o_swim), a->at<double>(P.o_theta),
                                                          a->at<double>(P.o_drv), R, lam_fn, a->tbase(set), k,
                                                          a->at<double>(P.o_lR), a->at<double>(P.o_grad));
-        k_adj_tri<<<(P.T + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, r, lam_fn,
-                                                                                a->at<double>(P.o_tria));
+        if ((e = cudaStreamWaitEvent(st, a->e_tr_join, 0)) != cudaSuccess) return e;
         k_adj_node<<<(M + TRI_THREADS - 1) / TRI_THREADS, TRI_THREADS, 0, st>>>(a->m, a->at<double>(P.o_tria),
                                                                                a->at<double>(P.o_lR), lam_r);
         a->launches += 4;
@@ -1361,10 +1390,10 @@ cudaError_t capture(lbib_adjoint *a, bool reverse, int par, int set) {
     for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
         if (reverse) {
             const int kk = P.K - 1 - k;
-            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, a->cap_b, set);
+            e = adj_step<T>(a, kk, lam[nxt], lam[1 - nxt], a->cap, a->cap_b, a->cap_t, set);
             nxt = 1 - nxt;
         } else {
-            e = fwd_step<T>(a, k, a->cap, a->cap_b, set);
+            e = fwd_step<T>(a, k, a->cap, a->cap_b, a->cap_t, set);
         }
     }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(a->cap, reverse ? a->e_bulk : a->e_bulkf, 0);
@@ -1385,7 +1414,7 @@ cudaError_t set_tbase(lbib_adjoint *a, int g, int set, cudaStream_t st) {
 
 // run segment g forward from its checkpoint, filling slots 0..len of a set
 template <typename T>
-cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st, cudaStream_t sb) {
+cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st, cudaStream_t sb, cudaStream_t sx) {
     const Plan &P = a->P;
     char *s0 = a->slot(0, set), *c = a->ck(g);
     cudaError_t e;
@@ -1405,7 +1434,7 @@ cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st, cudaSt
     } else {
         if ((e = fwd_fork(a, st, sb)) != cudaSuccess) return e;
         for (int k = 0; k < len; ++k)
-            if ((e = fwd_step<T>(a, k, st, sb, set)) != cudaSuccess) return e;
+            if ((e = fwd_step<T>(a, k, st, sb, sx, set)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(st, a->e_bulkf, 0)) != cudaSuccess) return e;
     }
     a->slots_seg[set] = g;
@@ -1438,7 +1467,7 @@ int forward_impl(lbib_adjoint *a, double *disp) {
     }
     a->slots_seg[1] = -1;
     for (int g = 0; g < P.n_seg; ++g) {
-        CU(run_segment<T>(a, g, 0, a->s, a->s_fb));
+        CU(run_segment<T>(a, g, 0, a->s, a->s_fb, a->s_t));
         CU(save_ck(a, a->seg_len(g), g + 1));  // the next checkpoint (the last one: the final state)
     }
     if (P.S > 0) {
@@ -1529,7 +1558,7 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
     int cur = a->slots_seg[0] == P.n_seg - 1 ? 0 : (a->slots_seg[1] == P.n_seg - 1 ? 1 : -1);
     if (cur < 0) {
         cur = 0;
-        CU(run_segment<T>(a, P.n_seg - 1, 0, a->s, a->s_fb));
+        CU(run_segment<T>(a, P.n_seg - 1, 0, a->s, a->s_fb, a->s_t));
     }
     cudaStream_t rs = a->s_rev;
     CU(cudaEventRecord(a->e_fork, a->s));
@@ -1541,7 +1570,7 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
         const int oth = 1 - cur;
         if (g > 0) {
             CU(cudaStreamWaitEvent(a->s2, a->e_free[oth], 0));
-            CU(run_segment<T>(a, g - 1, oth, a->s2, a->s2b));
+            CU(run_segment<T>(a, g - 1, oth, a->s2, a->s2b, a->s2t));
             CU(cudaEventRecord(a->e_ready[oth], a->s2));
             ready_on_s2[oth] = true;
         }
@@ -1559,7 +1588,7 @@ int backward_impl(lbib_adjoint *a, const double *seed_disp, const double *seed_f
         } else {
             CU(rev_fork(a, rs, a->s_bulk));
             for (int k = len - 1; k >= 0; --k) {
-                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], rs, a->s_bulk, cur));
+                CU(adj_step<T>(a, k, lam[nxt], lam[1 - nxt], rs, a->s_bulk, a->s_revt, cur));
                 nxt = 1 - nxt;
             }
             CU(cudaStreamWaitEvent(rs, a->e_bulk, 0));
@@ -1612,12 +1641,13 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     const int M = P.M, T = P.T, B = P.B, S = P.S;
     // host tables
     std::vector<int> tris(3 * (size_t)T), cptr(M + 1, 0), cent(3 * (size_t)T), nb(M), bs(B), bc(B), bw(B, 0);
-    std::vector<double> G(3 * (size_t)T), A0(T), theta(6 * (size_t)S);
+    std::vector<double> G(3 * (size_t)T), A0(T), iG(T), bi(B), theta(6 * (size_t)S);
     std::vector<Swim> sw(S);
     for (int b = 0; b < B; ++b) {
         const lbib_bead &bd = s->beads[b];
         bs[b] = bd.node_start;
         bc[b] = bd.node_count;
+        bi[b] = 1.0 / bd.node_count;
         for (int j = bd.node_start; j < bd.node_start + bd.node_count; ++j) nb[j] = b;
         for (int t = bd.tri_start; t < bd.tri_start + bd.tri_count; ++t) {
             const int *v = s->tris + 3 * t;
@@ -1634,6 +1664,7 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
             const double det = G[3 * t] * G[3 * t + 2] - G[3 * t + 1] * G[3 * t + 1];
             if (!(det > 0.0)) return fail(LBIB_EINVAL, "degenerate rest triangle");
             A0[t] = 0.5 * std::sqrt(det) * bd.Gs;
+            iG[t] = 1.0 / det;
         }
     }
     for (int t = 0; t < T; ++t)
@@ -1676,6 +1707,8 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     m.tris = a->at<int>(P.o_tris);
     m.G = a->at<double>(P.o_G);
     m.A0Gs = a->at<double>(P.o_A0);
+    m.iG = a->at<double>(P.o_iG);
+    m.bead_inv = a->at<double>(P.o_bi);
     m.csr_ptr = a->at<int>(P.o_cptr);
     m.csr_ent = a->at<int>(P.o_cent);
     m.node_bead = a->at<int>(P.o_nb);
@@ -1703,6 +1736,7 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
         int lo = 0, hi = 0;
         CUA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         CUA(cudaStreamCreateWithPriority(&a->s_rev, cudaStreamNonBlocking, hi));
+        CUA(cudaStreamCreateWithPriority(&a->s_revt, cudaStreamNonBlocking, hi));
     }
     CUA(cudaEventCreateWithFlags(&a->e_fork, cudaEventDisableTiming));
     CUA(cudaStreamCreateWithFlags(&a->s_bulk, cudaStreamNonBlocking));
@@ -1713,6 +1747,11 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     CUA(cudaStreamCreateWithFlags(&a->s2b, cudaStreamNonBlocking));
     CUA(cudaEventCreateWithFlags(&a->e_nearf, cudaEventDisableTiming));
     CUA(cudaEventCreateWithFlags(&a->e_bulkf, cudaEventDisableTiming));
+    CUA(cudaStreamCreateWithFlags(&a->s_t, cudaStreamNonBlocking));
+    CUA(cudaStreamCreateWithFlags(&a->s2t, cudaStreamNonBlocking));
+    CUA(cudaStreamCreateWithFlags(&a->cap_t, cudaStreamNonBlocking));
+    for (cudaEvent_t *x : {&a->e_tf_fork, &a->e_tf_join, &a->e_tr_fork, &a->e_tr_join})
+        CUA(cudaEventCreateWithFlags(x, cudaEventDisableTiming));
     CUA(cudaEventCreateWithFlags(&a->e_join, cudaEventDisableTiming));
     std::vector<long long> tb(P.n_seg);
     for (int g = 0; g < P.n_seg; ++g) tb[g] = (long long)g * K;
@@ -1722,6 +1761,8 @@ int lb_adjoint_create(const lb_params *p, const lbib_structure *s, long long n_s
     CUA(put(P.o_tris, tris.data(), tris.size() * 4));
     CUA(put(P.o_G, G.data(), G.size() * 8));
     CUA(put(P.o_A0, A0.data(), A0.size() * 8));
+    CUA(put(P.o_iG, iG.data(), iG.size() * 8));
+    CUA(put(P.o_bi, bi.data(), bi.size() * 8));
     CUA(put(P.o_cptr, cptr.data(), cptr.size() * 4));
     CUA(put(P.o_cent, cent.data(), cent.size() * 4));
     CUA(put(P.o_nb, nb.data(), nb.size() * 4));
