@@ -33,11 +33,11 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS incl. IBM and % of HBM roofline (FP32 vs FP16-storage vs batched) at stated error"
 FALLBACK_HBM_GBS = 6800.0
 E2E_CHUNK = 16  # steps between trajectory copies in the end-to-end measurement
-# DRAM bytes (read + write) per launch of the FP32 main fluid kernel on one
+# DRAM bytes (read + write) per launch of the main fluid kernel on one
 # 256x128x128 two-swimmer box, from an ncu capture of that kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum, mean of both AA parities).
-# Reported as roofline.traffic only for FP32 storage.
-K_LB_MAIN_F32_DRAM_BYTES = 558.6e6
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of both AA parities),
+# for the storage formats captured (BF16 was not: reported as null).
+K_LB_MAIN_DRAM_BYTES = {"f32": 560.1e6, "f16": 258.9e6}
 WORKLOAD = "two_swimmer_boxes_256x128x128_x6"
 
 
@@ -621,6 +621,7 @@ def run_ours(a):
             variants[st] = {"value": job_mlups(ws, cells_per_step, a.steps, vms), "unit": "MLUPS",
                             "ms_per_step": vms / a.steps, "speedup_vs_f32": ms / vms,
                             "roofline": {"achieved": vach, "peak": peak, "frac": vach / peak,
+                                         "traffic": K_LB_MAIN_DRAM_BYTES.get(st),
                                          "avg_launch_us": t_lb / n_lb * 1e3, "bytes_per_launch": vbytes,
                                          "step_achieved": vstep, "step_frac": vstep / peak}}
             for s in vs:
@@ -708,7 +709,7 @@ def run_ours(a):
                                  "event-record node before and after every main fluid-kernel launch"},
             "roofline": {"bound": "hbm", "kernel": "k_lb_main", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": K_LB_MAIN_F32_DRAM_BYTES if a.storage == "f32" else None,
+                         "traffic": K_LB_MAIN_DRAM_BYTES.get(a.storage),
                          "bytes_per_launch": bytes_per_launch, "avg_launch_us": lb_avg_s * 1e6,
                          "launches": lb_n, "cells_per_launch": N - marked,
                          "step_achieved": step_ach, "step_frac": step_ach / peak,
