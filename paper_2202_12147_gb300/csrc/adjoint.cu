@@ -1186,9 +1186,6 @@ struct lbib_adjoint {
 
 namespace {
 
-// One recorded forward step.  (The swimmer and membrane kernels are
-// independent, but running them on two graph branches measured slower than
-// one chain: 75 against 61 us per step on the 96^3 workload.)
 // the two-cell row kernels exist for FP32 only
 template <typename T, bool NEAR>
 void fwd_rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1,
