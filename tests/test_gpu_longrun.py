@@ -44,8 +44,8 @@ V_TOL = 1e-2
 PAIR_CASES = [f"{arr}{gap}_256x128x128" for arr in ("inline", "side") for gap in (3, 5, 8)]
 # BF16 cases whose period velocity misses 1 % (measured, deterministic spreading)
 BF16_V_MISS = {
-    "side3_256x128x128": "BF16 storage: per-period swimming velocity 1.48e-2 off over three periods (8-bit "
-                         "significand; FP16 1.7e-3, FP32 3.5e-4 on the same run)",
+    "side3_256x128x128": "BF16 storage: per-period swimming velocity 1.89e-2 off over three periods (8-bit "
+                         "significand; FP16 1.3e-3, FP32 3.4e-4 on the same run)",
     "inline3_256x128x128": "BF16 storage: first-period swimming velocity 1.74e-2 off (FP16 2.4e-3, FP32 2.8e-4)",
     "inline5_256x128x128": "BF16 storage: first-period swimming velocity 1.91e-2 off (FP16 6.1e-4, FP32 1.1e-4)",
 }
