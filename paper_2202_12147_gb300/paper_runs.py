@@ -20,12 +20,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def run(case, periods, storage="f32", deterministic=False):
+def run(case, periods, storage="f32", deterministic=False, tau=1.0):
     import numpy as np
     import torch
     from paper_2202_12147_gb300 import Simulation
     from workloads import assemble, paper_study_box
-    box = paper_study_box(case)
+    box = paper_study_box(case, tau=tau)
     T = int(box.swimmers[0].period)
     sim = Simulation(box.dims, assemble(box), tau=box.tau, rho0=box.rho0, storage=storage, forcing=box.forcing,
                      kernel=box.kernel, deterministic=deterministic)
@@ -41,7 +41,7 @@ def run(case, periods, storage="f32", deterministic=False):
     sim.close()
     x = np.array(xs)
     v = (x[1:, :, 0] - x[:-1, :, 0]) / T
-    return {"case": case, "dims": list(box.dims), "storage": storage, "forcing": box.forcing,
+    return {"case": case, "dims": list(box.dims), "tau": box.tau, "storage": storage, "forcing": box.forcing,
             "delta_kernel": box.kernel, "period": T, "periods": periods,
             "swimmer_centres": [list(s.center) for s in box.swimmers], "x_cm": xs,
             "v_period_x": v.tolist(), "re_swim": [s["re_swim"] for s in st], "re_bead": [s["re_bead"] for s in st],
@@ -54,10 +54,11 @@ def main(argv=None):
                     help="lone | inline_<n> | side_<n> (n swimmer lengths between the centres); repeatable")
     ap.add_argument("--periods", type=int, default=12)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--tau", type=float, default=1.0, help="relaxation time (viscosity (tau - 1/2) / 3)")
     ap.add_argument("--out", required=True, help="JSON file (one object per case, appended as lines)")
     a = ap.parse_args(argv)
     for c in a.case:
-        r = run(c, a.periods, a.storage)
+        r = run(c, a.periods, a.storage, tau=a.tau)
         with open(a.out, "a") as fh:
             fh.write(json.dumps(r) + "\n")
         print(f"{c}: last-period velocity {r['v_period_x'][-1]}, {r['wall_s']:.0f} s, {r['mlups']:.0f} MLUPS",

@@ -148,3 +148,28 @@ def test_membrane_model_sizes_and_validation():
         st[key] = val
         with pytest.raises(_lib.LbibError):
             required_sizes((32, 24, 24), st)
+
+
+def test_paper_study_workloads():
+    """The paper-scale study boxes (Sec. 3): 1024 x 256 x 256, swimmers of
+    radius 5 with springs of length 36 (swimmer length 72), the paper's
+    membrane, Shan-Chen forcing; pairs placed symmetrically about the centre
+    n swimmer lengths apart, in line along x or side by side along y; the
+    viscosity set by tau.  Every structure passes the library's validation."""
+    from paper_2202_12147_gb300 import required_sizes
+    from workloads import PAPER_L_SWIM, assemble, paper_study_box
+    assert PAPER_L_SWIM == 72
+    for case, axis, n in (("lone", None, 0), ("inline_2", 0, 2.0), ("side_1.5", 1, 1.5)):
+        box = paper_study_box(case, tau=2.0)
+        assert box.dims == (1024, 256, 256) and box.tau == 2.0 and box.forcing == "shan_chen"
+        sw = box.swimmers
+        assert all(s.radius == 5.0 and s.spacing == 36.0 and s.law == "skalak" for s in sw)
+        if axis is None:
+            assert len(sw) == 1 and sw[0].center == (512.0, 128.0, 128.0)
+        else:
+            c = np.array([s.center for s in sw])
+            assert np.allclose(c.mean(axis=0), (512.0, 128.0, 128.0))
+            sep = c[1] - c[0]
+            assert sep[axis] == n * PAPER_L_SWIM and np.count_nonzero(sep) == 1
+        sizes = required_sizes(box.dims, assemble(box), tau=box.tau, forcing=box.forcing)
+        assert sizes[0] == 19 * 1024 * 256 * 256 * 4

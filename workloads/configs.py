@@ -213,11 +213,12 @@ def _paper_swimmer(center, period=20000.0, A=5e-3):
         A, A, math.pi / 2).with_paper_membrane()
 
 
-def paper_study_box(case, dims=(1024, 256, 256), period=20000.0):
+def paper_study_box(case, dims=(1024, 256, 256), period=20000.0, tau=1.0):
     """The paper's 1024 x 256 x 256 box (Sec. 3) with: "lone" one swimmer
     at the centre; "inline_<n>" two swimmers on the x axis whose centres are
     n swimmer lengths apart; "side_<n>" two swimmers side by side along y, n
-    swimmer lengths apart; placed symmetrically about the box centre."""
+    swimmer lengths apart; placed symmetrically about the box centre.  tau
+    sets the viscosity, mu = rho0 (tau - 1/2) / 3 (1/6 at tau = 1)."""
     cx, cy, cz = (float(d // 2) for d in dims)
     if case == "lone":
         sw = (_paper_swimmer((cx, cy, cz), period),)
@@ -230,7 +231,7 @@ def paper_study_box(case, dims=(1024, 256, 256), period=20000.0):
             sw = tuple(_paper_swimmer((cx, cy + s * h, cz), period) for s in (-1.0, 1.0))
         else:
             raise ValueError(case)
-    return BoxSpec(dims=dims, swimmers=sw, forcing="shan_chen", kernel="peskin4", name=f"paper_{case}")
+    return BoxSpec(dims=dims, swimmers=sw, tau=tau, forcing="shan_chen", kernel="peskin4", name=f"paper_{case}")
 
 
 def balanced_drive(A=1e-3, B=1e-3, alpha=math.pi / 2):
