@@ -58,8 +58,11 @@ V_MISS = {
                                   "9): the stationary velocity is 2.2e-9 once the start-up relaxation has decayed, "
                                   "and FP16 rounding leaves ~6e-11 (FP32 ~1e-11, 5.4e-3 at period 10)",
     ("side3_256cube", "bf16"): "BF16 storage: period velocity 5.3e-2 off at period 5 (3.1e-2 at 4, 2e-3 at 1)",
-    ("inline3_256x128x128", "bf16"): "BF16 storage: first-period swimming velocity 1.74e-2 off (FP16 2.4e-3, "
-                                     "FP32 2.8e-4)",
+    ("inline3_256x128x128", "bf16"): "BF16 storage: period velocity 1.7e-2 off in period 1, 0.10 at period 9 "
+                                     "(8-bit significand)",
+    ("inline3_256x128x128", "f16"): "FP16 storage: period velocity 2.3e-2 off in period 3, where one swimmer's "
+                                    "velocity passes through zero (4.2e-9), 1.8e-2 at period 10 (velocity 5e-9; "
+                                    "FP32 3.6e-3 and 2.7e-3)",
     ("inline5_256x128x128", "bf16"): "BF16 storage: first-period swimming velocity 1.91e-2 off (FP16 6.1e-4, "
                                      "FP32 1.1e-4)",
 }
