@@ -339,7 +339,7 @@ __global__ void k_fwd_tri(Mesh m, const double *r, double *tri_f) {
 // the corners, fixed order), recorded, then F(x) += f_j Delta(x - r_j)
 template <typename T>
 __global__ void k_fwd_spread(Dims d, Mesh m, const double *r, const double *tri_f, const double *ext, double *fn,
-                             T *F, int *rowtag, const long long *tb, int k) {
+                             T *F, int *rowtag, int *rlist, int *rcnt, const long long *tb, int k) {
     const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= m.M) return;
     const int e0 = m.csr_ptr[j], e1 = m.csr_ptr[j + 1];
@@ -357,13 +357,30 @@ __global__ void k_fwd_spread(Dims d, Mesh m, const double *r, const double *tri_
     T w[2], g[2][3];
     lane_cells<T>(d, r + 3 * j, lane, cell, w, g);
     // tag the rows (y, z) of the stencil cells with the step (absolute index
-    // + 1): the reverse sweep updates them apart from the rest of the box
+    // + 1) and list each row once (the lane that changes its tag): both fluid
+    // updates of this step treat them apart from the rest of the box.  The
+    // tags of a slot set are cleared before it is recorded again.
     const int tag = (int)(*tb + k + 1);
     for (int h = 0; h < 2; ++h) {
         atomicAdd(F + cell[h], (T)f[0] * w[h]);
         atomicAdd(F + d.Npad + cell[h], (T)f[1] * w[h]);
         atomicAdd(F + 2 * d.Npad + cell[h], (T)f[2] * w[h]);
-        rowtag[cell[h] / d.nx] = tag;
+        if ((lane & 3) == 0) {  // one lane per stencil row
+            const int row = cell[h] / d.nx;
+            if (rowtag[row] != tag && atomicExch(rowtag + row, tag) != tag) rlist[atomicAdd(rcnt, 1)] = row;
+        }
+    }
+}
+
+// zero the row tags and row counts of the n_slots slots of a slot set
+__global__ void k_clear_rows(char *slot0, size_t slot_bytes, size_t off_tags, size_t off_count, int nrow,
+                             int n_slots) {
+    const long long n = (long long)n_slots * nrow;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int sl = (int)(i / nrow), r = (int)(i - (long long)sl * nrow);
+        char *base = slot0 + (size_t)sl * slot_bytes;
+        reinterpret_cast<int *>(base + off_tags)[r] = 0;
+        if (r == 0) *reinterpret_cast<int *>(base + off_count) = 0;
     }
 }
 
@@ -511,54 +528,61 @@ __global__ void __launch_bounds__(128, 4) k_fwd_lb2(Dims d, float omega, float r
 template <typename T, bool NEAR, bool PAIR>
 __global__ void __launch_bounds__(128) k_fwd_lb_rows(Dims d, T omega, T rho0, double gx, double gy, double gz,
                                                      const T *pops, const T *F, T *out, T *u_out, T *F_next,
-                                                     const int *rowtag, const long long *tb, int k) {
-    const int row = blockIdx.x;
-    const bool near = rowtag[row] == (int)(*tb + k + 1);
-    if (near != NEAR) return;
-    const int y = row % d.ny, z = row / d.ny;
+                                                     const int *rowtag, const int *rlist, const int *rcnt,
+                                                     const long long *tb, int k) {
+    // NEAR: the rows the spreading listed, grid-stride; otherwise one block
+    // per row, skipping the tagged ones
+    const int tag = (int)(*tb + k + 1);
+    const int n_it = NEAR ? *rcnt : 1;
     constexpr int CPT = PAIR ? 2 : 1;
-    for (int x = CPT * threadIdx.x; x < d.nx; x += CPT * blockDim.x) {
-        const int cell = x + d.nx * row;
-        T dv[CPT][Q], p[CPT][Q], u[CPT][3];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if constexpr (PAIR) {
-                const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
-                dv[0][i] = v.x;
-                dv[1][i] = v.y;
-            } else {
-                dv[0][i] = pops[i * d.Npad + cell];
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            T Fv[3] = {(T)gx, (T)gy, (T)gz};
-            if constexpr (NEAR)
-                for (int a = 0; a < 3; ++a) Fv[a] += F[a * d.Npad + cell + c];
-            fwd_cell(dv[c], Fv[0], Fv[1], Fv[2], omega, rho0, p[c], u[c]);
-        }
-        const Nbr n0(d, x, y, z);
-        if constexpr (PAIR) {
-            const Nbr n1(d, x + 1, y, z);
+    const T G[3] = {(T)gx, (T)gy, (T)gz};  // converted once, not per cell (FP64 converts issue slowly here)
+    for (int it = NEAR ? (int)blockIdx.x : 0; it < n_it; it += NEAR ? (int)gridDim.x : 1) {
+        const int row = NEAR ? rlist[it] : (int)blockIdx.x;
+        if (!NEAR && rowtag[row] == tag) return;
+        const int y = row % d.ny, z = row / d.ny;
+        for (int x = CPT * threadIdx.x; x < d.nx; x += CPT * blockDim.x) {
+            const int cell = x + d.nx * row;
+            T dv[CPT][Q], p[CPT][Q], u[CPT][3];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                float *pl = out + i * d.Npad;
-                if (cx(i) == 0) {
-                    *reinterpret_cast<float2 *>(pl + cell + n0.off(i)) = make_float2(p[0][i], p[1][i]);
+                if constexpr (PAIR) {
+                    const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
+                    dv[0][i] = v.x;
+                    dv[1][i] = v.y;
                 } else {
-                    pl[cell + n0.off(i)] = p[0][i];
-                    pl[cell + 1 + n1.off(i)] = p[1][i];
+                    dv[0][i] = pops[i * d.Npad + cell];
                 }
             }
-        } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) out[i * d.Npad + cell + n0.off(i)] = p[0][i];
-        }
-        for (int a = 0; a < 3; ++a)
             for (int c = 0; c < CPT; ++c) {
-                if constexpr (NEAR) u_out[a * d.Npad + cell + c] = u[c][a];
-                F_next[a * d.Npad + cell + c] = (T)0;
+                T Fv[3] = {G[0], G[1], G[2]};
+                if constexpr (NEAR)
+                    for (int a = 0; a < 3; ++a) Fv[a] += F[a * d.Npad + cell + c];
+                fwd_cell(dv[c], Fv[0], Fv[1], Fv[2], omega, rho0, p[c], u[c]);
             }
+            const Nbr n0(d, x, y, z);
+            if constexpr (PAIR) {
+                const Nbr n1(d, x + 1, y, z);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    float *pl = out + i * d.Npad;
+                    if (cx(i) == 0) {
+                        *reinterpret_cast<float2 *>(pl + cell + n0.off(i)) = make_float2(p[0][i], p[1][i]);
+                    } else {
+                        pl[cell + n0.off(i)] = p[0][i];
+                        pl[cell + 1 + n1.off(i)] = p[1][i];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) out[i * d.Npad + cell + n0.off(i)] = p[0][i];
+            }
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < CPT; ++c) {
+                    if constexpr (NEAR) u_out[a * d.Npad + cell + c] = u[c][a];
+                    F_next[a * d.Npad + cell + c] = (T)0;
+                }
+        }
     }
 }
 
@@ -788,64 +812,71 @@ __global__ void __launch_bounds__(128, 4) k_adj_lb2(Dims d, float omega, float r
 template <typename T, bool NEAR, bool PAIR>
 __global__ void __launch_bounds__(128) k_adj_lb_rows(Dims d, T omega, T rho0, double gx, double gy, double gz,
                                                      const T *pops, const T *F, const T *lam_next, T *lam_u, T *lam_cur,
-                                                     T *lam_F, const int *rowtag, const long long *tb, int k) {
-    const int row = blockIdx.x;
-    const bool near = rowtag[row] == (int)(*tb + k + 1);
-    if (near != NEAR) return;
-    const int y = row % d.ny, z = row / d.ny;
+                                                     T *lam_F, const int *rowtag, const int *rlist, const int *rcnt,
+                                                     const long long *tb, int k) {
+    // NEAR: the rows the spreading listed, grid-stride; otherwise one block
+    // per row, skipping the tagged ones
+    const int tag = (int)(*tb + k + 1);
+    const int n_it = NEAR ? *rcnt : 1;
     constexpr int CPT = PAIR ? 2 : 1;
-    for (int x = CPT * threadIdx.x; x < d.nx; x += CPT * blockDim.x) {
-        const int cell = x + d.nx * row;
-        T ls[CPT][Q], dv[CPT][Q];
-        const Nbr n0(d, x, y, z);
-        if constexpr (PAIR) {
-            // 8-byte vector accesses wherever both cells' values stay adjacent
-            const Nbr n1(d, x + 1, y, z);
+    const T G[3] = {(T)gx, (T)gy, (T)gz};  // converted once, not per cell (FP64 converts issue slowly here)
+    for (int it = NEAR ? (int)blockIdx.x : 0; it < n_it; it += NEAR ? (int)gridDim.x : 1) {
+        const int row = NEAR ? rlist[it] : (int)blockIdx.x;
+        if (!NEAR && rowtag[row] == tag) return;
+        const int y = row % d.ny, z = row / d.ny;
+        for (int x = CPT * threadIdx.x; x < d.nx; x += CPT * blockDim.x) {
+            const int cell = x + d.nx * row;
+            T ls[CPT][Q], dv[CPT][Q];
+            const Nbr n0(d, x, y, z);
+            if constexpr (PAIR) {
+                // 8-byte vector accesses wherever both cells' values stay adjacent
+                const Nbr n1(d, x + 1, y, z);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float *pl = lam_next + i * d.Npad;
-                if (cx(i) == 0) {
-                    const float2 v = *reinterpret_cast<const float2 *>(pl + cell + n0.off(i));
-                    ls[0][i] = v.x;
-                    ls[1][i] = v.y;
-                } else {
-                    ls[0][i] = pl[cell + n0.off(i)];
-                    ls[1][i] = pl[cell + 1 + n1.off(i)];
+                for (int i = 0; i < Q; ++i) {
+                    const float *pl = lam_next + i * d.Npad;
+                    if (cx(i) == 0) {
+                        const float2 v = *reinterpret_cast<const float2 *>(pl + cell + n0.off(i));
+                        ls[0][i] = v.x;
+                        ls[1][i] = v.y;
+                    } else {
+                        ls[0][i] = pl[cell + n0.off(i)];
+                        ls[1][i] = pl[cell + 1 + n1.off(i)];
+                    }
+                    const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
+                    dv[0][i] = v.x;
+                    dv[1][i] = v.y;
                 }
-                const float2 v = *reinterpret_cast<const float2 *>(pops + i * d.Npad + cell);
-                dv[0][i] = v.x;
-                dv[1][i] = v.y;
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    ls[0][i] = lam_next[i * d.Npad + cell + n0.off(i)];
+                    dv[0][i] = pops[i * d.Npad + cell];
+                }
             }
-        } else {
+            T lam[CPT][Q], lF[CPT][3];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                T Fv[3] = {G[0], G[1], G[2]}, lu[3] = {0, 0, 0};
+                if constexpr (NEAR) {
+                    for (int a = 0; a < 3; ++a) {
+                        Fv[a] += F[a * d.Npad + cell + c];
+                        lu[a] = lam_u[a * d.Npad + cell + c];
+                    }
+                }
+                adj_cell(ls[c], dv[c], Fv, lu, omega, rho0, lam[c], lF[c]);
+            }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                ls[0][i] = lam_next[i * d.Npad + cell + n0.off(i)];
-                dv[0][i] = pops[i * d.Npad + cell];
+                if constexpr (PAIR) *reinterpret_cast<float2 *>(lam_cur + i * d.Npad + cell) = make_float2(lam[0][i], lam[1][i]);
+                else lam_cur[i * d.Npad + cell] = lam[0][i];
             }
-        }
-        T lam[CPT][Q], lF[CPT][3];
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            T Fv[3] = {(T)gx, (T)gy, (T)gz}, lu[3] = {0, 0, 0};
             if constexpr (NEAR) {
-                for (int a = 0; a < 3; ++a) {
-                    Fv[a] += F[a * d.Npad + cell + c];
-                    lu[a] = lam_u[a * d.Npad + cell + c];
-                }
+                for (int a = 0; a < 3; ++a)
+                    for (int c = 0; c < CPT; ++c) {
+                        lam_F[a * d.Npad + cell + c] = lF[c][a];
+                        lam_u[a * d.Npad + cell + c] = 0;
+                    }
             }
-            adj_cell(ls[c], dv[c], Fv, lu, omega, rho0, lam[c], lF[c]);
-        }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if constexpr (PAIR) *reinterpret_cast<float2 *>(lam_cur + i * d.Npad + cell) = make_float2(lam[0][i], lam[1][i]);
-            else lam_cur[i * d.Npad + cell] = lam[0][i];
-        }
-        if constexpr (NEAR) {
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < CPT; ++c) {
-                    lam_F[a * d.Npad + cell + c] = lF[c][a];
-                    lam_u[a * d.Npad + cell + c] = 0;
-                }
         }
     }
 }
@@ -1000,7 +1031,7 @@ struct Plan {
     long long n_steps;
     int K, n_seg;
     // per-slot offsets
-    size_t s_pops, s_F, s_u, s_r, s_fn, s_R, s_ext, s_rows, slot_bytes;
+    size_t s_pops, s_F, s_u, s_r, s_fn, s_R, s_ext, s_rows, s_rlist, s_rcnt, slot_bytes;
     // per-checkpoint offsets
     size_t c_pops, c_r, ck_bytes;
     // workspace offsets
@@ -1034,7 +1065,9 @@ Plan make_plan(const lb_params *p, const lbib_structure *s, long long n_steps, i
     P.s_fn = o; o += up(nd);
     P.s_R = o; o += up(bd);
     P.s_ext = o; o += up(bd);
-    P.s_rows = o; o += up((size_t)p->ny * p->nz * 4);  // rows (y, z) under the step's node stencils
+    P.s_rows = o; o += up((size_t)p->ny * p->nz * 4);   // tags of the rows (y, z) under the step's stencils
+    P.s_rlist = o; o += up((size_t)p->ny * p->nz * 4);  // those rows, listed once each
+    P.s_rcnt = o; o += up(16);                          // how many
     P.slot_bytes = o;
     o = 0;
     P.c_pops = o; o += up(Q * fp);
@@ -1186,23 +1219,48 @@ struct lbib_adjoint {
 
 namespace {
 
-// the two-cell row kernels exist for FP32 only
+// Row-kernel launches.  The stencil rows (NEAR) run on a fixed grid that
+// walks the step's row list; every other row is one block.  Two cells per
+// thread (FP32, even rows) or one.
+constexpr unsigned NEAR_BLOCKS = 512;
+
+template <bool NEAR>
+unsigned rows_grid(unsigned nrow) { return NEAR ? std::min(nrow, NEAR_BLOCKS) : nrow; }
+
 template <typename T, bool NEAR>
-void fwd_rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1,
-                   double g2, const T *pops, const T *F, T *out, T *u, T *F_next, const int *rows, const long long *tb,
-                   int k) {
-    if constexpr (sizeof(T) == 4)
-        k_fwd_lb_rows<T, NEAR, true><<<nrow, tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, out, u, F_next, rows, tb,
-                                                          k);
+void fwd_rows(const Plan &P, bool pair, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1,
+              double g2, const char *sl, const T *F, T *out, T *u, T *F_next, const long long *tb, int k) {
+    const int *tags = (const int *)(sl + P.s_rows), *list = (const int *)(sl + P.s_rlist),
+              *cnt = (const int *)(sl + P.s_rcnt);
+    const T *pops = (const T *)(sl + P.s_pops);
+    if constexpr (sizeof(T) == 4) {
+        if (pair) {
+            k_fwd_lb_rows<T, NEAR, true><<<rows_grid<NEAR>(nrow), tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, out, u,
+                                                                             F_next, tags, list, cnt, tb, k);
+            return;
+        }
+    }
+    k_fwd_lb_rows<T, NEAR, false><<<rows_grid<NEAR>(nrow), tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, out, u,
+                                                                      F_next, tags, list, cnt, tb, k);
 }
 
 template <typename T, bool NEAR>
-void rows_pair(const Plan &P, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1, double g2,
-               const T *pops, const T *F, const T *lam_next, T *lam_u, T *lam_cur, T *lam_F, const int *rows,
-               const long long *tb, int k) {
-    if constexpr (sizeof(T) == 4)
-        k_adj_lb_rows<T, NEAR, true><<<nrow, tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, lam_next, lam_u, lam_cur,
-                                                          lam_F, rows, tb, k);
+void adj_rows(const Plan &P, bool pair, unsigned nrow, unsigned tpb, cudaStream_t s, T om, T r0, double g0, double g1,
+              double g2, const char *sl, const T *F, const T *lam_next, T *lam_u, T *lam_cur, T *lam_F,
+              const long long *tb, int k) {
+    const int *tags = (const int *)(sl + P.s_rows), *list = (const int *)(sl + P.s_rlist),
+              *cnt = (const int *)(sl + P.s_rcnt);
+    const T *pops = (const T *)(sl + P.s_pops);
+    if constexpr (sizeof(T) == 4) {
+        if (pair) {
+            k_adj_lb_rows<T, NEAR, true><<<rows_grid<NEAR>(nrow), tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F,
+                                                                             lam_next, lam_u, lam_cur, lam_F, tags,
+                                                                             list, cnt, tb, k);
+            return;
+        }
+    }
+    k_adj_lb_rows<T, NEAR, false><<<rows_grid<NEAR>(nrow), tpb, 0, s>>>(P.d, om, r0, g0, g1, g2, pops, F, lam_next,
+                                                                      lam_u, lam_cur, lam_F, tags, list, cnt, tb, k);
 }
 
 // One recorded forward step on two streams: st carries the node-level chain
@@ -1225,7 +1283,6 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t sb, c
     const bool pair = sizeof(T) == 4 && P.d.nx % 2 == 0;
     cudaError_t e;
     if (M > 0) {
-        const int *rows = (const int *)(sl + P.s_rows);
         const unsigned nrow = (unsigned)(P.d.ny * P.d.nz);
         const unsigned tpb = (unsigned)std::min(128, std::max(32, (P.d.nx / (pair ? 2 : 1) + 31) / 32 * 32));
         // the triangles' corner forces (sx) beside the bead centres and
@@ -1240,25 +1297,16 @@ cudaError_t fwd_step(lbib_adjoint *a, int k, cudaStream_t st, cudaStream_t sb, c
         if ((e = cudaStreamWaitEvent(st, a->e_tf_join, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(st, a->e_bulkf, 0)) != cudaSuccess) return e;
         k_fwd_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, a->m, r, a->at<double>(P.o_trif), ext, fn, F,
-                                                      (int *)(sl + P.s_rows), a->tbase(set), k);
+                                                      (int *)(sl + P.s_rows), (int *)(sl + P.s_rlist),
+                                                      (int *)(sl + P.s_rcnt), a->tbase(set), k);
         a->launches += 3;
         if ((e = cudaEventRecord(a->e_nearf, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(sb, a->e_nearf, 0)) != cudaSuccess) return e;
-        if (pair)
-            fwd_rows_pair<T, false>(P, nrow, tpb, sb, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
-                                    (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows, a->tbase(set), k);
-        else
-            k_fwd_lb_rows<T, false, false><<<nrow, tpb, 0, sb>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
-                                                                  (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows,
-                                                                  a->tbase(set), k);
+        fwd_rows<T, false>(P, pair, nrow, tpb, sb, om, r0, g0, g1, g2, sl, F, (T *)(sn + P.s_pops), u,
+                           (T *)(sn + P.s_F), a->tbase(set), k);
         if ((e = cudaEventRecord(a->e_bulkf, sb)) != cudaSuccess) return e;
-        if (pair)
-            fwd_rows_pair<T, true>(P, nrow, tpb, st, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
-                                   (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows, a->tbase(set), k);
-        else
-            k_fwd_lb_rows<T, true, false><<<nrow, tpb, 0, st>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
-                                                                 (T *)(sn + P.s_pops), u, (T *)(sn + P.s_F), rows,
-                                                                 a->tbase(set), k);
+        fwd_rows<T, true>(P, pair, nrow, tpb, st, om, r0, g0, g1, g2, sl, F, (T *)(sn + P.s_pops), u,
+                          (T *)(sn + P.s_F), a->tbase(set), k);
         k_fwd_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, (double *)(sn + P.s_r), a->at<int>(P.o_err));
         a->launches += 3;
         return cudaGetLastError();
@@ -1294,7 +1342,6 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
     T *lam_u = a->at<T>(P.o_lu), *lam_F = a->at<T>(P.o_lF);
     double *lam_r = a->at<double>(P.o_lr), *lam_fn = a->at<double>(P.o_lfn);
     const int M = P.M;
-    const int *rows = (const int *)(sl + P.s_rows);
     const unsigned nrow = (unsigned)(P.d.ny * P.d.nz);
     const bool pair = sizeof(T) == 4 && P.d.nx % 2 == 0;
     const unsigned tpb = (unsigned)std::min(128, std::max(32, (P.d.nx / (pair ? 2 : 1) + 31) / 32 * 32));
@@ -1305,21 +1352,13 @@ cudaError_t adj_step(lbib_adjoint *a, int k, T *lam_next, T *lam_cur, cudaStream
         k_adj_interp<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, u, lam_r, lam_u);
         a->launches += 1;
         if ((e = cudaStreamWaitEvent(st, a->e_bulk, 0)) != cudaSuccess) return e;
-        if (pair)
-            rows_pair<T, true>(P, nrow, tpb, st, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F, lam_next, lam_u,
-                               lam_cur, lam_F, rows, a->tbase(set), k);
-        else
-            k_adj_lb_rows<T, true, false><<<nrow, tpb, 0, st>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
-                                                                 lam_next, lam_u, lam_cur, lam_F, rows, a->tbase(set), k);
+        adj_rows<T, true>(P, pair, nrow, tpb, st, om, r0, g0, g1, g2, sl, F, lam_next, lam_u, lam_cur, lam_F,
+                          a->tbase(set), k);
         a->launches += 1;
         if ((e = cudaEventRecord(a->e_near, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(sb, a->e_near, 0)) != cudaSuccess) return e;
-        if (pair)
-            rows_pair<T, false>(P, nrow, tpb, sb, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F, lam_next, lam_u,
-                                lam_cur, lam_F, rows, a->tbase(set), k);
-        else
-            k_adj_lb_rows<T, false, false><<<nrow, tpb, 0, sb>>>(P.d, om, r0, g0, g1, g2, (const T *)(sl + P.s_pops), F,
-                                                                  lam_next, lam_u, lam_cur, lam_F, rows, a->tbase(set), k);
+        adj_rows<T, false>(P, pair, nrow, tpb, sb, om, r0, g0, g1, g2, sl, F, lam_next, lam_u, lam_cur, lam_F,
+                           a->tbase(set), k);
         a->launches += 1;
         if ((e = cudaEventRecord(a->e_bulk, sb)) != cudaSuccess) return e;
         k_adj_spread<T><<<(M + 3) / 4, 128, 0, st>>>(P.d, M, r, fn, lam_F, lam_r, lam_fn);
@@ -1423,6 +1462,14 @@ cudaError_t run_segment(lbib_adjoint *a, int g, int set, cudaStream_t st, cudaSt
         return e;
     if ((e = cudaMemsetAsync(s0 + P.s_F, 0, 3 * (size_t)P.d.Npad * P.esize, st)) != cudaSuccess) return e;
     if ((e = set_tbase(a, g, set, st)) != cudaSuccess) return e;
+    if (P.M > 0) {
+        // fresh row tags and lists: a row is listed by the lane that changes its tag
+        const int nrow = P.d.ny * P.d.nz;
+        k_clear_rows<<<(unsigned)std::min<long long>(1024, ((long long)(P.K + 1) * nrow + 255) / 256), 256, 0, st>>>(
+            s0, P.slot_bytes, P.s_rows, P.s_rcnt, nrow, P.K + 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        a->launches += 1;
+    }
     const int len = a->seg_len(g);
     if (len == P.K && a->graphs) {
         if (!a->g_fwd[set] && (e = capture<T>(a, false, 0, set)) != cudaSuccess) return e;
