@@ -109,6 +109,11 @@ def test_backward_twice_and_error_paths(gpu_lib, small):
     assert np.abs(g1 - g2).max() < 1e-12 * np.abs(g1).max()
     g3 = eng.backward(np.array([[2.0, 0.0, 0.0]]))  # linear in the seed
     assert np.abs(g3 - 2 * g1).max() < 1e-12 * np.abs(g1).max()
+    # a second forward sweep records into slot sets the reverse sweeps used
+    # (their row tags and lists start afresh): the same gradient again
+    eng.forward()
+    g4 = eng.backward(np.array([[1.0, 0.0, 0.0]]))
+    assert np.abs(g4 - g1).max() < 1e-12 * np.abs(g1).max()
     eng.set_drive(eng.theta0)
     with pytest.raises(LbibError):
         eng.backward(np.array([[1.0, 0.0, 0.0]]))  # the drive changed: forward first
