@@ -57,6 +57,10 @@ V_MISS = {
     ("side3_256x128x128", "f16"): "FP16 storage: period velocity 3.0e-2 off at period 10 (1.5e-2 at 8, 1.3e-2 at "
                                   "9): the stationary velocity is 2.2e-9 once the start-up relaxation has decayed, "
                                   "and FP16 rounding leaves ~6e-11 (FP32 ~1e-11, 5.4e-3 at period 10)",
+    ("side5_256x128x128", "f16"): "FP16 storage: period velocity 1.6e-2 off at period 7, 2.9e-2 at period 10 "
+                                  "(velocity 2.1e-9 after the start-up relaxation; FP32 4.7e-3)",
+    ("side5_256x128x128", "bf16"): "BF16 storage: period velocity 1.3e-2 off in period 2, 0.18 at period 9 "
+                                   "(8-bit significand)",
     ("side3_256cube", "bf16"): "BF16 storage: period velocity 5.3e-2 off at period 5 (3.1e-2 at 4, 2e-3 at 1)",
     ("inline3_256x128x128", "bf16"): "BF16 storage: period velocity 1.7e-2 off in period 1, 0.10 at period 9 "
                                      "(8-bit significand)",
